@@ -1,0 +1,343 @@
+"""RU-QLP benchmark: GB/s of A streamed on the dense 20000 x 20000 workload.
+
+One step = one whole RU-QLP decomposition (Algorithm 1 + Algorithm 2,
+Section III) of a device-resident A: sketch, q power steps with orth() after
+every product, B^T = A^T Q and its QR.  The workload is the dense
+20000 x 20000 matrix A = U diag(sigma) V^T + N with U, V Haar, sigma_i = 1
+(i <= 200), 1e-2/(i-200) after, N iid N(0, 1e-12), k=200, p=20, q=2
+(6 passes over A).  Metric: (2q+2) * bytes(A in the streamed dtype) / time.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--dtype bf16|f32|f64]
+  python bench.py --impl reference ...   (the FP64 CPU oracle on host cores)
+
+Under torchrun each rank runs its own replica of the workload (weak scaling,
+no data-path collective); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+M, N, K_RANK, P_OVER, Q_POW = 20000, 20000, 200, 20, 2
+TAIL, NOISE = 1e-2, 1e-6
+SEED = 20260 + 1
+DT_BYTES = {"bf16": 2, "f32": 4, "f64": 8}
+METRIC = "RU-QLP GB/s of A streamed vs HBM peak at fixed residual"
+WORKLOAD = "dense 20000x20000, sigma_i=1 (i<=200) then 1e-2/(i-200), +N(0,1e-6^2); k=200 p=20 q=2"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--dtype", default="bf16", choices=list(DT_BYTES))
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--size", type=int, default=0, help="override m = n (testing only)")
+    return ap.parse_args()
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)),
+            int(os.environ.get("WORLD_SIZE", 1)))
+
+
+# ---------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------
+class Clocks:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device = device
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.device), "--query-gpu=" + self.Q,
+                                       "--format=csv,noheader,nounits", "-lms", "100"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.p.terminate()
+        self.p.wait()
+        self.f.flush()
+        rows = [r.split(",") for r in open(self.f.name).read().strip().splitlines() if r.strip()]
+        os.unlink(self.f.name)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            r = [x.strip() for x in r]
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+            except (ValueError, IndexError):
+                continue
+            for nm, v in zip(names, r[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+def make_inputs(torch, device, dtype, m, n):
+    from paper_2209_12464_gb300 import workloads as wl
+    sig = wl.spectrum_gap(min(m, n), K_RANK, TAIL)
+    A = wl.dense_spectral_torch(SEED, m, n, sig, noise_std=NOISE, device=device,
+                                dtype={"bf16": torch.bfloat16, "f32": torch.float32,
+                                       "f64": torch.float64}[dtype])
+    Om = wl.omega_torch(SEED + 1, n, K_RANK + P_OVER, device=device)
+    return A, Om, sig
+
+
+def residual_gpu(torch, A, Q, L, P):
+    """||A - Q L P^T||_F / ||A||_F in FP64 on the device (measurement only)."""
+    A64 = A.double()
+    E = A64 - (Q.double() @ L.double()) @ P.double().T
+    return float(torch.linalg.norm(E) / torch.linalg.norm(A64))
+
+
+def cpu_baseline(dtype, rows):
+    """Time the FP64 oracle, as it stands, on the leading `rows` rows of the
+    workload (a bounded sample), in a spawned process using every host core."""
+    code = r"""
+import os, sys, time, json
+sys.path.insert(0, %r)
+import numpy as np
+import oracle
+from paper_2209_12464_gb300 import workloads as wl
+rows, n, k, p, q = %d, %d, %d, %d, %d
+rng = np.random.default_rng(5)
+sig = wl.spectrum_gap(rows, k, %r)
+A, _, _, _ = wl.dense_spectral(11, rows, n, sig, noise_std=%r)
+Om = wl.omega(12, n, k + p)
+t0 = time.perf_counter()
+oracle.ruqlp(A, Om, q)
+t = time.perf_counter() - t0
+print(json.dumps({"seconds": t}))
+""" % (ROOT, rows, N, K_RANK, P_OVER, Q_POW, TAIL, NOISE)
+    env = dict(os.environ)
+    cores = os.cpu_count() or 1
+    for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        env[v] = str(cores)
+    env["CUDA_VISIBLE_DEVICES"] = ""
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env,
+                       timeout=900)
+    if r.returncode != 0:
+        return {"value": None, "error": r.stderr[-400:]}
+    t = json.loads(r.stdout.strip().splitlines()[-1])["seconds"]
+    gbytes = (2 * Q_POW + 2) * rows * N * DT_BYTES[dtype] / 1e9
+    return {"value": gbytes / t, "unit": "GB/s", "cores": cores, "kind": "oracle",
+            "seconds": t,
+            "sample": f"oracle.ruqlp (FP64 numpy, own Householder QR) on a {rows} x {N} row "
+                      f"sample of the workload (same spectrum form, k={K_RANK}, p={P_OVER}, "
+                      f"q={Q_POW}); bytes counted as (2q+2) x {rows}x{N} x {DT_BYTES[dtype]} B "
+                      f"({dtype}) so the ratio is the time per decomposition"}
+
+
+def run_reference(args):
+    rank, _, world = dist_env()
+    if rank != 0:
+        return 0
+    rows = 1000
+    for _ in range(args.warmup):
+        cpu_baseline(args.dtype, rows)
+    vals, secs = [], []
+    for _ in range(args.steps):
+        r = cpu_baseline(args.dtype, rows)
+        if r.get("value") is None:
+            print(json.dumps({"impl": "reference", "unavailable": r.get("error", "oracle failed")}))
+            return 0
+        vals.append(r["value"])
+        secs.append(r["seconds"])
+    v = statistics.median(vals)
+    cb = cpu_baseline(args.dtype, rows)
+    out = {"metric": METRIC, "value": v, "unit": "GB/s", "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.median(secs),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic", "impl": "reference",
+           "config": {"workload": WORKLOAD, "sample_rows": rows, "m": M, "n": N, "k": K_RANK,
+                      "p": P_OVER, "q": Q_POW, "l2": "inputs larger than L2 (host run)"},
+           "cpu_baseline": {"kind": "oracle", "cores": cb.get("cores"), "sample": cb.get("sample"),
+                            "value": v, "unit": "GB/s"},
+           "e2e": {"value": v, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+    import torch.distributed as dist
+    rank, local, world = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    import __graft_entry__ as g
+    g.build()
+    from paper_2209_12464_gb300 import ruqlp
+
+    m = n = args.size or M
+    k, p, q = K_RANK, P_OVER, Q_POW
+    d = k + p
+    A, Om, sig = make_inputs(torch, dev, args.dtype, m, n)
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream(dev)
+    h = ruqlp.Handle(local, stream.cuda_stream)
+    od = torch.float64 if args.dtype == "f64" else torch.float32
+    outs = (torch.empty(m, d, dtype=od, device=dev), torch.empty(d, d, dtype=od, device=dev),
+            torch.empty(n, d, dtype=od, device=dev))
+
+    def step():
+        return h.decompose(A, Om, k, p, q, outs=outs)
+
+    for _ in range(max(args.warmup, 3) if args.steps > 0 else args.warmup):
+        step()
+    torch.cuda.synchronize()
+    clocks = Clocks(local)
+    clocks.start()
+    time.sleep(0.3)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    l0 = ruqlp.ruqlp_launch_count()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    flags = 0
+    for _ in range(args.steps):
+        flags |= step()[3]
+    e1.record(stream)
+    torch.cuda.synchronize()
+    launches = (ruqlp.ruqlp_launch_count() - l0) // max(args.steps, 1)
+    if world > 1:
+        dist.barrier()
+    ck = clocks.stop()
+    ms = e0.elapsed_time(e1) / max(args.steps, 1)
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    bytes_a = m * n * DT_BYTES[args.dtype]
+    passes = 2 * q + 2
+    value = world * passes * bytes_a / (ms * 1e-3) / 1e9
+
+    # accuracy at this speed (FP64 measurement on the device)
+    Qo, Lo, Po = outs
+    resid = residual_gpu(torch, A, Qo, Lo, Po)
+    # approximate Eckart-Young floor: spectrum tail plus the noise energy
+    # outside a rank-d subspace ((m-d)(n-d) of its m n entries)
+    floor = math.sqrt(float((sig[d:] ** 2).sum()) + (NOISE ** 2) * (m - d) * (n - d)) / math.sqrt(
+        float((sig ** 2).sum()) + (NOISE ** 2) * m * n)
+
+    # live per-phase timing of the dominant kernels (CUDA events on the stream)
+    h.set_option("profile", 1)
+    nprof = 2
+    for _ in range(nprof):
+        step()
+    torch.cuda.synchronize()
+    prof = {ph: h.profile(ph) for ph in ("ax", "atx", "orth", "step")}
+    h.set_option("profile", 0)
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except OSError:
+        pass
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    # dominant product phase (the one with the largest share of the step)
+    dom = max(("ax", "atx"), key=lambda ph: prof[ph][1])
+    cnt, tot = prof[dom]
+    avg_ms = tot / max(cnt, 1)
+    alg_bytes = bytes_a + (n + m) * d * (DT_BYTES[args.dtype] if args.dtype != "bf16" else 4)
+    flops = 2.0 * m * n * d
+    # SIMT path: FP32 (or FP64) FMA-bound; peak from unit counts and clock
+    sm_mhz = ck.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
+    if args.dtype == "f64":
+        alu_peak = 152 * 4 * sm_mhz * 1e6 / 1e12           # 2 DFMA/clk/SM
+    else:
+        alu_peak = 152 * 256 * sm_mhz * 1e6 / 1e12         # 128 FFMA/clk/SM
+    achieved_tf = flops / (avg_ms * 1e-3) / 1e12
+    achieved_gbs = alg_bytes / (avg_ms * 1e-3) / 1e9
+    roofline = {"bound": "alu", "achieved": achieved_tf, "peak": alu_peak, "unit": "TFLOP/s",
+                "frac": achieved_tf / alu_peak, "traffic": None, "kernel": dom,
+                "hbm_achieved_gbs": achieved_gbs, "hbm_peak_gbs": hbm_peak,
+                "peak_source": "derived: 152 SMs x FMA lanes x 2 x median SM clock under load",
+                "phase_ms": {ph: (prof[ph][1] / max(prof[ph][0], 1)) for ph in prof},
+                "phase_share": {ph: prof[ph][1] / max(prof["step"][1], 1e-9)
+                                for ph in ("ax", "atx", "orth")}}
+
+    # end to end through the host entry point (pinned host buffers)
+    e2e = None
+    if not args.no_e2e:
+        Ah = A.cpu().pin_memory()
+        Omh = Om.cpu().pin_memory()
+        ho = (torch.empty(m, d, dtype=od).pin_memory(), torch.empty(d, d, dtype=od).pin_memory(),
+              torch.empty(n, d, dtype=od).pin_memory())
+        h.decompose_host(Ah, Omh, k, p, q, ho)
+        ke = max(1, min(args.steps, 3))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(ke):
+            h.decompose_host(Ah, Omh, k, p, q, ho)
+        te = (time.perf_counter() - t0) / ke
+        if world > 1:
+            t = torch.tensor([te], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            te = float(t.item())
+        bi = Ah.numel() * Ah.element_size() + Omh.numel() * 8
+        bo = sum(x.numel() * x.element_size() for x in ho)
+        e2e = {"value": world * passes * bytes_a / te / 1e9, "unit": "GB/s",
+               "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo, "ms_per_step": te * 1e3}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(args.dtype, rows=2000)
+
+    if rank == 0:
+        out = {"metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world,
+               "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+               "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+               "dtype": args.dtype, "data": "synthetic",
+               "config": {"workload": WORKLOAD, "m": m, "n": n, "k": k, "p": p, "q": q,
+                          "passes": passes, "bytes_A": bytes_a,
+                          "l2": "inputs larger than L2 (A is %.0f MB vs 129 MB L2)" % (bytes_a / 1e6),
+                          "parallelism": f"replicas x{world}"},
+               "accuracy": {"residual_fro": resid, "approx_floor_fro": floor,
+                            "flags": flags},
+               "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+               "gpu_launches": launches, "clocks": ck,
+               "hbm_frac_of_measured": value / world / hbm_peak}
+        print(json.dumps(out))
+    h.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

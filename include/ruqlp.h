@@ -1,0 +1,197 @@
+/*
+ * ruqlp.h -- C ABI of the GB300 RU-QLP library (libruqlp.so).
+ *
+ * Randomized Unpivoted QLP (arXiv 2209.12464, Section III, Algorithms 1-2),
+ * in the right-sketch orientation: for A (m x n) and a Gaussian test matrix
+ * Omega (n x d, d = k + p) the library computes
+ *
+ *     Y = A Omega;  Q = orth(Y);
+ *     q times:  Z = A^T Q;  Q~ = orth(Z);  Y = A Q~;  Q = orth(Y);   (Alg. 2)
+ *     B^T = A^T Q;  [P, R_B] = qr(B^T);  L = R_B^T                   (Alg. 1)
+ *
+ * so that A ~= Q L P^T with Q (m x d), P (n x d) orthonormal and L (d x d)
+ * lower triangular; |diag(L)| estimate sigma_1..sigma_d of A (Section III-A,
+ * Theorem 1).  This is the paper's Algorithm 1 + 2 applied to A^T with
+ * Phi = Omega, stopped before its d x d QR of R^T (Algorithm 1, step 5);
+ * that last QR is available with ruqlp_params.finish_paper.
+ *
+ * Conventions for every entry point:
+ *   - Matrices are row-major.  Sizes are element counts.  "Device" pointers
+ *     are CUDA device memory on the handle's device; "host" pointers are CPU
+ *     memory (pinned or pageable).
+ *   - The caller owns every buffer it passes (A, Omega, outputs); the
+ *     library owns only its workspace arena.  Buffers must stay valid until
+ *     the call returns (ruqlp_decompose*) or until ruqlp_poll reports
+ *     completion (ruqlp_submit).
+ *   - Errors are returned as ruqlp_status; nothing is thrown or aborted
+ *     across the ABI.  Invalid arguments give RUQLP_ERR_INVALID and leave the
+ *     outputs untouched; ruqlp_last_error(h) returns a message.
+ *   - A handle is not reentrant: one thread at a time per handle, except
+ *     ruqlp_submit / ruqlp_poll, which are thread-safe.
+ */
+#ifndef RUQLP_H
+#define RUQLP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ruqlp_ctx* ruqlp_handle;
+
+typedef enum {
+  RUQLP_OK = 0,
+  RUQLP_NOT_READY = 1,      /* ruqlp_poll: request still running */
+  RUQLP_ERR_INVALID = 2,    /* bad argument (sizes, pointers, dtype) */
+  RUQLP_ERR_BUDGET = 3,     /* workspace would exceed the HBM budget */
+  RUQLP_ERR_CUDA = 4,       /* a CUDA runtime / launch error */
+  RUQLP_ERR_BREAKDOWN = 5,  /* orth() failed even after its fallbacks */
+  RUQLP_ERR_TIMEOUT = 6     /* a bounded device wait ran out */
+} ruqlp_status;
+
+typedef enum {
+  RUQLP_F64 = 0,   /* IEEE binary64 */
+  RUQLP_F32 = 1,   /* IEEE binary32 */
+  RUQLP_BF16 = 2   /* bfloat16 (8-bit exponent, 7-bit mantissa) */
+} ruqlp_dtype;
+
+/* Output flags (ruqlp_outputs.flags), OR-ed over all orth() calls. */
+#define RUQLP_FLAG_SHIFTED 0x1u    /* a Cholesky broke down; the shifted
+                                      CholeskyQR3 path was taken */
+#define RUQLP_FLAG_RANKDEF 0x2u    /* even the shifted Cholesky broke down:
+                                      the input is numerically rank deficient */
+
+typedef struct {
+  int device;               /* CUDA device ordinal */
+  size_t hbm_budget_bytes;  /* cap on the workspace arena (0 = no cap) */
+  int max_slots;            /* serving: requests in flight at once (0 = 8) */
+  void* cuda_stream;        /* cudaStream_t the work is ordered on (NULL =
+                               the legacy default stream) */
+} ruqlp_config;
+
+/* Dense A, row-major, leading dimension ld >= n (elements). */
+typedef struct {
+  int64_t m, n, ld;
+  ruqlp_dtype dtype;
+  const void* data;
+} ruqlp_dense;
+
+/* Sparse A in CSR: rowptr[m+1] non-decreasing from 0 to nnz, colidx[nnz] in
+ * [0, n) and strictly increasing inside each row, values[nnz] of dtype. */
+typedef struct {
+  int64_t m, n, nnz;
+  const int32_t* rowptr;
+  const int32_t* colidx;
+  const void* values;
+  ruqlp_dtype dtype;
+} ruqlp_csr;
+
+typedef struct {
+  int is_csr;          /* 0: dense, 1: csr */
+  ruqlp_dense dense;
+  ruqlp_csr csr;
+} ruqlp_matrix;
+
+/* k >= 1 (target rank), p >= 0 (oversampling), d = k + p with
+ * d <= min(m, n) (Section III-A asks d < n; d = n is accepted and exact),
+ * q >= 0 power steps (Algorithm 2; q = 0 is Algorithm 1 alone).
+ * compute: precision A is streamed in.  F64: everything in FP64.  F32: A,
+ * sketches and Q/P in FP32.  BF16: A in BF16 through the tensor cores with
+ * FP32 accumulation; sketches and Q/P kept in FP32.  In every mode the d x d
+ * Gram, Cholesky and R factors are FP64.  compute must equal A's dtype.
+ * omega: n x d row-major FP64 Gaussian test matrix (device memory for
+ * ruqlp_decompose / ruqlp_submit; host memory for ruqlp_decompose_host).
+ * finish_paper: 1 = also take the d x d QR of L, [P~, R~] = qr(L)
+ * (Algorithm 1, step 5, in the paper's orientation).  On return Q holds
+ * Q P~ and L holds R~ (UPPER triangular), so A ~= Q L P^T still holds and
+ * diag(L) are the paper's L-values of A^T (Corollary 1). */
+typedef struct {
+  int k, p, q;
+  ruqlp_dtype compute;
+  const double* omega;
+  int finish_paper;
+} ruqlp_params;
+
+/* Q: m x d, L: d x d (dense, zero upper triangle), P: n x d, all row-major
+ * with leading dimension d, in out_dtype (F64 or F32).  flags: written by
+ * the library (RUQLP_FLAG_*). */
+typedef struct {
+  void* Q;
+  void* L;
+  void* P;
+  ruqlp_dtype out_dtype;
+  uint32_t flags;
+} ruqlp_outputs;
+
+/* Create a handle on cfg->device.  No workspace is allocated until the first
+ * decomposition (or ruqlp_reserve).  Errors: INVALID (NULL args, bad
+ * device), CUDA. */
+ruqlp_status ruqlp_create(ruqlp_handle* h, const ruqlp_config* cfg);
+
+/* Free the handle and its workspace (waits for its work to finish). */
+ruqlp_status ruqlp_destroy(ruqlp_handle h);
+
+/* Point the handle at another stream (cudaStream_t as void*). */
+ruqlp_status ruqlp_set_stream(ruqlp_handle h, void* cuda_stream);
+
+/* Set a tuning option of the handle.  Known names:
+ *   "gram1_exact": 1 (default) = the first CholeskyQR pass of each orth()
+ *   forms its Gram with FP64 products (exact for FP32 data); 0 = FP32
+ *   products summed in FP64 (faster; relies on the shifted fallback for
+ *   ill-conditioned sketches).  Ignored on the FP64 path.
+ *   "profile": 1 = bracket every phase with CUDA events on the handle's
+ *   stream and accumulate their durations (read with ruqlp_profile); setting
+ *   it (to 0 or 1) also zeroes the accumulators.
+ * Errors: INVALID (unknown name). */
+ruqlp_status ruqlp_set_option(ruqlp_handle h, const char* name, int64_t value);
+
+/* Grow the workspace arena now for problems up to m x n with d columns in
+ * the given compute dtype, so that later calls allocate nothing.
+ * Errors: INVALID, BUDGET, CUDA. */
+ruqlp_status ruqlp_reserve(ruqlp_handle h, int64_t m, int64_t n, int d,
+                           ruqlp_dtype compute, int is_csr);
+
+/* Workspace bytes a problem needs (0 on invalid sizes). */
+size_t ruqlp_workspace_bytes(int64_t m, int64_t n, int d, ruqlp_dtype compute,
+                             int is_csr);
+
+/* One RU-QLP decomposition (Section III-A; Algorithms 1 and 2), all buffers
+ * in device memory.  Work is ordered on the handle's stream; the call
+ * returns when it has completed (it synchronises that stream once to read
+ * the device status word).  On RUQLP_OK, out->Q/L/P hold Q, L = R_B^T, P
+ * (or, with finish_paper, Q P~, R~ and P, where [P~, R~] = qr(R_B^T)) and
+ * out->flags the fallbacks taken.  Errors: INVALID, BUDGET, CUDA,
+ * BREAKDOWN. */
+ruqlp_status ruqlp_decompose(ruqlp_handle h, const ruqlp_matrix* A,
+                             const ruqlp_params* prm, ruqlp_outputs* out);
+
+/* The same decomposition with A, prm->omega and the outputs in HOST memory:
+ * the library copies A and Omega into its arena, runs ruqlp_decompose's
+ * path and copies Q, L, P back.  Errors as ruqlp_decompose. */
+ruqlp_status ruqlp_decompose_host(ruqlp_handle h, const ruqlp_matrix* A,
+                                  const ruqlp_params* prm, ruqlp_outputs* out);
+
+/* Message of the last error on this handle (never NULL; "" if none). */
+const char* ruqlp_last_error(ruqlp_handle h);
+
+/* Kernels launched by this library in this process so far (all handles). */
+int64_t ruqlp_launch_count(void);
+
+/* With the "profile" option on: number of spans and their summed device time
+ * (milliseconds, CUDA events on the handle's stream) of a phase:
+ *   "ax"   sketch products A X (Algorithm 1 step 3 / Algorithm 2),
+ *   "atx"  transposed products A^T Y (Algorithm 2; B^T = A^T Q),
+ *   "orth" whole orth() calls (Gram, Cholesky, triangular solve passes),
+ *   "step" whole decompositions.
+ * Errors: INVALID (unknown phase, NULL pointers). */
+ruqlp_status ruqlp_profile(ruqlp_handle h, const char* phase, int64_t* count, double* total_ms);
+
+/* Library version string. */
+const char* ruqlp_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RUQLP_H */

@@ -1,0 +1,63 @@
+// Internal launchers of the RU-QLP CUDA library (not part of the C ABI).
+#pragma once
+
+#include "common.cuh"
+
+namespace ruqlp {
+
+// How a SIMT product accumulates.
+enum class Mul : int {
+  F64 = 0,        // products and sums in FP64 (exact products for FP32/BF16 inputs)
+  F32 = 1,        // products and sums in FP32
+  F32_ACC64 = 2,  // FP32 products summed in FP32 over 16-row chunks, chunks summed in FP64
+};
+
+// C[M x N] = A[M x K] B[K x N]; all row-major with the given leading dims.
+cudaError_t simt_gemm_nn(Ty ta, Ty tb, Ty tc, Mul mul, const void* A, int64_t lda,
+                         const void* B, int64_t ldb, void* C, int64_t ldc, int64_t M,
+                         int64_t K, int64_t N, cudaStream_t st);
+
+// C[M x N] = A^T B with A (K x M) and B (K x N) row-major.  With splits > 1
+// the K range is cut into `splits` slabs whose FP64 partial products go to
+// `partial` ([splits][M][N], FP64) and are summed in slab order into C.
+// A non-null `gate` makes the launch a no-op unless *gate != 0 (device word).
+cudaError_t simt_gemm_tn(Ty ta, Ty tb, Ty tc, Mul mul, const void* A, int64_t lda,
+                         const void* B, int64_t ldb, void* C, int64_t ldc, int64_t M,
+                         int64_t K, int64_t N, int splits, double* partial,
+                         const int32_t* gate, cudaStream_t st);
+
+// Number of K slabs simt_gemm_tn should use for a small M x N output.
+int tn_splits(int64_t M, int64_t K, int64_t N, int max_splits);
+
+// Cholesky G = R^T R of the d x d FP64 Gram G (row-major, full symmetric),
+// in one CTA, in FP64.  On a non-positive pivot it retries once on
+// G + shift I with shift = shift_rel * trace(G) and sets status->shifted
+// (and RUQLP_FLAG_SHIFTED); a second breakdown sets RUQLP_FLAG_RANKDEF and
+// replaces the failed pivots by shift-sized ones so the output stays finite.
+// Writes R (upper, FP64, ld d, zero lower part) and Rw = R in type tw.
+// A non-null `gate` makes it a no-op unless *gate != 0.
+cudaError_t chol_upper(const double* G, int d, double shift_rel, double* R, void* Rw,
+                       Ty tw, DevStatus* status, const int32_t* gate, cudaStream_t st);
+
+// X[M x d] <- Y[M x d] R^{-1} for upper-triangular R (type ty, ld d): each
+// row solves x R = y by forward substitution.  X may alias Y.  A non-null
+// `gate` makes it a no-op unless *gate != 0.
+cudaError_t trsm_right_upper(Ty ty, const void* Y, int64_t ldy, const void* R, void* X,
+                             int64_t ldx, int64_t M, int d, const int32_t* gate,
+                             cudaStream_t st);
+
+// dst[rows x cols] (type td, ld lds) <- src (type ts, ld lds), zeroing nothing else.
+cudaError_t copy_cast_2d(Ty ts, const void* src, int64_t lds, Ty td, void* dst, int64_t ldd,
+                         int64_t rows, int64_t cols, cudaStream_t st);
+
+// L (d x d, type tl, ld d) <- transpose of the upper triangle of R (FP64,
+// ld d), zeros above the diagonal.  With `upper` the upper triangle is
+// copied as is instead (finish_paper output).
+cudaError_t write_L(const double* R, int d, Ty tl, void* L, bool upper, cudaStream_t st);
+
+// Zero the status word.
+cudaError_t status_reset(DevStatus* s, cudaStream_t st);
+// Clear only the per-orth `shifted` field.
+cudaError_t status_clear_shift(DevStatus* s, cudaStream_t st);
+
+}  // namespace ruqlp

@@ -1,0 +1,507 @@
+// Tensor-core sketch products of RU-QLP on sm_103a (Section III-D: the
+// O(mnd) products A X and A^T Y that make up the 2q+2 passes over A):
+//
+//   Y[m x dp] = A[m x n] X        (A K-major;   "NT" below)
+//   Z[n x dp] = A^T[n x m] Y      (A MN-major;  "TN" below)
+//
+// A is BF16 row-major; the skinny operand is given transposed, Bt[dp x K]
+// (BF16, K contiguous), so it is always the K-major B operand.  Outputs are
+// FP32 (accumulated in TMEM).
+//
+// Structure (one CTA per SM, 192 threads):
+//   warp 0  : TMA producer (one lane) -- A tile 128 x 64 and Bt tile dp x 64
+//             per stage into a 128B-swizzled shared-memory ring;
+//   warp 1  : TMEM allocation + tcgen05.mma issue (one lane), M=128, N=dp,
+//             K=16 per instruction, two TMEM accumulators (ping-pong);
+//   warps 2-5: epilogue -- tcgen05.ld of the accumulator, FP32 stores.
+// Work split: output tiles of 128 rows are dealt to the CTAs in whole waves
+// (data parallel); the tiles of the last partial wave are split over all
+// CTAs along K (stream-K) into FP32 fragments, summed afterwards in CTA
+// order by a fix-up kernel (deterministic; no atomics).
+// Every mbarrier wait is bounded (~2 s of %globaltimer); on timeout the CTA
+// sets an error word, stops issuing work, and frees its TMEM before exiting.
+#include <cuda.h>
+
+#include "internal.h"
+
+namespace ruqlp {
+namespace {
+
+constexpr int BM = 128;       // rows of an output tile (MMA M)
+constexpr int BK = 64;        // K per stage (one 128-byte swizzle row of BF16)
+constexpr int NTHREADS = 192;
+constexpr int A_TILE_BYTES = BM * BK * 2;  // 16 KB
+constexpr uint64_t WAIT_NS = 2000000000ull;
+
+struct TcParams {
+  int64_t Mout;   // output rows
+  int64_t K;      // contraction length
+  int dp;         // N (multiple of 16, <= 256)
+  int stages;
+  float* out;
+  int64_t ldo;
+  float* frag;    // [P][2][BM][dp]
+  int T, KB, full_waves, tail;
+  int64_t U;      // stream-K units = tail * KB
+  int* err;
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ uint64_t gtimer() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait on an mbarrier phase; false on timeout or when another role
+// of the CTA has already given up.
+__device__ __noinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = gtimer();
+  for (uint32_t it = 1;; ++it) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((it & 63) == 0) {
+      if (*abort_flag) return false;
+      if (gtimer() - t0 > WAIT_NS) return false;
+    }
+  }
+}
+
+__device__ __forceinline__ uint64_t policy_evict_first() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ uint64_t policy_evict_last() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, uint32_t bar,
+                                            int x, int y, uint64_t policy) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint"
+      " [%0], [%1, {%3, %4}], [%2], %5;" ::"r"(dst),
+      "l"((uint64_t)map), "r"(bar), "r"(x), "r"(y), "l"(policy)
+      : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+// Shared-memory matrix descriptor (tcgen05): start address, leading and
+// stride byte offsets, version 1, 128-byte swizzle.
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((saddr & 0x3FFFF) >> 4) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | (1ull << 46) | (2ull << 61);
+}
+
+// Instruction descriptor, kind::f16: BF16 x BF16 -> FP32, M = 128, N = n.
+__device__ __forceinline__ uint32_t idesc_bf16(int n, bool a_mn_major) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((a_mn_major ? 1u : 0u) << 15) |
+         ((uint32_t)(n >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc,
+                                         uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+      : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+        "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// A CTA's work: whole tiles first (data parallel), then at most two
+// stream-K segments of tail tiles.
+struct Item {
+  int tile, kb0, kb1, slot;  // slot < 0: write the output; else fragment slot
+};
+
+__device__ __forceinline__ int64_t sk_start(int64_t c, int64_t U, int P) { return c * U / P; }
+
+__device__ int build_items(const TcParams& p, Item* items) {
+  const int P = gridDim.x, c = blockIdx.x;
+  int n = 0;
+  for (int w = 0; w < p.full_waves; ++w) items[n++] = {c + w * P, 0, p.KB, -1};
+  if (p.tail > 0) {
+    const int64_t u0 = sk_start(c, p.U, P), u1 = sk_start(c + 1, p.U, P);
+    if (u1 > u0) {
+      const int base = p.full_waves * P;
+      const int64_t t0 = u0 / p.KB;
+      const int64_t e0 = min(u1, (t0 + 1) * (int64_t)p.KB);
+      items[n++] = {base + (int)t0, (int)(u0 - t0 * p.KB), (int)(e0 - t0 * p.KB), 0};
+      if (u1 > e0) items[n++] = {base + (int)t0 + 1, 0, (int)(u1 - (t0 + 1) * p.KB), 1};
+    }
+  }
+  return n;
+}
+
+constexpr int MAX_ITEMS = 8;
+
+template <bool TRANS>
+__global__ void __launch_bounds__(NTHREADS, 1)
+k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+          TcParams p) {
+  extern __shared__ uint8_t smem_raw[];
+  const uint32_t raw = smem_u32(smem_raw);
+  const uint32_t base = (raw + 1023u) & ~1023u;
+  uint8_t* base_ptr = smem_raw + (base - raw);
+  const int S = p.stages;
+  const uint32_t b_bytes = (uint32_t)p.dp * BK * 2;
+  const uint32_t stage_bytes = A_TILE_BYTES + b_bytes;
+  const uint32_t bar_base = base + S * stage_bytes;
+  // barriers: full[S], empty[S], tfull[2], tempty[2]; then the TMEM address
+  auto full_bar = [&](int s) { return bar_base + 8u * s; };
+  auto empty_bar = [&](int s) { return bar_base + 8u * (S + s); };
+  auto tfull_bar = [&](int a) { return bar_base + 8u * (2 * S + a); };
+  auto tempty_bar = [&](int a) { return bar_base + 8u * (2 * S + 2 + a); };
+  uint32_t* tmem_slot = (uint32_t*)(base_ptr + S * stage_bytes + 8 * (2 * S + 4));
+  __shared__ int s_abort;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < S; ++s) {
+      mbar_init(full_bar(s), 1);
+      mbar_init(empty_bar(s), 1);
+    }
+    for (int a = 0; a < 2; ++a) {
+      mbar_init(tfull_bar(a), 1);
+      mbar_init(tempty_bar(a), 4);  // one arrival per epilogue warp
+    }
+    s_abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tmA) : "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tmB) : "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(
+                     smem_u32(tmem_slot))
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+  volatile int* abort_flag = &s_abort;
+
+  Item items[MAX_ITEMS];
+  const int nitems = build_items(p, items);
+
+  if (warp == 0) {
+    // ---------------- TMA producer ----------------
+    if (lane == 0) {
+      const uint64_t pol_a = policy_evict_first(), pol_b = policy_evict_last();
+      int stage = 0;
+      uint32_t phase = 0;
+      bool ok = true;
+      for (int i = 0; i < nitems && ok; ++i) {
+        const Item it = items[i];
+        for (int kb = it.kb0; kb < it.kb1; ++kb) {
+          if (!mbar_wait(empty_bar(stage), phase ^ 1u, abort_flag)) { ok = false; break; }
+          const uint32_t sa = base + stage * stage_bytes, sb = sa + A_TILE_BYTES;
+          mbar_expect_tx(full_bar(stage), stage_bytes);
+          if (!TRANS) {
+            tma_load_2d(sa, &tmA, full_bar(stage), kb * BK, it.tile * BM, pol_a);
+          } else {
+            tma_load_2d(sa, &tmA, full_bar(stage), it.tile * BM, kb * BK, pol_a);
+            tma_load_2d(sa + A_TILE_BYTES / 2, &tmA, full_bar(stage), it.tile * BM + 64, kb * BK,
+                        pol_a);
+          }
+          tma_load_2d(sb, &tmB, full_bar(stage), kb * BK, 0, pol_b);
+          if (++stage == S) { stage = 0; phase ^= 1u; }
+        }
+      }
+      if (!ok) { *abort_flag = 1; atomicExch(p.err, 1); }
+    }
+  } else if (warp == 1) {
+    // ---------------- MMA issuer ----------------
+    if (lane == 0) {
+      const uint32_t idesc = idesc_bf16(p.dp, TRANS);
+      int stage = 0;
+      uint32_t phase = 0;
+      bool ok = true;
+      for (int i = 0; i < nitems && ok; ++i) {
+        const Item it = items[i];
+        const int acc = i & 1;
+        const uint32_t use = (uint32_t)(i >> 1);
+        if (!mbar_wait(tempty_bar(acc), (use & 1u) ^ 1u, abort_flag)) { ok = false; break; }
+        tc_fence_after();
+        const uint32_t tmem_d = tmem_base + (uint32_t)(acc * 256);
+        for (int kb = it.kb0; kb < it.kb1; ++kb) {
+          if (!mbar_wait(full_bar(stage), phase, abort_flag)) { ok = false; break; }
+          tc_fence_after();
+          const uint32_t sa = base + stage * stage_bytes, sb = sa + A_TILE_BYTES;
+#pragma unroll
+          for (int kk = 0; kk < BK / 16; ++kk) {
+            uint64_t ad, bd;
+            if (!TRANS) ad = sdesc(sa + kk * 32, 16, 1024);
+            else        ad = sdesc(sa + kk * 2048, A_TILE_BYTES / 2, 1024);
+            bd = sdesc(sb + kk * 32, 16, 1024);
+            mma_bf16(tmem_d, ad, bd, idesc, (kb > it.kb0 || kk > 0) ? 1u : 0u);
+          }
+          mma_commit(empty_bar(stage));
+          if (++stage == S) { stage = 0; phase ^= 1u; }
+        }
+        if (!ok) break;
+        mma_commit(tfull_bar(acc));
+      }
+      if (!ok) { *abort_flag = 1; atomicExch(p.err, 1); }
+    }
+  } else {
+    // ---------------- epilogue (warps 2..5) ----------------
+    const int g = warp & 3;  // TMEM lane quarter this warp may access
+    const int row = g * 32 + lane;
+    bool ok = true;
+    for (int i = 0; i < nitems && ok; ++i) {
+      const Item it = items[i];
+      const int acc = i & 1;
+      const uint32_t use = (uint32_t)(i >> 1);
+      if (!mbar_wait(tfull_bar(acc), use & 1u, abort_flag)) { ok = false; break; }
+      tc_fence_after();
+      const uint32_t taddr = tmem_base + (uint32_t)(acc * 256) + ((uint32_t)(g * 32) << 16);
+      float* dst;
+      bool valid;
+      if (it.slot < 0) {
+        const int64_t r = (int64_t)it.tile * BM + row;
+        valid = r < p.Mout;
+        dst = p.out + r * p.ldo;
+      } else {
+        valid = true;
+        dst = p.frag + (((int64_t)blockIdx.x * 2 + it.slot) * BM + row) * p.dp;
+      }
+      for (int c = 0; c < p.dp; c += 16) {
+        float v[16];
+        tmem_ld16(taddr + c, v);
+        if (valid) {
+          float4* d4 = reinterpret_cast<float4*>(dst + c);
+#pragma unroll
+          for (int j = 0; j < 4; ++j) d4[j] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(tempty_bar(acc));
+    }
+    if (!ok) { *abort_flag = 1; if (lane == 0) atomicExch(p.err, 1); }
+  }
+
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem_base)
+                 : "memory");
+  }
+}
+
+// Sum the stream-K fragments of each tail tile in CTA order into the output.
+__global__ void k_tc_fixup(TcParams p, int P) {
+  const int tt = blockIdx.x;  // tail tile index
+  const int64_t KB = p.KB;
+  const int64_t lo = tt * KB, hi = lo + KB;
+  int c = (int)((lo * P) / p.U);
+  while (c + 1 < P && sk_start(c + 1, p.U, P) <= lo) ++c;
+  while (c > 0 && sk_start(c, p.U, P) > lo) --c;
+  const int tile = p.full_waves * P + tt;
+  const int r0 = blockIdx.y * 16;
+  for (int e = threadIdx.x; e < 16 * p.dp; e += blockDim.x) {
+    const int r = r0 + e / p.dp, col = e % p.dp;
+    float s = 0.f;
+    for (int cc = c; cc < P; ++cc) {
+      const int64_t u0 = sk_start(cc, p.U, P), u1 = sk_start(cc + 1, p.U, P);
+      if (u0 >= hi) break;
+      if (u1 <= lo || u1 == u0) continue;
+      const int slot = (u0 / KB == tt) ? 0 : 1;
+      s += p.frag[(((int64_t)cc * 2 + slot) * BM + r) * p.dp + col];
+    }
+    const int64_t gr = (int64_t)tile * BM + r;
+    if (gr < p.Mout) p.out[gr * p.ldo + col] = s;
+  }
+}
+
+// dst[c][r] = bf16(src[r][c]) for c < cols, 0 for cols <= c < dp (r < rows).
+template <typename TS>
+__global__ void k_transpose_bf16(const TS* __restrict__ src, int64_t lds, int64_t rows, int cols,
+                                 int dp, __nv_bfloat16* __restrict__ dst, int64_t ldd) {
+  __shared__ float t[32][33];
+  const int64_t r0 = (int64_t)blockIdx.x * 32;
+  const int c0 = blockIdx.y * 32;
+  for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+    const int64_t r = r0 + i;
+    const int c = c0 + threadIdx.x;
+    float v = 0.f;
+    if (r < rows && c < cols) v = (float)src[r * lds + c];
+    t[i][threadIdx.x] = v;
+  }
+  __syncthreads();
+  for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+    const int c = c0 + i;
+    const int64_t r = r0 + threadIdx.x;
+    if (c < dp && r < rows) dst[(int64_t)c * ldd + r] = __float2bfloat16_rn(t[threadIdx.x][i]);
+  }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* ptr = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (PFN_cuTensorMapEncodeTiled_v12000)ptr;
+  }
+  return fn;
+}
+
+bool make_map(CUtensorMap* m, const void* ptr, uint64_t inner, uint64_t outer, uint64_t ld_elems,
+              uint32_t box_inner, uint32_t box_outer) {
+  auto fn = encode_fn();
+  if (!fn) return false;
+  cuuint64_t dims[2] = {inner, outer};
+  cuuint64_t strides[1] = {ld_elems * 2};
+  cuuint32_t box[2] = {box_inner, box_outer};
+  cuuint32_t es[2] = {1, 1};
+  return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(ptr), dims, strides, box, es,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+int sm_count() {
+  static int n = 0;
+  if (!n) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    if (n <= 0) n = 1;
+  }
+  return n;
+}
+
+}  // namespace
+
+size_t tc_frag_bytes(int dp) { return (size_t)sm_count() * 2 * BM * dp * sizeof(float); }
+
+cudaError_t tc_gemm(bool trans, const void* A, int64_t lda, int64_t m, int64_t n, const void* Bt,
+                    int64_t ldb, int dp, float* out, int64_t ldo, float* frag, int* err,
+                    cudaStream_t st) {
+  if (dp < 16 || dp > 256 || dp % 16 != 0) return cudaErrorInvalidValue;
+  if (lda % 8 != 0 || ldb % 8 != 0 || ((uintptr_t)A & 15) || ((uintptr_t)Bt & 15) || ldo % 4 != 0 ||
+      ((uintptr_t)out & 15))
+    return cudaErrorInvalidValue;
+  const int64_t Mout = trans ? n : m, K = trans ? m : n;
+  CUtensorMap mA, mB;
+  if (!make_map(&mA, A, (uint64_t)n, (uint64_t)m, (uint64_t)lda, 64, trans ? 64 : BM))
+    return cudaErrorInvalidValue;
+  if (!make_map(&mB, Bt, (uint64_t)K, (uint64_t)dp, (uint64_t)ldb, 64, (uint32_t)dp))
+    return cudaErrorInvalidValue;
+  TcParams p{};
+  p.Mout = Mout;
+  p.K = K;
+  p.dp = dp;
+  p.out = out;
+  p.ldo = ldo;
+  p.frag = frag;
+  p.err = err;
+  p.T = ceil_div(Mout, BM);
+  p.KB = ceil_div(K, BK);
+  int P = sm_count();
+  if ((int64_t)p.T * p.KB < P) P = p.T * p.KB;
+  p.full_waves = p.T / P;
+  p.tail = p.T - p.full_waves * P;
+  p.U = (int64_t)p.tail * p.KB;
+  if (p.full_waves + 2 > MAX_ITEMS) {
+    // very tall outputs: more whole tiles per CTA than the item list holds
+    P = (p.T + MAX_ITEMS - 3) / (MAX_ITEMS - 2);
+    p.full_waves = p.T / P;
+    p.tail = p.T - p.full_waves * P;
+    p.U = (int64_t)p.tail * p.KB;
+  }
+  const size_t stage_bytes = A_TILE_BYTES + (size_t)dp * BK * 2;
+  int stages = (int)((200 * 1024) / stage_bytes);
+  if (stages > 8) stages = 8;
+  if (stages < 2) return cudaErrorInvalidValue;
+  p.stages = stages;
+  const size_t smem = 1024 + stages * stage_bytes + 8 * (2 * stages + 4) + 16;
+  cudaError_t e;
+  if (trans) {
+    e = cudaFuncSetAttribute(k_tc_gemm<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
+    if (e != cudaSuccess) return e;
+    k_tc_gemm<true><<<P, NTHREADS, smem, st>>>(mA, mB, p);
+  } else {
+    e = cudaFuncSetAttribute(k_tc_gemm<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
+    if (e != cudaSuccess) return e;
+    k_tc_gemm<false><<<P, NTHREADS, smem, st>>>(mA, mB, p);
+  }
+  count_launch();
+  e = cudaGetLastError();
+  if (e != cudaSuccess || p.tail == 0) return e;
+  k_tc_fixup<<<dim3(p.tail, BM / 16), 256, 0, st>>>(p, P);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t transpose_to_bf16(Ty ts, const void* src, int64_t lds, int64_t rows, int cols, int dp,
+                              void* dst, int64_t ldd, cudaStream_t st) {
+  dim3 grid(ceil_div(rows, 32), ceil_div(dp, 32)), block(32, 8);
+  if (ts == Ty::F64)
+    k_transpose_bf16<double><<<grid, block, 0, st>>>((const double*)src, lds, rows, cols, dp,
+                                                     (__nv_bfloat16*)dst, ldd);
+  else if (ts == Ty::F32)
+    k_transpose_bf16<float><<<grid, block, 0, st>>>((const float*)src, lds, rows, cols, dp,
+                                                    (__nv_bfloat16*)dst, ldd);
+  else
+    return cudaErrorInvalidValue;
+  count_launch();
+  return cudaGetLastError();
+}
+
+}  // namespace ruqlp

@@ -1,0 +1,244 @@
+"""Thin ctypes binding of libruqlp.so (include/ruqlp.h).
+
+The ``ruqlp_*`` functions here have the names and arguments of the C ABI and
+only marshal arguments; every step of RU-QLP runs in the library's CUDA
+kernels.  ``decompose`` / ``decompose_host`` are conveniences that allocate
+the outputs with torch and raise on a non-OK status.  There is no fallback:
+if the library is missing or fails to load, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libruqlp.so")
+
+OK, NOT_READY, ERR_INVALID, ERR_BUDGET, ERR_CUDA, ERR_BREAKDOWN, ERR_TIMEOUT = range(7)
+F64, F32, BF16 = 0, 1, 2
+FLAG_SHIFTED, FLAG_RANKDEF = 0x1, 0x2
+STATUS_NAMES = {0: "OK", 1: "NOT_READY", 2: "ERR_INVALID", 3: "ERR_BUDGET", 4: "ERR_CUDA",
+                5: "ERR_BREAKDOWN", 6: "ERR_TIMEOUT"}
+
+c_int, c_int64, c_size_t, c_void_p, c_char_p = (ctypes.c_int, ctypes.c_int64, ctypes.c_size_t,
+                                                 ctypes.c_void_p, ctypes.c_char_p)
+
+
+class Config(ctypes.Structure):
+    _fields_ = [("device", c_int), ("hbm_budget_bytes", c_size_t), ("max_slots", c_int),
+                ("cuda_stream", c_void_p)]
+
+
+class Dense(ctypes.Structure):
+    _fields_ = [("m", c_int64), ("n", c_int64), ("ld", c_int64), ("dtype", c_int),
+                ("data", c_void_p)]
+
+
+class Csr(ctypes.Structure):
+    _fields_ = [("m", c_int64), ("n", c_int64), ("nnz", c_int64), ("rowptr", c_void_p),
+                ("colidx", c_void_p), ("values", c_void_p), ("dtype", c_int)]
+
+
+class Matrix(ctypes.Structure):
+    _fields_ = [("is_csr", c_int), ("dense", Dense), ("csr", Csr)]
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("k", c_int), ("p", c_int), ("q", c_int), ("compute", c_int),
+                ("omega", c_void_p), ("finish_paper", c_int)]
+
+
+class Outputs(ctypes.Structure):
+    _fields_ = [("Q", c_void_p), ("L", c_void_p), ("P", c_void_p), ("out_dtype", c_int),
+                ("flags", ctypes.c_uint32)]
+
+
+_lib = None
+_lock = threading.Lock()
+
+_SIGS = {
+    "ruqlp_create": (c_int, [ctypes.POINTER(c_void_p), ctypes.POINTER(Config)]),
+    "ruqlp_destroy": (c_int, [c_void_p]),
+    "ruqlp_set_stream": (c_int, [c_void_p, c_void_p]),
+    "ruqlp_set_option": (c_int, [c_void_p, c_char_p, c_int64]),
+    "ruqlp_reserve": (c_int, [c_void_p, c_int64, c_int64, c_int, c_int, c_int]),
+    "ruqlp_workspace_bytes": (c_size_t, [c_int64, c_int64, c_int, c_int, c_int]),
+    "ruqlp_decompose": (c_int, [c_void_p, ctypes.POINTER(Matrix), ctypes.POINTER(Params),
+                                ctypes.POINTER(Outputs)]),
+    "ruqlp_decompose_host": (c_int, [c_void_p, ctypes.POINTER(Matrix), ctypes.POINTER(Params),
+                                     ctypes.POINTER(Outputs)]),
+    "ruqlp_last_error": (c_char_p, [c_void_p]),
+    "ruqlp_launch_count": (c_int64, []),
+    "ruqlp_profile": (c_int, [c_void_p, c_char_p, ctypes.POINTER(c_int64),
+                              ctypes.POINTER(ctypes.c_double)]),
+    "ruqlp_version": (c_char_p, []),
+}
+
+
+def lib():
+    """Load libruqlp.so once; raise if it is missing (no fallback path)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"{LIB_PATH} is not built; run __graft_entry__.build()")
+            L = ctypes.CDLL(LIB_PATH)
+            for name, (res, args) in _SIGS.items():
+                f = getattr(L, name)
+                f.restype = res
+                f.argtypes = args
+            _lib = L
+    return _lib
+
+
+def exported_symbols():
+    """Names the binding expects the library to export."""
+    return sorted(_SIGS)
+
+
+# ---- same-name wrappers of the C ABI --------------------------------------
+def ruqlp_create(config):
+    h = c_void_p()
+    st = lib().ruqlp_create(ctypes.byref(h), ctypes.byref(config))
+    return st, h
+
+
+def ruqlp_destroy(h):
+    return lib().ruqlp_destroy(h)
+
+
+def ruqlp_set_stream(h, stream):
+    return lib().ruqlp_set_stream(h, stream)
+
+
+def ruqlp_set_option(h, name, value):
+    return lib().ruqlp_set_option(h, name.encode(), int(value))
+
+
+def ruqlp_reserve(h, m, n, d, compute, is_csr=0):
+    return lib().ruqlp_reserve(h, m, n, d, compute, is_csr)
+
+
+def ruqlp_workspace_bytes(m, n, d, compute, is_csr=0):
+    return lib().ruqlp_workspace_bytes(m, n, d, compute, is_csr)
+
+
+def ruqlp_decompose(h, A, prm, out):
+    return lib().ruqlp_decompose(h, ctypes.byref(A), ctypes.byref(prm), ctypes.byref(out))
+
+
+def ruqlp_decompose_host(h, A, prm, out):
+    return lib().ruqlp_decompose_host(h, ctypes.byref(A), ctypes.byref(prm), ctypes.byref(out))
+
+
+def ruqlp_last_error(h):
+    return lib().ruqlp_last_error(h).decode()
+
+
+def ruqlp_version():
+    return lib().ruqlp_version().decode()
+
+
+def ruqlp_launch_count():
+    return lib().ruqlp_launch_count()
+
+
+def ruqlp_profile(h, phase):
+    c = c_int64()
+    ms = ctypes.c_double()
+    st = lib().ruqlp_profile(h, phase.encode(), ctypes.byref(c), ctypes.byref(ms))
+    return st, c.value, ms.value
+
+
+# ---- conveniences over torch tensors ---------------------------------------
+class RuqlpError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+def _dtype_code(t):
+    import torch
+    return {torch.float64: F64, torch.float32: F32, torch.bfloat16: BF16}[t]
+
+
+class Handle:
+    """Owns one library handle bound to a device and stream."""
+
+    def __init__(self, device=0, stream=None, hbm_budget_bytes=0, max_slots=0):
+        cfg = Config(device, hbm_budget_bytes, max_slots, stream or None)
+        st, h = ruqlp_create(cfg)
+        if st != OK:
+            raise RuqlpError(st, "ruqlp_create failed")
+        self.h = h
+
+    def check(self, st):
+        if st != OK:
+            raise RuqlpError(st, ruqlp_last_error(self.h))
+
+    def set_stream(self, stream):
+        self.check(ruqlp_set_stream(self.h, stream))
+
+    def set_option(self, name, value):
+        self.check(ruqlp_set_option(self.h, name, value))
+
+    def profile(self, phase):
+        st, c, ms = ruqlp_profile(self.h, phase)
+        self.check(st)
+        return c, ms
+
+    def close(self):
+        if self.h:
+            ruqlp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def decompose(self, A, omega, k, p, q, out_dtype=None, outs=None, finish_paper=False):
+        """RU-QLP of the CUDA tensor A (m x n, row-major) with the FP64 CUDA
+        tensor omega (n x d).  Returns (Q, L, P, flags) as torch tensors."""
+        import torch
+        if A.dim() != 2 or A.stride(1) != 1:
+            raise ValueError("A must be a 2-D row-major tensor")
+        m, n = A.shape
+        d = k + p
+        omega = omega.contiguous()
+        if out_dtype is None:
+            out_dtype = torch.float64 if A.dtype == torch.float64 else torch.float32
+        if outs is None:
+            Q = torch.empty(m, d, dtype=out_dtype, device=A.device)
+            L = torch.empty(d, d, dtype=out_dtype, device=A.device)
+            P = torch.empty(n, d, dtype=out_dtype, device=A.device)
+        else:
+            Q, L, P = outs
+        M = Matrix(0, Dense(m, n, A.stride(0), _dtype_code(A.dtype), A.data_ptr()), Csr())
+        prm = Params(k, p, q, _dtype_code(A.dtype), omega.data_ptr(), int(finish_paper))
+        out = Outputs(Q.data_ptr(), L.data_ptr(), P.data_ptr(), _dtype_code(out_dtype), 0)
+        self.check(ruqlp_decompose(self.h, M, prm, out))
+        return Q, L, P, out.flags
+
+    def decompose_host(self, A, omega, k, p, q, outs):
+        """Same with CPU tensors (pinned or pageable); outs = (Q, L, P) CPU tensors."""
+        m, n = A.shape
+        Q, L, P = outs
+        M = Matrix(0, Dense(m, n, A.stride(0), _dtype_code(A.dtype), A.data_ptr()), Csr())
+        prm = Params(k, p, q, _dtype_code(A.dtype), omega.data_ptr(), 0)
+        out = Outputs(Q.data_ptr(), L.data_ptr(), P.data_ptr(), _dtype_code(Q.dtype), 0)
+        self.check(ruqlp_decompose_host(self.h, M, prm, out))
+        return Q, L, P, out.flags
+
+
+def decompose(A, omega, k, p, q, **kw):
+    """One-shot RU-QLP on A's device and torch's current stream."""
+    import torch
+    dev = A.device.index or 0
+    h = Handle(device=dev, stream=torch.cuda.current_stream(A.device).cuda_stream)
+    try:
+        return h.decompose(A, omega, k, p, q, **kw)
+    finally:
+        h.close()

@@ -1,0 +1,136 @@
+"""GPU parity of the dense RU-QLP path against the FP64 oracle, through the C ABI.
+
+Tolerances (stated per result, Section III-A outputs):
+  * FP64 path: L element-wise and |diag(L)| within 1e-10 |L_11|; relative
+    residual ||A - Q L P^T||_F / ||A||_F within 1e-10 of the oracle's.
+  * FP32 path: the same at 1e-5.
+  * Q and P: the leading k columns element-wise within 1e-9 (FP64) / 1e-4
+    (FP32); they span the well-separated dominant subspaces, so they are
+    determined to about u * sigma_1 / (sigma_k - sigma_{k+1}).  The trailing
+    p columns are checked through the residual and orthonormality instead
+    (their sensitivity grows with kappa of the sketch).
+The oracle runs on the exact values the GPU sees (A rounded to the compute
+dtype, then widened to float64).
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2209_12464_gb300 import ruqlp
+from paper_2209_12464_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+TOL = {torch.float64: 1e-10, torch.float32: 1e-5}
+TOLQ = {torch.float64: 1e-9, torch.float32: 1e-4}
+TOLO = {torch.float64: 1e-12, torch.float32: 2e-5}
+
+CASES = [
+    # name, m, n, k, p, q, spectrum tail
+    ("cfg1-1000x800", 1000, 800, 20, 10, 1, 1e-3),
+    ("ragged-777x555-q2", 777, 555, 25, 12, 2, 1e-2),
+    ("wide-300x700", 300, 700, 12, 5, 1, 1e-2),
+    ("q0-640x512", 640, 512, 16, 8, 0, 1e-2),
+    ("k1-p0-200x150", 200, 150, 1, 0, 1, 1e-2),
+    ("p0-500x400-q2", 500, 400, 30, 0, 2, 1e-2),
+    ("tall-3000x200-d64", 3000, 200, 48, 16, 1, 1e-2),
+]
+
+
+@pytest.fixture(scope="module")
+def handle():
+    import __graft_entry__ as g
+    g.build()
+    h = ruqlp.Handle(0, torch.cuda.current_stream().cuda_stream)
+    yield h
+    h.close()
+
+
+def _case(name, m, n, k, p, q, tail, seed):
+    sig = wl.spectrum_gap(min(m, n), k, tail)
+    A, _, _, _ = wl.dense_spectral(seed, m, n, sig)
+    Om = wl.omega(seed + 1, n, k + p)
+    return A, Om
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32], ids=["f64", "f32"])
+@pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
+def test_dense_parity(handle, case, dtype):
+    name, m, n, k, p, q, tail = case
+    A, Om = _case(*case, seed=wl.MASTER_SEED + 11 * m + n)
+    Ag = torch.from_numpy(A).to(dtype).cuda()
+    Aseen = Ag.double().cpu().numpy()
+    ref = oracle.ruqlp(Aseen, Om, q)
+    Q, L, P, flags = handle.decompose(Ag, torch.from_numpy(Om).cuda(), k, p, q)
+    torch.cuda.synchronize()
+    Q, L, P = (t.double().cpu().numpy() for t in (Q, L, P))
+    tol = TOL[dtype]
+    l11 = abs(ref["L"][0, 0])
+    d = k + p
+    assert flags & ruqlp.FLAG_RANKDEF == 0
+    assert np.all(np.triu(L, 1) == 0.0)
+    assert np.max(np.abs(L - ref["L"])) <= tol * l11, np.max(np.abs(L - ref["L"])) / l11
+    assert np.max(np.abs(np.abs(np.diag(L)) - np.abs(np.diag(ref["L"])))) <= tol * l11
+    r = oracle.residual_fro_small(Aseen, Q, L, P)
+    r0 = oracle.residual_fro_small(Aseen, ref["Q"], ref["L"], ref["P"])
+    assert abs(r - r0) <= tol, (r, r0)
+    assert np.max(np.abs(Q[:, :k] - ref["Q"][:, :k])) <= TOLQ[dtype]
+    assert np.max(np.abs(P[:, :k] - ref["P"][:, :k])) <= TOLQ[dtype]
+    assert np.max(np.abs(Q.T @ Q - np.eye(d))) <= TOLO[dtype]
+    assert np.max(np.abs(P.T @ P - np.eye(d))) <= TOLO[dtype]
+
+
+def test_host_entry_matches_device_entry(handle):
+    m, n, k, p, q = 900, 700, 15, 7, 1
+    A, Om = _case("host", m, n, k, p, q, 1e-2, seed=4242)
+    d = k + p
+    Ah = torch.from_numpy(A).pin_memory()
+    Omh = torch.from_numpy(Om).pin_memory()
+    outs = (torch.empty(m, d, dtype=torch.float64).pin_memory(),
+            torch.empty(d, d, dtype=torch.float64).pin_memory(),
+            torch.empty(n, d, dtype=torch.float64).pin_memory())
+    Qh, Lh, Ph, _ = handle.decompose_host(Ah, Omh, k, p, q, outs)
+    Qd, Ld, Pd, _ = handle.decompose(Ah.cuda(), Omh.cuda(), k, p, q)
+    torch.cuda.synchronize()
+    assert torch.equal(Qh, Qd.cpu()) and torch.equal(Lh, Ld.cpu()) and torch.equal(Ph, Pd.cpu())
+
+
+def test_repeat_is_bitwise_deterministic(handle):
+    A, Om = _case("det", 1500, 1100, 30, 10, 2, 1e-2, seed=99)
+    Ag = torch.from_numpy(A).float().cuda()
+    Omg = torch.from_numpy(Om).cuda()
+    a = handle.decompose(Ag, Omg, 30, 10, 2)
+    b = handle.decompose(Ag, Omg, 30, 10, 2)
+    for x, y in zip(a[:3], b[:3]):
+        assert torch.equal(x, y)
+
+
+@pytest.mark.parametrize("bad", ["k0", "pneg", "qneg", "dbig", "nullomega", "d513"])
+def test_invalid_arguments_rejected(handle, bad):
+    m, n = 64, 48
+    A = torch.randn(m, n, dtype=torch.float64, device="cuda")
+    k, p, q = 4, 2, 1
+    om = torch.randn(n, k + p, dtype=torch.float64, device="cuda")
+    if bad == "k0":
+        k = 0
+    elif bad == "pneg":
+        p = -1
+    elif bad == "qneg":
+        q = -1
+    elif bad == "dbig":
+        k, p = 40, 10
+    elif bad == "d513":
+        A = torch.randn(600, 600, dtype=torch.float64, device="cuda")
+        k, p = 500, 13
+    d = max(k + p, 1)
+    Q = torch.empty(A.shape[0], d, dtype=torch.float64, device="cuda")
+    L = torch.empty(d, d, dtype=torch.float64, device="cuda")
+    P = torch.empty(A.shape[1], d, dtype=torch.float64, device="cuda")
+    M = ruqlp.Matrix(0, ruqlp.Dense(A.shape[0], A.shape[1], A.shape[1], ruqlp.F64,
+                                    A.data_ptr()), ruqlp.Csr())
+    prm = ruqlp.Params(k, p, q, ruqlp.F64, 0 if bad == "nullomega" else om.data_ptr(), 0)
+    out = ruqlp.Outputs(Q.data_ptr(), L.data_ptr(), P.data_ptr(), ruqlp.F64, 0)
+    st = ruqlp.ruqlp_decompose(handle.h, M, prm, out)
+    assert st == ruqlp.ERR_INVALID
+    assert ruqlp.ruqlp_last_error(handle.h) != ""
