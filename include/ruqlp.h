@@ -173,6 +173,19 @@ ruqlp_status ruqlp_decompose(ruqlp_handle h, const ruqlp_matrix* A,
 ruqlp_status ruqlp_decompose_host(ruqlp_handle h, const ruqlp_matrix* A,
                                   const ruqlp_params* prm, ruqlp_outputs* out);
 
+/* Gram matrix of a tall-skinny matrix, the l x l product that orth()'s
+ * CholeskyQR factors (Section II-A orth(); Algorithm 2):
+ *   G (d x d, FP64, row-major, ld d) = Y^T Y,
+ * Y: M x d row-major with leading dimension ldy >= d, dtype F64 or F32, all
+ * in device memory on the handle's device.  Products and sums are FP64 (the
+ * products of FP32 inputs are exact).  The M range is split into slabs whose
+ * FP64 partial Grams go to the handle's workspace arena and are summed in a
+ * fixed order, so repeated calls give bitwise-equal results.  Ordered on the
+ * handle's stream; returns after completion.  Errors: INVALID (NULL
+ * pointers, M < 1, d outside 1..512, ldy < d, other dtype), BUDGET, CUDA. */
+ruqlp_status ruqlp_gram(ruqlp_handle h, const void* Y, int64_t M, int d, int64_t ldy,
+                        ruqlp_dtype dtype, double* G);
+
 /* Message of the last error on this handle (never NULL; "" if none). */
 const char* ruqlp_last_error(ruqlp_handle h);
 

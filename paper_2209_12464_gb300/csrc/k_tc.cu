@@ -21,6 +21,7 @@
 // Every mbarrier wait is bounded (~2 s of %globaltimer); on timeout the CTA
 // sets an error word, stops issuing work, and frees its TMEM before exiting.
 #include <cuda.h>
+#include <cudaTypedefs.h>
 
 #include "internal.h"
 

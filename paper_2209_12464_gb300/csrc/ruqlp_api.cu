@@ -509,6 +509,26 @@ const char* ruqlp_last_error(ruqlp_handle h) { return h ? h->err.c_str() : "NULL
 
 int64_t ruqlp_launch_count(void) { return launch_count(); }
 
+ruqlp_status ruqlp_gram(ruqlp_handle h, const void* Y, int64_t M, int d, int64_t ldy,
+                        ruqlp_dtype dtype, double* G) {
+  if (!h) return RUQLP_ERR_INVALID;
+  h->err.clear();
+  if (!Y || !G) return fail(h, RUQLP_ERR_INVALID, "NULL pointer");
+  if (M < 1 || d < 1 || d > 512 || ldy < d)
+    return fail(h, RUQLP_ERR_INVALID, "need M >= 1, 1 <= d <= 512, ldy >= d");
+  if (dtype != RUQLP_F64 && dtype != RUQLP_F32)
+    return fail(h, RUQLP_ERR_INVALID, "dtype must be F64 or F32");
+  const Ty ty = dtype == RUQLP_F64 ? Ty::F64 : Ty::F32;
+  const size_t bytes = (size_t)kMaxSplits * d * d * sizeof(double);
+  ruqlp_status s = ensure_arena(h, bytes);
+  if (s != RUQLP_OK) return s;
+  CK(cudaSetDevice(h->device));
+  CK(simt_gemm_tn(ty, ty, Ty::F64, Mul::F64, Y, ldy, Y, ldy, G, d, d, M, d,
+                  tn_splits(d, M, d, kMaxSplits), (double*)h->arena, nullptr, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  return RUQLP_OK;
+}
+
 ruqlp_status ruqlp_profile(ruqlp_handle h, const char* phase, int64_t* count, double* total_ms) {
   if (!h || !phase || !count || !total_ms) return RUQLP_ERR_INVALID;
   for (int i = 0; i < 4; ++i) {

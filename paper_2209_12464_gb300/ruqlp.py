@@ -70,6 +70,7 @@ _SIGS = {
                                      ctypes.POINTER(Outputs)]),
     "ruqlp_last_error": (c_char_p, [c_void_p]),
     "ruqlp_launch_count": (c_int64, []),
+    "ruqlp_gram": (c_int, [c_void_p, c_void_p, c_int64, c_int, c_int64, c_int, c_void_p]),
     "ruqlp_profile": (c_int, [c_void_p, c_char_p, ctypes.POINTER(c_int64),
                               ctypes.POINTER(ctypes.c_double)]),
     "ruqlp_version": (c_char_p, []),
@@ -140,6 +141,10 @@ def ruqlp_version():
     return lib().ruqlp_version().decode()
 
 
+def ruqlp_gram(h, Y, M, d, ldy, dtype, G):
+    return lib().ruqlp_gram(h, Y, M, d, ldy, dtype, G)
+
+
 def ruqlp_launch_count():
     return lib().ruqlp_launch_count()
 
@@ -187,6 +192,15 @@ class Handle:
         st, c, ms = ruqlp_profile(self.h, phase)
         self.check(st)
         return c, ms
+
+    def gram(self, Y):
+        """G = Y^T Y (FP64) of a CUDA tensor Y (M x d, FP64 or FP32, row-major)."""
+        import torch
+        M, d = Y.shape
+        G = torch.empty(d, d, dtype=torch.float64, device=Y.device)
+        self.check(ruqlp_gram(self.h, Y.data_ptr(), M, d, Y.stride(0), _dtype_code(Y.dtype),
+                              G.data_ptr()))
+        return G
 
     def close(self):
         if self.h:

@@ -134,3 +134,17 @@ def test_invalid_arguments_rejected(handle, bad):
     st = ruqlp.ruqlp_decompose(handle.h, M, prm, out)
     assert st == ruqlp.ERR_INVALID
     assert ruqlp.ruqlp_last_error(handle.h) != ""
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32], ids=["f64", "f32"])
+@pytest.mark.parametrize("shape", [(1000, 30), (20011, 220), (77, 77), (5, 1), (3000, 300)])
+def test_gram_entry_matches_fp64_products(handle, shape, dtype):
+    """ruqlp_gram: G = Y^T Y with exact FP64 products; compared with numpy's
+    FP64 product of the same (rounded) values, relative to ||Y||_F^2."""
+    M, d = shape
+    Y = torch.from_numpy(np.random.default_rng(M + d).standard_normal((M, d))).to(dtype).cuda()
+    G = handle.gram(Y).cpu().numpy()
+    Yh = Y.double().cpu().numpy()
+    ref = Yh.T @ Yh
+    assert np.max(np.abs(G - ref)) <= 1e-13 * np.sum(Yh * Yh)
+    assert np.array_equal(G, G.T)
