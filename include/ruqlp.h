@@ -186,6 +186,28 @@ ruqlp_status ruqlp_decompose_host(ruqlp_handle h, const ruqlp_matrix* A,
 ruqlp_status ruqlp_gram(ruqlp_handle h, const void* Y, int64_t M, int d, int64_t ldy,
                         ruqlp_dtype dtype, double* G);
 
+/* ruqlp_gram for callers that cannot allocate device memory -- for example
+ * code recording a CUDA graph (allocation is refused inside stream capture),
+ * host programs whose own allocator owns all device memory, or loops that
+ * cannot afford cudaMalloc's implicit synchronisation.  The paper has no
+ * counterpart; it is a deployment variant of the Gram above.
+ *   G (d x d, FP64, ld d) = Y^T Y, Y: M x d, ld ldy >= d, F64 or F32.
+ * Y and G are device memory on the calling thread's current device; the work
+ * is ordered on cuda_stream (cudaStream_t, NULL = legacy default stream) and
+ * the call returns after enqueueing it (no synchronisation).  The library
+ * allocates nothing: the FP64 partial sums live in one fixed 4 MiB device
+ * array that every GPU loading the library keeps until the process exits, so
+ * d is limited to 256 (larger d returns RUQLP_ERR_BUDGET).  The first call
+ * on each device looks up that array's device address (cudaGetSymbolAddress);
+ * make that first call before any stream capture.  All calls share the one
+ * array: calls whose work overlaps on the GPU (other streams, other host
+ * threads) race and give wrong results -- order them on one stream.  Each
+ * call overwrites what it uses, so no clearing is needed between calls.
+ * Errors: INVALID (NULL pointers, M < 1, d < 1, ldy < d, other dtype),
+ * BUDGET (d > 256), CUDA. */
+ruqlp_status ruqlp_gram_noalloc(const void* Y, int64_t M, int d, int64_t ldy,
+                                ruqlp_dtype dtype, double* G, void* cuda_stream);
+
 /* Message of the last error on this handle (never NULL; "" if none). */
 const char* ruqlp_last_error(ruqlp_handle h);
 

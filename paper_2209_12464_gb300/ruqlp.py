@@ -71,6 +71,8 @@ _SIGS = {
     "ruqlp_last_error": (c_char_p, [c_void_p]),
     "ruqlp_launch_count": (c_int64, []),
     "ruqlp_gram": (c_int, [c_void_p, c_void_p, c_int64, c_int, c_int64, c_int, c_void_p]),
+    "ruqlp_gram_noalloc": (c_int, [c_void_p, c_int64, c_int, c_int64, c_int, c_void_p,
+                                   c_void_p]),
     "ruqlp_profile": (c_int, [c_void_p, c_char_p, ctypes.POINTER(c_int64),
                               ctypes.POINTER(ctypes.c_double)]),
     "ruqlp_version": (c_char_p, []),
@@ -143,6 +145,10 @@ def ruqlp_version():
 
 def ruqlp_gram(h, Y, M, d, ldy, dtype, G):
     return lib().ruqlp_gram(h, Y, M, d, ldy, dtype, G)
+
+
+def ruqlp_gram_noalloc(Y, M, d, ldy, dtype, G, stream):
+    return lib().ruqlp_gram_noalloc(Y, M, d, ldy, dtype, G, stream)
 
 
 def ruqlp_launch_count():
