@@ -46,6 +46,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--size", type=int, default=0, help="override m = n (testing only)")
+    ap.add_argument("--gen", default="haar", choices=["haar", "fast"],
+                    help="haar: the workload's Haar U, V (torch.linalg.qr); fast: Gaussian "
+                         "low-rank stand-in for profiling tools that cannot load torch.linalg")
     return ap.parse_args()
 
 
@@ -102,14 +105,19 @@ class Clocks:
 
 
 # ---------------------------------------------------------------------------
-def make_inputs(torch, device, dtype, m, n):
+def make_inputs(torch, device, dtype, m, n, gen="haar"):
+    """A in the streamed dtype, the FP32 original it was rounded from (for the
+    residual), Omega (FP64) and the spectrum."""
     from paper_2209_12464_gb300 import workloads as wl
     sig = wl.spectrum_gap(min(m, n), K_RANK, TAIL)
-    A = wl.dense_spectral_torch(SEED, m, n, sig, noise_std=NOISE, device=device,
-                                dtype={"bf16": torch.bfloat16, "f32": torch.float32,
-                                       "f64": torch.float64}[dtype])
+    if gen == "haar":
+        A32 = wl.dense_spectral_torch(SEED, m, n, sig, noise_std=NOISE, device=device,
+                                      dtype=torch.float32)
+    else:
+        A32 = wl.dense_lowrank_gauss_torch(SEED, m, n, K_RANK, noise_std=NOISE, device=device)
+    A = A32.to({"bf16": torch.bfloat16, "f32": torch.float32, "f64": torch.float64}[dtype])
     Om = wl.omega_torch(SEED + 1, n, K_RANK + P_OVER, device=device)
-    return A, Om, sig
+    return A, A32, Om, sig
 
 
 def residual_gpu(torch, A, Q, L, P):
@@ -205,7 +213,7 @@ def main():
     m = n = args.size or M
     k, p, q = K_RANK, P_OVER, Q_POW
     d = k + p
-    A, Om, sig = make_inputs(torch, dev, args.dtype, m, n)
+    A, A32, Om, sig = make_inputs(torch, dev, args.dtype, m, n, args.gen)
     torch.cuda.synchronize()
     stream = torch.cuda.current_stream(dev)
     h = ruqlp.Handle(local, stream.cuda_stream)
@@ -247,9 +255,11 @@ def main():
     passes = 2 * q + 2
     value = world * passes * bytes_a / (ms * 1e-3) / 1e9
 
-    # accuracy at this speed (FP64 measurement on the device)
+    # accuracy at this speed (FP64 measurement on the device, against the
+    # unrounded A)
     Qo, Lo, Po = outs
-    resid = residual_gpu(torch, A, Qo, Lo, Po)
+    resid = residual_gpu(torch, A32, Qo, Lo, Po)
+    del A32
     # approximate Eckart-Young floor: spectrum tail plus the noise energy
     # outside a rank-d subspace ((m-d)(n-d) of its m n entries)
     floor = math.sqrt(float((sig[d:] ** 2).sum()) + (NOISE ** 2) * (m - d) * (n - d)) / math.sqrt(
@@ -323,7 +333,9 @@ def main():
                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                "dtype": args.dtype, "data": "synthetic",
-               "config": {"workload": WORKLOAD, "m": m, "n": n, "k": k, "p": p, "q": q,
+               "config": {"workload": WORKLOAD if args.gen == "haar" else
+                          "Gaussian low-rank stand-in of the same shape (profiling)",
+                          "m": m, "n": n, "k": k, "p": p, "q": q,
                           "passes": passes, "bytes_A": bytes_a,
                           "l2": "inputs larger than L2 (A is %.0f MB vs 129 MB L2)" % (bytes_a / 1e6),
                           "parallelism": f"replicas x{world}"},

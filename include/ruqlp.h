@@ -99,8 +99,12 @@ typedef struct {
  * q >= 0 power steps (Algorithm 2; q = 0 is Algorithm 1 alone).
  * compute: precision A is streamed in.  F64: everything in FP64.  F32: A,
  * sketches and Q/P in FP32.  BF16: A in BF16 through the tensor cores with
- * FP32 accumulation; sketches and Q/P kept in FP32.  In every mode the d x d
- * Gram, Cholesky and R factors are FP64.  compute must equal A's dtype.
+ * FP32 accumulation; sketches and Q/P kept in FP32.  d x d Grams and R_B are
+ * accumulated in FP64 in every mode; the Cholesky factorisations are FP64 on
+ * the FP64 path and FP32 (shifted CholeskyQR3) on the FP32/BF16 paths unless
+ * the "orth_fp64" option is set.  compute must equal A's dtype.
+ * BF16 inputs use the tensor cores when A's leading dimension is a multiple
+ * of 8 elements, A is 16-byte aligned and d <= 256; otherwise CUDA cores.
  * omega: n x d row-major FP64 Gaussian test matrix (device memory for
  * ruqlp_decompose / ruqlp_submit; host memory for ruqlp_decompose_host).
  * finish_paper: 1 = also take the d x d QR of L, [P~, R~] = qr(L)
@@ -137,10 +141,12 @@ ruqlp_status ruqlp_destroy(ruqlp_handle h);
 ruqlp_status ruqlp_set_stream(ruqlp_handle h, void* cuda_stream);
 
 /* Set a tuning option of the handle.  Known names:
- *   "gram1_exact": 1 (default) = the first CholeskyQR pass of each orth()
- *   forms its Gram with FP64 products (exact for FP32 data); 0 = FP32
- *   products summed in FP64 (faster; relies on the shifted fallback for
- *   ill-conditioned sketches).  Ignored on the FP64 path.
+ *   "orth_fp64": 1 = on the FP32/BF16 paths, orth() runs CholeskyQR2 with
+ *   FP64 products in the Gram and an FP64 Cholesky (slow on GB300's FP64
+ *   units); 0 (default) = shifted CholeskyQR3 in FP32 with FP64 sums across
+ *   row slabs.  The FP64 path always uses the FP64 form.
+ *   "bf16_simt": 1 = run BF16 products on the CUDA cores instead of the
+ *   tensor cores (comparison baseline); 0 (default) = tensor cores.
  *   "profile": 1 = bracket every phase with CUDA events on the handle's
  *   stream and accumulate their durations (read with ruqlp_profile); setting
  *   it (to 0 or 1) also zeroes the accumulators.
@@ -172,6 +178,29 @@ ruqlp_status ruqlp_decompose(ruqlp_handle h, const ruqlp_matrix* A,
  * path and copies Q, L, P back.  Errors as ruqlp_decompose. */
 ruqlp_status ruqlp_decompose_host(ruqlp_handle h, const ruqlp_matrix* A,
                                   const ruqlp_params* prm, ruqlp_outputs* out);
+
+/* One pass over A, the O(mnd) product step of RU-QLP (Algorithm 1 step 3,
+ * the products of Algorithm 2, B^T = A^T Q; Section III-D):
+ *   trans = 0:  Y (m x d) = A X,    X: n x d;
+ *   trans = 1:  Y (n x d) = A^T X,  X: m x d.
+ * A is dense (device memory, any dtype); X and Y are row-major device
+ * buffers (leading dimensions ldx, ldy >= d) in FP64 when A is FP64, else
+ * FP32.  The kernel is the one ruqlp_decompose uses for A's dtype (BF16:
+ * X rounded to BF16, tensor cores, FP32 accumulation).  Returns after
+ * completion.  Errors: INVALID, BUDGET, CUDA, TIMEOUT. */
+ruqlp_status ruqlp_sketch(ruqlp_handle h, const ruqlp_matrix* A, int trans, const void* X,
+                          int64_t ldx, int d, void* Y, int64_t ldy);
+
+/* orth() of Section II-A as used by the path: Q (M x d) with orthonormal
+ * columns spanning range(Y), Y = Q R with R upper triangular and positive
+ * diagonal (the unique thin-QR Q when Y has full column rank).  Y and Q:
+ * device memory, row-major, ld >= d, dtype F64 (CholeskyQR2 in FP64) or F32
+ * (shifted CholeskyQR3 in FP32, or CholeskyQR2 with FP64 Gram and Cholesky
+ * under the "orth_fp64" option).  Q may alias Y.  Returns after completion.
+ * Errors: INVALID (NULL, d outside 1..512, M < d, ld < d, dtype), BUDGET,
+ * CUDA. */
+ruqlp_status ruqlp_orth(ruqlp_handle h, const void* Y, int64_t M, int d, int64_t ldy,
+                        ruqlp_dtype dtype, void* Q, int64_t ldq);
 
 /* Gram matrix of a tall-skinny matrix, the l x l product that orth()'s
  * CholeskyQR factors (Section II-A orth(); Algorithm 2):

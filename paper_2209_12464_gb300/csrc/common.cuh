@@ -17,7 +17,7 @@ struct DevStatus {
   int32_t flags;      // RUQLP_FLAG_* bits
   int32_t breakdown;  // non-zero: an orth() failed after its fallbacks
   int32_t shifted;    // set by the Cholesky of the current orth when it shifted
-  int32_t pad;
+  int32_t timeout;    // a bounded device wait ran out
 };
 
 template <typename T> __device__ __forceinline__ float to_f32(T v);

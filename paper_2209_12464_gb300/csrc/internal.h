@@ -35,9 +35,29 @@ int tn_splits(int64_t M, int64_t K, int64_t N, int max_splits);
 // (and RUQLP_FLAG_SHIFTED); a second breakdown sets RUQLP_FLAG_RANKDEF and
 // replaces the failed pivots by shift-sized ones so the output stays finite.
 // Writes R (upper, FP64, ld d, zero lower part) and Rw = R in type tw.
-// A non-null `gate` makes it a no-op unless *gate != 0.
+// A non-null `gate` makes it a no-op unless *gate != 0.  tf: arithmetic of
+// the factorisation (F64 or F32); force_shift: factor G + shift I directly.
 cudaError_t chol_upper(const double* G, int d, double shift_rel, double* R, void* Rw,
-                       Ty tw, DevStatus* status, const int32_t* gate, cudaStream_t st);
+                       Ty tw, DevStatus* status, const int32_t* gate, cudaStream_t st,
+                       Ty tf = Ty::F64, bool force_shift = false);
+
+// FP32 Cholesky + triangular inverse of a d x d FP64 Gram in one CTA
+// (d <= 288): Rinv (FP32, ld d, zero lower part) = R^{-1}, G + shift I = R^T R
+// with shift = shift_rel * trace(G) when force_shift (or after a breakdown).
+bool chol_inv_f32_supported(int d);
+cudaError_t chol_inv_f32(const double* G, int d, double shift_rel, bool force_shift, float* Rinv,
+                         DevStatus* status, const int32_t* gate, cudaStream_t st);
+// X (M x d, ld ldx) = Y (ld ldy) U for upper-triangular U (d x d, ld d); X may alias Y.
+cudaError_t mul_upper_f32(const float* Y, int64_t ldy, const float* U, float* X, int64_t ldx,
+                          int64_t M, int d, cudaStream_t st);
+
+// C (d1 x d2, FP64, ld d2) = X^T W for FP32 X (M x d1, ld ldx) and W (M x d2,
+// ld ldw): FP32 products summed in FP32 within a row slab, slabs summed in
+// FP64 in order.  X == W computes only the upper tiles and mirrors them.
+// partial: max_slabs * d1 * d2 doubles of scratch.
+cudaError_t gram_f32(const float* X, int64_t ldx, const float* W, int64_t ldw, int64_t M, int d1,
+                     int d2, double* C, double* partial, int max_slabs, const int32_t* gate,
+                     cudaStream_t st);
 
 // X[M x d] <- Y[M x d] R^{-1} for upper-triangular R (type ty, ld d): each
 // row solves x R = y by forward substitution.  X may alias Y.  A non-null
@@ -54,6 +74,22 @@ cudaError_t copy_cast_2d(Ty ts, const void* src, int64_t lds, Ty td, void* dst, 
 // ld d), zeros above the diagonal.  With `upper` the upper triangle is
 // copied as is instead (finish_paper output).
 cudaError_t write_L(const double* R, int d, Ty tl, void* L, bool upper, cudaStream_t st);
+
+// Tensor-core BF16 products (k_tc.cu).  trans = false: out[m x dp] = A Bt^T;
+// trans = true: out[n x dp] = A^T Bt^T, with A (m x n, BF16, ld lda) and
+// Bt (dp x K, BF16, ld ldb, K = n or m).  frag: tc_frag_bytes(dp) of scratch
+// for the stream-K fragments; err: device word set on a wait timeout.
+cudaError_t tc_gemm(bool trans, const void* A, int64_t lda, int64_t m, int64_t n, const void* Bt,
+                    int64_t ldb, int dp, float* out, int64_t ldo, float* frag, int* err,
+                    cudaStream_t st);
+size_t tc_frag_bytes(int dp);
+// Whether tc_gemm accepts these operands (alignment / size rules).
+bool tc_supported(const void* A, int64_t lda, int dp);
+
+// dst[dp x rows] (BF16, ld ldd) = transpose of src[rows x cols] (ld lds), rows
+// cols..dp-1 of dst zero.
+cudaError_t transpose_to_bf16(Ty ts, const void* src, int64_t lds, int64_t rows, int cols, int dp,
+                              void* dst, int64_t ldd, cudaStream_t st);
 
 // Zero the status word.
 cudaError_t status_reset(DevStatus* s, cudaStream_t st);

@@ -1,0 +1,166 @@
+// Tall-skinny cross products C = X^T W (d1 x d2) for orth() (Section II-A;
+// the l x l Gram of CholeskyQR and the R factor of qr(B^T)), FP32 inputs.
+//
+// One CTA of 64 threads owns a 64 x 64 tile of C; every thread accumulates an
+// 8 x 8 sub-tile in FP32 over the CTA's slab of rows (32-row chunks staged in
+// shared memory, next chunk prefetched into registers).  The FP32 slab sums
+// are written as FP64 partials and summed across slabs in slab order (FP64,
+// deterministic).  For X == W only the tiles on or above the diagonal are
+// computed and the reduction mirrors them.
+#include "internal.h"
+
+namespace ruqlp {
+namespace {
+
+constexpr int TM = 64, TK = 32, NT = 64;
+
+__global__ void __launch_bounds__(NT)
+k_gram_tiles(const float* __restrict__ X, int64_t ldx, const float* __restrict__ W, int64_t ldw,
+             int64_t M, int d1, int d2, bool sym, int64_t slab, double* __restrict__ partial,
+             const int32_t* __restrict__ gate) {
+  if (gate != nullptr && *gate == 0) return;
+  __shared__ __align__(16) float Xs[TK][TM];
+  __shared__ __align__(16) float Ws[TK][TM];
+  // tile coordinates: blockIdx.x enumerates (bi, bj) pairs
+  const int nb1 = (d1 + TM - 1) / TM, nb2 = (d2 + TM - 1) / TM;
+  int bi, bj;
+  if (sym) {  // upper triangle of an nb1 x nb1 tile grid, row by row
+    int t = blockIdx.x;
+    bi = 0;
+    while (t >= nb1 - bi) { t -= nb1 - bi; ++bi; }
+    bj = bi + t;
+  } else {
+    bi = blockIdx.x / nb2;
+    bj = blockIdx.x % nb2;
+  }
+  const int c0 = bi * TM, c1 = bj * TM;
+  const bool diag = sym && bi == bj;
+  const int64_t r_begin = (int64_t)blockIdx.y * slab;
+  const int64_t r_end = min(M, r_begin + slab);
+  const int t = threadIdx.x;
+  const int ty = t >> 3, tx = t & 7;
+
+  float acc[8][8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+#pragma unroll
+    for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
+
+  // a chunk is 32 rows x 64 columns = 2048 floats: 8 float4s per thread
+  auto load = [&](const float* S, int64_t lds, int c0_, int dmax, int64_t r0, float4 (&v)[8]) {
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int e = (q * NT + t) * 4;  // element index in the 32 x 64 chunk
+      const int rr = e / TM, cc = e % TM;
+      const int64_t r = r0 + rr;
+      const int c = c0_ + cc;
+      float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (r < r_end) {
+        const float* p = S + r * lds + c;
+        if (c + 3 < dmax) {
+          x = *reinterpret_cast<const float4*>(p);
+        } else {
+          if (c < dmax) x.x = p[0];
+          if (c + 1 < dmax) x.y = p[1];
+          if (c + 2 < dmax) x.z = p[2];
+        }
+      }
+      v[q] = x;
+    }
+  };
+  auto store = [&](float (*Ss)[TM], const float4 (&v)[8]) {
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int e = (q * NT + t) * 4;
+      *reinterpret_cast<float4*>(&Ss[e / TM][e % TM]) = v[q];
+    }
+  };
+
+  float4 vx[8], vw[8];
+  int64_t r0 = r_begin;
+  if (r0 < r_end) {
+    load(X, ldx, c0, d1, r0, vx);
+    if (!diag) load(W, ldw, c1, d2, r0, vw);
+  }
+  for (; r0 < r_end; r0 += TK) {
+    store(Xs, vx);
+    if (!diag) store(Ws, vw);
+    __syncthreads();
+    if (r0 + TK < r_end) {  // prefetch the next chunk while computing this one
+      load(X, ldx, c0, d1, r0 + TK, vx);
+      if (!diag) load(W, ldw, c1, d2, r0 + TK, vw);
+    }
+    const float(*Bs)[TM] = diag ? Xs : Ws;
+#pragma unroll 4
+    for (int k = 0; k < TK; ++k) {
+      const float4 a0 = *reinterpret_cast<const float4*>(&Xs[k][ty * 8]);
+      const float4 a1 = *reinterpret_cast<const float4*>(&Xs[k][ty * 8 + 4]);
+      const float4 b0 = *reinterpret_cast<const float4*>(&Bs[k][tx * 8]);
+      const float4 b1 = *reinterpret_cast<const float4*>(&Bs[k][tx * 8 + 4]);
+      const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+      const float b[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+  double* P = partial + (int64_t)blockIdx.y * d1 * d2;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const int r = c0 + ty * 8 + i;
+    if (r >= d1) continue;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int c = c1 + tx * 8 + j;
+      if (c < d2) P[(int64_t)r * d2 + c] = (double)acc[i][j];
+    }
+  }
+}
+
+// C[i][j] = sum over slabs of the partials (slab order); with sym the entry
+// is taken from the computed upper triangle.
+__global__ void k_gram_reduce(const double* __restrict__ P, int slabs, int d1, int d2, bool sym,
+                              double* __restrict__ C, const int32_t* __restrict__ gate) {
+  if (gate != nullptr && *gate == 0) return;
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (int64_t)d1 * d2) return;
+  int i = (int)(idx / d2), j = (int)(idx % d2);
+  const int64_t src = (sym && j < i) ? ((int64_t)j * d2 + i) : idx;
+  double s = 0.0;
+  for (int z = 0; z < slabs; ++z) s += P[(int64_t)z * d1 * d2 + src];
+  C[idx] = s;
+}
+
+}  // namespace
+
+cudaError_t gram_f32(const float* X, int64_t ldx, const float* W, int64_t ldw, int64_t M, int d1,
+                     int d2, double* C, double* partial, int max_slabs, const int32_t* gate,
+                     cudaStream_t st) {
+  if (M <= 0 || d1 <= 0 || d2 <= 0) return cudaSuccess;
+  const bool sym = (X == W) && (ldx == ldw) && (d1 == d2);
+  const int nb1 = (d1 + TM - 1) / TM, nb2 = (d2 + TM - 1) / TM;
+  const int tiles = sym ? nb1 * (nb1 + 1) / 2 : nb1 * nb2;
+  // slabs: about 4 CTAs per SM, at least 128 rows each
+  int64_t slabs = (4 * 152 + tiles - 1) / tiles;
+  const int64_t by_rows = (M + 127) / 128;
+  if (slabs > by_rows) slabs = by_rows;
+  if (slabs > max_slabs) slabs = max_slabs;
+  if (slabs < 1) slabs = 1;
+  int64_t slab = (M + slabs - 1) / slabs;
+  slab = (slab + TK - 1) / TK * TK;
+  slabs = (M + slab - 1) / slab;
+  if ((((uintptr_t)X | (uintptr_t)W) & 15) || (ldx & 3) || (ldw & 3)) return cudaErrorInvalidValue;
+  k_gram_tiles<<<dim3(tiles, (unsigned)slabs), NT, 0, st>>>(X, ldx, W, ldw, M, d1, d2, sym, slab,
+                                                            partial, gate);
+  count_launch();
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const int64_t tot = (int64_t)d1 * d2;
+  k_gram_reduce<<<ceil_div(tot, 256), 256, 0, st>>>(partial, (int)slabs, d1, d2, sym, C, gate);
+  count_launch();
+  return cudaGetLastError();
+}
+
+}  // namespace ruqlp

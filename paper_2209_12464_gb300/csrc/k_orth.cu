@@ -25,19 +25,21 @@ template <typename TW> __device__ __forceinline__ TW from_f64(double v);
 template <> __device__ __forceinline__ double from_f64<double>(double v) { return v; }
 template <> __device__ __forceinline__ float from_f64<float>(double v) { return (float)v; }
 
-// Right-looking Cholesky G = R^T R (upper R), one CTA.  Attempt 0 factors G;
-// if a pivot is not positive it restarts on G + shift I (attempt 1), where a
-// pivot that is still not positive is replaced by `shift` (rank deficiency).
-template <bool PACKED, typename TW>
+// Right-looking Cholesky G = R^T R (upper R), one CTA, arithmetic in TF.
+// Attempt 0 factors G (skipped with force_shift); if a pivot is not positive
+// it restarts on G + shift I (attempt 1), where a pivot that is still not
+// positive is replaced by `shift` (rank deficiency, flagged).
+template <bool PACKED, typename TF, typename TW>
 __global__ void __launch_bounds__(CHOL_THREADS)
-k_chol(const double* __restrict__ G, int d, double shift_rel, double* __restrict__ R,
-       TW* __restrict__ Rw, DevStatus* __restrict__ status, const int32_t* __restrict__ gate) {
+k_chol(const double* __restrict__ G, int d, double shift_rel, int force_shift,
+       double* __restrict__ R, TW* __restrict__ Rw, DevStatus* __restrict__ status,
+       const int32_t* __restrict__ gate) {
   if (gate != nullptr && *gate == 0) return;
-  extern __shared__ double smem[];
+  extern __shared__ double smem_d[];
   __shared__ int s_bad;
   __shared__ int s_rankdef;
   __shared__ double s_shift;
-  double* W = PACKED ? smem : R;
+  TF* W = PACKED ? reinterpret_cast<TF*>(smem_d) : reinterpret_cast<TF*>(R);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int nwarps = blockDim.x >> 5;
 
@@ -49,23 +51,23 @@ k_chol(const double* __restrict__ G, int d, double shift_rel, double* __restrict
     s_shift = sh;
     s_rankdef = 0;
   }
-  int attempt = 0;
+  int attempt = force_shift ? 1 : 0;
   for (; attempt < 2; ++attempt) {
     __syncthreads();
     const double add = attempt ? s_shift : 0.0;
     for (int i = warp; i < d; i += nwarps)
       for (int j = i + lane; j < d; j += 32)
-        W[uidx<PACKED>(i, j, d)] = G[(int64_t)i * d + j] + (i == j ? add : 0.0);
+        W[uidx<PACKED>(i, j, d)] = (TF)(G[(int64_t)i * d + j] + (i == j ? add : 0.0));
     if (tid == 0) s_bad = 0;
     __syncthreads();
     for (int k = 0; k < d; ++k) {
       if (tid == 0) {
-        double piv = W[uidx<PACKED>(k, k, d)];
-        if (!(piv > 0.0) || !isfinite(piv)) {
+        TF piv = W[uidx<PACKED>(k, k, d)];
+        if (!(piv > TF(0)) || !isfinite((double)piv)) {
           if (attempt == 0) {
             s_bad = 1;
           } else {
-            piv = s_shift;
+            piv = (TF)s_shift;
             s_rankdef = 1;
           }
         }
@@ -73,11 +75,11 @@ k_chol(const double* __restrict__ G, int d, double shift_rel, double* __restrict
       }
       __syncthreads();
       if (s_bad) break;
-      const double rkk = W[uidx<PACKED>(k, k, d)];
+      const TF rkk = W[uidx<PACKED>(k, k, d)];
       for (int j = k + 1 + tid; j < d; j += blockDim.x) W[uidx<PACKED>(k, j, d)] /= rkk;
       __syncthreads();
       for (int i = k + 1 + warp; i < d; i += nwarps) {
-        const double rki = W[uidx<PACKED>(k, i, d)];
+        const TF rki = W[uidx<PACKED>(k, i, d)];
         for (int j = i + lane; j < d; j += 32)
           W[uidx<PACKED>(i, j, d)] -= rki * W[uidx<PACKED>(k, j, d)];
       }
@@ -86,18 +88,33 @@ k_chol(const double* __restrict__ G, int d, double shift_rel, double* __restrict
     if (!s_bad) break;
   }
   __syncthreads();
-  // R (full, zero lower part) and its working-type copy
-  for (int i = warp; i < d; i += nwarps) {
-    for (int j = lane; j < d; j += 32) {
-      const double v = (j >= i) ? W[uidx<PACKED>(i, j, d)] : 0.0;
-      if (PACKED || j < i) R[(int64_t)i * d + j] = v;
-      Rw[(int64_t)i * d + j] = from_f64<TW>(v);
+  // R (full FP64, zero lower part) and its working-type copy; in global mode
+  // with TF = double the upper part of R already holds the factor
+  if (!PACKED && sizeof(TF) != sizeof(double)) {
+    // float factor stored in R's memory: widen in place from the end
+    if (tid == 0) {
+      for (int64_t e = (int64_t)d * d - 1; e >= 0; --e) {
+        const int i = (int)(e / d), j = (int)(e % d);
+        const double v = (j >= i) ? (double)W[e] : 0.0;
+        R[e] = v;
+      }
+    }
+    __syncthreads();
+    for (int i = warp; i < d; i += nwarps)
+      for (int j = lane; j < d; j += 32) Rw[(int64_t)i * d + j] = (TW)R[(int64_t)i * d + j];
+  } else {
+    for (int i = warp; i < d; i += nwarps) {
+      for (int j = lane; j < d; j += 32) {
+        const double v = (j >= i) ? (double)W[uidx<PACKED>(i, j, d)] : 0.0;
+        if (PACKED || j < i) R[(int64_t)i * d + j] = v;
+        Rw[(int64_t)i * d + j] = (TW)v;
+      }
     }
   }
   if (tid == 0) {
     if (attempt > 0) {
       status->shifted = 1;
-      status->flags |= RUQLP_FLAG_SHIFTED;
+      if (!force_shift) status->flags |= RUQLP_FLAG_SHIFTED;
     }
     if (s_rankdef) status->flags |= RUQLP_FLAG_RANKDEF;
   }
@@ -159,32 +176,40 @@ __global__ void k_write_L(const double* __restrict__ R, int d, TL* __restrict__ 
 }
 
 __global__ void k_status(DevStatus* s, int full) {
-  if (full) { s->flags = 0; s->breakdown = 0; }
+  if (full) { s->flags = 0; s->breakdown = 0; s->timeout = 0; }
   s->shifted = 0;
 }
 
 }  // namespace
 
 cudaError_t chol_upper(const double* G, int d, double shift_rel, double* R, void* Rw, Ty tw,
-                       DevStatus* status, const int32_t* gate, cudaStream_t st) {
-  const size_t packed = (size_t)d * (d + 1) / 2 * sizeof(double);
+                       DevStatus* status, const int32_t* gate, cudaStream_t st, Ty tf,
+                       bool force_shift) {
+  const size_t esz = (tf == Ty::F64) ? sizeof(double) : sizeof(float);
+  const size_t packed = (size_t)d * (d + 1) / 2 * esz;
   const bool use_smem = packed <= CHOL_SMEM_MAX;
   const size_t sm = use_smem ? packed : 0;
+  const int fs = force_shift ? 1 : 0;
   cudaError_t e = cudaSuccess;
-#define RUQLP_CHOL(PK, TW)                                                                  \
+#define RUQLP_CHOL(PK, TF, TW)                                                              \
   {                                                                                         \
-    if (PK) e = cudaFuncSetAttribute(k_chol<PK, TW>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+    if (PK) e = cudaFuncSetAttribute(k_chol<PK, TF, TW>,                                    \
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize,           \
                                      (int)CHOL_SMEM_MAX);                                   \
     if (e != cudaSuccess) return e;                                                         \
-    k_chol<PK, TW><<<1, CHOL_THREADS, sm, st>>>(G, d, shift_rel, R, (TW*)Rw, status, gate); \
+    k_chol<PK, TF, TW><<<1, CHOL_THREADS, sm, st>>>(G, d, shift_rel, fs, R, (TW*)Rw, status, \
+                                                    gate);                                  \
     count_launch();                                                                         \
     return cudaGetLastError();                                                              \
   }
-  if (tw == Ty::F64) {
-    if (use_smem) RUQLP_CHOL(true, double) else RUQLP_CHOL(false, double)
+  if (tf == Ty::F64 && tw == Ty::F64) {
+    if (use_smem) RUQLP_CHOL(true, double, double) else RUQLP_CHOL(false, double, double)
   }
-  if (tw == Ty::F32) {
-    if (use_smem) RUQLP_CHOL(true, float) else RUQLP_CHOL(false, float)
+  if (tf == Ty::F64 && tw == Ty::F32) {
+    if (use_smem) RUQLP_CHOL(true, double, float) else RUQLP_CHOL(false, double, float)
+  }
+  if (tf == Ty::F32 && tw == Ty::F32) {
+    if (use_smem) RUQLP_CHOL(true, float, float) else RUQLP_CHOL(false, float, float)
   }
 #undef RUQLP_CHOL
   return cudaErrorInvalidValue;

@@ -176,6 +176,7 @@ cudaError_t simt_gemm_nn(Ty ta, Ty tb, Ty tc, Mul mul, const void* A, int64_t ld
   RUQLP_DISPATCH(false, Ty::F64, Ty::F64, Ty::F64, Mul::F64, double, double, double)
   RUQLP_DISPATCH(false, Ty::F32, Ty::F32, Ty::F32, Mul::F32, float, float, float)
   RUQLP_DISPATCH(false, Ty::BF16, Ty::F32, Ty::F32, Mul::F32, __nv_bfloat16, float, float)
+  RUQLP_DISPATCH(false, Ty::BF16, Ty::BF16, Ty::F32, Mul::F32, __nv_bfloat16, __nv_bfloat16, float)
   RUQLP_DISPATCH(false, Ty::F32, Ty::F32, Ty::F32, Mul::F32_ACC64, float, float, float)
   return cudaErrorInvalidValue;
 }
@@ -188,6 +189,7 @@ cudaError_t simt_gemm_tn(Ty ta, Ty tb, Ty tc, Mul mul, const void* A, int64_t ld
   RUQLP_DISPATCH(true, Ty::F64, Ty::F64, Ty::F64, Mul::F64, double, double, double)
   RUQLP_DISPATCH(true, Ty::F32, Ty::F32, Ty::F32, Mul::F32, float, float, float)
   RUQLP_DISPATCH(true, Ty::BF16, Ty::F32, Ty::F32, Mul::F32, __nv_bfloat16, float, float)
+  RUQLP_DISPATCH(true, Ty::BF16, Ty::BF16, Ty::F32, Mul::F32, __nv_bfloat16, __nv_bfloat16, float)
   RUQLP_DISPATCH(true, Ty::F32, Ty::F32, Ty::F64, Mul::F32_ACC64, float, float, double)
   RUQLP_DISPATCH(true, Ty::F32, Ty::F32, Ty::F64, Mul::F64, float, float, double)
   return cudaErrorInvalidValue;

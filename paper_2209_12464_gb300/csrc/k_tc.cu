@@ -158,32 +158,34 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-// A CTA's work: whole tiles first (data parallel), then at most two
-// stream-K segments of tail tiles.
+// A CTA's work, generated on the fly: items 0..full_waves-1 are whole tiles
+// (data parallel), then at most two stream-K segments of tail tiles.
 struct Item {
   int tile, kb0, kb1, slot;  // slot < 0: write the output; else fragment slot
 };
 
 __device__ __forceinline__ int64_t sk_start(int64_t c, int64_t U, int P) { return c * U / P; }
 
-__device__ int build_items(const TcParams& p, Item* items) {
+__device__ __forceinline__ int item_count(const TcParams& p) {
   const int P = gridDim.x, c = blockIdx.x;
-  int n = 0;
-  for (int w = 0; w < p.full_waves; ++w) items[n++] = {c + w * P, 0, p.KB, -1};
+  int n = p.full_waves;
   if (p.tail > 0) {
     const int64_t u0 = sk_start(c, p.U, P), u1 = sk_start(c + 1, p.U, P);
-    if (u1 > u0) {
-      const int base = p.full_waves * P;
-      const int64_t t0 = u0 / p.KB;
-      const int64_t e0 = min(u1, (t0 + 1) * (int64_t)p.KB);
-      items[n++] = {base + (int)t0, (int)(u0 - t0 * p.KB), (int)(e0 - t0 * p.KB), 0};
-      if (u1 > e0) items[n++] = {base + (int)t0 + 1, 0, (int)(u1 - (t0 + 1) * p.KB), 1};
-    }
+    if (u1 > u0) n += (u1 > (u0 / p.KB + 1) * (int64_t)p.KB) ? 2 : 1;
   }
   return n;
 }
 
-constexpr int MAX_ITEMS = 8;
+__device__ __forceinline__ Item get_item(const TcParams& p, int i) {
+  const int P = gridDim.x, c = blockIdx.x;
+  if (i < p.full_waves) return {c + i * P, 0, p.KB, -1};
+  const int64_t u0 = sk_start(c, p.U, P), u1 = sk_start(c + 1, p.U, P);
+  const int base = p.full_waves * P;
+  const int64_t t0 = u0 / p.KB;
+  const int64_t e0 = min(u1, (t0 + 1) * (int64_t)p.KB);
+  if (i == p.full_waves) return {base + (int)t0, (int)(u0 - t0 * p.KB), (int)(e0 - t0 * p.KB), 0};
+  return {base + (int)t0 + 1, 0, (int)(u1 - (t0 + 1) * p.KB), 1};
+}
 
 template <bool TRANS>
 __global__ void __launch_bounds__(NTHREADS, 1)
@@ -197,12 +199,13 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
   const uint32_t b_bytes = (uint32_t)p.dp * BK * 2;
   const uint32_t stage_bytes = A_TILE_BYTES + b_bytes;
   const uint32_t bar_base = base + S * stage_bytes;
-  // barriers: full[S], empty[S], tfull[2], tempty[2]; then the TMEM address
+  // barriers: full[S], empty[S], tfull[2], tempty[2], drain; then the TMEM address
   auto full_bar = [&](int s) { return bar_base + 8u * s; };
   auto empty_bar = [&](int s) { return bar_base + 8u * (S + s); };
   auto tfull_bar = [&](int a) { return bar_base + 8u * (2 * S + a); };
   auto tempty_bar = [&](int a) { return bar_base + 8u * (2 * S + 2 + a); };
-  uint32_t* tmem_slot = (uint32_t*)(base_ptr + S * stage_bytes + 8 * (2 * S + 4));
+  const uint32_t drain_bar = bar_base + 8u * (2 * S + 4);
+  uint32_t* tmem_slot = (uint32_t*)(base_ptr + S * stage_bytes + 8 * (2 * S + 5));
   __shared__ int s_abort;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -215,6 +218,7 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
       mbar_init(tfull_bar(a), 1);
       mbar_init(tempty_bar(a), 4);  // one arrival per epilogue warp
     }
+    mbar_init(drain_bar, 1);
     s_abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tmA) : "memory");
@@ -232,8 +236,7 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
   const uint32_t tmem_base = *tmem_slot;
   volatile int* abort_flag = &s_abort;
 
-  Item items[MAX_ITEMS];
-  const int nitems = build_items(p, items);
+  const int nitems = item_count(p);
 
   if (warp == 0) {
     // ---------------- TMA producer ----------------
@@ -242,10 +245,12 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
       int stage = 0;
       uint32_t phase = 0;
       bool ok = true;
+      int64_t issued = 0;
       for (int i = 0; i < nitems && ok; ++i) {
-        const Item it = items[i];
+        const Item it = get_item(p, i);
         for (int kb = it.kb0; kb < it.kb1; ++kb) {
           if (!mbar_wait(empty_bar(stage), phase ^ 1u, abort_flag)) { ok = false; break; }
+          ++issued;
           const uint32_t sa = base + stage * stage_bytes, sb = sa + A_TILE_BYTES;
           mbar_expect_tx(full_bar(stage), stage_bytes);
           if (!TRANS) {
@@ -259,7 +264,21 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
           if (++stage == S) { stage = 0; phase ^= 1u; }
         }
       }
-      if (!ok) { *abort_flag = 1; atomicExch(p.err, 1); }
+      if (!ok) {
+        *abort_flag = 1;
+        atomicExch(p.err, 1);
+        // let the loads already issued land before the CTA releases its
+        // shared memory: wait (bounded) on the newest phase of each stage
+        int st2 = stage;
+        uint32_t ph2 = phase;
+        const int64_t back = issued < S ? issued : S;
+        for (int64_t j = 0; j < back; ++j) {
+          if (st2 == 0) { st2 = S; ph2 ^= 1u; }
+          --st2;
+          volatile int never = 0;
+          mbar_wait(full_bar(st2), ph2, &never);
+        }
+      }
     }
   } else if (warp == 1) {
     // ---------------- MMA issuer ----------------
@@ -269,7 +288,7 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
       uint32_t phase = 0;
       bool ok = true;
       for (int i = 0; i < nitems && ok; ++i) {
-        const Item it = items[i];
+        const Item it = get_item(p, i);
         const int acc = i & 1;
         const uint32_t use = (uint32_t)(i >> 1);
         if (!mbar_wait(tempty_bar(acc), (use & 1u) ^ 1u, abort_flag)) { ok = false; break; }
@@ -294,6 +313,10 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
         mma_commit(tfull_bar(acc));
       }
       if (!ok) { *abort_flag = 1; atomicExch(p.err, 1); }
+      // every MMA this thread issued has completed before TMEM is freed
+      mma_commit(drain_bar);
+      volatile int never = 0;
+      mbar_wait(drain_bar, 0, &never);
     }
   } else {
     // ---------------- epilogue (warps 2..5) ----------------
@@ -301,7 +324,7 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
     const int row = g * 32 + lane;
     bool ok = true;
     for (int i = 0; i < nitems && ok; ++i) {
-      const Item it = items[i];
+      const Item it = get_item(p, i);
       const int acc = i & 1;
       const uint32_t use = (uint32_t)(i >> 1);
       if (!mbar_wait(tfull_bar(acc), use & 1u, abort_flag)) { ok = false; break; }
@@ -342,25 +365,35 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
 }
 
 // Sum the stream-K fragments of each tail tile in CTA order into the output.
-__global__ void k_tc_fixup(TcParams p, int P) {
+// Thread 0 lists the tile's contributing CTAs and fragment slots once.
+constexpr int FIX_ROWS = 4;
+__global__ void __launch_bounds__(256) k_tc_fixup(TcParams p, int P) {
+  __shared__ int s_src[512];
+  __shared__ int s_n;
   const int tt = blockIdx.x;  // tail tile index
   const int64_t KB = p.KB;
   const int64_t lo = tt * KB, hi = lo + KB;
-  int c = (int)((lo * P) / p.U);
-  while (c + 1 < P && sk_start(c + 1, p.U, P) <= lo) ++c;
-  while (c > 0 && sk_start(c, p.U, P) > lo) --c;
-  const int tile = p.full_waves * P + tt;
-  const int r0 = blockIdx.y * 16;
-  for (int e = threadIdx.x; e < 16 * p.dp; e += blockDim.x) {
-    const int r = r0 + e / p.dp, col = e % p.dp;
-    float s = 0.f;
-    for (int cc = c; cc < P; ++cc) {
+  if (threadIdx.x == 0) {
+    int c = (int)((lo * P) / p.U);
+    while (c + 1 < P && sk_start(c + 1, p.U, P) <= lo) ++c;
+    while (c > 0 && sk_start(c, p.U, P) > lo) --c;
+    int n = 0;
+    for (int cc = c; cc < P && n < 512; ++cc) {
       const int64_t u0 = sk_start(cc, p.U, P), u1 = sk_start(cc + 1, p.U, P);
       if (u0 >= hi) break;
       if (u1 <= lo || u1 == u0) continue;
-      const int slot = (u0 / KB == tt) ? 0 : 1;
-      s += p.frag[(((int64_t)cc * 2 + slot) * BM + r) * p.dp + col];
+      s_src[n++] = cc * 2 + ((u0 / KB == tt) ? 0 : 1);
     }
+    s_n = n;
+  }
+  __syncthreads();
+  const int tile = p.full_waves * P + tt;
+  const int r0 = blockIdx.y * FIX_ROWS;
+  const int n = s_n;
+  for (int e = threadIdx.x; e < FIX_ROWS * p.dp; e += blockDim.x) {
+    const int r = r0 + e / p.dp, col = e % p.dp;
+    float s = 0.f;
+    for (int i = 0; i < n; ++i) s += p.frag[((int64_t)s_src[i] * BM + r) * p.dp + col];
     const int64_t gr = (int64_t)tile * BM + r;
     if (gr < p.Mout) p.out[gr * p.ldo + col] = s;
   }
@@ -427,6 +460,11 @@ int sm_count() {
 
 }  // namespace
 
+bool tc_supported(const void* A, int64_t lda, int dp) {
+  return dp >= 16 && dp <= 256 && dp % 16 == 0 && lda % 8 == 0 && ((uintptr_t)A & 15) == 0 &&
+         encode_fn() != nullptr;
+}
+
 size_t tc_frag_bytes(int dp) { return (size_t)sm_count() * 2 * BM * dp * sizeof(float); }
 
 cudaError_t tc_gemm(bool trans, const void* A, int64_t lda, int64_t m, int64_t n, const void* Bt,
@@ -452,24 +490,17 @@ cudaError_t tc_gemm(bool trans, const void* A, int64_t lda, int64_t m, int64_t n
   p.err = err;
   p.T = ceil_div(Mout, BM);
   p.KB = ceil_div(K, BK);
-  int P = sm_count();
+  int P = sm_count();  // never more CTAs than the fragment buffer has slots for
   if ((int64_t)p.T * p.KB < P) P = p.T * p.KB;
   p.full_waves = p.T / P;
   p.tail = p.T - p.full_waves * P;
   p.U = (int64_t)p.tail * p.KB;
-  if (p.full_waves + 2 > MAX_ITEMS) {
-    // very tall outputs: more whole tiles per CTA than the item list holds
-    P = (p.T + MAX_ITEMS - 3) / (MAX_ITEMS - 2);
-    p.full_waves = p.T / P;
-    p.tail = p.T - p.full_waves * P;
-    p.U = (int64_t)p.tail * p.KB;
-  }
   const size_t stage_bytes = A_TILE_BYTES + (size_t)dp * BK * 2;
   int stages = (int)((200 * 1024) / stage_bytes);
   if (stages > 8) stages = 8;
   if (stages < 2) return cudaErrorInvalidValue;
   p.stages = stages;
-  const size_t smem = 1024 + stages * stage_bytes + 8 * (2 * stages + 4) + 16;
+  const size_t smem = 1024 + stages * stage_bytes + 8 * (2 * stages + 5) + 16;
   cudaError_t e;
   if (trans) {
     e = cudaFuncSetAttribute(k_tc_gemm<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -485,7 +516,7 @@ cudaError_t tc_gemm(bool trans, const void* A, int64_t lda, int64_t m, int64_t n
   count_launch();
   e = cudaGetLastError();
   if (e != cudaSuccess || p.tail == 0) return e;
-  k_tc_fixup<<<dim3(p.tail, BM / 16), 256, 0, st>>>(p, P);
+  k_tc_fixup<<<dim3(p.tail, BM / FIX_ROWS), 256, 0, st>>>(p, P);
   count_launch();
   return cudaGetLastError();
 }

@@ -26,7 +26,8 @@ struct ruqlp_ctx {
   DevStatus* status_host = nullptr;  // pinned host
   std::string err;
   // policy knobs (ruqlp_set_option)
-  int gram1_exact = 1;  // first CholeskyQR pass: FP64 products (1) or FP32 chunked (0)
+  int orth_fp64 = 0;    // FP32/BF16 paths: CholeskyQR2 with FP64 Gram and Cholesky
+  int bf16_simt = 0;    // 1: BF16 products on CUDA cores instead of tensor cores
   // phase timing with CUDA events on the handle's stream (option "profile")
   bool profile = false;
   struct Span { int cat; cudaEvent_t a, b; };
@@ -131,8 +132,10 @@ constexpr int kMaxSplits = 64;
 
 // Workspace layout for one problem.
 struct Layout {
-  size_t X, Y, Z, P, partial, G, R, Rw, total;
+  size_t X, Y, Z, P, partial, G, R, Rw, Bt, frag, total;
 };
+
+inline int64_t round8(int64_t x) { return (x + 7) / 8 * 8; }
 
 Layout layout_of(int64_t m, int64_t n, int d, Ty ct) {
   Layout L{};
@@ -152,6 +155,10 @@ Layout layout_of(int64_t m, int64_t n, int d, Ty ct) {
   L.G = take((size_t)d * d * sizeof(double));
   L.R = take((size_t)d * d * sizeof(double));
   L.Rw = take((size_t)d * d * sizeof(double));
+  if (ct == Ty::BF16) {
+    L.Bt = take((size_t)dp * round8(m > n ? m : n) * 2);
+    L.frag = take(dp <= 256 ? tc_frag_bytes(dp) : 0);
+  }
   L.total = off;
   return L;
 }
@@ -217,10 +224,20 @@ struct Job {
   void* Pout;
   Ty ot;
   bool finish_paper;
+  bool use_tc;  // BF16 products on the tensor cores (k_tc.cu)
 };
 
-// orth(): Q = Yin R^{-1} by CholeskyQR2, with a third (shifted-CholeskyQR3)
-// pass that runs only when a Cholesky of this orth had to shift.
+// orth() of Section II-A: Q = Yin R^{-1} with R from Cholesky factorisations
+// of Gram matrices (CholeskyQR, Fukaya et al. 2020).
+//  * FP64 work type (and the "orth_fp64" option): CholeskyQR2 with FP64
+//    products and an FP64 Cholesky; a third pass runs only when a Cholesky of
+//    this orth had to shift (status->shifted gates the launches).
+//  * FP32 work type (default for FP32/BF16): shifted CholeskyQR3 in FP32 --
+//    the first Cholesky always factors G + s I, s = 64 u_32 trace(G), so it
+//    cannot break down for kappa(Y) up to about 1/u_32; two more unshifted
+//    passes restore orthonormality.  FP32 Grams are summed in FP64 across row
+//    slabs.  (A single-SM FP64 Cholesky of a 220 x 220 Gram costs ~0.45 ms on
+//    GB300, whose FP64 rate is 1/58 of FP32.)
 ruqlp_status orth(ruqlp_ctx* h, const Layout& Lo, const Job& J, const void* Yin, void* Qout,
                   int64_t M) {
   ProfScope ps(h, PROF_ORTH);
@@ -231,33 +248,78 @@ ruqlp_status orth(ruqlp_ctx* h, const Layout& Lo, const Job& J, const void* Yin,
   void* Rw = base + Lo.Rw;
   const int d = J.d, dp = J.dp;
   const Ty wt = J.wt;
-  const bool f64 = (wt == Ty::F64);
-  const Mul g1 = (f64 || h->gram1_exact) ? Mul::F64 : Mul::F32_ACC64;
-  const Mul g2 = f64 ? Mul::F64 : Mul::F32_ACC64;
-  // shift = c * u * trace(G) (Fukaya et al. 2020 with ||Y||_2^2 <= trace(G));
-  // u is the unit roundoff of the Gram's arithmetic.
-  auto shift_rel = [&](Mul g) {
-    if (g == Mul::F64) return 11.0 * ((double)M * d + (double)d * (d + 1)) * 1.1102230246251565e-16;
-    return 4.0 * 17.0 * 5.960464477539063e-08;
-  };
+  cudaStream_t st = h->stream;
+  CK(status_clear_shift(h->status, st));
+  if (wt == Ty::F32 && !h->orth_fp64) {
+    const double s1 = 64.0 * 5.960464477539063e-08;
+    const bool blocked = chol_inv_f32_supported(d);
+    for (int pass = 0; pass < 3; ++pass) {
+      const float* src = (const float*)(pass == 0 ? Yin : Qout);
+      CK(gram_f32(src, dp, src, dp, M, d, d, G, partial, kMaxSplits, nullptr, st));
+      if (blocked) {
+        CK(chol_inv_f32(G, d, s1, pass == 0, (float*)Rw, h->status, nullptr, st));
+        CK(mul_upper_f32(src, dp, (const float*)Rw, (float*)Qout, dp, M, d, st));
+      } else {
+        CK(chol_upper(G, d, s1, R, Rw, Ty::F32, h->status, nullptr, st, Ty::F32, pass == 0));
+        CK(trsm_right_upper(Ty::F32, src, dp, Rw, Qout, dp, M, d, nullptr, st));
+      }
+    }
+    return RUQLP_OK;
+  }
+  const Mul g = Mul::F64;  // FP64 products (exact for FP32 data)
+  const double srel =
+      11.0 * ((double)M * d + (double)d * (d + 1)) * 1.1102230246251565e-16;
   const int S = tn_splits(d, M, d, kMaxSplits);
   const int32_t* gate = &h->status->shifted;
-  CK(status_clear_shift(h->status, h->stream));
   // pass 1
-  CK(simt_gemm_tn(wt, wt, Ty::F64, g1, Yin, dp, Yin, dp, G, d, d, M, d, S, partial, nullptr,
-                  h->stream));
-  CK(chol_upper(G, d, shift_rel(g1), R, Rw, wt, h->status, nullptr, h->stream));
-  CK(trsm_right_upper(wt, Yin, dp, Rw, Qout, dp, M, d, nullptr, h->stream));
+  CK(simt_gemm_tn(wt, wt, Ty::F64, g, Yin, dp, Yin, dp, G, d, d, M, d, S, partial, nullptr, st));
+  CK(chol_upper(G, d, srel, R, Rw, wt, h->status, nullptr, st));
+  CK(trsm_right_upper(wt, Yin, dp, Rw, Qout, dp, M, d, nullptr, st));
   // pass 2
-  CK(simt_gemm_tn(wt, wt, Ty::F64, g2, Qout, dp, Qout, dp, G, d, d, M, d, S, partial, nullptr,
-                  h->stream));
-  CK(chol_upper(G, d, shift_rel(g2), R, Rw, wt, h->status, nullptr, h->stream));
-  CK(trsm_right_upper(wt, Qout, dp, Rw, Qout, dp, M, d, nullptr, h->stream));
+  CK(simt_gemm_tn(wt, wt, Ty::F64, g, Qout, dp, Qout, dp, G, d, d, M, d, S, partial, nullptr, st));
+  CK(chol_upper(G, d, srel, R, Rw, wt, h->status, nullptr, st));
+  CK(trsm_right_upper(wt, Qout, dp, Rw, Qout, dp, M, d, nullptr, st));
   // pass 3 (only after a shift)
-  CK(simt_gemm_tn(wt, wt, Ty::F64, g2, Qout, dp, Qout, dp, G, d, d, M, d, S, partial, gate,
-                  h->stream));
-  CK(chol_upper(G, d, shift_rel(g2), R, Rw, wt, h->status, gate, h->stream));
-  CK(trsm_right_upper(wt, Qout, dp, Rw, Qout, dp, M, d, gate, h->stream));
+  CK(simt_gemm_tn(wt, wt, Ty::F64, g, Qout, dp, Qout, dp, G, d, d, M, d, S, partial, gate, st));
+  CK(chol_upper(G, d, srel, R, Rw, wt, h->status, gate, st));
+  CK(trsm_right_upper(wt, Qout, dp, Rw, Qout, dp, M, d, gate, st));
+  return RUQLP_OK;
+}
+
+// One pass over A (Algorithm 1 step 3, Algorithm 2, B^T = A^T Q):
+//   trans = false: out[m x dp] = A Xin, Xin n x d;
+//   trans = true:  out[n x dp] = A^T Xin, Xin m x d;
+// Xin has type xt and leading dimension ldx; out is the work type, ld dp.
+ruqlp_status product(ruqlp_ctx* h, const Layout& Lo, const Job& J, bool trans, Ty xt,
+                     const void* Xin, int64_t ldx, void* out) {
+  ProfScope p(h, trans ? PROF_ATX : PROF_AX);
+  cudaStream_t st = h->stream;
+  char* base = (char*)h->arena;
+  const int64_t K = trans ? J.m : J.n;
+  const int64_t Mout = trans ? J.n : J.m;
+  if (J.use_tc) {
+    void* Bt = base + Lo.Bt;
+    const int64_t ldb = round8(K);
+    CK(transpose_to_bf16(xt, Xin, ldx, K, J.d, J.dp, Bt, ldb, st));
+    CK(tc_gemm(trans, J.A, J.lda, J.m, J.n, Bt, ldb, J.dp, (float*)out, J.dp,
+               (float*)(base + Lo.frag), &h->status->timeout, st));
+    return RUQLP_OK;
+  }
+  const Mul mul = (J.ct == Ty::F64) ? Mul::F64 : Mul::F32;
+  if (J.ct == Ty::BF16) {
+    // BF16 compute rounds the skinny operand to BF16 on either kernel, so the
+    // CUDA-core kernel computes the same product as the tensor cores
+    void* Xb = base + Lo.Bt;
+    CK(copy_cast_2d(xt, Xin, ldx, Ty::BF16, Xb, J.d, K, J.d, st));
+    Xin = Xb;
+    xt = Ty::BF16;
+    ldx = J.d;
+  }
+  if (!trans)
+    CK(simt_gemm_nn(J.ct, xt, J.wt, mul, J.A, J.lda, Xin, ldx, out, J.dp, Mout, K, J.d, st));
+  else
+    CK(simt_gemm_tn(J.ct, xt, J.wt, mul, J.A, J.lda, Xin, ldx, out, J.dp, Mout, K, J.d, 1,
+                    nullptr, nullptr, st));
   return RUQLP_OK;
 }
 
@@ -273,52 +335,48 @@ ruqlp_status run_dense(ruqlp_ctx* h, const Job& J) {
   double* partial = (double*)(base + Lo.partial);
   double* G = (double*)(base + Lo.G);
   const int d = J.d, dp = J.dp;
-  const Ty ct = J.ct, wt = J.wt;
-  const Mul mul = (ct == Ty::F64) ? Mul::F64 : Mul::F32;
+  const Ty wt = J.wt;
   const size_t wes = ty_size(wt);
   cudaStream_t st = h->stream;
 
   ProfScope pstep(h, PROF_STEP);
   CK(status_reset(h->status, st));
-  // a1: Omega (FP64, n x d) -> X (work type, n x dp, zero padding)
-  CK(cudaMemsetAsync(X, 0, (size_t)J.n * dp * wes, st));
-  CK(copy_cast_2d(Ty::F64, J.omega, d, wt, X, dp, J.n, d, st));
-  // a2: Y = A Omega
-  {
-    ProfScope p(h, PROF_AX);
-    CK(simt_gemm_nn(ct, wt, wt, mul, J.A, J.lda, X, dp, Y, dp, J.m, J.n, d, st));
+  // a1 + a2: Y = A Omega (Omega is FP64 n x d; the tensor-core path transposes
+  // it straight to BF16, the SIMT path casts it to the work type first)
+  if (J.use_tc) {
+    s = product(h, Lo, J, false, Ty::F64, J.omega, d, Y);
+  } else {
+    CK(cudaMemsetAsync(X, 0, (size_t)J.n * dp * wes, st));
+    CK(copy_cast_2d(Ty::F64, J.omega, d, wt, X, dp, J.n, d, st));
+    s = product(h, Lo, J, false, wt, X, dp, Y);
   }
+  if (s != RUQLP_OK) return s;
   // a3: Q = orth(Y)
   s = orth(h, Lo, J, Y, Y, J.m);
   if (s != RUQLP_OK) return s;
   // a4: power iteration with orthonormalisation (Algorithm 2)
   for (int it = 0; it < J.q; ++it) {
-    {
-      ProfScope p(h, PROF_ATX);
-      CK(simt_gemm_tn(ct, wt, wt, mul, J.A, J.lda, Y, dp, Z, dp, J.n, J.m, d, 1, nullptr,
-                      nullptr, st));
-    }
+    s = product(h, Lo, J, true, wt, Y, dp, Z);
+    if (s != RUQLP_OK) return s;
     s = orth(h, Lo, J, Z, Z, J.n);
     if (s != RUQLP_OK) return s;
-    {
-      ProfScope p(h, PROF_AX);
-      CK(simt_gemm_nn(ct, wt, wt, mul, J.A, J.lda, Z, dp, Y, dp, J.m, J.n, d, st));
-    }
+    s = product(h, Lo, J, false, wt, Z, dp, Y);
+    if (s != RUQLP_OK) return s;
     s = orth(h, Lo, J, Y, Y, J.m);
     if (s != RUQLP_OK) return s;
   }
   // a5: B^T = A^T Q
-  {
-    ProfScope p(h, PROF_ATX);
-    CK(simt_gemm_tn(ct, wt, wt, mul, J.A, J.lda, Y, dp, Z, dp, J.n, J.m, d, 1, nullptr,
-                    nullptr, st));
-  }
+  s = product(h, Lo, J, true, wt, Y, dp, Z);
+  if (s != RUQLP_OK) return s;
   // a6: [P, R_B] = qr(B^T): P = orth(B^T), R_B = P^T B^T
   s = orth(h, Lo, J, Z, Pb, J.n);
   if (s != RUQLP_OK) return s;
-  const Mul gr = (wt == Ty::F64) ? Mul::F64 : Mul::F32_ACC64;
-  CK(simt_gemm_tn(wt, wt, Ty::F64, gr, Pb, dp, Z, dp, G, d, d, J.n, d,
-                  tn_splits(d, J.n, d, kMaxSplits), partial, nullptr, st));
+  if (wt == Ty::F64)
+    CK(simt_gemm_tn(wt, wt, Ty::F64, Mul::F64, Pb, dp, Z, dp, G, d, d, J.n, d,
+                    tn_splits(d, J.n, d, kMaxSplits), partial, nullptr, st));
+  else
+    CK(gram_f32((const float*)Pb, dp, (const float*)Z, dp, J.n, d, d, G, partial, kMaxSplits,
+                nullptr, st));
   // a7: outputs
   CK(write_L(G, d, J.ot, J.Lout, false, st));
   CK(copy_cast_2d(wt, Y, dp, J.ot, J.Qout, d, J.m, d, st));
@@ -332,6 +390,8 @@ ruqlp_status finish(ruqlp_ctx* h, ruqlp_outputs* out) {
   CK(cudaStreamSynchronize(h->stream));
   if (h->profile) prof_collect(h);
   out->flags = (uint32_t)h->status_host->flags;
+  if (h->status_host->timeout)
+    return fail(h, RUQLP_ERR_TIMEOUT, "a bounded device wait ran out in a tensor-core product");
   if (h->status_host->breakdown)
     return fail(h, RUQLP_ERR_BREAKDOWN, "orth() broke down after its fallbacks");
   return RUQLP_OK;
@@ -384,8 +444,12 @@ ruqlp_status ruqlp_set_stream(ruqlp_handle h, void* stream) {
 
 ruqlp_status ruqlp_set_option(ruqlp_handle h, const char* name, int64_t value) {
   if (!h || !name) return RUQLP_ERR_INVALID;
-  if (strcmp(name, "gram1_exact") == 0) {
-    h->gram1_exact = value ? 1 : 0;
+  if (strcmp(name, "orth_fp64") == 0) {
+    h->orth_fp64 = value ? 1 : 0;
+    return RUQLP_OK;
+  }
+  if (strcmp(name, "bf16_simt") == 0) {
+    h->bf16_simt = value ? 1 : 0;
     return RUQLP_OK;
   }
   if (strcmp(name, "profile") == 0) {
@@ -440,6 +504,7 @@ ruqlp_status ruqlp_decompose(ruqlp_handle h, const ruqlp_matrix* A, const ruqlp_
   J.finish_paper = prm->finish_paper != 0;
   if (J.finish_paper)
     return fail(h, RUQLP_ERR_INVALID, "finish_paper is not available in this build");
+  J.use_tc = J.ct == Ty::BF16 && !h->bf16_simt && tc_supported(J.A, J.lda, J.dp);
   s = run_dense(h, J);
   if (s != RUQLP_OK) return s;
   return finish(h, out);
@@ -461,8 +526,9 @@ ruqlp_status ruqlp_decompose_host(ruqlp_handle h, const ruqlp_matrix* A,
   // host staging region: A (m x n, packed), Omega, Q, L, P after the workspace
   Layout Lo = layout_of(m, n, d, at);
   size_t off = align_up(Lo.total, 256);
+  const int64_t lds = (at == Ty::BF16) ? round8(n) : n;  // TMA needs 16-byte row pitch
   const size_t oA = off;
-  off = align_up(off + (size_t)m * n * aes, 256);
+  off = align_up(off + (size_t)m * lds * aes, 256);
   const size_t oOm = off;
   off = align_up(off + (size_t)n * d * sizeof(double), 256);
   const size_t oQ = off;
@@ -475,13 +541,13 @@ ruqlp_status ruqlp_decompose_host(ruqlp_handle h, const ruqlp_matrix* A,
   if (s != RUQLP_OK) return s;
   char* base = (char*)h->arena;
   cudaStream_t st = h->stream;
-  CK(cudaMemcpy2DAsync(base + oA, (size_t)n * aes, A->dense.data, (size_t)A->dense.ld * aes,
+  CK(cudaMemcpy2DAsync(base + oA, (size_t)lds * aes, A->dense.data, (size_t)A->dense.ld * aes,
                        (size_t)n * aes, (size_t)m, cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(base + oOm, prm->omega, (size_t)n * d * sizeof(double),
                      cudaMemcpyHostToDevice, st));
   Job J{};
   J.A = base + oA;
-  J.lda = n;
+  J.lda = lds;
   J.m = m;
   J.n = n;
   J.d = d;
@@ -497,6 +563,7 @@ ruqlp_status ruqlp_decompose_host(ruqlp_handle h, const ruqlp_matrix* A,
   J.finish_paper = prm->finish_paper != 0;
   if (J.finish_paper)
     return fail(h, RUQLP_ERR_INVALID, "finish_paper is not available in this build");
+  J.use_tc = J.ct == Ty::BF16 && !h->bf16_simt && tc_supported(J.A, J.lda, J.dp);
   s = run_dense(h, J);
   if (s != RUQLP_OK) return s;
   CK(cudaMemcpyAsync(out->Q, base + oQ, (size_t)m * d * oes, cudaMemcpyDeviceToHost, st));
@@ -508,6 +575,73 @@ ruqlp_status ruqlp_decompose_host(ruqlp_handle h, const ruqlp_matrix* A,
 const char* ruqlp_last_error(ruqlp_handle h) { return h ? h->err.c_str() : "NULL handle"; }
 
 int64_t ruqlp_launch_count(void) { return launch_count(); }
+
+ruqlp_status ruqlp_sketch(ruqlp_handle h, const ruqlp_matrix* A, int trans, const void* X,
+                          int64_t ldx, int d, void* Y, int64_t ldy) {
+  if (!h) return RUQLP_ERR_INVALID;
+  h->err.clear();
+  if (!A || !X || !Y) return fail(h, RUQLP_ERR_INVALID, "NULL argument");
+  if (A->is_csr) return fail(h, RUQLP_ERR_INVALID, "CSR input is not supported by this entry");
+  const ruqlp_dense& D = A->dense;
+  Ty ct;
+  if (!D.data || D.m < 1 || D.n < 1 || D.ld < D.n || !ty_of(D.dtype, &ct))
+    return fail(h, RUQLP_ERR_INVALID, "invalid dense A");
+  const int64_t K = trans ? D.m : D.n, Mout = trans ? D.n : D.m;
+  if (d < 1 || d > 512 || ldx < d || ldy < d)
+    return fail(h, RUQLP_ERR_INVALID, "need 1 <= d <= 512, ldx >= d, ldy >= d");
+  CK(cudaSetDevice(h->device));
+  Job J{};
+  J.A = D.data;
+  J.lda = D.ld;
+  J.m = D.m;
+  J.n = D.n;
+  J.d = d;
+  J.dp = round16(d);
+  J.ct = ct;
+  J.wt = work_ty(ct);
+  J.use_tc = ct == Ty::BF16 && !h->bf16_simt && tc_supported(J.A, J.lda, J.dp);
+  const Layout Lo = layout_of(J.m, J.n, d, ct);
+  ruqlp_status s = ensure_arena(h, Lo.total);
+  if (s != RUQLP_OK) return s;
+  CK(status_reset(h->status, h->stream));
+  void* stage = (char*)h->arena + (trans ? Lo.Z : Lo.Y);
+  s = product(h, Lo, J, trans != 0, J.wt, X, ldx, stage);
+  if (s != RUQLP_OK) return s;
+  CK(copy_cast_2d(J.wt, stage, J.dp, J.wt, Y, ldy, Mout, d, h->stream));
+  (void)K;
+  ruqlp_outputs dummy{};
+  return finish(h, &dummy);
+}
+
+ruqlp_status ruqlp_orth(ruqlp_handle h, const void* Y, int64_t M, int d, int64_t ldy,
+                        ruqlp_dtype dtype, void* Q, int64_t ldq) {
+  if (!h) return RUQLP_ERR_INVALID;
+  h->err.clear();
+  if (!Y || !Q) return fail(h, RUQLP_ERR_INVALID, "NULL pointer");
+  if (d < 1 || d > 512 || M < d || ldy < d || ldq < d)
+    return fail(h, RUQLP_ERR_INVALID, "need 1 <= d <= 512, M >= d, ldy >= d, ldq >= d");
+  if (dtype != RUQLP_F64 && dtype != RUQLP_F32)
+    return fail(h, RUQLP_ERR_INVALID, "dtype must be F64 or F32");
+  CK(cudaSetDevice(h->device));
+  Job J{};
+  J.m = M;
+  J.n = d;
+  J.d = d;
+  J.dp = round16(d);
+  J.ct = dtype == RUQLP_F64 ? Ty::F64 : Ty::F32;
+  J.wt = J.ct;
+  const Layout Lo = layout_of(M, d, d, J.ct);
+  ruqlp_status s = ensure_arena(h, Lo.total);
+  if (s != RUQLP_OK) return s;
+  void* W = (char*)h->arena + Lo.Y;
+  CK(status_reset(h->status, h->stream));
+  CK(copy_cast_2d(J.wt, Y, ldy, J.wt, W, J.dp, M, d, h->stream));
+  s = orth(h, Lo, J, W, W, M);
+  if (s != RUQLP_OK) return s;
+  CK(copy_cast_2d(J.wt, W, J.dp, J.wt, Q, ldq, M, d, h->stream));
+  ruqlp_outputs dummy{};
+  return finish(h, &dummy);
+}
 
 ruqlp_status ruqlp_gram(ruqlp_handle h, const void* Y, int64_t M, int d, int64_t ldy,
                         ruqlp_dtype dtype, double* G) {

@@ -70,6 +70,10 @@ _SIGS = {
                                      ctypes.POINTER(Outputs)]),
     "ruqlp_last_error": (c_char_p, [c_void_p]),
     "ruqlp_launch_count": (c_int64, []),
+    "ruqlp_sketch": (c_int, [c_void_p, ctypes.POINTER(Matrix), c_int, c_void_p, c_int64, c_int,
+                             c_void_p, c_int64]),
+    "ruqlp_orth": (c_int, [c_void_p, c_void_p, c_int64, c_int, c_int64, c_int, c_void_p,
+                           c_int64]),
     "ruqlp_gram": (c_int, [c_void_p, c_void_p, c_int64, c_int, c_int64, c_int, c_void_p]),
     "ruqlp_gram_noalloc": (c_int, [c_void_p, c_int64, c_int, c_int64, c_int, c_void_p,
                                    c_void_p]),
@@ -143,6 +147,14 @@ def ruqlp_version():
     return lib().ruqlp_version().decode()
 
 
+def ruqlp_sketch(h, A, trans, X, ldx, d, Y, ldy):
+    return lib().ruqlp_sketch(h, ctypes.byref(A), trans, X, ldx, d, Y, ldy)
+
+
+def ruqlp_orth(h, Y, M, d, ldy, dtype, Q, ldq):
+    return lib().ruqlp_orth(h, Y, M, d, ldy, dtype, Q, ldq)
+
+
 def ruqlp_gram(h, Y, M, d, ldy, dtype, G):
     return lib().ruqlp_gram(h, Y, M, d, ldy, dtype, G)
 
@@ -198,6 +210,28 @@ class Handle:
         st, c, ms = ruqlp_profile(self.h, phase)
         self.check(st)
         return c, ms
+
+    def sketch(self, A, X, trans=False):
+        """Y = A X (or A^T X) with the library's product kernel for A's dtype."""
+        import torch
+        m, n = A.shape
+        K, Mout = (m, n) if trans else (n, m)
+        d = X.shape[1]
+        assert X.shape[0] == K
+        Y = torch.empty(Mout, d, dtype=X.dtype, device=A.device)
+        M = Matrix(0, Dense(m, n, A.stride(0), _dtype_code(A.dtype), A.data_ptr()), Csr())
+        self.check(ruqlp_sketch(self.h, M, int(trans), X.data_ptr(), X.stride(0), d,
+                                Y.data_ptr(), d))
+        return Y
+
+    def orth(self, Y):
+        """Q with orthonormal columns, Y = Q R (R upper, positive diagonal)."""
+        import torch
+        M, d = Y.shape
+        Q = torch.empty_like(Y)
+        self.check(ruqlp_orth(self.h, Y.data_ptr(), M, d, Y.stride(0), _dtype_code(Y.dtype),
+                              Q.data_ptr(), d))
+        return Q
 
     def gram(self, Y):
         """G = Y^T Y (FP64) of a CUDA tensor Y (M x d, FP64 or FP32, row-major)."""

@@ -125,6 +125,24 @@ def dense_spectral_torch(seed, m, n, sigma, noise_std=0.0, device="cuda",
     return A.to(dtype)
 
 
+def dense_lowrank_gauss_torch(seed, m, n, k, tail_scale=1e-2, noise_std=0.0, device="cuda"):
+    """Cheap stand-in with the same shape and a gapped spectrum, for profiling
+    runs where torch.linalg is unavailable: A = G1 G2^T / sqrt(n) + tail_scale *
+    G3 G4^T / sqrt(n) (G1, G2: k Gaussian columns; G3, G4: 2k columns) plus
+    N(0, noise_std^2) noise, float32 on ``device``.  Its spectrum is not the
+    Haar workload's; it is used only to time kernels."""
+    import torch
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed))
+    f = 1.0 / math.sqrt(n)
+    A = (torch.randn(m, k, generator=g, device=device) * f) @ torch.randn(k, n, generator=g, device=device)
+    A.addmm_(torch.randn(m, 2 * k, generator=g, device=device) * (f * tail_scale),
+             torch.randn(2 * k, n, generator=g, device=device))
+    if noise_std:
+        A.add_(torch.randn(m, n, generator=g, device=device), alpha=float(noise_std))
+    return A
+
+
 def lowrank_gap(seed, n, k, mu):
     """LowRank{Large,Medium}Gap of Section V-B: U Sigma V^T + mu sigma_k A_N."""
     sigma = spectrum_linear_rank(n, k)

@@ -148,3 +148,31 @@ def test_gram_entry_matches_fp64_products(handle, shape, dtype):
     ref = Yh.T @ Yh
     assert np.max(np.abs(G - ref)) <= 1e-13 * np.sum(Yh * Yh)
     assert np.array_equal(G, G.T)
+
+
+ORTH_CASES = [  # M, d, log10 kappa
+    (1000, 30, 1), (1000, 30, 5), (20011, 220, 3), (5003, 64, 6), (300, 300, 2), (129, 1, 0),
+    (777, 37, 4), (4096, 272, 3),
+]
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32], ids=["f64", "f32"])
+@pytest.mark.parametrize("case", ORTH_CASES, ids=[f"{a}x{b}k1e{c}" for a, b, c in ORTH_CASES])
+def test_orth_matches_householder_q(handle, case, dtype):
+    """ruqlp_orth (CholeskyQR2 / shifted CholeskyQR3) against the oracle's
+    Householder Q of the same (rounded) Y.  Q is unique for full column rank
+    (diag R > 0); column j is determined to about kappa_j u, so the bound is
+    50 kappa u with kappa = sigma_1 / sigma_d of Y."""
+    M, d, lk = case
+    rng = np.random.default_rng(M + d + lk)
+    Uy = wl.haar(rng, M, d)
+    Vy = wl.haar(rng, d, d)
+    Y = (Uy * np.logspace(0, -lk, d)[None, :]) @ Vy.T
+    Yg = torch.from_numpy(Y).to(dtype).cuda()
+    Yh = Yg.double().cpu().numpy()
+    Q = handle.orth(Yg).double().cpu().numpy()
+    Qr, Rr = oracle.householder_qr(Yh)
+    u = 2.0 ** -53 if dtype == torch.float64 else 2.0 ** -24
+    kappa = 10.0 ** lk
+    assert np.max(np.abs(Q.T @ Q - np.eye(d))) <= 50 * d * u
+    assert np.max(np.abs(Q - Qr)) <= 50 * kappa * u * max(1.0, np.sqrt(d))

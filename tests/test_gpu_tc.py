@@ -1,0 +1,138 @@
+"""GPU parity of the BF16 tensor-core path (tcgen05 products) through the C ABI.
+
+* Product kernel (ruqlp_sketch, Algorithm 1 step 3 / Algorithm 2 / B^T = A^T Q):
+  Y = A X or A^T X with A and X rounded to BF16, FP32 accumulation in TMEM,
+  against the FP64 product of the same BF16 values (oracle.apply_A /
+  apply_At).  Bound per element: 4 sqrt(K) u_32 (|A||X|)_ij, the typical
+  size of FP32 accumulation error over K terms (u_32 = 2^-24).
+* Whole decomposition: the residual against the FP64 oracle's on the same
+  (unrounded) A must be <= 1.05x on the 20000 x 20000 workload (the bar of the
+  reduced-precision path); at test sizes the BF16 rounding of A is larger
+  than the workload's noise, so only structure and a loose ratio are checked.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2209_12464_gb300 import ruqlp
+from paper_2209_12464_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+U32 = 2.0 ** -24
+
+
+@pytest.fixture(scope="module")
+def handle():
+    import __graft_entry__ as g
+    g.build()
+    h = ruqlp.Handle(0, torch.cuda.current_stream().cuda_stream)
+    yield h
+    h.close()
+
+
+def _bf16(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).to(torch.bfloat16)
+
+
+# n a multiple of 8 runs on the tensor cores (16-byte TMA row pitch); the
+# 777 x 555 case runs on the CUDA-core BF16 kernel.  Ragged tiles in m, n and
+# d, stream-K tails (fewer tiles than SMs, one more tile than a wave) included.
+SHAPES = [
+    (1000, 800, 30), (777, 552, 37), (777, 555, 37), (300, 7000, 16), (7000, 296, 256),
+    (129, 72, 1), (128, 64, 16), (4096, 2048, 72), (19459, 136, 100), (152 * 128 + 5, 96, 224),
+]
+
+
+@pytest.mark.parametrize("trans", [False, True], ids=["AX", "AtX"])
+@pytest.mark.parametrize("shape", SHAPES, ids=[f"{a}x{b}d{c}" for a, b, c in SHAPES])
+def test_tc_product_parity(handle, shape, trans):
+    m, n, d = shape
+    rng = np.random.default_rng(m * 7 + n + d)
+    A = _bf16(rng.standard_normal((m, n)))
+    K = m if trans else n
+    X = torch.from_numpy(rng.standard_normal((K, d))).float()
+    Y = handle.sketch(A.cuda(), X.cuda(), trans=trans).double().cpu().numpy()
+    Ah = A.double().numpy()
+    Xh = X.to(torch.bfloat16).double().numpy()
+    ref = oracle.apply_At(Ah, Xh) if trans else oracle.apply_A(Ah, Xh)
+    mag = (np.abs(Ah).T if trans else np.abs(Ah)) @ np.abs(Xh)
+    err = np.abs(Y - ref)
+    assert np.all(err <= 4.0 * math.sqrt(K) * U32 * mag + 1e-30), float((err / (mag + 1e-300)).max())
+
+
+def test_tc_product_matches_cuda_core_kernel_and_is_deterministic(handle):
+    m, n, d = 5000, 3000, 64
+    rng = np.random.default_rng(3)
+    A = _bf16(rng.standard_normal((m, n))).cuda()
+    X = torch.from_numpy(rng.standard_normal((n, d))).float().cuda()
+    y1 = handle.sketch(A, X)
+    y2 = handle.sketch(A, X)
+    assert torch.equal(y1, y2)
+    handle.set_option("bf16_simt", 1)
+    try:
+        ys = handle.sketch(A, X)
+    finally:
+        handle.set_option("bf16_simt", 0)
+    mag = (A.double().abs() @ X.to(torch.bfloat16).double().abs())
+    assert float(((y1.double() - ys.double()).abs() / mag).max()) <= 8.0 * math.sqrt(n) * U32
+
+
+def test_tc_product_full_size_sampled(handle):
+    """20000 x 20000 BF16 A, d = 220 (the bench's launch configuration): 64
+    sampled output rows (A X) and columns (A^T X) against FP64 products."""
+    m = n = 20000
+    d = 220
+    g = torch.Generator(device="cuda")
+    g.manual_seed(5)
+    A = torch.randn(m, n, generator=g, device="cuda").to(torch.bfloat16)
+    X = torch.randn(n, d, generator=g, device="cuda")
+    rows = np.random.default_rng(1).choice(m, 64, replace=False)
+    for trans in (False, True):
+        Y = handle.sketch(A, X, trans=trans)
+        Ys = Y[rows].double().cpu().numpy()
+        Xh = X.to(torch.bfloat16).double().cpu().numpy()
+        As = (A[:, rows].T if trans else A[rows]).double().cpu().numpy()
+        ref = As @ Xh
+        mag = np.abs(As) @ np.abs(Xh)
+        assert np.all(np.abs(Ys - ref) <= 4.0 * math.sqrt(n) * U32 * mag)
+
+
+def test_bf16_decompose_structure_small(handle):
+    m, n, k, p, q = 4000, 3000, 40, 10, 2
+    A, _, s, _ = wl.dense_spectral(77, m, n, wl.spectrum_gap(n, k, 1e-2), noise_std=2e-6)
+    Om = wl.omega(78, n, k + p)
+    Ag = torch.from_numpy(A).to(torch.bfloat16).cuda()
+    Q, L, P, flags = handle.decompose(Ag, torch.from_numpy(Om).cuda(), k, p, q)
+    Q, L, P = (t.double().cpu().numpy() for t in (Q, L, P))
+    d = k + p
+    assert np.all(np.triu(L, 1) == 0.0)
+    assert np.max(np.abs(Q.T @ Q - np.eye(d))) <= 2e-5
+    assert np.max(np.abs(P.T @ P - np.eye(d))) <= 2e-5
+    ref = oracle.ruqlp(A, Om, q)
+    r = oracle.residual_fro(A, Q, L, P)
+    r0 = oracle.residual_fro(A, ref["Q"], ref["L"], ref["P"])
+    assert r <= 1.3 * r0, (r, r0)
+    assert np.max(np.abs(np.abs(np.diag(L)) - np.abs(np.diag(ref["L"])))) <= 2e-3 * abs(ref["L"][0, 0])
+
+
+def test_bf16_decompose_full_size_residual_vs_fp64_oracle(handle):
+    """The bench workload (20000 x 20000, k=200, p=20, q=2, noise std 1e-6):
+    BF16 tensor-core residual <= 1.05x the FP64 oracle's on the same A."""
+    m = n = 20000
+    k, p, q = 200, 20, 2
+    sig = wl.spectrum_gap(n, k, 1e-2)
+    A32 = wl.dense_spectral_torch(20261, m, n, sig, noise_std=1e-6, device="cuda")
+    Om = wl.omega_torch(20262, n, k + p)
+    Ab = A32.to(torch.bfloat16)
+    Q, L, P, _ = handle.decompose(Ab, Om, k, p, q)
+    A64 = A32.double()
+    r_gpu = float(torch.linalg.norm(A64 - (Q.double() @ L.double()) @ P.double().T)
+                  / torch.linalg.norm(A64))
+    Ah = A32.double().cpu().numpy()
+    del A64
+    ref = oracle.ruqlp(Ah, Om.cpu().numpy(), q)
+    r0 = oracle.residual_fro(Ah, ref["Q"], ref["L"], ref["P"])
+    assert r_gpu <= 1.05 * r0, (r_gpu, r0)
