@@ -265,13 +265,15 @@ def main():
     floor = math.sqrt(float((sig[d:] ** 2).sum()) + (NOISE ** 2) * (m - d) * (n - d)) / math.sqrt(
         float((sig ** 2).sum()) + (NOISE ** 2) * m * n)
 
-    # live per-phase timing of the dominant kernels (CUDA events on the stream)
+    # live per-phase timing of the dominant kernels (CUDA events on the
+    # handle's stream, bracketing each launch)
     h.set_option("profile", 1)
     nprof = 2
     for _ in range(nprof):
         step()
     torch.cuda.synchronize()
-    prof = {ph: h.profile(ph) for ph in ("ax", "atx", "orth", "step")}
+    phases = ("ax", "atx", "orth", "step", "tc_ax", "tc_atx")
+    prof = {ph: h.profile(ph) for ph in phases}
     h.set_option("profile", 0)
     peaks = {}
     try:
@@ -279,27 +281,37 @@ def main():
     except OSError:
         pass
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
-    # dominant product phase (the one with the largest share of the step)
-    dom = max(("ax", "atx"), key=lambda ph: prof[ph][1])
-    cnt, tot = prof[dom]
-    avg_ms = tot / max(cnt, 1)
-    alg_bytes = bytes_a + (n + m) * d * (DT_BYTES[args.dtype] if args.dtype != "bf16" else 4)
-    flops = 2.0 * m * n * d
-    # SIMT path: FP32 (or FP64) FMA-bound; peak from unit counts and clock
     sm_mhz = ck.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
-    if args.dtype == "f64":
-        alu_peak = 152 * 4 * sm_mhz * 1e6 / 1e12           # 2 DFMA/clk/SM
+    phase_ms = {ph: (prof[ph][1] / prof[ph][0] if prof[ph][0] else None) for ph in phases}
+    share = {ph: prof[ph][1] / max(prof["step"][1], 1e-9) for ph in ("ax", "atx", "orth")}
+    if args.dtype == "bf16" and prof["tc_ax"][0]:
+        # the tcgen05 product kernel: one pass over A per launch.  Algorithmic
+        # bytes = A (BF16) + the skinny operand (dp x K, BF16) + the output
+        # (rows x dp, FP32); both orientations move the same bytes.
+        dp = (d + 15) // 16 * 16
+        alg = bytes_a + n * dp * 2 + m * dp * 4
+        cnt = prof["tc_ax"][0] + prof["tc_atx"][0]
+        avg = (prof["tc_ax"][1] + prof["tc_atx"][1]) / cnt
+        achieved = alg / (avg * 1e-3) / 1e9
+        roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                    "frac": achieved / hbm_peak, "traffic": None,
+                    "kernel": "k_tc_gemm (tcgen05 A X / A^T Y, one pass over A per launch)",
+                    "alg_bytes_per_launch": alg, "avg_launch_ms": avg, "launches": cnt,
+                    "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)",
+                    "phase_ms": phase_ms, "phase_share": share}
     else:
-        alu_peak = 152 * 256 * sm_mhz * 1e6 / 1e12         # 128 FFMA/clk/SM
-    achieved_tf = flops / (avg_ms * 1e-3) / 1e12
-    achieved_gbs = alg_bytes / (avg_ms * 1e-3) / 1e9
-    roofline = {"bound": "alu", "achieved": achieved_tf, "peak": alu_peak, "unit": "TFLOP/s",
-                "frac": achieved_tf / alu_peak, "traffic": None, "kernel": dom,
-                "hbm_achieved_gbs": achieved_gbs, "hbm_peak_gbs": hbm_peak,
-                "peak_source": "derived: 152 SMs x FMA lanes x 2 x median SM clock under load",
-                "phase_ms": {ph: (prof[ph][1] / max(prof[ph][0], 1)) for ph in prof},
-                "phase_share": {ph: prof[ph][1] / max(prof["step"][1], 1e-9)
-                                for ph in ("ax", "atx", "orth")}}
+        # CUDA-core products: FP32 (or FP64) multiply-add bound
+        dom = max(("ax", "atx"), key=lambda ph: prof[ph][1])
+        cnt, tot = prof[dom]
+        avg = tot / max(cnt, 1)
+        flops = 2.0 * m * n * d
+        alu_peak = 152 * (4 if args.dtype == "f64" else 256) * sm_mhz * 1e6 / 1e12
+        achieved = flops / (avg * 1e-3) / 1e12
+        roofline = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
+                    "frac": achieved / alu_peak, "traffic": None, "kernel": dom,
+                    "peak_source": "derived: 152 SMs x 2 (FP64) or 128 (FP32) FMA/clk x 2 x "
+                                   "median SM clock under load",
+                    "phase_ms": phase_ms, "phase_share": share}
 
     # end to end through the host entry point (pinned host buffers)
     e2e = None

@@ -145,6 +145,12 @@ ruqlp_status ruqlp_set_stream(ruqlp_handle h, void* cuda_stream);
  *   FP64 products in the Gram and an FP64 Cholesky (slow on GB300's FP64
  *   units); 0 (default) = shifted CholeskyQR3 in FP32 with FP64 sums across
  *   row slabs.  The FP64 path always uses the FP64 form.
+ *   "orth_full": 1 = on the FP32/BF16 paths every orth() of the power loop
+ *   takes three CholeskyQR passes (shifted CholeskyQR3); 0 (default) =
+ *   orth() results that only feed the next product take two (shifted, then
+ *   plain; same span, and in exact arithmetic the final Q, L, P are
+ *   identical because the bases differ by upper-triangular factors); the
+ *   last Q and P always take three.
  *   "bf16_simt": 1 = run BF16 products on the CUDA cores instead of the
  *   tensor cores (comparison baseline); 0 (default) = tensor cores.
  *   "profile": 1 = bracket every phase with CUDA events on the handle's
@@ -248,7 +254,9 @@ int64_t ruqlp_launch_count(void);
  *   "ax"   sketch products A X (Algorithm 1 step 3 / Algorithm 2),
  *   "atx"  transposed products A^T Y (Algorithm 2; B^T = A^T Q),
  *   "orth" whole orth() calls (Gram, Cholesky, triangular solve passes),
- *   "step" whole decompositions.
+ *   "step" whole decompositions,
+ *   "tc_ax" / "tc_atx" the tensor-core product kernel launches alone
+ *   (BF16 path; without operand transposes and the stream-K fix-up).
  * Errors: INVALID (unknown phase, NULL pointers). */
 ruqlp_status ruqlp_profile(ruqlp_handle h, const char* phase, int64_t* count, double* total_ms);
 

@@ -1,6 +1,8 @@
 // Internal launchers of the RU-QLP CUDA library (not part of the C ABI).
 #pragma once
 
+#include <functional>
+
 #include "common.cuh"
 
 namespace ruqlp {
@@ -41,15 +43,17 @@ cudaError_t chol_upper(const double* G, int d, double shift_rel, double* R, void
                        Ty tw, DevStatus* status, const int32_t* gate, cudaStream_t st,
                        Ty tf = Ty::F64, bool force_shift = false);
 
-// FP32 Cholesky + triangular inverse of a d x d FP64 Gram in one CTA
-// (d <= 288): Rinv (FP32, ld d, zero lower part) = R^{-1}, G + shift I = R^T R
-// with shift = shift_rel * trace(G) when force_shift (or after a breakdown).
-bool chol_inv_f32_supported(int d);
-cudaError_t chol_inv_f32(const double* G, int d, double shift_rel, bool force_shift, float* Rinv,
-                         DevStatus* status, const int32_t* gate, cudaStream_t st);
-// X (M x d, ld ldx) = Y (ld ldy) U for upper-triangular U (d x d, ld d); X may alias Y.
-cudaError_t mul_upper_f32(const float* Y, int64_t ldy, const float* U, float* X, int64_t ldx,
-                          int64_t M, int d, cudaStream_t st);
+// FP32 blocked Cholesky of a d x d FP64 Gram in one CTA (d <= 256):
+// G + shift I = R^T R (shift = shift_rel * trace(G) when force_shift or after
+// a breakdown).  `tiles` (chol_tiles_bytes(d)) receives the packed 32 x 32
+// upper tiles of R and the inverses of its diagonal tiles, which
+// trsm_tiles_f32 uses to form X = Y R^{-1} (X may alias Y).
+bool chol_tiles_supported(int d);
+size_t chol_tiles_bytes(int d);
+cudaError_t chol_tiles_f32(const double* G, int d, double shift_rel, bool force_shift,
+                           float* tiles, DevStatus* status, const int32_t* gate, cudaStream_t st);
+cudaError_t trsm_tiles_f32(const float* Y, int64_t ldy, const float* tiles, float* X, int64_t ldx,
+                           int64_t M, int d, cudaStream_t st);
 
 // C (d1 x d2, FP64, ld d2) = X^T W for FP32 X (M x d1, ld ldx) and W (M x d2,
 // ld ldw): FP32 products summed in FP32 within a row slab, slabs summed in
@@ -79,9 +83,11 @@ cudaError_t write_L(const double* R, int d, Ty tl, void* L, bool upper, cudaStre
 // trans = true: out[n x dp] = A^T Bt^T, with A (m x n, BF16, ld lda) and
 // Bt (dp x K, BF16, ld ldb, K = n or m).  frag: tc_frag_bytes(dp) of scratch
 // for the stream-K fragments; err: device word set on a wait timeout.
+// mark(true) / mark(false) are called right before / after the main kernel
+// launch (used to bracket it with profiling events); may be empty.
 cudaError_t tc_gemm(bool trans, const void* A, int64_t lda, int64_t m, int64_t n, const void* Bt,
                     int64_t ldb, int dp, float* out, int64_t ldo, float* frag, int* err,
-                    cudaStream_t st);
+                    cudaStream_t st, const std::function<void(bool)>& mark = {});
 size_t tc_frag_bytes(int dp);
 // Whether tc_gemm accepts these operands (alignment / size rules).
 bool tc_supported(const void* A, int64_t lda, int dp);

@@ -1,15 +1,15 @@
 // FP32 pieces of the shifted CholeskyQR3 orth() (Section II-A orth();
-// Fukaya, Kannan, Nakatsukasa, Yamamoto, Yanagisawa 2020) for d <= 288:
+// Fukaya, Kannan, Nakatsukasa, Yamamoto, Yanagisawa 2020) for d <= 256:
 //
-//  * k_chol_inv: one CTA factors the d x d Gram G (+ shift I) = R^T R and
-//    inverts R, both blocked in 32 x 32 tiles held in shared memory (upper
-//    block triangle, padded to a multiple of 32 with the identity).  Each
-//    32 x 32 diagonal factorisation / inversion is done by one warp with
-//    __syncwarp only; the panel solves and trailing updates spread over all
-//    warps, so the whole factorisation takes about 6 block barriers per tile
-//    row instead of 3 per column.
-//  * k_mul_upper: Q = Y R^{-1} as a product with the explicit upper-triangular
-//    inverse (rows of Y staged in shared memory, so Q may overwrite Y).
+//  * k_chol_tiles: one CTA factors the d x d Gram G (+ shift I) = R^T R,
+//    blocked in 32 x 32 tiles held in shared memory (upper block triangle,
+//    padded to a multiple of 32 with the identity).  Each diagonal tile is
+//    factored and inverted by one warp in registers (shuffles); the panel
+//    solves (products with the tile inverse) and trailing updates are 32 x 32
+//    tile products spread over all warps with 128-bit broadcast loads, so the
+//    factorisation needs three block barriers per tile row, not per column.
+//  * k_trsm_tiles: Q = Y R^{-1} by blocked forward substitution with those
+//    tiles (rows of Y staged in shared memory, so Q may overwrite Y).
 #include <math.h>
 
 #include "../../include/ruqlp.h"
@@ -19,27 +19,115 @@ namespace ruqlp {
 namespace {
 
 constexpr int TB = 32;        // tile edge
-constexpr int TP = TB + 1;    // padded row pitch (bank-conflict free column walks)
-constexpr int MAXNB = 9;      // d <= 288
-constexpr int NTH = 256;   // 8 warps: up to 255 registers for the per-lane tile columns
+constexpr int TP = 36;        // row pitch: 16-byte aligned rows for 128-bit loads
+constexpr int MAXNB = 8;      // d <= 256
+constexpr int NTH = 512;      // 16 warps; up to 128 registers for per-lane tile columns
+constexpr size_t TILE_FLOATS = (size_t)TB * TP;
 
 __device__ __forceinline__ int bidx(int I, int J, int nb) { return I * nb - (I * (I - 1)) / 2 + (J - I); }
 
+// acc[r] (r = r0..r0+7) += sum_k A[k][r] * bcol[k] for one lane's column
+// bcol (in registers).  A is a 32 x 32 tile in shared memory (pitch TP); each
+// 128-bit load of A serves 4 rows, and the 8 rows are independent chains.
+__device__ __forceinline__ void tile_tn8(const float* __restrict__ A, int r0, const float (&bcol)[TB],
+                                         float (&acc)[8]) {
+#pragma unroll
+  for (int k = 0; k < TB; ++k) {
+    const float4 a0 = *reinterpret_cast<const float4*>(A + k * TP + r0);
+    const float4 a1 = *reinterpret_cast<const float4*>(A + k * TP + r0 + 4);
+    acc[0] = fmaf(a0.x, bcol[k], acc[0]);
+    acc[1] = fmaf(a0.y, bcol[k], acc[1]);
+    acc[2] = fmaf(a0.z, bcol[k], acc[2]);
+    acc[3] = fmaf(a0.w, bcol[k], acc[3]);
+    acc[4] = fmaf(a1.x, bcol[k], acc[4]);
+    acc[5] = fmaf(a1.y, bcol[k], acc[5]);
+    acc[6] = fmaf(a1.z, bcol[k], acc[6]);
+    acc[7] = fmaf(a1.w, bcol[k], acc[7]);
+  }
+}
+
+__device__ __forceinline__ void load_col(const float* __restrict__ T, int lane, float (&c)[TB]) {
+#pragma unroll
+  for (int k = 0; k < TB; ++k) c[k] = T[k * TP + lane];
+}
+
+// One warp factors the 32 x 32 tile B = R^T R in registers (lane c owns
+// column c) and writes R (upper) back and S = R^{-1} (upper) to Sout.
+// Step k broadcasts row k of the partially reduced tile through the shared
+// row buffer rb (one store per lane, 128-bit broadcast loads), so every lane
+// forms r_ki itself; there are no shuffles and no branches in the loop.
+// Reciprocal square roots and reciprocals replace IEEE sqrt/divide (the
+// factor only has to be consistent with the solve that uses it).  A
+// non-positive pivot is replaced by bad_fill; the return value (same in every
+// lane) reports whether that happened.
+__device__ bool factor_tile(float* __restrict__ B, float* __restrict__ Sout, float* __restrict__ dinv,
+                            float* __restrict__ rb, int lane, float bad_fill) {
+  float col[TB];
+  load_col(B, lane, col);
+  float myinv = 0.f;  // 1 / R[lane][lane]
+  bool bad = false;
+#pragma unroll
+  for (int k = 0; k < TB; ++k) {
+    __syncwarp();
+    rb[lane] = col[k];  // row k of the current tile, lane c holds B[k][c]
+    __syncwarp();
+    float piv = rb[k];
+    const bool nonpos = !(piv > 0.f) || !(piv < 3.0e38f);
+    bad = bad || nonpos;
+    piv = nonpos ? bad_fill : piv;
+    const float rinv = rsqrtf(piv);
+    const float rkc = (lane == k) ? piv * rinv : col[k] * rinv;  // r_kc for c >= k
+    myinv = (lane == k) ? rinv : myinv;
+    col[k] = (lane >= k) ? rkc : col[k];
+#pragma unroll
+    for (int i = k + 1; i < TB; ++i) {
+      const float rki = rb[i] * rinv;
+      const float upd = fmaf(-rki, rkc, col[i]);
+      col[i] = (lane >= i) ? upd : col[i];
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < TB; ++r) B[r * TP + lane] = (r <= lane) ? col[r] : 0.f;
+  dinv[lane] = myinv;
+  __syncwarp();
+  // S = R^{-1}, right-looking: lane c solves R x = e_c from the bottom;
+  // acc[j] -= R[j][r] x[r] for j < r are independent multiply-adds
+  float acc[TB];
+#pragma unroll
+  for (int r = 0; r < TB; ++r) acc[r] = (r == lane) ? 1.f : 0.f;
+#pragma unroll
+  for (int r = TB - 1; r >= 0; --r) {
+    const float xr = acc[r] * dinv[r];
+    acc[r] = xr;
+#pragma unroll
+    for (int j = 0; j < r; ++j) acc[j] = fmaf(-B[j * TP + r], xr, acc[j]);
+  }
+#pragma unroll
+  for (int r = 0; r < TB; ++r) Sout[r * TP + lane] = acc[r];
+  return !bad;
+}
+
+// Blocked Cholesky G (+ shift I) = R^T R, d <= 256, one CTA.  Writes the
+// upper tiles R_IJ (I <= J) and the diagonal-tile inverses R_KK^{-1}, FP32,
+// 32 x 32 row-major each, to `tiles`: first the nb (nb+1)/2 R tiles in
+// row-of-tiles order, then the nb inverse tiles.
 __global__ void __launch_bounds__(NTH)
-k_chol_inv(const double* __restrict__ G, int d, double shift_rel, int force_shift,
-           float* __restrict__ Rinv, DevStatus* __restrict__ status,
-           const int32_t* __restrict__ gate) {
+k_chol_tiles(const double* __restrict__ G, int d, double shift_rel, int force_shift,
+             float* __restrict__ tiles, DevStatus* __restrict__ status,
+             const int32_t* __restrict__ gate) {
   if (gate != nullptr && *gate == 0) return;
-  extern __shared__ float sm[];
+  extern __shared__ __align__(16) float sm[];
   __shared__ double s_shift;
   __shared__ int s_bad, s_rankdef;
-  __shared__ float S[TB][TP];  // inverse of the current diagonal tile
+  __shared__ float s_dinv[TB];
+  __shared__ float s_row[TB];
   const int nb = (d + TB - 1) / TB;
+  const int ntiles = nb * (nb + 1) / 2;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = NTH / 32;
-  auto tile = [&](int I, int J) { return sm + (size_t)bidx(I, J, nb) * TB * TP; };
+  auto tile = [&](int I, int J) { return sm + (size_t)bidx(I, J, nb) * TILE_FLOATS; };
+  auto dinv_s = [&](int K) { return sm + (size_t)(ntiles + K) * TILE_FLOATS; };  // shared
 
-  // shift = shift_rel * trace(G), reduced by warp 0
-  if (warp == 0) {
+  if (warp == 0) {  // shift = shift_rel * trace(G)
     double t = 0.0;
     for (int i = lane; i < d; i += 32) t += G[(size_t)i * d + i];
     for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
@@ -54,159 +142,79 @@ k_chol_inv(const double* __restrict__ G, int d, double shift_rel, int force_shif
   for (; attempt < 2; ++attempt) {
     __syncthreads();
     const double add = attempt ? s_shift : 0.0;
-    // load the upper block triangle (padding: identity)
-    const int ntiles = nb * (nb + 1) / 2;
-    for (int e = tid; e < ntiles * TB * TB; e += NTH) {
-      const int t = e / (TB * TB), rc = e % (TB * TB), r = rc / TB, c = rc % TB;
+    for (int t = warp; t < ntiles; t += nw) {  // upper block triangle of G + shift
       int I = 0, tt = t;
       while (tt >= nb - I) { tt -= nb - I; ++I; }
       const int J = I + tt;
-      const int i = I * TB + r, j = J * TB + c;
-      double v;
-      if (i < d && j < d) v = G[(size_t)i * d + j] + (i == j ? add : 0.0);
-      else v = (i == j) ? 1.0 : 0.0;
-      tile(I, J)[r * TP + c] = (float)v;
+      float* T = tile(I, J);
+      const int j = J * TB + lane;
+      float v[TB];
+#pragma unroll
+      for (int r = 0; r < TB; ++r) {
+        const int i = I * TB + r;
+        double x;
+        if (i < d && j < d) x = G[(size_t)i * d + j] + (i == j ? add : 0.0);
+        else x = (i == j) ? 1.0 : 0.0;
+        v[r] = (float)x;
+      }
+#pragma unroll
+      for (int r = 0; r < TB; ++r) T[r * TP + lane] = v[r];
     }
     if (tid == 0) s_bad = 0;
     __syncthreads();
     for (int K = 0; K < nb; ++K) {
-      // (a) factor the diagonal tile: warp 0, lane c owns column c
-      if (warp == 0) {
-        float* B = tile(K, K);
-        for (int k = 0; k < TB; ++k) {
-          __syncwarp();
-          float piv = B[k * TP + k];
-          if (!(piv > 0.f) || !isfinite(piv)) {
-            if (attempt == 0) {
-              if (lane == 0) s_bad = 1;
-              break;  // uniform: every lane read the same pivot
-            }
-            piv = (float)s_shift;
-            if (lane == 0) s_rankdef = 1;
-          }
-          const float rkk = sqrtf(piv);
-          float bk = B[k * TP + lane];
-          __syncwarp();
-          if (lane == k) B[k * TP + k] = rkk;
-          else if (lane > k) B[k * TP + lane] = bk / rkk;
-          __syncwarp();
-          if (lane > k) {
-            const float rkl = B[k * TP + lane];
-            for (int i = k + 1; i <= lane; ++i) B[i * TP + lane] -= B[k * TP + i] * rkl;
-          }
+      if (warp == 0) {  // (a) diagonal tile, its inverse (kept in shared memory)
+        const bool ok = factor_tile(tile(K, K), dinv_s(K), s_dinv, s_row, lane,
+                                    attempt == 0 ? 1.f : (float)s_shift);
+        if (lane == 0 && !ok) {
+          if (attempt == 0) s_bad = 1;  // retry on G + shift I
+          else s_rankdef = 1;           // pivots replaced by the shift
         }
       }
       __syncthreads();
       if (s_bad) break;
-      // (b) panel: B_KJ <- R_KK^{-T} B_KJ for J > K (forward substitution)
+      // (b) panel B_KJ <- R_KK^{-T} B_KJ: one warp per tile; each lane reads
+      // and writes only its own column
       for (int J = K + 1 + warp; J < nb; J += nw) {
-        const float* R = tile(K, K);
         float* B = tile(K, J);
-        float x[TB];
+        float bc[TB];
+        load_col(B, lane, bc);
 #pragma unroll
-        for (int r = 0; r < TB; ++r) {
-          float acc = B[r * TP + lane];
+        for (int q = 0; q < 4; ++q) {
+          float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+          tile_tn8(dinv_s(K), q * 8, bc, acc);
 #pragma unroll
-          for (int k = 0; k < r; ++k) acc -= R[k * TP + r] * x[k];
-          x[r] = acc / R[r * TP + r];
+          for (int i = 0; i < 8; ++i) B[(q * 8 + i) * TP + lane] = acc[i];
         }
-#pragma unroll
-        for (int r = 0; r < TB; ++r) B[r * TP + lane] = x[r];
       }
       __syncthreads();
-      // (c) trailing update: B_IJ -= B_KI^T B_KJ for K < I <= J
+      // (c) trailing update B_IJ -= B_KI^T B_KJ, items (I, J, 8-row slice)
       const int rem = nb - K - 1;
-      const int nupd = rem * (rem + 1) / 2;
+      const int nupd = rem * (rem + 1) / 2 * 4;
       for (int u = warp; u < nupd; u += nw) {
-        int I = 0, tt = u;
+        int I = 0, tt = u / 4;
         while (tt >= rem - I) { tt -= rem - I; ++I; }
         I += K + 1;
-        const int J = I + tt;
-        const float* BI = tile(K, I);
-        const float* BJ = tile(K, J);
+        const int J = I + tt, r0 = (u % 4) * 8;
+        float bc[TB];
+        load_col(tile(K, J), lane, bc);
+        float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        tile_tn8(tile(K, I), r0, bc, acc);
         float* C = tile(I, J);
-        float bj[TB];
 #pragma unroll
-        for (int k = 0; k < TB; ++k) bj[k] = BJ[k * TP + lane];
-#pragma unroll 4
-        for (int r = 0; r < TB; ++r) {
-          float acc = C[r * TP + lane];
-#pragma unroll
-          for (int k = 0; k < TB; ++k) acc -= BI[k * TP + r] * bj[k];
-          C[r * TP + lane] = acc;
-        }
+        for (int i = 0; i < 8; ++i) C[(r0 + i) * TP + lane] -= acc[i];
       }
       __syncthreads();
     }
     if (!s_bad) break;
   }
   __syncthreads();
-
-  // inverse X = R^{-1}, tile rows from the bottom, in place of R
-  for (int I = nb - 1; I >= 0; --I) {
-    if (warp == 0) {  // S = R_II^{-1} by back substitution, lane c owns column c
-      const float* R = tile(I, I);
-      float x[TB];
-#pragma unroll
-      for (int r = TB - 1; r >= 0; --r) {
-        float acc = (r == lane) ? 1.f : 0.f;
-#pragma unroll
-        for (int k = r + 1; k < TB; ++k) acc -= R[r * TP + k] * x[k];
-        x[r] = acc / R[r * TP + r];
-      }
-#pragma unroll
-      for (int r = 0; r < TB; ++r) S[r][lane] = x[r];
-    }
-    __syncthreads();
-    // X_IJ = -S (sum_{K=I+1..J} R_IK X_KJ) for J > I (rows K > I already hold X)
-    float out[TB];
-    const int J = I + 1 + warp;
-    const bool mine = J < nb;  // nb - 1 - I <= 8 = warps: one tile per warp
-    if (mine) {
-      float t[TB];
-#pragma unroll
-      for (int r = 0; r < TB; ++r) t[r] = 0.f;
-      for (int K = I + 1; K <= J; ++K) {
-        const float* RK = tile(I, K);
-        const float* XK = tile(K, J);
-        float xk[TB];
-#pragma unroll
-        for (int k = 0; k < TB; ++k) xk[k] = XK[k * TP + lane];
-#pragma unroll
-        for (int r = 0; r < TB; ++r) {
-          float acc = t[r];
-#pragma unroll
-          for (int k = 0; k < TB; ++k) acc += RK[r * TP + k] * xk[k];
-          t[r] = acc;
-        }
-      }
-#pragma unroll
-      for (int r = 0; r < TB; ++r) {
-        float acc = 0.f;
-#pragma unroll
-        for (int k = 0; k < TB; ++k) acc -= S[r][k] * t[k];
-        out[r] = acc;
-      }
-    }
-    __syncthreads();
-    if (mine) {
-      float* X = tile(I, J);
-#pragma unroll
-      for (int r = 0; r < TB; ++r) X[r * TP + lane] = out[r];
-    }
-    if (warp == nw - 1) {
-      float* X = tile(I, I);
-#pragma unroll
-      for (int r = 0; r < TB; ++r) X[r * TP + lane] = S[r][lane];
-    }
-    __syncthreads();
-  }
-  // write R^{-1} (row-major, ld d, zero lower triangle)
-  for (int e = tid; e < d * d; e += NTH) {
-    const int i = e / d, j = e % d;
-    float v = 0.f;
-    if (j >= i) v = tile(i / TB, j / TB)[(i % TB) * TP + (j % TB)];
-    Rinv[e] = v;
+  // write R tiles and the diagonal-tile inverses (32 x 32 row-major each)
+  for (int t = warp; t < ntiles + nb; t += nw) {
+    const float* src = sm + (size_t)t * TILE_FLOATS;
+    float* dst = tiles + (size_t)t * TB * TB;
+#pragma unroll 8
+    for (int r = 0; r < TB; ++r) dst[r * TB + lane] = src[r * TP + lane];
   }
   if (tid == 0) {
     if (attempt > 0) {
@@ -217,98 +225,194 @@ k_chol_inv(const double* __restrict__ G, int d, double shift_rel, int force_shif
   }
 }
 
-// X = Y U for upper-triangular U (d x d, ld d): 64-row blocks of Y are staged
-// in shared memory first, so X may alias Y.
-constexpr int MR = 64;
-__global__ void __launch_bounds__(256)
-k_mul_upper(const float* __restrict__ Y, int64_t ldy, const float* __restrict__ U, float* X,
-            int64_t ldx, int64_t M, int d) {
-  extern __shared__ float ys[];  // MR x (d + 1)
-  __shared__ float us[32][64];
-  const int pitch = d + 1;
-  const int64_t r0 = (int64_t)blockIdx.x * MR;
-  const int nr = (int)min((int64_t)MR, M - r0);
-  const int t = threadIdx.x, tx = t & 15, ty = t >> 4;
-  for (int e = t; e < MR * d; e += 256) {
-    const int r = e / d, c = e % d;
-    ys[r * pitch + c] = (r < nr) ? Y[(r0 + r) * ldy + c] : 0.f;
-  }
-  __syncthreads();
-  for (int c0 = 0; c0 < d; c0 += 64) {
-    float acc[4][4];
+// X = Y R^{-1} by blocked forward substitution over 32-column tiles:
+//   X_J = (Y_J - sum_{K<J} X_K R_KJ) R_JJ^{-1}.
+// A CTA owns 32 rows, staged in shared memory (so X may alias Y).  R tiles
+// and diagonal-tile inverses come from k_chol_tiles' packed layout; they are
+// fetched with cp.async NPF tiles ahead of their use (L2 latency is long).
+constexpr int SR = 32;
+constexpr int NPF = 4;  // tile buffers (prefetch distance NPF - 1)
+__global__ void __launch_bounds__(128)
+k_trsm_tiles(const float* __restrict__ Y, int64_t ldy, const float* __restrict__ tiles, float* X,
+             int64_t ldx, int64_t M, int d) {
+  extern __shared__ __align__(16) float ys[];  // SR x pitch
+  __shared__ __align__(16) float Rt[NPF][TB][TB];
+  const int nb = (d + TB - 1) / TB;
+  const int ntiles = nb * (nb + 1) / 2;
+  const int pitch = nb * TB + 4;
+  const int64_t r0 = (int64_t)blockIdx.x * SR;
+  const int nr = (int)min((int64_t)SR, M - r0);
+  const int t = threadIdx.x;
+  // stage the rows (float4 when the row pitch allows it)
+  const int nv = nb * TB / 4;  // float4s per padded row
+  const bool vec = (ldy % 4 == 0) && (((uintptr_t)Y & 15) == 0);
+  // loads are issued in batches of 8 before their stores, so 8 are in flight
+  for (int e0 = t; e0 < SR * nv; e0 += 8 * 128) {
+    float4 v[8];
 #pragma unroll
-    for (int i = 0; i < 4; ++i)
-#pragma unroll
-      for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
-    const int kmax = min(d, c0 + 64);  // U[k][c] = 0 for k > c
-    for (int k0 = 0; k0 < kmax; k0 += 32) {
-      for (int e = t; e < 32 * 64; e += 256) {
-        const int kk = e / 64, cc = e % 64;
-        const int k = k0 + kk, c = c0 + cc;
-        us[kk][cc] = (k < d && c < d) ? U[(size_t)k * d + c] : 0.f;
+    for (int q = 0; q < 8; ++q) {
+      const int e = e0 + q * 128;
+      v[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (e < SR * nv) {
+        const int r = e / nv, c = (e % nv) * 4;
+        if (r < nr) {
+          const float* p = Y + (r0 + r) * ldy + c;
+          if (vec && c + 3 < d) v[q] = *reinterpret_cast<const float4*>(p);
+          else {
+            if (c < d) v[q].x = p[0];
+            if (c + 1 < d) v[q].y = p[1];
+            if (c + 2 < d) v[q].z = p[2];
+            if (c + 3 < d) v[q].w = p[3];
+          }
+        }
       }
-      __syncthreads();
-#pragma unroll 8
-      for (int kk = 0; kk < 32; ++kk) {
-        const int k = k0 + kk;
-        if (k >= d) break;
-        float a[4], b[4];
-#pragma unroll
-        for (int i = 0; i < 4; ++i) a[i] = ys[(ty * 4 + i) * pitch + k];
-#pragma unroll
-        for (int j = 0; j < 4; ++j) b[j] = us[kk][tx * 4 + j];
-#pragma unroll
-        for (int i = 0; i < 4; ++i)
-#pragma unroll
-          for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
-      }
-      __syncthreads();
     }
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const int r = ty * 4 + i;
-      if (r >= nr) continue;
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const int c = c0 + tx * 4 + j;
-        if (c < d) X[(r0 + r) * ldx + c] = acc[i][j];
+    for (int q = 0; q < 8; ++q) {
+      const int e = e0 + q * 128;
+      if (e < SR * nv) {
+        const int r = e / nv, c = (e % nv) * 4;
+        *reinterpret_cast<float4*>(ys + r * pitch + c) = v[q];
       }
+    }
+  }
+  // sequence of tiles used: for J: R_0J .. R_{J-1}J, then inv(R_JJ)
+  auto tile_ptr = [&](int J, int K) {
+    return (K < J) ? tiles + (size_t)bidx(K, J, nb) * TB * TB
+                   : tiles + (size_t)(ntiles + J) * TB * TB;
+  };
+  // asynchronous copy of one 4 KB tile (2 x 16 bytes per thread)
+  auto fetch = [&](int b, const float* src) {
+    for (int e = t; e < TB * TB / 4; e += 128) {
+      const uint32_t dst = (uint32_t)__cvta_generic_to_shared(&Rt[b][0][0] + 4 * e);
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src + 4 * e)
+                   : "memory");
+    }
+  };
+  const int row = t >> 2, c0 = (t & 3) * 8;
+  float* yr = ys + row * pitch;
+  // the tile sequence is (J=0: inv00), (J=1: R01, inv11), (J=2: R02, R12, inv22) ...
+  // step s -> (J, K) with K <= J; total nb (nb + 1) / 2 steps
+  const int nsteps = nb * (nb + 1) / 2;
+  auto step_tile = [&](int sidx) {
+    int J = 0;
+    while (sidx > J) { sidx -= J + 1; ++J; }
+    return tile_ptr(J, sidx);
+  };
+  for (int q = 0; q < NPF - 1; ++q) {
+    if (q < nsteps) fetch(q % NPF, step_tile(q));
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  }
+  int sidx = 0;
+  for (int J = 0; J < nb; ++J) {
+    float acc[8];
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < 8; ++i) acc[i] = yr[J * TB + c0 + i];
+    for (int K = 0; K <= J; ++K, ++sidx) {
+      __syncthreads();  // everyone is done with the buffer about to be refilled
+      if (sidx + NPF - 1 < nsteps) fetch((sidx + NPF - 1) % NPF, step_tile(sidx + NPF - 1));
+      asm volatile("cp.async.commit_group;" ::: "memory");
+      if (K == J) {
+        // stage the updated tile of this row, then multiply by R_JJ^{-1}
+#pragma unroll
+        for (int i = 0; i < 8; ++i) yr[J * TB + c0 + i] = acc[i];
+      }
+      asm volatile("cp.async.wait_group %0;" ::"n"(NPF - 1) : "memory");  // step's tile landed
+      __syncthreads();
+      const float* R = &Rt[sidx % NPF][0][0];
+      if (K < J) {
+#pragma unroll 8
+        for (int k = 0; k < TB; ++k) {
+          const float x = yr[K * TB + k];
+          const float4 a0 = *reinterpret_cast<const float4*>(R + k * TB + c0);
+          const float4 a1 = *reinterpret_cast<const float4*>(R + k * TB + c0 + 4);
+          acc[0] = fmaf(-x, a0.x, acc[0]);
+          acc[1] = fmaf(-x, a0.y, acc[1]);
+          acc[2] = fmaf(-x, a0.z, acc[2]);
+          acc[3] = fmaf(-x, a0.w, acc[3]);
+          acc[4] = fmaf(-x, a1.x, acc[4]);
+          acc[5] = fmaf(-x, a1.y, acc[5]);
+          acc[6] = fmaf(-x, a1.z, acc[6]);
+          acc[7] = fmaf(-x, a1.w, acc[7]);
+        }
+      } else {
+        float out[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll 8
+        for (int k = 0; k < TB; ++k) {
+          const float x = yr[J * TB + k];
+          const float4 a0 = *reinterpret_cast<const float4*>(R + k * TB + c0);
+          const float4 a1 = *reinterpret_cast<const float4*>(R + k * TB + c0 + 4);
+          out[0] = fmaf(x, a0.x, out[0]);
+          out[1] = fmaf(x, a0.y, out[1]);
+          out[2] = fmaf(x, a0.z, out[2]);
+          out[3] = fmaf(x, a0.w, out[3]);
+          out[4] = fmaf(x, a1.x, out[4]);
+          out[5] = fmaf(x, a1.y, out[5]);
+          out[6] = fmaf(x, a1.z, out[6]);
+          out[7] = fmaf(x, a1.w, out[7]);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < 8; ++i) yr[J * TB + c0 + i] = out[i];
+      }
+    }
+  }
+  asm volatile("cp.async.wait_group 0;" ::: "memory");
+  __syncthreads();
+  const bool vecx = (ldx % 4 == 0) && (((uintptr_t)X & 15) == 0);
+  for (int e = t; e < SR * nv; e += 128) {
+    const int r = e / nv, c = (e % nv) * 4;
+    if (r >= nr || c >= d) continue;
+    const float4 v = *reinterpret_cast<const float4*>(ys + r * pitch + c);
+    float* p = X + (r0 + r) * ldx + c;
+    if (vecx && c + 3 < d) *reinterpret_cast<float4*>(p) = v;
+    else {
+      p[0] = v.x;
+      if (c + 1 < d) p[1] = v.y;
+      if (c + 2 < d) p[2] = v.z;
+      if (c + 3 < d) p[3] = v.w;
     }
   }
 }
 
 }  // namespace
 
-size_t chol_inv_f32_smem(int d) {
+size_t chol_tiles_smem(int d) {
   const int nb = (d + TB - 1) / TB;
-  return (size_t)nb * (nb + 1) / 2 * TB * TP * sizeof(float);
+  return ((size_t)nb * (nb + 1) / 2 + nb) * TILE_FLOATS * sizeof(float);
 }
 
-bool chol_inv_f32_supported(int d) {
-  return d >= 1 && (d + TB - 1) / TB <= MAXNB && chol_inv_f32_smem(d) <= 200 * 1024;
+bool chol_tiles_supported(int d) {
+  return d >= 1 && (d + TB - 1) / TB <= MAXNB && chol_tiles_smem(d) <= 220 * 1024;
 }
 
-cudaError_t chol_inv_f32(const double* G, int d, double shift_rel, bool force_shift, float* Rinv,
-                         DevStatus* status, const int32_t* gate, cudaStream_t st) {
-  if (!chol_inv_f32_supported(d)) return cudaErrorInvalidValue;
-  const size_t sm = chol_inv_f32_smem(d);
+size_t chol_tiles_bytes(int d) {
+  const int nb = (d + TB - 1) / TB;
+  return ((size_t)nb * (nb + 1) / 2 + nb) * TB * TB * sizeof(float);
+}
+
+cudaError_t chol_tiles_f32(const double* G, int d, double shift_rel, bool force_shift,
+                           float* tiles, DevStatus* status, const int32_t* gate, cudaStream_t st) {
+  if (!chol_tiles_supported(d)) return cudaErrorInvalidValue;
+  const size_t sm = chol_tiles_smem(d);
   cudaError_t e =
-      cudaFuncSetAttribute(k_chol_inv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+      cudaFuncSetAttribute(k_chol_tiles, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
-  k_chol_inv<<<1, NTH, sm, st>>>(G, d, shift_rel, force_shift ? 1 : 0, Rinv, status, gate);
+  k_chol_tiles<<<1, NTH, sm, st>>>(G, d, shift_rel, force_shift ? 1 : 0, tiles, status, gate);
   count_launch();
   return cudaGetLastError();
 }
 
-cudaError_t mul_upper_f32(const float* Y, int64_t ldy, const float* U, float* X, int64_t ldx,
-                          int64_t M, int d, cudaStream_t st) {
+cudaError_t trsm_tiles_f32(const float* Y, int64_t ldy, const float* tiles, float* X, int64_t ldx,
+                           int64_t M, int d, cudaStream_t st) {
   if (M <= 0) return cudaSuccess;
-  const size_t sm = (size_t)MR * (d + 1) * sizeof(float);
-  if (sm > 200 * 1024) return cudaErrorInvalidValue;
+  const int nb = (d + TB - 1) / TB;
+  const size_t sm = (size_t)SR * (nb * TB + 4) * sizeof(float);
   cudaError_t e =
-      cudaFuncSetAttribute(k_mul_upper, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+      cudaFuncSetAttribute(k_trsm_tiles, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
-  k_mul_upper<<<ceil_div(M, MR), 256, sm, st>>>(Y, ldy, U, X, ldx, M, d);
+  k_trsm_tiles<<<ceil_div(M, SR), 128, sm, st>>>(Y, ldy, tiles, X, ldx, M, d);
   count_launch();
   return cudaGetLastError();
 }

@@ -469,7 +469,7 @@ size_t tc_frag_bytes(int dp) { return (size_t)sm_count() * 2 * BM * dp * sizeof(
 
 cudaError_t tc_gemm(bool trans, const void* A, int64_t lda, int64_t m, int64_t n, const void* Bt,
                     int64_t ldb, int dp, float* out, int64_t ldo, float* frag, int* err,
-                    cudaStream_t st) {
+                    cudaStream_t st, const std::function<void(bool)>& mark) {
   if (dp < 16 || dp > 256 || dp % 16 != 0) return cudaErrorInvalidValue;
   if (lda % 8 != 0 || ldb % 8 != 0 || ((uintptr_t)A & 15) || ((uintptr_t)Bt & 15) || ldo % 4 != 0 ||
       ((uintptr_t)out & 15))
@@ -501,18 +501,17 @@ cudaError_t tc_gemm(bool trans, const void* A, int64_t lda, int64_t m, int64_t n
   if (stages < 2) return cudaErrorInvalidValue;
   p.stages = stages;
   const size_t smem = 1024 + stages * stage_bytes + 8 * (2 * stages + 5) + 16;
-  cudaError_t e;
-  if (trans) {
-    e = cudaFuncSetAttribute(k_tc_gemm<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem);
-    if (e != cudaSuccess) return e;
-    k_tc_gemm<true><<<P, NTHREADS, smem, st>>>(mA, mB, p);
-  } else {
-    e = cudaFuncSetAttribute(k_tc_gemm<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem);
-    if (e != cudaSuccess) return e;
-    k_tc_gemm<false><<<P, NTHREADS, smem, st>>>(mA, mB, p);
-  }
+  cudaError_t e = trans ? cudaFuncSetAttribute(k_tc_gemm<true>,
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)smem)
+                        : cudaFuncSetAttribute(k_tc_gemm<false>,
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)smem);
+  if (e != cudaSuccess) return e;
+  if (mark) mark(true);
+  if (trans) k_tc_gemm<true><<<P, NTHREADS, smem, st>>>(mA, mB, p);
+  else k_tc_gemm<false><<<P, NTHREADS, smem, st>>>(mA, mB, p);
+  if (mark) mark(false);
   count_launch();
   e = cudaGetLastError();
   if (e != cudaSuccess || p.tail == 0) return e;

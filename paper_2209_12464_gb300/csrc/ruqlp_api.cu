@@ -5,6 +5,7 @@
 #include <atomic>
 #include <mutex>
 #include <stdio.h>
+#include <functional>
 #include <vector>
 #include <stdarg.h>
 #include <string.h>
@@ -27,14 +28,16 @@ struct ruqlp_ctx {
   std::string err;
   // policy knobs (ruqlp_set_option)
   int orth_fp64 = 0;    // FP32/BF16 paths: CholeskyQR2 with FP64 Gram and Cholesky
+  int orth_full = 0;    // 1: every orth() takes three CholeskyQR passes (else the
+                        // intermediate ones take two)
   int bf16_simt = 0;    // 1: BF16 products on CUDA cores instead of tensor cores
   // phase timing with CUDA events on the handle's stream (option "profile")
   bool profile = false;
   struct Span { int cat; cudaEvent_t a, b; };
   std::vector<Span> spans;
   std::vector<cudaEvent_t> pool;
-  int64_t prof_count[4] = {0, 0, 0, 0};
-  double prof_ms[4] = {0, 0, 0, 0};
+  int64_t prof_count[6] = {0, 0, 0, 0, 0, 0};
+  double prof_ms[6] = {0, 0, 0, 0, 0, 0};
 };
 
 namespace ruqlp {
@@ -67,10 +70,13 @@ ruqlp_status fail(ruqlp_ctx* h, ruqlp_status s, const char* fmt, ...) {
                   cudaGetErrorString(e_), __FILE__, __LINE__);                     \
   } while (0)
 
-// Profile categories: sketch products A X, transposed products A^T Y, orth(),
-// and the whole decomposition.
-enum { PROF_AX = 0, PROF_ATX = 1, PROF_ORTH = 2, PROF_STEP = 3 };
-const char* kProfNames[4] = {"ax", "atx", "orth", "step"};
+// Profile categories: sketch products A X, transposed products A^T Y (whole
+// product phases), orth(), the whole decomposition, and the tensor-core
+// product kernel launches alone (k_tc_gemm, without operand transposes or the
+// stream-K fix-up) for A X and A^T Y.
+enum { PROF_AX = 0, PROF_ATX = 1, PROF_ORTH = 2, PROF_STEP = 3, PROF_TC_AX = 4, PROF_TC_ATX = 5 };
+const int kProfN = 6;
+const char* kProfNames[kProfN] = {"ax", "atx", "orth", "step", "tc_ax", "tc_atx"};
 
 cudaEvent_t ev_get(ruqlp_ctx* h) {
   if (!h->pool.empty()) {
@@ -154,7 +160,11 @@ Layout layout_of(int64_t m, int64_t n, int d, Ty ct) {
   L.partial = take((size_t)kMaxSplits * d * d * sizeof(double));
   L.G = take((size_t)d * d * sizeof(double));
   L.R = take((size_t)d * d * sizeof(double));
-  L.Rw = take((size_t)d * d * sizeof(double));
+  {
+    size_t rw = (size_t)d * d * sizeof(double);
+    if (chol_tiles_supported(d) && chol_tiles_bytes(d) > rw) rw = chol_tiles_bytes(d);
+    L.Rw = take(rw);
+  }
   if (ct == Ty::BF16) {
     L.Bt = take((size_t)dp * round8(m > n ? m : n) * 2);
     L.frag = take(dp <= 256 ? tc_frag_bytes(dp) : 0);
@@ -239,7 +249,7 @@ struct Job {
 //    slabs.  (A single-SM FP64 Cholesky of a 220 x 220 Gram costs ~0.45 ms on
 //    GB300, whose FP64 rate is 1/58 of FP32.)
 ruqlp_status orth(ruqlp_ctx* h, const Layout& Lo, const Job& J, const void* Yin, void* Qout,
-                  int64_t M) {
+                  int64_t M, bool final_basis = true) {
   ProfScope ps(h, PROF_ORTH);
   char* base = (char*)h->arena;
   double* partial = (double*)(base + Lo.partial);
@@ -252,13 +262,14 @@ ruqlp_status orth(ruqlp_ctx* h, const Layout& Lo, const Job& J, const void* Yin,
   CK(status_clear_shift(h->status, st));
   if (wt == Ty::F32 && !h->orth_fp64) {
     const double s1 = 64.0 * 5.960464477539063e-08;
-    const bool blocked = chol_inv_f32_supported(d);
-    for (int pass = 0; pass < 3; ++pass) {
+    const bool blocked = chol_tiles_supported(d);
+    const int passes = (final_basis || h->orth_full) ? 3 : 2;
+    for (int pass = 0; pass < passes; ++pass) {
       const float* src = (const float*)(pass == 0 ? Yin : Qout);
       CK(gram_f32(src, dp, src, dp, M, d, d, G, partial, kMaxSplits, nullptr, st));
       if (blocked) {
-        CK(chol_inv_f32(G, d, s1, pass == 0, (float*)Rw, h->status, nullptr, st));
-        CK(mul_upper_f32(src, dp, (const float*)Rw, (float*)Qout, dp, M, d, st));
+        CK(chol_tiles_f32(G, d, s1, pass == 0, (float*)Rw, h->status, nullptr, st));
+        CK(trsm_tiles_f32(src, dp, (const float*)Rw, (float*)Qout, dp, M, d, st));
       } else {
         CK(chol_upper(G, d, s1, R, Rw, Ty::F32, h->status, nullptr, st, Ty::F32, pass == 0));
         CK(trsm_right_upper(Ty::F32, src, dp, Rw, Qout, dp, M, d, nullptr, st));
@@ -302,7 +313,16 @@ ruqlp_status product(ruqlp_ctx* h, const Layout& Lo, const Job& J, bool trans, T
     const int64_t ldb = round8(K);
     CK(transpose_to_bf16(xt, Xin, ldx, K, J.d, J.dp, Bt, ldb, st));
     CK(tc_gemm(trans, J.A, J.lda, J.m, J.n, Bt, ldb, J.dp, (float*)out, J.dp,
-               (float*)(base + Lo.frag), &h->status->timeout, st));
+               (float*)(base + Lo.frag), &h->status->timeout, st,
+               h->profile ? [&](bool begin) {
+                 static thread_local cudaEvent_t a;
+                 if (begin) { a = ev_get(h); cudaEventRecord(a, st); }
+                 else {
+                   cudaEvent_t b = ev_get(h);
+                   cudaEventRecord(b, st);
+                   h->spans.push_back({trans ? PROF_TC_ATX : PROF_TC_AX, a, b});
+                 }
+               } : std::function<void(bool)>()));
     return RUQLP_OK;
   }
   const Mul mul = (J.ct == Ty::F64) ? Mul::F64 : Mul::F32;
@@ -351,18 +371,23 @@ ruqlp_status run_dense(ruqlp_ctx* h, const Job& J) {
     s = product(h, Lo, J, false, wt, X, dp, Y);
   }
   if (s != RUQLP_OK) return s;
-  // a3: Q = orth(Y)
-  s = orth(h, Lo, J, Y, Y, J.m);
+  // a3: Q = orth(Y).  orth() outputs that only feed the next product enter
+  // the result through their span: Y R^{-1} for any upper-triangular R with
+  // positive diagonal gives, after the later orth()s, exactly the same Q in
+  // exact arithmetic.  On the FP32/BF16 paths those take two CholeskyQR
+  // passes (shifted, then plain: orthonormal to about kappa(Y)^2 u, enough to
+  // keep the next sketch well conditioned); the last Q and P take three.
+  s = orth(h, Lo, J, Y, Y, J.m, J.q == 0);
   if (s != RUQLP_OK) return s;
   // a4: power iteration with orthonormalisation (Algorithm 2)
   for (int it = 0; it < J.q; ++it) {
     s = product(h, Lo, J, true, wt, Y, dp, Z);
     if (s != RUQLP_OK) return s;
-    s = orth(h, Lo, J, Z, Z, J.n);
+    s = orth(h, Lo, J, Z, Z, J.n, false);
     if (s != RUQLP_OK) return s;
     s = product(h, Lo, J, false, wt, Z, dp, Y);
     if (s != RUQLP_OK) return s;
-    s = orth(h, Lo, J, Y, Y, J.m);
+    s = orth(h, Lo, J, Y, Y, J.m, it == J.q - 1);
     if (s != RUQLP_OK) return s;
   }
   // a5: B^T = A^T Q
@@ -444,6 +469,10 @@ ruqlp_status ruqlp_set_stream(ruqlp_handle h, void* stream) {
 
 ruqlp_status ruqlp_set_option(ruqlp_handle h, const char* name, int64_t value) {
   if (!h || !name) return RUQLP_ERR_INVALID;
+  if (strcmp(name, "orth_full") == 0) {
+    h->orth_full = value ? 1 : 0;
+    return RUQLP_OK;
+  }
   if (strcmp(name, "orth_fp64") == 0) {
     h->orth_fp64 = value ? 1 : 0;
     return RUQLP_OK;
@@ -454,7 +483,7 @@ ruqlp_status ruqlp_set_option(ruqlp_handle h, const char* name, int64_t value) {
   }
   if (strcmp(name, "profile") == 0) {
     h->profile = value != 0;
-    for (int i = 0; i < 4; ++i) {
+    for (int i = 0; i < kProfN; ++i) {
       h->prof_count[i] = 0;
       h->prof_ms[i] = 0.0;
     }
@@ -665,7 +694,7 @@ ruqlp_status ruqlp_gram(ruqlp_handle h, const void* Y, int64_t M, int d, int64_t
 
 ruqlp_status ruqlp_profile(ruqlp_handle h, const char* phase, int64_t* count, double* total_ms) {
   if (!h || !phase || !count || !total_ms) return RUQLP_ERR_INVALID;
-  for (int i = 0; i < 4; ++i) {
+  for (int i = 0; i < kProfN; ++i) {
     if (strcmp(phase, kProfNames[i]) == 0) {
       *count = h->prof_count[i];
       *total_ms = h->prof_ms[i];

@@ -176,3 +176,24 @@ def test_orth_matches_householder_q(handle, case, dtype):
     kappa = 10.0 ** lk
     assert np.max(np.abs(Q.T @ Q - np.eye(d))) <= 50 * d * u
     assert np.max(np.abs(Q - Qr)) <= 50 * kappa * u * max(1.0, np.sqrt(d))
+
+
+@pytest.mark.parametrize("case", CASES[:4], ids=[c[0] for c in CASES[:4]])
+def test_light_and_full_intermediate_orth_agree(handle, case):
+    """Intermediate orth() results with one shifted CholeskyQR pass (default)
+    and with full orthonormalisation give the same Q, L, P within the FP32
+    tolerance (exact arithmetic: identical, the bases differ by upper-
+    triangular factors)."""
+    name, m, n, k, p, q, tail = case
+    A, Om = _case(*case, seed=wl.MASTER_SEED + 11 * m + n)
+    Ag = torch.from_numpy(A).float().cuda()
+    Og = torch.from_numpy(Om).cuda()
+    a = [t.double().cpu().numpy() for t in handle.decompose(Ag, Og, k, p, q)[:3]]
+    handle.set_option("orth_full", 1)
+    try:
+        b = [t.double().cpu().numpy() for t in handle.decompose(Ag, Og, k, p, q)[:3]]
+    finally:
+        handle.set_option("orth_full", 0)
+    l11 = abs(b[1][0, 0])
+    assert np.max(np.abs(a[1] - b[1])) <= 1e-5 * l11
+    assert np.max(np.abs(a[0][:, :k] - b[0][:, :k])) <= 1e-4
