@@ -79,7 +79,11 @@ typedef struct {
 } ruqlp_dense;
 
 /* Sparse A in CSR: rowptr[m+1] non-decreasing from 0 to nnz, colidx[nnz] in
- * [0, n) and strictly increasing inside each row, values[nnz] of dtype. */
+ * [0, n) and strictly increasing inside each row, values[nnz] of dtype (F32
+ * or BF16; products are accumulated in FP32).  m, n and nnz must fit int32.
+ * The library checks this structure on the device and returns INVALID when
+ * it fails; the transposed products use a CSC copy built in the workspace,
+ * which allows at most 1024 nonzeros per column. */
 typedef struct {
   int64_t m, n, nnz;
   const int32_t* rowptr;
@@ -160,14 +164,16 @@ ruqlp_status ruqlp_set_stream(ruqlp_handle h, void* cuda_stream);
 ruqlp_status ruqlp_set_option(ruqlp_handle h, const char* name, int64_t value);
 
 /* Grow the workspace arena now for problems up to m x n with d columns in
- * the given compute dtype, so that later calls allocate nothing.
+ * the given compute dtype (nnz < 0: dense A; nnz >= 0: CSR A with that many
+ * nonzeros), so that later calls allocate nothing.
  * Errors: INVALID, BUDGET, CUDA. */
 ruqlp_status ruqlp_reserve(ruqlp_handle h, int64_t m, int64_t n, int d,
-                           ruqlp_dtype compute, int is_csr);
+                           ruqlp_dtype compute, int64_t nnz);
 
-/* Workspace bytes a problem needs (0 on invalid sizes). */
+/* Workspace bytes a problem needs (0 on invalid sizes); nnz as for
+ * ruqlp_reserve. */
 size_t ruqlp_workspace_bytes(int64_t m, int64_t n, int d, ruqlp_dtype compute,
-                             int is_csr);
+                             int64_t nnz);
 
 /* One RU-QLP decomposition (Section III-A; Algorithms 1 and 2), all buffers
  * in device memory.  Work is ordered on the handle's stream; the call
@@ -189,9 +195,9 @@ ruqlp_status ruqlp_decompose_host(ruqlp_handle h, const ruqlp_matrix* A,
  * the products of Algorithm 2, B^T = A^T Q; Section III-D):
  *   trans = 0:  Y (m x d) = A X,    X: n x d;
  *   trans = 1:  Y (n x d) = A^T X,  X: m x d.
- * A is dense (device memory, any dtype); X and Y are row-major device
- * buffers (leading dimensions ldx, ldy >= d) in FP64 when A is FP64, else
- * FP32.  The kernel is the one ruqlp_decompose uses for A's dtype (BF16:
+ * A is dense (device memory, any dtype) or CSR (F32 or BF16 values); X and
+ * Y are row-major device buffers (leading dimensions ldx, ldy >= d) in FP64
+ * when A is FP64, else FP32.  The kernel is the one ruqlp_decompose uses for A's dtype (BF16:
  * X rounded to BF16, tensor cores, FP32 accumulation).  Returns after
  * completion.  Errors: INVALID, BUDGET, CUDA, TIMEOUT. */
 ruqlp_status ruqlp_sketch(ruqlp_handle h, const ruqlp_matrix* A, int trans, const void* X,

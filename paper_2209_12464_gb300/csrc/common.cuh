@@ -18,6 +18,8 @@ struct DevStatus {
   int32_t breakdown;  // non-zero: an orth() failed after its fallbacks
   int32_t shifted;    // set by the Cholesky of the current orth when it shifted
   int32_t timeout;    // a bounded device wait ran out
+  int32_t invalid;    // input checks on the device (CSR structure) failed
+  int32_t pad[3];
 };
 
 template <typename T> __device__ __forceinline__ float to_f32(T v);

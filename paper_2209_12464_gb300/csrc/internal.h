@@ -97,6 +97,20 @@ bool tc_supported(const void* A, int64_t lda, int dp);
 cudaError_t transpose_to_bf16(Ty ts, const void* src, int64_t lds, int64_t rows, int cols, int dp,
                               void* dst, int64_t ldd, cudaStream_t st);
 
+// CSR products (k_csr.cu), values FP32 or BF16, dense operands FP32.
+// csr_validate ORs into *flag: 1 bad rowptr, 2 bad / unsorted / duplicate
+// column index.  csr_transpose builds the CSR of A^T (colptr n+1, rowidx and
+// cvals nnz) with rows sorted inside each column (deterministic); scratch:
+// 2n ints; *flag |= 4 if a column has more than 1024 nonzeros.
+cudaError_t csr_validate(const int32_t* rowptr, const int32_t* colidx, int64_t m, int64_t n,
+                         int64_t nnz, int* flag, cudaStream_t st);
+cudaError_t csr_transpose(Ty tv, const int32_t* rowptr, const int32_t* colidx, const void* vals,
+                          int64_t m, int64_t n, int64_t nnz, int32_t* colptr, int32_t* rowidx,
+                          void* cvals, int32_t* scratch, int* flag, cudaStream_t st);
+// Y[rows x d] (ld ldy) = A X with A given by (ptr, idx, vals), X FP32 (ld ldx).
+cudaError_t spmm_csr(Ty tv, const int32_t* ptr, const int32_t* idx, const void* vals, int64_t rows,
+                     const float* X, int64_t ldx, int d, float* Y, int64_t ldy, cudaStream_t st);
+
 // Zero the status word.
 cudaError_t status_reset(DevStatus* s, cudaStream_t st);
 // Clear only the per-orth `shifted` field.

@@ -176,7 +176,7 @@ __global__ void k_write_L(const double* __restrict__ R, int d, TL* __restrict__ 
 }
 
 __global__ void k_status(DevStatus* s, int full) {
-  if (full) { s->flags = 0; s->breakdown = 0; s->timeout = 0; }
+  if (full) { s->flags = 0; s->breakdown = 0; s->timeout = 0; s->invalid = 0; }
   s->shifted = 0;
 }
 

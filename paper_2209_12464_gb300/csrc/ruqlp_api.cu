@@ -138,12 +138,13 @@ constexpr int kMaxSplits = 64;
 
 // Workspace layout for one problem.
 struct Layout {
-  size_t X, Y, Z, P, partial, G, R, Rw, Bt, frag, total;
+  size_t X, Y, Z, P, partial, G, R, Rw, Bt, frag, colptr, rowidx, cvals, cscratch, total;
 };
 
 inline int64_t round8(int64_t x) { return (x + 7) / 8 * 8; }
 
-Layout layout_of(int64_t m, int64_t n, int d, Ty ct) {
+// nnz >= 0: A is CSR with nnz nonzeros of val_bytes each (CSC copy kept too).
+Layout layout_of(int64_t m, int64_t n, int d, Ty ct, int64_t nnz = -1, size_t val_bytes = 0) {
   Layout L{};
   const int dp = round16(d);
   const size_t wes = ty_size(work_ty(ct));
@@ -165,9 +166,15 @@ Layout layout_of(int64_t m, int64_t n, int d, Ty ct) {
     if (chol_tiles_supported(d) && chol_tiles_bytes(d) > rw) rw = chol_tiles_bytes(d);
     L.Rw = take(rw);
   }
-  if (ct == Ty::BF16) {
+  if (ct == Ty::BF16 && nnz < 0) {
     L.Bt = take((size_t)dp * round8(m > n ? m : n) * 2);
     L.frag = take(dp <= 256 ? tc_frag_bytes(dp) : 0);
+  }
+  if (nnz >= 0) {
+    L.colptr = take((size_t)(n + 1) * sizeof(int32_t));
+    L.rowidx = take((size_t)(nnz > 0 ? nnz : 1) * sizeof(int32_t));
+    L.cvals = take((size_t)(nnz > 0 ? nnz : 1) * val_bytes);
+    L.cscratch = take((size_t)2 * n * sizeof(int32_t));
   }
   L.total = off;
   return L;
@@ -190,36 +197,56 @@ ruqlp_status ensure_arena(ruqlp_ctx* h, size_t bytes) {
   return RUQLP_OK;
 }
 
-ruqlp_status validate(ruqlp_ctx* h, const ruqlp_matrix* A, const ruqlp_params* prm,
-                      const ruqlp_outputs* out, int64_t* m, int64_t* n, int* d) {
-  if (!A || !prm || !out) return fail(h, RUQLP_ERR_INVALID, "NULL argument");
-  if (A->is_csr) return fail(h, RUQLP_ERR_INVALID, "CSR input is not supported by this entry");
-  const ruqlp_dense& D = A->dense;
-  if (D.m < 1 || D.n < 1) return fail(h, RUQLP_ERR_INVALID, "A must be at least 1 x 1");
-  if (D.ld < D.n) return fail(h, RUQLP_ERR_INVALID, "ld (%lld) < n (%lld)", (long long)D.ld,
-                              (long long)D.n);
-  if (!D.data) return fail(h, RUQLP_ERR_INVALID, "A.data is NULL");
-  Ty at, ct;
-  if (!ty_of(D.dtype, &at) || !ty_of(prm->compute, &ct))
-    return fail(h, RUQLP_ERR_INVALID, "unknown dtype");
+ruqlp_status validate_params(ruqlp_ctx* h, int64_t m, int64_t n, Ty at, const ruqlp_params* prm,
+                             const ruqlp_outputs* out, int* d) {
+  Ty ct;
+  if (!ty_of(prm->compute, &ct)) return fail(h, RUQLP_ERR_INVALID, "unknown compute dtype");
   if (at != ct) return fail(h, RUQLP_ERR_INVALID, "compute dtype must equal A's dtype");
   if (prm->k < 1) return fail(h, RUQLP_ERR_INVALID, "k must be >= 1 (got %d)", prm->k);
   if (prm->p < 0) return fail(h, RUQLP_ERR_INVALID, "p must be >= 0 (got %d)", prm->p);
   if (prm->q < 0) return fail(h, RUQLP_ERR_INVALID, "q must be >= 0 (got %d)", prm->q);
   const int64_t dd = (int64_t)prm->k + prm->p;
-  if (dd > D.m || dd > D.n)
+  if (dd > m || dd > n)
     return fail(h, RUQLP_ERR_INVALID, "d = k + p = %lld exceeds min(m, n) = %lld",
-                (long long)dd, (long long)(D.m < D.n ? D.m : D.n));
+                (long long)dd, (long long)(m < n ? m : n));
   if (dd > 512) return fail(h, RUQLP_ERR_INVALID, "d = %lld exceeds the maximum of 512",
                             (long long)dd);
   if (!prm->omega) return fail(h, RUQLP_ERR_INVALID, "omega is NULL");
   if (!out->Q || !out->L || !out->P) return fail(h, RUQLP_ERR_INVALID, "NULL output buffer");
   if (out->out_dtype != RUQLP_F64 && out->out_dtype != RUQLP_F32)
     return fail(h, RUQLP_ERR_INVALID, "out_dtype must be F64 or F32");
-  *m = D.m;
-  *n = D.n;
   *d = (int)dd;
   return RUQLP_OK;
+}
+
+ruqlp_status validate(ruqlp_ctx* h, const ruqlp_matrix* A, const ruqlp_params* prm,
+                      const ruqlp_outputs* out, int64_t* m, int64_t* n, int* d) {
+  if (!A || !prm || !out) return fail(h, RUQLP_ERR_INVALID, "NULL argument");
+  Ty at;
+  if (A->is_csr) {
+    const ruqlp_csr& C = A->csr;
+    if (C.m < 1 || C.n < 1) return fail(h, RUQLP_ERR_INVALID, "A must be at least 1 x 1");
+    if (C.nnz < 0 || C.nnz >= (int64_t)1 << 31)
+      return fail(h, RUQLP_ERR_INVALID, "nnz must be in [0, 2^31)");
+    if (C.m >= (int64_t)1 << 31 || C.n >= (int64_t)1 << 31)
+      return fail(h, RUQLP_ERR_INVALID, "CSR dimensions must fit int32 indices");
+    if (!C.rowptr || (C.nnz > 0 && (!C.colidx || !C.values)))
+      return fail(h, RUQLP_ERR_INVALID, "NULL CSR array");
+    if (!ty_of(C.dtype, &at) || at == Ty::F64)
+      return fail(h, RUQLP_ERR_INVALID, "CSR values must be F32 or BF16");
+    *m = C.m;
+    *n = C.n;
+  } else {
+    const ruqlp_dense& D = A->dense;
+    if (D.m < 1 || D.n < 1) return fail(h, RUQLP_ERR_INVALID, "A must be at least 1 x 1");
+    if (D.ld < D.n) return fail(h, RUQLP_ERR_INVALID, "ld (%lld) < n (%lld)", (long long)D.ld,
+                                (long long)D.n);
+    if (!D.data) return fail(h, RUQLP_ERR_INVALID, "A.data is NULL");
+    if (!ty_of(D.dtype, &at)) return fail(h, RUQLP_ERR_INVALID, "unknown dtype");
+    *m = D.m;
+    *n = D.n;
+  }
+  return validate_params(h, *m, *n, at, prm, out, d);
 }
 
 // Everything the orchestration needs for one decomposition.
@@ -235,6 +262,16 @@ struct Job {
   Ty ot;
   bool finish_paper;
   bool use_tc;  // BF16 products on the tensor cores (k_tc.cu)
+  // CSR input (work type FP32): A's arrays and the CSC copy in the arena
+  bool csr = false;
+  const int32_t* rowptr = nullptr;
+  const int32_t* colidx = nullptr;
+  const void* vals = nullptr;
+  int64_t nnz = 0;
+  Ty tv = Ty::F32;
+  int32_t* colptr = nullptr;
+  int32_t* rowidx = nullptr;
+  void* cvals = nullptr;
 };
 
 // orth() of Section II-A: Q = Yin R^{-1} with R from Cholesky factorisations
@@ -308,6 +345,16 @@ ruqlp_status product(ruqlp_ctx* h, const Layout& Lo, const Job& J, bool trans, T
   char* base = (char*)h->arena;
   const int64_t K = trans ? J.m : J.n;
   const int64_t Mout = trans ? J.n : J.m;
+  if (J.csr) {
+    if (xt != Ty::F32) return fail(h, RUQLP_ERR_INVALID, "internal: CSR operand type");
+    if (!trans)
+      CK(spmm_csr(J.tv, J.rowptr, J.colidx, J.vals, J.m, (const float*)Xin, ldx, J.d,
+                  (float*)out, J.dp, st));
+    else
+      CK(spmm_csr(J.tv, J.colptr, J.rowidx, J.cvals, J.n, (const float*)Xin, ldx, J.d,
+                  (float*)out, J.dp, st));
+    return RUQLP_OK;
+  }
   if (J.use_tc) {
     void* Bt = base + Lo.Bt;
     const int64_t ldb = round8(K);
@@ -343,10 +390,69 @@ ruqlp_status product(ruqlp_ctx* h, const Layout& Lo, const Job& J, bool trans, T
   return RUQLP_OK;
 }
 
-ruqlp_status run_dense(ruqlp_ctx* h, const Job& J) {
-  const Layout Lo = layout_of(J.m, J.n, J.d, J.ct);
+// Job fields shared by the device and host entry points.
+void fill_job(const ruqlp_matrix* A, const ruqlp_params* prm, const ruqlp_outputs* out, int64_t m,
+              int64_t n, int d, Job& J) {
+  J.m = m;
+  J.n = n;
+  J.d = d;
+  J.dp = round16(d);
+  J.q = prm->q;
+  ty_of(prm->compute, &J.ct);
+  J.wt = work_ty(J.ct);
+  J.omega = prm->omega;
+  ty_of(out->out_dtype, &J.ot);
+  J.finish_paper = prm->finish_paper != 0;
+  if (A->is_csr) {
+    J.csr = true;
+    J.rowptr = A->csr.rowptr;
+    J.colidx = A->csr.colidx;
+    J.vals = A->csr.values;
+    J.nnz = A->csr.nnz;
+    ty_of(A->csr.dtype, &J.tv);
+    J.wt = Ty::F32;
+  } else {
+    J.A = A->dense.data;
+    J.lda = A->dense.ld;
+  }
+}
+
+// CSR inputs: check the structure on the device and build the CSC copy in
+// the arena (used by the A^T products); one synchronisation to read the
+// check result.  Jm receives the CSC pointers.
+ruqlp_status prepare_csr(ruqlp_ctx* h, const Layout& Lo, Job& J) {
+  char* base = (char*)h->arena;
+  J.colptr = (int32_t*)(base + Lo.colptr);
+  J.rowidx = (int32_t*)(base + Lo.rowidx);
+  J.cvals = base + Lo.cvals;
+  int* flag = &h->status->invalid;
+  // the structure is checked (and the result read) before any kernel indexes
+  // with the column indices
+  CK(csr_validate(J.rowptr, J.colidx, J.m, J.n, J.nnz, flag, h->stream));
+  CK(cudaMemcpyAsync(h->status_host, h->status, sizeof(DevStatus), cudaMemcpyDeviceToHost,
+                     h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  const int f = h->status_host->invalid;
+  if (f & 1) return fail(h, RUQLP_ERR_INVALID, "CSR rowptr is not a valid prefix array");
+  if (f & 2)
+    return fail(h, RUQLP_ERR_INVALID,
+                "CSR column index out of range or not strictly increasing within a row");
+  CK(csr_transpose(J.tv, J.rowptr, J.colidx, J.vals, J.m, J.n, J.nnz, J.colptr, J.rowidx,
+                   J.cvals, (int32_t*)(base + Lo.cscratch), flag, h->stream));
+  return RUQLP_OK;
+}
+
+ruqlp_status run_dense(ruqlp_ctx* h, const Job& J0) {
+  Job J = J0;
+  const Layout Lo = J.csr ? layout_of(J.m, J.n, J.d, J.ct, J.nnz, ty_size(J.tv))
+                          : layout_of(J.m, J.n, J.d, J.ct);
   ruqlp_status s = ensure_arena(h, Lo.total);
   if (s != RUQLP_OK) return s;
+  CK(status_reset(h->status, h->stream));
+  if (J.csr) {
+    s = prepare_csr(h, Lo, J);
+    if (s != RUQLP_OK) return s;
+  }
   char* base = (char*)h->arena;
   void* X = base + Lo.X;
   void* Y = base + Lo.Y;
@@ -360,9 +466,8 @@ ruqlp_status run_dense(ruqlp_ctx* h, const Job& J) {
   cudaStream_t st = h->stream;
 
   ProfScope pstep(h, PROF_STEP);
-  CK(status_reset(h->status, st));
   // a1 + a2: Y = A Omega (Omega is FP64 n x d; the tensor-core path transposes
-  // it straight to BF16, the SIMT path casts it to the work type first)
+  // it straight to BF16, the other paths cast it to the work type first)
   if (J.use_tc) {
     s = product(h, Lo, J, false, Ty::F64, J.omega, d, Y);
   } else {
@@ -417,6 +522,8 @@ ruqlp_status finish(ruqlp_ctx* h, ruqlp_outputs* out) {
   out->flags = (uint32_t)h->status_host->flags;
   if (h->status_host->timeout)
     return fail(h, RUQLP_ERR_TIMEOUT, "a bounded device wait ran out in a tensor-core product");
+  if (h->status_host->invalid & 4)
+    return fail(h, RUQLP_ERR_INVALID, "a CSR column has more than 1024 nonzeros");
   if (h->status_host->breakdown)
     return fail(h, RUQLP_ERR_BREAKDOWN, "orth() broke down after its fallbacks");
   return RUQLP_OK;
@@ -492,16 +599,20 @@ ruqlp_status ruqlp_set_option(ruqlp_handle h, const char* name, int64_t value) {
   return fail(h, RUQLP_ERR_INVALID, "unknown option '%s'", name);
 }
 
-size_t ruqlp_workspace_bytes(int64_t m, int64_t n, int d, ruqlp_dtype compute, int is_csr) {
+size_t ruqlp_workspace_bytes(int64_t m, int64_t n, int d, ruqlp_dtype compute, int64_t nnz) {
   Ty ct;
-  if (m < 1 || n < 1 || d < 1 || d > 512 || !ty_of(compute, &ct) || is_csr) return 0;
+  if (m < 1 || n < 1 || d < 1 || d > 512 || !ty_of(compute, &ct)) return 0;
+  if (nnz >= 0) {
+    if (ct == Ty::F64) return 0;
+    return layout_of(m, n, d, Ty::F32, nnz, ty_size(ct)).total;
+  }
   return layout_of(m, n, d, ct).total;
 }
 
 ruqlp_status ruqlp_reserve(ruqlp_handle h, int64_t m, int64_t n, int d, ruqlp_dtype compute,
-                           int is_csr) {
+                           int64_t nnz) {
   if (!h) return RUQLP_ERR_INVALID;
-  const size_t b = ruqlp_workspace_bytes(m, n, d, compute, is_csr);
+  const size_t b = ruqlp_workspace_bytes(m, n, d, compute, nnz);
   if (b == 0) return fail(h, RUQLP_ERR_INVALID, "invalid sizes for ruqlp_reserve");
   return ensure_arena(h, b);
 }
@@ -516,24 +627,13 @@ ruqlp_status ruqlp_decompose(ruqlp_handle h, const ruqlp_matrix* A, const ruqlp_
   if (s != RUQLP_OK) return s;
   CK(cudaSetDevice(h->device));
   Job J{};
-  J.A = A->dense.data;
-  J.lda = A->dense.ld;
-  J.m = m;
-  J.n = n;
-  J.d = d;
-  J.dp = round16(d);
-  J.q = prm->q;
-  ty_of(prm->compute, &J.ct);
-  J.wt = work_ty(J.ct);
-  J.omega = prm->omega;
+  fill_job(A, prm, out, m, n, d, J);
   J.Qout = out->Q;
   J.Lout = out->L;
   J.Pout = out->P;
-  ty_of(out->out_dtype, &J.ot);
-  J.finish_paper = prm->finish_paper != 0;
   if (J.finish_paper)
     return fail(h, RUQLP_ERR_INVALID, "finish_paper is not available in this build");
-  J.use_tc = J.ct == Ty::BF16 && !h->bf16_simt && tc_supported(J.A, J.lda, J.dp);
+  J.use_tc = !J.csr && J.ct == Ty::BF16 && !h->bf16_simt && tc_supported(J.A, J.lda, J.dp);
   s = run_dense(h, J);
   if (s != RUQLP_OK) return s;
   return finish(h, out);
@@ -548,51 +648,64 @@ ruqlp_status ruqlp_decompose_host(ruqlp_handle h, const ruqlp_matrix* A,
   ruqlp_status s = validate(h, A, prm, out, &m, &n, &d);
   if (s != RUQLP_OK) return s;
   CK(cudaSetDevice(h->device));
-  Ty at, ot;
-  ty_of(A->dense.dtype, &at);
-  ty_of(out->out_dtype, &ot);
-  const size_t aes = ty_size(at), oes = ty_size(ot);
-  // host staging region: A (m x n, packed), Omega, Q, L, P after the workspace
-  Layout Lo = layout_of(m, n, d, at);
+  Job J{};
+  fill_job(A, prm, out, m, n, d, J);
+  if (J.finish_paper)
+    return fail(h, RUQLP_ERR_INVALID, "finish_paper is not available in this build");
+  const size_t oes = ty_size(J.ot);
+  // the workspace first, then staging for A, Omega and the outputs
+  const Layout Lo = J.csr ? layout_of(m, n, d, J.ct, J.nnz, ty_size(J.tv))
+                          : layout_of(m, n, d, J.ct);
   size_t off = align_up(Lo.total, 256);
-  const int64_t lds = (at == Ty::BF16) ? round8(n) : n;  // TMA needs 16-byte row pitch
-  const size_t oA = off;
-  off = align_up(off + (size_t)m * lds * aes, 256);
-  const size_t oOm = off;
-  off = align_up(off + (size_t)n * d * sizeof(double), 256);
-  const size_t oQ = off;
-  off = align_up(off + (size_t)m * d * oes, 256);
-  const size_t oL = off;
-  off = align_up(off + (size_t)d * d * oes, 256);
-  const size_t oP = off;
-  off = align_up(off + (size_t)n * d * oes, 256);
+  auto take = [&](size_t bytes) {
+    const size_t o = off;
+    off = align_up(off + bytes, 256);
+    return o;
+  };
+  size_t oA = 0, oRp = 0, oCi = 0, oV = 0;
+  int64_t lds = n;
+  if (J.csr) {
+    oRp = take((size_t)(m + 1) * sizeof(int32_t));
+    oCi = take((size_t)(J.nnz > 0 ? J.nnz : 1) * sizeof(int32_t));
+    oV = take((size_t)(J.nnz > 0 ? J.nnz : 1) * ty_size(J.tv));
+  } else {
+    lds = (J.ct == Ty::BF16) ? round8(n) : n;  // TMA needs a 16-byte row pitch
+    oA = take((size_t)m * lds * ty_size(J.ct));
+  }
+  const size_t oOm = take((size_t)n * d * sizeof(double));
+  const size_t oQ = take((size_t)m * d * oes);
+  const size_t oL = take((size_t)d * d * oes);
+  const size_t oP = take((size_t)n * d * oes);
   s = ensure_arena(h, off);
   if (s != RUQLP_OK) return s;
   char* base = (char*)h->arena;
   cudaStream_t st = h->stream;
-  CK(cudaMemcpy2DAsync(base + oA, (size_t)lds * aes, A->dense.data, (size_t)A->dense.ld * aes,
-                       (size_t)n * aes, (size_t)m, cudaMemcpyHostToDevice, st));
+  if (J.csr) {
+    CK(cudaMemcpyAsync(base + oRp, A->csr.rowptr, (size_t)(m + 1) * sizeof(int32_t),
+                       cudaMemcpyHostToDevice, st));
+    if (J.nnz > 0) {
+      CK(cudaMemcpyAsync(base + oCi, A->csr.colidx, (size_t)J.nnz * sizeof(int32_t),
+                         cudaMemcpyHostToDevice, st));
+      CK(cudaMemcpyAsync(base + oV, A->csr.values, (size_t)J.nnz * ty_size(J.tv),
+                         cudaMemcpyHostToDevice, st));
+    }
+    J.rowptr = (const int32_t*)(base + oRp);
+    J.colidx = (const int32_t*)(base + oCi);
+    J.vals = base + oV;
+  } else {
+    const size_t aes = ty_size(J.ct);
+    CK(cudaMemcpy2DAsync(base + oA, (size_t)lds * aes, A->dense.data, (size_t)A->dense.ld * aes,
+                         (size_t)n * aes, (size_t)m, cudaMemcpyHostToDevice, st));
+    J.A = base + oA;
+    J.lda = lds;
+  }
   CK(cudaMemcpyAsync(base + oOm, prm->omega, (size_t)n * d * sizeof(double),
                      cudaMemcpyHostToDevice, st));
-  Job J{};
-  J.A = base + oA;
-  J.lda = lds;
-  J.m = m;
-  J.n = n;
-  J.d = d;
-  J.dp = round16(d);
-  J.q = prm->q;
-  J.ct = at;
-  J.wt = work_ty(at);
   J.omega = (const double*)(base + oOm);
   J.Qout = base + oQ;
   J.Lout = base + oL;
   J.Pout = base + oP;
-  J.ot = ot;
-  J.finish_paper = prm->finish_paper != 0;
-  if (J.finish_paper)
-    return fail(h, RUQLP_ERR_INVALID, "finish_paper is not available in this build");
-  J.use_tc = J.ct == Ty::BF16 && !h->bf16_simt && tc_supported(J.A, J.lda, J.dp);
+  J.use_tc = !J.csr && J.ct == Ty::BF16 && !h->bf16_simt && tc_supported(J.A, J.lda, J.dp);
   s = run_dense(h, J);
   if (s != RUQLP_OK) return s;
   CK(cudaMemcpyAsync(out->Q, base + oQ, (size_t)m * d * oes, cudaMemcpyDeviceToHost, st));
@@ -610,34 +723,51 @@ ruqlp_status ruqlp_sketch(ruqlp_handle h, const ruqlp_matrix* A, int trans, cons
   if (!h) return RUQLP_ERR_INVALID;
   h->err.clear();
   if (!A || !X || !Y) return fail(h, RUQLP_ERR_INVALID, "NULL argument");
-  if (A->is_csr) return fail(h, RUQLP_ERR_INVALID, "CSR input is not supported by this entry");
-  const ruqlp_dense& D = A->dense;
-  Ty ct;
-  if (!D.data || D.m < 1 || D.n < 1 || D.ld < D.n || !ty_of(D.dtype, &ct))
-    return fail(h, RUQLP_ERR_INVALID, "invalid dense A");
-  const int64_t K = trans ? D.m : D.n, Mout = trans ? D.n : D.m;
   if (d < 1 || d > 512 || ldx < d || ldy < d)
     return fail(h, RUQLP_ERR_INVALID, "need 1 <= d <= 512, ldx >= d, ldy >= d");
+  // reuse the decomposition's checks with a stand-in parameter set
+  ruqlp_params prm{};
+  prm.k = 1;
+  prm.p = 0;
+  prm.q = 0;
+  prm.compute = A->is_csr ? A->csr.dtype : A->dense.dtype;
+  prm.omega = (const double*)X;
+  ruqlp_outputs o{};
+  o.Q = o.L = o.P = Y;
+  o.out_dtype = RUQLP_F32;
+  int64_t m, n;
+  int d1;
+  ruqlp_status s = validate(h, A, &prm, &o, &m, &n, &d1);
+  if (s != RUQLP_OK) return s;
   CK(cudaSetDevice(h->device));
   Job J{};
-  J.A = D.data;
-  J.lda = D.ld;
-  J.m = D.m;
-  J.n = D.n;
+  fill_job(A, &prm, &o, m, n, 1, J);
   J.d = d;
   J.dp = round16(d);
-  J.ct = ct;
-  J.wt = work_ty(ct);
-  J.use_tc = ct == Ty::BF16 && !h->bf16_simt && tc_supported(J.A, J.lda, J.dp);
-  const Layout Lo = layout_of(J.m, J.n, d, ct);
-  ruqlp_status s = ensure_arena(h, Lo.total);
+  J.use_tc = !J.csr && J.ct == Ty::BF16 && !h->bf16_simt && tc_supported(J.A, J.lda, J.dp);
+  const int64_t Mout = trans ? n : m;
+  const Layout Lo = J.csr ? layout_of(m, n, d, J.ct, J.nnz, ty_size(J.tv))
+                          : layout_of(m, n, d, J.ct);
+  s = ensure_arena(h, Lo.total);
   if (s != RUQLP_OK) return s;
   CK(status_reset(h->status, h->stream));
+  if (J.csr) {
+    s = prepare_csr(h, Lo, J);
+    if (s != RUQLP_OK) return s;
+  }
   void* stage = (char*)h->arena + (trans ? Lo.Z : Lo.Y);
-  s = product(h, Lo, J, trans != 0, J.wt, X, ldx, stage);
+  const void* Xuse = X;
+  int64_t ldxu = ldx;
+  if (J.csr && ((ldx % 4) || ((uintptr_t)X & 15))) {  // 128-bit gathers need aligned rows
+    void* Xa = (char*)h->arena + (trans ? Lo.Y : Lo.X);  // m x dp or n x dp
+    const int64_t K = trans ? m : n;
+    CK(copy_cast_2d(J.wt, X, ldx, J.wt, Xa, J.dp, K, d, h->stream));
+    Xuse = Xa;
+    ldxu = J.dp;
+  }
+  s = product(h, Lo, J, trans != 0, J.wt, Xuse, ldxu, stage);
   if (s != RUQLP_OK) return s;
   CK(copy_cast_2d(J.wt, stage, J.dp, J.wt, Y, ldy, Mout, d, h->stream));
-  (void)K;
   ruqlp_outputs dummy{};
   return finish(h, &dummy);
 }

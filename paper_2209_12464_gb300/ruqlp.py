@@ -62,8 +62,8 @@ _SIGS = {
     "ruqlp_destroy": (c_int, [c_void_p]),
     "ruqlp_set_stream": (c_int, [c_void_p, c_void_p]),
     "ruqlp_set_option": (c_int, [c_void_p, c_char_p, c_int64]),
-    "ruqlp_reserve": (c_int, [c_void_p, c_int64, c_int64, c_int, c_int, c_int]),
-    "ruqlp_workspace_bytes": (c_size_t, [c_int64, c_int64, c_int, c_int, c_int]),
+    "ruqlp_reserve": (c_int, [c_void_p, c_int64, c_int64, c_int, c_int, c_int64]),
+    "ruqlp_workspace_bytes": (c_size_t, [c_int64, c_int64, c_int, c_int, c_int64]),
     "ruqlp_decompose": (c_int, [c_void_p, ctypes.POINTER(Matrix), ctypes.POINTER(Params),
                                 ctypes.POINTER(Outputs)]),
     "ruqlp_decompose_host": (c_int, [c_void_p, ctypes.POINTER(Matrix), ctypes.POINTER(Params),
@@ -123,12 +123,12 @@ def ruqlp_set_option(h, name, value):
     return lib().ruqlp_set_option(h, name.encode(), int(value))
 
 
-def ruqlp_reserve(h, m, n, d, compute, is_csr=0):
-    return lib().ruqlp_reserve(h, m, n, d, compute, is_csr)
+def ruqlp_reserve(h, m, n, d, compute, nnz=-1):
+    return lib().ruqlp_reserve(h, m, n, d, compute, nnz)
 
 
-def ruqlp_workspace_bytes(m, n, d, compute, is_csr=0):
-    return lib().ruqlp_workspace_bytes(m, n, d, compute, is_csr)
+def ruqlp_workspace_bytes(m, n, d, compute, nnz=-1):
+    return lib().ruqlp_workspace_bytes(m, n, d, compute, nnz)
 
 
 def ruqlp_decompose(h, A, prm, out):
@@ -275,6 +275,37 @@ class Handle:
         out = Outputs(Q.data_ptr(), L.data_ptr(), P.data_ptr(), _dtype_code(out_dtype), 0)
         self.check(ruqlp_decompose(self.h, M, prm, out))
         return Q, L, P, out.flags
+
+    def decompose_csr(self, rowptr, colidx, values, shape, omega, k, p, q, out_dtype=None):
+        """RU-QLP of a CSR matrix given as CUDA tensors (rowptr, colidx int32;
+        values float32 or bfloat16).  Returns (Q, L, P, flags)."""
+        import torch
+        m, n = shape
+        d = k + p
+        od = out_dtype or torch.float32
+        dev = values.device
+        Q = torch.empty(m, d, dtype=od, device=dev)
+        L = torch.empty(d, d, dtype=od, device=dev)
+        P = torch.empty(n, d, dtype=od, device=dev)
+        M = Matrix(1, Dense(), Csr(m, n, values.numel(), rowptr.data_ptr(), colidx.data_ptr(),
+                                   values.data_ptr(), _dtype_code(values.dtype)))
+        prm = Params(k, p, q, _dtype_code(values.dtype), omega.contiguous().data_ptr(), 0)
+        out = Outputs(Q.data_ptr(), L.data_ptr(), P.data_ptr(), _dtype_code(od), 0)
+        self.check(ruqlp_decompose(self.h, M, prm, out))
+        return Q, L, P, out.flags
+
+    def sketch_csr(self, rowptr, colidx, values, shape, X, trans=False):
+        """Y = A X (or A^T X) for a CSR A on the device; X float32."""
+        import torch
+        m, n = shape
+        K, Mout = (m, n) if trans else (n, m)
+        d = X.shape[1]
+        Y = torch.empty(Mout, d, dtype=torch.float32, device=X.device)
+        M = Matrix(1, Dense(), Csr(m, n, values.numel(), rowptr.data_ptr(), colidx.data_ptr(),
+                                   values.data_ptr(), _dtype_code(values.dtype)))
+        self.check(ruqlp_sketch(self.h, M, int(trans), X.data_ptr(), X.stride(0), d,
+                                Y.data_ptr(), d))
+        return Y
 
     def decompose_host(self, A, omega, k, p, q, outs):
         """Same with CPU tensors (pinned or pageable); outs = (Q, L, P) CPU tensors."""

@@ -56,6 +56,11 @@ def test_workspace_bytes_host_logic(lib):
     a = lib.ruqlp_workspace_bytes(20000, 20000, 220, lib.BF16)
     b = lib.ruqlp_workspace_bytes(20000, 20000, 220, lib.F64)
     assert 0 < a < b
+    # CSR: the CSC copy grows with nnz; FP64 values are not supported
+    c0 = lib.ruqlp_workspace_bytes(200000, 100000, 110, lib.F32, 0)
+    c1 = lib.ruqlp_workspace_bytes(200000, 100000, 110, lib.F32, 20000000)
+    assert 0 < c0 < c1 and c1 - c0 >= 20000000 * 8 - 1024
+    assert lib.ruqlp_workspace_bytes(200, 100, 10, lib.F64, 50) == 0
 
 
 def test_version(lib):
