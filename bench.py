@@ -9,6 +9,9 @@ every product, B^T = A^T Q and its QR.  The workload is the dense
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--dtype bf16|f32|f64]
   python bench.py --impl reference ...   (the FP64 CPU oracle on host cores)
+  python bench.py --workload batch [--dtype bf16|f32]   (512 uneven matrices:
+      m log-uniform in [256, 4096], n in [128, 2048], k uniform in [8, 64],
+      p=8, q=1, same spectrum form; one ruqlp_decompose_batch call per step)
 
 Under torchrun each rank runs its own replica of the workload (weak scaling,
 no data-path collective); rank 0 prints one JSON line.
@@ -46,6 +49,10 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--size", type=int, default=0, help="override m = n (testing only)")
+    ap.add_argument("--workload", default="dense", choices=["dense", "batch"],
+                    help="dense: one 20000 x 20000 matrix (the metric's workload); batch: "
+                         "512 matrices of uneven shapes in one batched call")
+    ap.add_argument("--count", type=int, default=512, help="batch size (batch workload)")
     ap.add_argument("--gen", default="haar", choices=["haar", "fast"],
                     help="haar: the workload's Haar U, V (torch.linalg.qr); fast: Gaussian "
                          "low-rank stand-in for profiling tools that cannot load torch.linalg")
@@ -195,6 +202,226 @@ def run_reference(args):
     return 0
 
 
+# ---------------------------------------------------------------------------
+# batched workload
+# ---------------------------------------------------------------------------
+B_SEED, B_P, B_Q = 20260 + 3, 8, 1
+B_WORKLOAD = ("batched: 512 dense matrices, m log-uniform [256,4096], n log-uniform [128,2048], "
+              "k uniform [8,64], p=8, q=1, sigma_i=1 (i<=k) then 1e-2/(i-k)")
+
+
+def batch_inputs(torch, dev, count, dtype, gen):
+    from paper_2209_12464_gb300 import workloads as wl
+    shapes = wl.batch_shapes(B_SEED, count=count, p=B_P)
+    A32, Om = [], []
+    for i, (m, n, k, p) in enumerate(shapes):
+        if gen == "haar":
+            A32.append(wl.dense_spectral_torch(B_SEED + 1000 + i, m, n,
+                                               wl.spectrum_gap(min(m, n), k, TAIL), device=dev))
+        else:
+            A32.append(wl.dense_lowrank_gauss_torch(B_SEED + 1000 + i, m, n, k, device=dev))
+        Om.append(wl.omega_torch(B_SEED + 5000 + i, n, k + p, device=dev))
+    tdt = {"bf16": torch.bfloat16, "f32": torch.float32}[dtype]
+    A = [a.to(tdt) for a in A32]
+    return shapes, A, A32, Om
+
+
+def batch_cpu_baseline(dtype, count, items):
+    """The FP64 oracle on the first `items` matrices of the batch (a bounded
+    sample), in a spawned process using every host core."""
+    code = r"""
+import sys, time, json
+sys.path.insert(0, %r)
+import oracle
+from paper_2209_12464_gb300 import workloads as wl
+shapes = wl.batch_shapes(%d, count=%d, p=%d)[:%d]
+mats = []
+for i, (m, n, k, p) in enumerate(shapes):
+    A, _, _, _ = wl.dense_spectral(31 + i, m, n, wl.spectrum_gap(min(m, n), k, %r))
+    mats.append((A, wl.omega(77 + i, n, k + p)))
+t0 = time.perf_counter()
+for A, Om in mats:
+    oracle.ruqlp(A, Om, %d)
+t = time.perf_counter() - t0
+el = sum(m * n for m, n, k, p in shapes)
+print(json.dumps({"seconds": t, "elements": el, "items": len(shapes)}))
+""" % (ROOT, B_SEED, count, B_P, items, TAIL, B_Q)
+    env = dict(os.environ)
+    cores = os.cpu_count() or 1
+    for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        env[v] = str(cores)
+    env["CUDA_VISIBLE_DEVICES"] = ""
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env,
+                       timeout=900)
+    if r.returncode != 0:
+        return {"value": None, "error": r.stderr[-400:]}
+    j = json.loads(r.stdout.strip().splitlines()[-1])
+    gbytes = (2 * B_Q + 2) * j["elements"] * DT_BYTES[dtype] / 1e9
+    return {"value": gbytes / j["seconds"], "unit": "GB/s", "cores": cores, "kind": "oracle",
+            "seconds": j["seconds"], "decompositions_per_s": j["items"] / j["seconds"],
+            "sample": f"oracle.ruqlp (FP64 numpy) on the first {j['items']} matrices of the "
+                      f"batch (same shapes and spectrum form), bytes counted in {dtype}"}
+
+
+def run_batch(args, torch, dev, local, world, rank, dist):
+    from paper_2209_12464_gb300 import ruqlp
+    if args.dtype not in ("bf16", "f32"):
+        raise SystemExit("the batched workload runs in bf16 or f32")
+    shapes, A, A32, Om = batch_inputs(torch, dev, args.count, args.dtype, args.gen)
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream(dev)
+    h = ruqlp.Handle(local, stream.cuda_stream)
+    ks, ps = [s[2] for s in shapes], [s[3] for s in shapes]
+    batch = h.prepare_batch(A, Om, ks, B_P, B_Q, ps=ps)
+    for _ in range(max(args.warmup, 3)):
+        batch.run()
+    torch.cuda.synchronize()
+    clocks = Clocks(local)
+    clocks.start()
+    time.sleep(0.3)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    l0 = ruqlp.ruqlp_launch_count()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    flags = 0
+    for _ in range(args.steps):
+        for f in batch.run():
+            flags |= f
+    e1.record(stream)
+    torch.cuda.synchronize()
+    launches = (ruqlp.ruqlp_launch_count() - l0) // max(args.steps, 1)
+    if world > 1:
+        dist.barrier()
+    ck = clocks.stop()
+    ms = e0.elapsed_time(e1) / max(args.steps, 1)
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    passes = 2 * B_Q + 2
+    elements = sum(m * n for m, n, k, p in shapes)
+    bytes_a = elements * DT_BYTES[args.dtype]
+    value = world * passes * bytes_a / (ms * 1e-3) / 1e9
+    dps = world * len(shapes) / (ms * 1e-3)
+
+    # accuracy on a sample: relative residual against the unrounded matrix
+    # (FP64 on the device), and the same for the plain single-matrix FP32 path
+    rng = __import__("numpy").random.default_rng(3)
+    sample = sorted(rng.choice(len(shapes), 16, replace=False).tolist())
+    res_b, res_1 = [], []
+    for i in sample:
+        Q, L, P = batch.outs[i]
+        res_b.append(residual_gpu(torch, A32[i], Q, L, P))
+        Q1, L1, P1, _ = h.decompose(A32[i], Om[i], ks[i], ps[i], B_Q, out_dtype=torch.float32)
+        res_1.append(residual_gpu(torch, A32[i], Q1, L1, P1))
+    ratio = max(b / o for b, o in zip(res_b, res_1))
+
+    # the plain single-instance FP32 form: one ruqlp_decompose per matrix
+    outs1 = [(torch.empty(m, k + p, device=dev), torch.empty(k + p, k + p, device=dev),
+              torch.empty(n, k + p, device=dev)) for m, n, k, p in shapes]
+    for i in range(len(shapes)):
+        h.decompose(A32[i], Om[i], ks[i], ps[i], B_Q, outs=outs1[i])
+    torch.cuda.synchronize()
+    s0 = torch.cuda.Event(enable_timing=True)
+    s1 = torch.cuda.Event(enable_timing=True)
+    s0.record(stream)
+    for i in range(len(shapes)):
+        h.decompose(A32[i], Om[i], ks[i], ps[i], B_Q, outs=outs1[i])
+    s1.record(stream)
+    torch.cuda.synchronize()
+    ms1 = s0.elapsed_time(s1)
+    single = {"decompositions_per_s": len(shapes) / (ms1 * 1e-3), "ms_per_batch": ms1,
+              "form": "ruqlp_decompose per matrix, FP32 A, FP32 compute"}
+    del outs1
+
+    # live per-phase timing (eager batched launches, CUDA events on the stream)
+    h.set_option("profile", 1)
+    for _ in range(2):
+        batch.run()
+    torch.cuda.synchronize()
+    prof = {ph: h.profile(ph) for ph in ("ax", "atx", "orth", "step")}
+    h.set_option("profile", 0)
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except OSError:
+        pass
+    sm_mhz = ck.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
+    cnt = prof["ax"][0] + prof["atx"][0]
+    avg = (prof["ax"][1] + prof["atx"][1]) / max(cnt, 1)
+    flops = 2.0 * sum(m * n * (k + p) for m, n, k, p in shapes)
+    alu_peak = 152 * 256 * sm_mhz * 1e6 / 1e12
+    achieved = flops / (avg * 1e-3) / 1e12
+    step_ms = prof["step"][1] / max(prof["step"][0], 1)
+    roofline = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
+                "frac": achieved / alu_peak, "traffic": None,
+                "kernel": "k_bgemm (batched CUDA-core product, one pass over every A_i per launch)",
+                "alg_flops_per_launch": flops, "avg_launch_ms": avg, "launches": cnt,
+                "peak_source": "derived: 152 SMs x 128 FP32 FMA/clk x 2 x median SM clock",
+                "hbm_alg_gbs": bytes_a / (avg * 1e-3) / 1e9,
+                "phase_ms": {ph: prof[ph][1] / max(prof[ph][0], 1) for ph in prof},
+                "phase_share": {ph: prof[ph][1] / max(prof["step"][1], 1e-9)
+                                for ph in ("ax", "atx", "orth")},
+                "eager_step_ms": step_ms}
+
+    # end to end: pinned host inputs -> device, batched call, outputs -> host
+    e2e = None
+    if not args.no_e2e:
+        Ah = [a.cpu().pin_memory() for a in A]
+        Oh = [o.cpu().pin_memory() for o in Om]
+        Qh = [tuple(torch.empty_like(t, device="cpu").pin_memory() for t in o) for o in batch.outs]
+        bi = sum(a.numel() * a.element_size() for a in Ah) + sum(o.numel() * 8 for o in Oh)
+        bo = sum(t.numel() * t.element_size() for o in Qh for t in o)
+        ke = max(1, min(args.steps, 3))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(ke):
+            for dsrc, hsrc in zip(A, Ah):
+                dsrc.copy_(hsrc, non_blocking=True)
+            for dsrc, hsrc in zip(Om, Oh):
+                dsrc.copy_(hsrc, non_blocking=True)
+            batch.run()
+            for o, hq in zip(batch.outs, Qh):
+                for t, ht in zip(o, hq):
+                    ht.copy_(t, non_blocking=True)
+            torch.cuda.synchronize()
+        te = (time.perf_counter() - t0) / ke
+        if world > 1:
+            t = torch.tensor([te], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            te = float(t.item())
+        e2e = {"value": world * passes * bytes_a / te / 1e9, "unit": "GB/s",
+               "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo, "ms_per_step": te * 1e3,
+               "decompositions_per_s": world * len(shapes) / te}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = batch_cpu_baseline(args.dtype, args.count, 24)
+    if rank == 0:
+        out = {"metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world,
+               "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+               "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+               "dtype": args.dtype, "data": "synthetic",
+               "config": {"workload": B_WORKLOAD if args.gen == "haar" else
+                          "Gaussian low-rank stand-in of the batched shapes (profiling)",
+                          "count": len(shapes), "p": B_P, "q": B_Q, "passes": passes,
+                          "bytes_A": bytes_a,
+                          "l2": "inputs larger than L2 (%.0f MB of A vs 129 MB L2)" % (bytes_a / 1e6),
+                          "parallelism": f"replicas x{world}"},
+               "decompositions_per_s": dps,
+               "single_fp32": single,
+               "accuracy": {"sample": len(sample), "residual_fro_max": max(res_b),
+                            "max_ratio_vs_single_fp32": ratio, "flags": flags},
+               "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+               "gpu_launches": launches, "clocks": ck}
+        print(json.dumps(out))
+    h.close()
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -209,6 +436,11 @@ def main():
     import __graft_entry__ as g
     g.build()
     from paper_2209_12464_gb300 import ruqlp
+    if args.workload == "batch":
+        rc = run_batch(args, torch, dev, local, world, rank, dist)
+        if world > 1:
+            dist.destroy_process_group()
+        return rc
 
     m = n = args.size or M
     k, p, q = K_RANK, P_OVER, Q_POW

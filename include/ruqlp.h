@@ -185,6 +185,22 @@ size_t ruqlp_workspace_bytes(int64_t m, int64_t n, int d, ruqlp_dtype compute,
 ruqlp_status ruqlp_decompose(ruqlp_handle h, const ruqlp_matrix* A,
                              const ruqlp_params* prm, ruqlp_outputs* out);
 
+/* `count` independent decompositions in one call (the batched workload:
+ * many dense matrices of uneven shapes).  A[i], prm[i], out[i] as for
+ * ruqlp_decompose (device memory); every item must be dense, share one
+ * compute dtype (F32 or BF16) and one q, have d <= 256 and finish_paper = 0.
+ * Each phase of the method (sketch products, Grams, Cholesky factorisations,
+ * triangular solves) is one launch over all items; the launch sequence is
+ * captured in a CUDA graph the second time a batch signature (shapes, q,
+ * dtype) is seen and replayed afterwards (option "batch_graph" = 0 turns
+ * this off).  BF16 products run on the CUDA cores here.  An FP32 item gives
+ * bitwise the result of ruqlp_decompose on it (for BF16: with option
+ * "bf16_simt" = 1).  Returns after completion; out[i].flags per item.
+ * Errors: INVALID (with the failing item's index in ruqlp_last_error),
+ * BUDGET, CUDA. */
+ruqlp_status ruqlp_decompose_batch(ruqlp_handle h, int count, const ruqlp_matrix* A,
+                                   const ruqlp_params* prm, ruqlp_outputs* out);
+
 /* The same decomposition with A, prm->omega and the outputs in HOST memory:
  * the library copies A and Omega into its arena, runs ruqlp_decompose's
  * path and copies Q, L, P back.  Errors as ruqlp_decompose. */

@@ -74,10 +74,11 @@ cudaError_t trsm_right_upper(Ty ty, const void* Y, int64_t ldy, const void* R, v
 cudaError_t copy_cast_2d(Ty ts, const void* src, int64_t lds, Ty td, void* dst, int64_t ldd,
                          int64_t rows, int64_t cols, cudaStream_t st);
 
-// L (d x d, type tl, ld d) <- transpose of the upper triangle of R (FP64,
-// ld d), zeros above the diagonal.  With `upper` the upper triangle is
+// L (d x d, type tl, ld ldl (0: d)) <- transpose of the upper triangle of R
+// (FP64, ld d), zeros above the diagonal.  With `upper` the upper triangle is
 // copied as is instead (finish_paper output).
-cudaError_t write_L(const double* R, int d, Ty tl, void* L, bool upper, cudaStream_t st);
+cudaError_t write_L(const double* R, int d, Ty tl, void* L, bool upper, cudaStream_t st,
+                    int ldl = 0);
 
 // Tensor-core BF16 products (k_tc.cu).  trans = false: out[m x dp] = A Bt^T;
 // trans = true: out[n x dp] = A^T Bt^T, with A (m x n, BF16, ld lda) and
@@ -110,6 +111,55 @@ cudaError_t csr_transpose(Ty tv, const int32_t* rowptr, const int32_t* colidx, c
 // Y[rows x d] (ld ldy) = A X with A given by (ptr, idx, vals), X FP32 (ld ldx).
 cudaError_t spmm_csr(Ty tv, const int32_t* ptr, const int32_t* idx, const void* vals, int64_t rows,
                      const float* X, int64_t ldx, int d, float* Y, int64_t ldy, cudaStream_t st);
+
+// ---- batched execution (ruqlp_decompose_batch) ----------------------------
+// One entry of the device problem table: matrix A_i, its FP32 work buffers
+// (ld dp) and its outputs.
+enum BufId : int { B_X = 0, B_Y = 1, B_Z = 2, B_P = 3 };
+struct BMat {
+  const void* A;
+  int64_t lda, m, n;
+  int d, dp, ot, pad;
+  float* X;  // n x dp
+  float* Y;  // m x dp
+  float* Z;  // n x dp
+  float* P;  // n x dp
+  double* partial;
+  double* G;
+  float* tiles;
+  const double* omega;
+  void* Qout;
+  void* Lout;
+  void* Pout;
+  DevStatus* status;
+};
+__host__ __device__ inline float* bbuf(const BMat& b, int id) {
+  return id == B_X ? b.X : (id == B_Y ? b.Y : (id == B_Z ? b.Z : b.P));
+}
+// Row slabs of a Gram over M rows (a function of the shape only, so a matrix
+// gets the same summation order alone and inside a batch).
+__host__ __device__ inline int64_t gram_slabs(int64_t M, int max_slabs, int64_t* slab_rows) {
+  int64_t slabs = (M + 511) / 512;
+  if (slabs > max_slabs) slabs = max_slabs;
+  if (slabs < 1) slabs = 1;
+  int64_t slab = (M + slabs - 1) / slabs;
+  slab = (slab + 31) / 32 * 32;
+  *slab_rows = slab;
+  return (M + slab - 1) / slab;
+}
+int bgemm_tiles(int64_t rows, int d);
+cudaError_t bgemm(bool trans, Ty ta, Ty tb, const BMat* T, const int* prefix, int total, int count,
+                  int src, int dst, cudaStream_t st);
+int bgram_tiles(int64_t M, int d, bool sym, int max_slabs);
+cudaError_t bgram(const BMat* T, const int* prefix, int total, int count, int src, int src2,
+                  int max_slabs, int dmax, cudaStream_t st);
+int btrsm_blocks(int64_t M);
+cudaError_t bchol(const BMat* T, int count, double shift_rel, bool force_shift, int dmax,
+                  cudaStream_t st);
+cudaError_t btrsm(const BMat* T, const int* prefix, int total, int count, int src, int dst,
+                  int dmax, cudaStream_t st);
+cudaError_t bcast_omega(const BMat* T, int count, int64_t max_elems, cudaStream_t st);
+cudaError_t boutputs(const BMat* T, int count, int64_t max_elems, cudaStream_t st);
 
 // Zero the status word.
 cudaError_t status_reset(DevStatus* s, cudaStream_t st);

@@ -16,6 +16,7 @@
 #include "internal.h"
 
 namespace ruqlp {
+size_t chol_tiles_smem(int d);
 namespace {
 
 constexpr int TB = 32;        // tile edge
@@ -111,11 +112,9 @@ __device__ bool factor_tile(float* __restrict__ B, float* __restrict__ Sout, flo
 // upper tiles R_IJ (I <= J) and the diagonal-tile inverses R_KK^{-1}, FP32,
 // 32 x 32 row-major each, to `tiles`: first the nb (nb+1)/2 R tiles in
 // row-of-tiles order, then the nb inverse tiles.
-__global__ void __launch_bounds__(NTH)
-k_chol_tiles(const double* __restrict__ G, int d, double shift_rel, int force_shift,
-             float* __restrict__ tiles, DevStatus* __restrict__ status,
-             const int32_t* __restrict__ gate) {
-  if (gate != nullptr && *gate == 0) return;
+__device__ __forceinline__ void chol_body(const double* __restrict__ G, int d, double shift_rel,
+                                          int force_shift, float* __restrict__ tiles,
+                                          DevStatus* __restrict__ status) {
   extern __shared__ __align__(16) float sm[];
   __shared__ double s_shift;
   __shared__ int s_bad, s_rankdef;
@@ -225,6 +224,21 @@ k_chol_tiles(const double* __restrict__ G, int d, double shift_rel, int force_sh
   }
 }
 
+__global__ void __launch_bounds__(NTH)
+k_chol_tiles(const double* __restrict__ G, int d, double shift_rel, int force_shift,
+             float* __restrict__ tiles, DevStatus* __restrict__ status,
+             const int32_t* __restrict__ gate) {
+  if (gate != nullptr && *gate == 0) return;
+  chol_body(G, d, shift_rel, force_shift, tiles, status);
+}
+
+// One CTA per matrix of the problem table.
+__global__ void __launch_bounds__(NTH)
+k_bchol(const BMat* __restrict__ T, double shift_rel, int force_shift) {
+  const BMat& b = T[blockIdx.x];
+  chol_body(b.G, b.d, shift_rel, force_shift, b.tiles, b.status);
+}
+
 // X = Y R^{-1} by blocked forward substitution over 32-column tiles:
 //   X_J = (Y_J - sum_{K<J} X_K R_KJ) R_JJ^{-1}.
 // A CTA owns 32 rows, staged in shared memory (so X may alias Y).  R tiles
@@ -232,15 +246,15 @@ k_chol_tiles(const double* __restrict__ G, int d, double shift_rel, int force_sh
 // fetched with cp.async NPF tiles ahead of their use (L2 latency is long).
 constexpr int SR = 32;
 constexpr int NPF = 4;  // tile buffers (prefetch distance NPF - 1)
-__global__ void __launch_bounds__(128)
-k_trsm_tiles(const float* __restrict__ Y, int64_t ldy, const float* __restrict__ tiles, float* X,
-             int64_t ldx, int64_t M, int d) {
+__device__ __forceinline__ void trsm_body(const float* __restrict__ Y, int64_t ldy,
+                                          const float* __restrict__ tiles, float* X, int64_t ldx,
+                                          int64_t M, int d, int rb) {
   extern __shared__ __align__(16) float ys[];  // SR x pitch
   __shared__ __align__(16) float Rt[NPF][TB][TB];
   const int nb = (d + TB - 1) / TB;
   const int ntiles = nb * (nb + 1) / 2;
   const int pitch = nb * TB + 4;
-  const int64_t r0 = (int64_t)blockIdx.x * SR;
+  const int64_t r0 = (int64_t)rb * SR;
   const int nr = (int)min((int64_t)SR, M - r0);
   const int t = threadIdx.x;
   // stage the rows (float4 when the row pitch allows it)
@@ -376,7 +390,55 @@ k_trsm_tiles(const float* __restrict__ Y, int64_t ldy, const float* __restrict__
   }
 }
 
+__global__ void __launch_bounds__(128)
+k_trsm_tiles(const float* __restrict__ Y, int64_t ldy, const float* __restrict__ tiles, float* X,
+             int64_t ldx, int64_t M, int d) {
+  trsm_body(Y, ldy, tiles, X, ldx, M, d, blockIdx.x);
+}
+
+// Batched: block t -> (matrix, 32-row block); M = rows of buf[src].
+__global__ void __launch_bounds__(128)
+k_btrsm(const BMat* __restrict__ T, const int* __restrict__ prefix, int count, int src, int dst) {
+  const int t = blockIdx.x;
+  int lo = 0, hi = count;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (prefix[mid] <= t) lo = mid; else hi = mid;
+  }
+  const BMat& b = T[lo];
+  const int64_t M = (src == B_Y) ? b.m : b.n;
+  trsm_body(bbuf(b, src), b.dp, b.tiles, bbuf(b, dst), b.dp, M, b.d, t - prefix[lo]);
+}
+
 }  // namespace
+
+int btrsm_blocks(int64_t M) { return ceil_div(M, SR); }
+
+cudaError_t bchol(const BMat* T, int count, double shift_rel, bool force_shift, int dmax,
+                  cudaStream_t st) {
+  if (count <= 0) return cudaSuccess;
+  if (!chol_tiles_supported(dmax)) return cudaErrorInvalidValue;
+  const size_t sm = chol_tiles_smem(dmax);
+  cudaError_t e =
+      cudaFuncSetAttribute(k_bchol, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  k_bchol<<<count, NTH, sm, st>>>(T, shift_rel, force_shift ? 1 : 0);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t btrsm(const BMat* T, const int* prefix, int total, int count, int src, int dst,
+                  int dmax, cudaStream_t st) {
+  if (total <= 0) return cudaSuccess;
+  const int nb = (dmax + TB - 1) / TB;
+  const size_t sm = (size_t)SR * (nb * TB + 4) * sizeof(float);
+  cudaError_t e =
+      cudaFuncSetAttribute(k_btrsm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  k_btrsm<<<total, 128, sm, st>>>(T, prefix, count, src, dst);
+  count_launch();
+  return cudaGetLastError();
+}
 
 size_t chol_tiles_smem(int d) {
   const int nb = (d + TB - 1) / TB;

@@ -14,28 +14,27 @@ namespace {
 
 constexpr int TM = 64, TK = 32, NT = 64;
 
-__global__ void __launch_bounds__(NT)
-k_gram_tiles(const float* __restrict__ X, int64_t ldx, const float* __restrict__ W, int64_t ldw,
-             int64_t M, int d1, int d2, bool sym, int64_t slab, double* __restrict__ partial,
-             const int32_t* __restrict__ gate) {
-  if (gate != nullptr && *gate == 0) return;
+__device__ __forceinline__ void gram_tile(const float* __restrict__ X, int64_t ldx,
+                                          const float* __restrict__ W, int64_t ldw, int64_t M,
+                                          int d1, int d2, bool sym, int64_t slab,
+                                          double* __restrict__ partial, int tile_id, int slab_id) {
   __shared__ __align__(16) float Xs[TK][TM];
   __shared__ __align__(16) float Ws[TK][TM];
   // tile coordinates: blockIdx.x enumerates (bi, bj) pairs
   const int nb1 = (d1 + TM - 1) / TM, nb2 = (d2 + TM - 1) / TM;
   int bi, bj;
   if (sym) {  // upper triangle of an nb1 x nb1 tile grid, row by row
-    int t = blockIdx.x;
+    int t = tile_id;
     bi = 0;
     while (t >= nb1 - bi) { t -= nb1 - bi; ++bi; }
     bj = bi + t;
   } else {
-    bi = blockIdx.x / nb2;
-    bj = blockIdx.x % nb2;
+    bi = tile_id / nb2;
+    bj = tile_id % nb2;
   }
   const int c0 = bi * TM, c1 = bj * TM;
   const bool diag = sym && bi == bj;
-  const int64_t r_begin = (int64_t)blockIdx.y * slab;
+  const int64_t r_begin = (int64_t)slab_id * slab;
   const int64_t r_end = min(M, r_begin + slab);
   const int t = threadIdx.x;
   const int ty = t >> 3, tx = t & 7;
@@ -106,7 +105,7 @@ k_gram_tiles(const float* __restrict__ X, int64_t ldx, const float* __restrict__
     }
     __syncthreads();
   }
-  double* P = partial + (int64_t)blockIdx.y * d1 * d2;
+  double* P = partial + (int64_t)slab_id * d1 * d2;
 #pragma unroll
   for (int i = 0; i < 8; ++i) {
     const int r = c0 + ty * 8 + i;
@@ -117,6 +116,14 @@ k_gram_tiles(const float* __restrict__ X, int64_t ldx, const float* __restrict__
       if (c < d2) P[(int64_t)r * d2 + c] = (double)acc[i][j];
     }
   }
+}
+
+__global__ void __launch_bounds__(NT)
+k_gram_tiles(const float* __restrict__ X, int64_t ldx, const float* __restrict__ W, int64_t ldw,
+             int64_t M, int d1, int d2, bool sym, int64_t slab, double* __restrict__ partial,
+             const int32_t* __restrict__ gate) {
+  if (gate != nullptr && *gate == 0) return;
+  gram_tile(X, ldx, W, ldw, M, d1, d2, sym, slab, partial, blockIdx.x, blockIdx.y);
 }
 
 // C[i][j] = sum over slabs of the partials (slab order); with sym the entry
@@ -133,7 +140,65 @@ __global__ void k_gram_reduce(const double* __restrict__ P, int slabs, int d1, i
   C[idx] = s;
 }
 
+// Batched Grams: tile t of the launch -> (matrix, tile, slab) through prefix;
+// M = rows of buf[src] (m for Y, n otherwise).
+__global__ void __launch_bounds__(NT)
+k_bgram(const BMat* __restrict__ Tb, const int* __restrict__ prefix, int count, int src, int src2,
+        int max_slabs) {
+  const int t = blockIdx.x;
+  int lo = 0, hi = count;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (prefix[mid] <= t) lo = mid; else hi = mid;
+  }
+  const BMat& b = Tb[lo];
+  const int local = t - prefix[lo];
+  const bool sym = src == src2;
+  const int64_t M = (src == B_Y) ? b.m : b.n;
+  int64_t slab;
+  gram_slabs(M, max_slabs, &slab);
+  const int nb = (b.d + TM - 1) / TM;
+  const int tiles = sym ? nb * (nb + 1) / 2 : nb * nb;
+  gram_tile(bbuf(b, src), b.dp, bbuf(b, src2), b.dp, M, b.d, b.d, sym, slab, b.partial,
+            local % tiles, local / tiles);
+}
+
+__global__ void k_bgram_reduce(const BMat* __restrict__ Tb, int src, int src2, int max_slabs) {
+  const BMat& b = Tb[blockIdx.y];
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int d = b.d;
+  if (idx >= (int64_t)d * d) return;
+  const bool sym = src == src2;
+  const int64_t M = (src == B_Y) ? b.m : b.n;
+  int64_t slab;
+  const int slabs = (int)gram_slabs(M, max_slabs, &slab);
+  const int i = (int)(idx / d), j = (int)(idx % d);
+  const int64_t so = (sym && j < i) ? ((int64_t)j * d + i) : idx;
+  double s = 0.0;
+  for (int z = 0; z < slabs; ++z) s += b.partial[(int64_t)z * d * d + so];
+  b.G[idx] = s;
+}
+
 }  // namespace
+
+int bgram_tiles(int64_t M, int d, bool sym, int max_slabs) {
+  const int nb = (d + TM - 1) / TM;
+  int64_t slab;
+  return (sym ? nb * (nb + 1) / 2 : nb * nb) * (int)gram_slabs(M, max_slabs, &slab);
+}
+
+cudaError_t bgram(const BMat* T, const int* prefix, int total, int count, int src, int src2,
+                  int max_slabs, int dmax, cudaStream_t st) {
+  if (total <= 0) return cudaSuccess;
+  k_bgram<<<total, NT, 0, st>>>(T, prefix, count, src, src2, max_slabs);
+  count_launch();
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_bgram_reduce<<<dim3(ceil_div((int64_t)dmax * dmax, 256), count), 256, 0, st>>>(T, src, src2,
+                                                                                 max_slabs);
+  count_launch();
+  return cudaGetLastError();
+}
 
 cudaError_t gram_f32(const float* X, int64_t ldx, const float* W, int64_t ldw, int64_t M, int d1,
                      int d2, double* C, double* partial, int max_slabs, const int32_t* gate,
@@ -142,15 +207,8 @@ cudaError_t gram_f32(const float* X, int64_t ldx, const float* W, int64_t ldw, i
   const bool sym = (X == W) && (ldx == ldw) && (d1 == d2);
   const int nb1 = (d1 + TM - 1) / TM, nb2 = (d2 + TM - 1) / TM;
   const int tiles = sym ? nb1 * (nb1 + 1) / 2 : nb1 * nb2;
-  // slabs: about 4 CTAs per SM, at least 128 rows each
-  int64_t slabs = (4 * 152 + tiles - 1) / tiles;
-  const int64_t by_rows = (M + 127) / 128;
-  if (slabs > by_rows) slabs = by_rows;
-  if (slabs > max_slabs) slabs = max_slabs;
-  if (slabs < 1) slabs = 1;
-  int64_t slab = (M + slabs - 1) / slabs;
-  slab = (slab + TK - 1) / TK * TK;
-  slabs = (M + slab - 1) / slab;
+  int64_t slab;
+  const int64_t slabs = gram_slabs(M, max_slabs, &slab);
   if ((((uintptr_t)X | (uintptr_t)W) & 15) || (ldx & 3) || (ldw & 3)) return cudaErrorInvalidValue;
   k_gram_tiles<<<dim3(tiles, (unsigned)slabs), NT, 0, st>>>(X, ldx, W, ldw, M, d1, d2, sym, slab,
                                                             partial, gate);

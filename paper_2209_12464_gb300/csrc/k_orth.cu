@@ -165,14 +165,15 @@ __global__ void k_copy_cast(const TS* __restrict__ src, int64_t lds, TD* __restr
 }
 
 template <typename TL>
-__global__ void k_write_L(const double* __restrict__ R, int d, TL* __restrict__ L, bool upper) {
+__global__ void k_write_L(const double* __restrict__ R, int d, TL* __restrict__ L, bool upper,
+                          int ldl) {
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= d * d) return;
   const int i = idx / d, j = idx % d;
   double v;
   if (upper) v = (j >= i) ? R[(int64_t)i * d + j] : 0.0;
   else       v = (j <= i) ? R[(int64_t)j * d + i] : 0.0;
-  L[idx] = Cvt<TL>::from(v);
+  L[(int64_t)i * ldl + j] = Cvt<TL>::from(v);
 }
 
 __global__ void k_status(DevStatus* s, int full) {
@@ -267,15 +268,17 @@ cudaError_t copy_cast_2d(Ty ts, const void* src, int64_t lds, Ty td, void* dst, 
   return cudaErrorInvalidValue;
 }
 
-cudaError_t write_L(const double* R, int d, Ty tl, void* L, bool upper, cudaStream_t st) {
+cudaError_t write_L(const double* R, int d, Ty tl, void* L, bool upper, cudaStream_t st,
+                    int ldl) {
   const int grid = ceil_div((int64_t)d * d, 256);
+  if (ldl <= 0) ldl = d;
   if (tl == Ty::F64) {
-    k_write_L<double><<<grid, 256, 0, st>>>(R, d, (double*)L, upper);
+    k_write_L<double><<<grid, 256, 0, st>>>(R, d, (double*)L, upper, ldl);
     count_launch();
     return cudaGetLastError();
   }
   if (tl == Ty::F32) {
-    k_write_L<float><<<grid, 256, 0, st>>>(R, d, (float*)L, upper);
+    k_write_L<float><<<grid, 256, 0, st>>>(R, d, (float*)L, upper, ldl);
     count_launch();
     return cudaGetLastError();
   }

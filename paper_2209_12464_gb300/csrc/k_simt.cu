@@ -6,6 +6,8 @@
 // 4 x 4 sub-tile.  K is walked in 16-wide slabs staged in shared memory.
 // Out-of-range rows/columns are zero-filled on load and skipped on store, so
 // any M, K, N works (ragged tails included).
+#include <type_traits>
+
 #include "internal.h"
 
 namespace ruqlp {
@@ -24,21 +26,21 @@ template <typename T> __device__ __forceinline__ T zero() { return T(0); }
 // TRANS_A = true:  A is K x M (row-major, lda): C = A^T B.
 // blockIdx.z selects a K slab [kz0, kz1); with PARTIAL the FP64 tile sums go to
 // C + z*M*ldc (a [splits][M][ldc] FP64 buffer).
-template <bool TRANS_A, typename TA, typename TB, typename TC, Mul MODE, bool PARTIAL>
-__global__ void __launch_bounds__(NT)
-k_gemm(const TA* __restrict__ A, int64_t lda, const TB* __restrict__ B, int64_t ldb,
-       TC* __restrict__ C, int64_t ldc, int64_t M, int64_t K, int64_t N, int64_t kslab,
-       const int32_t* __restrict__ gate) {
-  if (gate != nullptr && *gate == 0) return;
+template <bool TRANS_A, typename TA, typename TB, typename TC, Mul MODE, bool PARTIAL,
+          bool ROUND_B = false>
+__device__ __forceinline__ void gemm_tile(const TA* __restrict__ A, int64_t lda,
+                                          const TB* __restrict__ B, int64_t ldb,
+                                          TC* __restrict__ C, int64_t ldc, int64_t M, int64_t K,
+                                          int64_t N, int64_t kslab, int bx, int by, int bz) {
   using TM = typename MulT<MODE>::mul;
   using TAcc = typename MulT<MODE>::acc;
   __shared__ TM As[BK][BM + 4];
   __shared__ TM Bs[BK][BN + 4];
   const int t = threadIdx.x;
   const int tx = t & 15, ty = t >> 4;
-  const int64_t m0 = (int64_t)blockIdx.x * BM;
-  const int64_t n0 = (int64_t)blockIdx.y * BN;
-  const int64_t kz0 = (int64_t)blockIdx.z * kslab;
+  const int64_t m0 = (int64_t)bx * BM;
+  const int64_t n0 = (int64_t)by * BN;
+  const int64_t kz0 = (int64_t)bz * kslab;
   const int64_t kz1 = min(K, kz0 + kslab);
 
   TAcc acc[4][4];
@@ -67,7 +69,10 @@ k_gemm(const TA* __restrict__ A, int64_t lda, const TB* __restrict__ B, int64_t 
       const int r = e / BN, c = e % BN;
       const int64_t gk = k0 + r, gn = n0 + c;
       TM v = zero<TM>();
-      if (gk < kz1 && gn < N) v = Cvt<TM>::from(B[gk * ldb + gn]);
+      if (gk < kz1 && gn < N) {
+        v = Cvt<TM>::from(B[gk * ldb + gn]);
+        if constexpr (ROUND_B) v = __bfloat162float(__float2bfloat16_rn(v));
+      }
       Bs[r][c] = v;
     }
     __syncthreads();
@@ -95,7 +100,7 @@ k_gemm(const TA* __restrict__ A, int64_t lda, const TB* __restrict__ B, int64_t 
     __syncthreads();
   }
 
-  TC* Cz = PARTIAL ? C + (int64_t)blockIdx.z * M * ldc : C;
+  TC* Cz = PARTIAL ? C + (int64_t)bz * M * ldc : C;
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
     const int64_t gm = m0 + ty * 4 + i;
@@ -106,6 +111,40 @@ k_gemm(const TA* __restrict__ A, int64_t lda, const TB* __restrict__ B, int64_t 
       if (gn < N) Cz[gm * ldc + gn] = Cvt<TC>::from(acc[i][j]);
     }
   }
+}
+
+template <bool TRANS_A, typename TA, typename TB, typename TC, Mul MODE, bool PARTIAL>
+__global__ void __launch_bounds__(NT)
+k_gemm(const TA* __restrict__ A, int64_t lda, const TB* __restrict__ B, int64_t ldb,
+       TC* __restrict__ C, int64_t ldc, int64_t M, int64_t K, int64_t N, int64_t kslab,
+       const int32_t* __restrict__ gate) {
+  if (gate != nullptr && *gate == 0) return;
+  gemm_tile<TRANS_A, TA, TB, TC, MODE, PARTIAL>(A, lda, B, ldb, C, ldc, M, K, N, kslab,
+                                                blockIdx.x, blockIdx.y, blockIdx.z);
+}
+
+// Batched products over a problem table: tile t of the whole launch maps to
+// matrix i = (prefix[i] <= t < prefix[i+1]) and a 64 x 64 output tile of it.
+//   TRANS_A = false: buf[dst] (m x d) = A buf[src] (n x d)
+//   TRANS_A = true:  buf[dst] (n x d) = A^T buf[src] (m x d)
+template <bool TRANS_A, typename TA, typename TB>
+__global__ void __launch_bounds__(NT)
+k_bgemm(const BMat* __restrict__ T, const int* __restrict__ prefix, int count, int src, int dst) {
+  const int t = blockIdx.x;
+  int lo = 0, hi = count;  // largest i with prefix[i] <= t
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (prefix[mid] <= t) lo = mid; else hi = mid;
+  }
+  const BMat& b = T[lo];
+  const int local = t - prefix[lo];
+  const int ntn = (b.d + BN - 1) / BN;
+  const int64_t Mout = TRANS_A ? b.n : b.m, K = TRANS_A ? b.m : b.n;
+  // with BF16 A the skinny operand is rounded to BF16 as it is staged, the
+  // product the single-matrix BF16 path computes
+  gemm_tile<TRANS_A, TA, TB, float, Mul::F32, false, std::is_same<TA, __nv_bfloat16>::value>(
+      (const TA*)b.A, b.lda, (const TB*)bbuf(b, src), b.dp, bbuf(b, dst), b.dp, Mout, K, b.d,
+      ((K + BK - 1) / BK) * BK, local / ntn, local % ntn, 0);
 }
 
 // C[i][j] = sum_z P[z][i][j] in z order (deterministic), cast to TC.
@@ -179,6 +218,28 @@ cudaError_t simt_gemm_nn(Ty ta, Ty tb, Ty tc, Mul mul, const void* A, int64_t ld
   RUQLP_DISPATCH(false, Ty::BF16, Ty::BF16, Ty::F32, Mul::F32, __nv_bfloat16, __nv_bfloat16, float)
   RUQLP_DISPATCH(false, Ty::F32, Ty::F32, Ty::F32, Mul::F32_ACC64, float, float, float)
   return cudaErrorInvalidValue;
+}
+
+int bgemm_tiles(int64_t rows, int d) { return ceil_div(rows, BM) * ceil_div(d, BN); }
+
+cudaError_t bgemm(bool trans, Ty ta, Ty tb, const BMat* T, const int* prefix, int total, int count,
+                  int src, int dst, cudaStream_t st) {
+  if (total <= 0) return cudaSuccess;
+  if (tb == Ty::F32) {
+    if (ta == Ty::F32) {
+      if (trans) k_bgemm<true, float, float><<<total, NT, 0, st>>>(T, prefix, count, src, dst);
+      else k_bgemm<false, float, float><<<total, NT, 0, st>>>(T, prefix, count, src, dst);
+    } else if (ta == Ty::BF16) {
+      if (trans) k_bgemm<true, __nv_bfloat16, float><<<total, NT, 0, st>>>(T, prefix, count, src, dst);
+      else k_bgemm<false, __nv_bfloat16, float><<<total, NT, 0, st>>>(T, prefix, count, src, dst);
+    } else {
+      return cudaErrorInvalidValue;
+    }
+  } else {
+    return cudaErrorInvalidValue;
+  }
+  count_launch();
+  return cudaGetLastError();
 }
 
 cudaError_t simt_gemm_tn(Ty ta, Ty tb, Ty tc, Mul mul, const void* A, int64_t lda,

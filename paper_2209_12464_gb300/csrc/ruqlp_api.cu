@@ -2,6 +2,7 @@
 // host-side orchestration of Algorithm 1 + Algorithm 2 (Section III) in the
 // right-sketch orientation.  Every arithmetic step runs in the kernels of
 // this library; the host only validates, carves the arena and launches.
+#include <algorithm>
 #include <atomic>
 #include <mutex>
 #include <stdio.h>
@@ -36,6 +37,16 @@ struct ruqlp_ctx {
   struct Span { int cat; cudaEvent_t a, b; };
   std::vector<Span> spans;
   std::vector<cudaEvent_t> pool;
+  // batched decompositions: CUDA graphs of the launch sequence, keyed by the
+  // batch signature (shapes, q, dtype, arena address)
+  struct BatchGraph {
+    std::vector<int64_t> key;
+    cudaGraphExec_t exec = nullptr;
+    int uses = 0;
+  };
+  std::vector<BatchGraph> graphs;
+  int batch_graphs = 1;  // option "batch_graph"
+  cudaStream_t cap_stream = nullptr;  // capture stream (the legacy stream cannot capture)
   int64_t prof_count[6] = {0, 0, 0, 0, 0, 0};
   double prof_ms[6] = {0, 0, 0, 0, 0, 0};
 };
@@ -93,14 +104,14 @@ struct ProfScope {
   ruqlp_ctx* h;
   int cat;
   cudaEvent_t a = nullptr;
-  ProfScope(ruqlp_ctx* h_, int c) : h(h_), cat(c) {
-    if (h->profile) {
+  ProfScope(ruqlp_ctx* h_, int c) : h(h_), cat(c) {  // h == nullptr: no span
+    if (h && h->profile) {
       a = ev_get(h);
       cudaEventRecord(a, h->stream);
     }
   }
   ~ProfScope() {
-    if (h->profile && a) {
+    if (h && h->profile && a) {
       cudaEvent_t b = ev_get(h);
       cudaEventRecord(b, h->stream);
       h->spans.push_back({cat, a, b});
@@ -138,13 +149,15 @@ constexpr int kMaxSplits = 64;
 
 // Workspace layout for one problem.
 struct Layout {
-  size_t X, Y, Z, P, partial, G, R, Rw, Bt, frag, colptr, rowidx, cvals, cscratch, total;
+  size_t X, Y, Z, P, partial, G, R, Rw, Bt, frag, colptr, rowidx, cvals, cscratch, T, total;
 };
 
 inline int64_t round8(int64_t x) { return (x + 7) / 8 * 8; }
 
 // nnz >= 0: A is CSR with nnz nonzeros of val_bytes each (CSC copy kept too).
-Layout layout_of(int64_t m, int64_t n, int d, Ty ct, int64_t nnz = -1, size_t val_bytes = 0) {
+// finish: room for Algorithm 1 step 5 (an m x dp buffer for Q P~).
+Layout layout_of(int64_t m, int64_t n, int d, Ty ct, int64_t nnz = -1, size_t val_bytes = 0,
+                 bool finish = false) {
   Layout L{};
   const int dp = round16(d);
   const size_t wes = ty_size(work_ty(ct));
@@ -170,6 +183,7 @@ Layout layout_of(int64_t m, int64_t n, int d, Ty ct, int64_t nnz = -1, size_t va
     L.Bt = take((size_t)dp * round8(m > n ? m : n) * 2);
     L.frag = take(dp <= 256 ? tc_frag_bytes(dp) : 0);
   }
+  if (finish) L.T = take((size_t)m * dp * wes);
   if (nnz >= 0) {
     L.colptr = take((size_t)(n + 1) * sizeof(int32_t));
     L.rowidx = take((size_t)(nnz > 0 ? nnz : 1) * sizeof(int32_t));
@@ -194,6 +208,9 @@ ruqlp_status ensure_arena(ruqlp_ctx* h, size_t bytes) {
   }
   CK(cudaMalloc(&h->arena, bytes));
   h->arena_bytes = bytes;
+  for (auto& g : h->graphs)
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+  h->graphs.clear();
   return RUQLP_OK;
 }
 
@@ -444,8 +461,8 @@ ruqlp_status prepare_csr(ruqlp_ctx* h, const Layout& Lo, Job& J) {
 
 ruqlp_status run_dense(ruqlp_ctx* h, const Job& J0) {
   Job J = J0;
-  const Layout Lo = J.csr ? layout_of(J.m, J.n, J.d, J.ct, J.nnz, ty_size(J.tv))
-                          : layout_of(J.m, J.n, J.d, J.ct);
+  const Layout Lo = J.csr ? layout_of(J.m, J.n, J.d, J.ct, J.nnz, ty_size(J.tv), J.finish_paper)
+                          : layout_of(J.m, J.n, J.d, J.ct, -1, 0, J.finish_paper);
   ruqlp_status s = ensure_arena(h, Lo.total);
   if (s != RUQLP_OK) return s;
   CK(status_reset(h->status, h->stream));
@@ -507,6 +524,29 @@ ruqlp_status run_dense(ruqlp_ctx* h, const Job& J0) {
   else
     CK(gram_f32((const float*)Pb, dp, (const float*)Z, dp, J.n, d, d, G, partial, kMaxSplits,
                 nullptr, st));
+  if (J.finish_paper) {
+    // Algorithm 1 step 5 in this orientation: [P~, R~] = qr(L), L = R_B^T;
+    // Q <- Q P~, middle factor R~ (upper triangular): A ~= (Q P~) R~ P^T.
+    void* Lw = X;   // d x dp: L, then P~
+    void* Lc = Z;   // d x dp: a copy of L for R~ = P~^T L
+    void* QP = base + Lo.T;
+    CK(write_L(G, d, wt, Lw, false, st, dp));
+    CK(write_L(G, d, wt, Lc, false, st, dp));
+    s = orth(h, Lo, J, Lw, Lw, d);
+    if (s != RUQLP_OK) return s;
+    if (wt == Ty::F64)
+      CK(simt_gemm_tn(wt, wt, Ty::F64, Mul::F64, Lw, dp, Lc, dp, G, d, d, d, d,
+                      tn_splits(d, d, d, kMaxSplits), partial, nullptr, st));
+    else
+      CK(gram_f32((const float*)Lw, dp, (const float*)Lc, dp, d, d, d, G, partial, kMaxSplits,
+                  nullptr, st));
+    CK(simt_gemm_nn(wt, wt, wt, wt == Ty::F64 ? Mul::F64 : Mul::F32, Y, dp, Lw, dp, QP, dp, J.m,
+                    d, d, st));
+    CK(write_L(G, d, J.ot, J.Lout, true, st));
+    CK(copy_cast_2d(wt, QP, dp, J.ot, J.Qout, d, J.m, d, st));
+    CK(copy_cast_2d(wt, Pb, dp, J.ot, J.Pout, d, J.n, d, st));
+    return RUQLP_OK;
+  }
   // a7: outputs
   CK(write_L(G, d, J.ot, J.Lout, false, st));
   CK(copy_cast_2d(wt, Y, dp, J.ot, J.Qout, d, J.m, d, st));
@@ -530,6 +570,235 @@ ruqlp_status finish(ruqlp_ctx* h, ruqlp_outputs* out) {
 }
 
 }  // namespace
+
+
+// ---------------------------------------------------------------------------
+// Batched decompositions (many dense matrices of uneven shapes, FP32 or BF16,
+// one q): every phase is one launch over a device problem table (BMat); the
+// per-matrix Cholesky runs one CTA per matrix.  The sequence of launches
+// depends only on the batch signature and is replayed from a CUDA graph.
+// Products use the CUDA-core kernels (BF16 A with FP32 accumulation); Grams,
+// Cholesky factorisations and triangular solves use the same device code and
+// shape-only work splits as single decompositions, so an FP32 matrix gives
+// bitwise the same Q, L, P alone (ruqlp_decompose, bf16_simt for BF16) and
+// inside a batch.
+namespace {
+
+struct BatchPlan {
+  std::vector<BMat> table;
+  std::vector<int> prefix[7];  // NN, TN, gramY, gramN, gramPZ, trsmY, trsmN
+  size_t off_table, off_prefix[7], off_status, total;
+  int dmax;
+  int64_t max_omega, max_out;
+};
+
+enum { PF_NN = 0, PF_TN, PF_GY, PF_GN, PF_GPZ, PF_TY, PF_TN2 };
+
+ruqlp_status batch_launches(ruqlp_ctx* h, const BatchPlan& bp, int count, int q, Ty ct,
+                            cudaStream_t st) {
+  char* base = (char*)h->arena;
+  const BMat* T = (const BMat*)(base + bp.off_table);
+  auto pre = [&](int k) { return (const int*)(base + bp.off_prefix[k]); };
+  auto tot = [&](int k) { return bp.prefix[k][count]; };
+  const double s1 = 64.0 * 5.960464477539063e-08;
+  // profiling spans only on the eager path (st is the handle's stream there)
+  ruqlp_ctx* ph = (st == h->stream) ? h : nullptr;
+  ProfScope step(ph, PROF_STEP);
+  CK(cudaMemsetAsync(base + bp.off_status, 0, sizeof(DevStatus) * count, st));
+  auto orth_b = [&](int src, int dst, int passes) -> ruqlp_status {
+    ProfScope sp(ph, PROF_ORTH);
+    const int gp = (src == B_Y) ? PF_GY : PF_GN;
+    const int tp = (src == B_Y) ? PF_TY : PF_TN2;
+    for (int pass = 0; pass < passes; ++pass) {
+      const int from = pass == 0 ? src : dst;
+      CK(bgram(T, pre(gp), tot(gp), count, from, from, kMaxSplits, bp.dmax, st));
+      CK(bchol(T, count, s1, pass == 0, bp.dmax, st));
+      CK(btrsm(T, pre(tp), tot(tp), count, from, dst, bp.dmax, st));
+    }
+    return RUQLP_OK;
+  };
+  auto prod = [&](bool trans, int src, int dst) -> ruqlp_status {
+    ProfScope sp(ph, trans ? PROF_ATX : PROF_AX);
+    const int pf = trans ? PF_TN : PF_NN;
+    CK(bgemm(trans, ct, Ty::F32, T, pre(pf), tot(pf), count, src, dst, st));
+    return RUQLP_OK;
+  };
+  ruqlp_status s;
+  CK(bcast_omega(T, count, bp.max_omega, st));
+  if ((s = prod(false, B_X, B_Y)) != RUQLP_OK) return s;
+  if ((s = orth_b(B_Y, B_Y, q == 0 ? 3 : 2)) != RUQLP_OK) return s;
+  for (int it = 0; it < q; ++it) {
+    if ((s = prod(true, B_Y, B_Z)) != RUQLP_OK) return s;
+    if ((s = orth_b(B_Z, B_Z, 2)) != RUQLP_OK) return s;
+    if ((s = prod(false, B_Z, B_Y)) != RUQLP_OK) return s;
+    if ((s = orth_b(B_Y, B_Y, it == q - 1 ? 3 : 2)) != RUQLP_OK) return s;
+  }
+  if ((s = prod(true, B_Y, B_Z)) != RUQLP_OK) return s;
+  if ((s = orth_b(B_Z, B_P, 3)) != RUQLP_OK) return s;
+  CK(bgram(T, pre(PF_GPZ), tot(PF_GPZ), count, B_P, B_Z, kMaxSplits, bp.dmax, st));
+  CK(boutputs(T, count, bp.max_out, st));
+  return RUQLP_OK;
+}
+
+}  // namespace
+
+extern "C" ruqlp_status ruqlp_decompose_batch(ruqlp_handle h, int count, const ruqlp_matrix* A,
+                                              const ruqlp_params* prm, ruqlp_outputs* out) {
+  if (!h) return RUQLP_ERR_INVALID;
+  h->err.clear();
+  if (count < 1 || !A || !prm || !out) return fail(h, RUQLP_ERR_INVALID, "empty or NULL batch");
+  Ty ct0 = Ty::F32;
+  int q0 = 0;
+  std::vector<int> dd(count);
+  for (int i = 0; i < count; ++i) {
+    int64_t m, n;
+    ruqlp_status s = validate(h, &A[i], &prm[i], &out[i], &m, &n, &dd[i]);
+    if (s != RUQLP_OK) return fail(h, s, "batch item %d: %s", i, h->err.c_str());
+    if (A[i].is_csr) return fail(h, RUQLP_ERR_INVALID, "batch item %d: CSR is not batched", i);
+    Ty ct;
+    ty_of(prm[i].compute, &ct);
+    if (ct == Ty::F64) return fail(h, RUQLP_ERR_INVALID, "batches are FP32 or BF16");
+    if (i == 0) {
+      ct0 = ct;
+      q0 = prm[i].q;
+    } else if (ct != ct0 || prm[i].q != q0) {
+      return fail(h, RUQLP_ERR_INVALID, "all items of a batch need the same dtype and q");
+    }
+    if (prm[i].finish_paper) return fail(h, RUQLP_ERR_INVALID, "finish_paper is not batched");
+    if (!chol_tiles_supported(dd[i])) return fail(h, RUQLP_ERR_INVALID, "batched d must be <= 256");
+  }
+  CK(cudaSetDevice(h->device));
+  // workspace: per-matrix buffers, then the table, prefix arrays and statuses
+  BatchPlan bp;
+  bp.table.resize(count);
+  bp.dmax = 0;
+  bp.max_omega = 0;
+  bp.max_out = 0;
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    const size_t o = off;
+    off = align_up(off + bytes, 256);
+    return o;
+  };
+  std::vector<size_t> oX(count), oY(count), oZ(count), oP(count), oPa(count), oG(count),
+      oT(count);
+  for (int i = 0; i < count; ++i) {
+    const int64_t m = A[i].dense.m, n = A[i].dense.n;
+    const int d = dd[i], dp = round16(d);
+    int64_t slab;
+    const int64_t sl = std::max(gram_slabs(m, kMaxSplits, &slab), gram_slabs(n, kMaxSplits, &slab));
+    oX[i] = take((size_t)n * dp * 4);
+    oY[i] = take((size_t)m * dp * 4);
+    oZ[i] = take((size_t)n * dp * 4);
+    oP[i] = take((size_t)n * dp * 4);
+    oPa[i] = take((size_t)sl * d * d * 8);
+    oG[i] = take((size_t)d * d * 8);
+    oT[i] = take(chol_tiles_bytes(d));
+    bp.dmax = std::max(bp.dmax, d);
+    bp.max_omega = std::max<int64_t>(bp.max_omega, n * dp);
+    bp.max_out = std::max<int64_t>(bp.max_out, (m + n) * d + (int64_t)d * d);
+    for (int k = 0; k < 7; ++k) bp.prefix[k].resize(count + 1);
+  }
+  bp.off_table = take(sizeof(BMat) * count);
+  for (int k = 0; k < 7; ++k) bp.off_prefix[k] = take(sizeof(int) * (count + 1));
+  bp.off_status = take(sizeof(DevStatus) * count);
+  bp.total = off;
+  ruqlp_status s = ensure_arena(h, bp.total);
+  if (s != RUQLP_OK) return s;
+  char* base = (char*)h->arena;
+  for (int k = 0; k < 7; ++k) bp.prefix[k][0] = 0;
+  for (int i = 0; i < count; ++i) {
+    BMat& b = bp.table[i];
+    const ruqlp_dense& D = A[i].dense;
+    b.A = D.data;
+    b.lda = D.ld;
+    b.m = D.m;
+    b.n = D.n;
+    b.d = dd[i];
+    b.dp = round16(dd[i]);
+    Ty ot;
+    ty_of(out[i].out_dtype, &ot);
+    b.ot = (int)ot;
+    b.X = (float*)(base + oX[i]);
+    b.Y = (float*)(base + oY[i]);
+    b.Z = (float*)(base + oZ[i]);
+    b.P = (float*)(base + oP[i]);
+    b.partial = (double*)(base + oPa[i]);
+    b.G = (double*)(base + oG[i]);
+    b.tiles = (float*)(base + oT[i]);
+    b.omega = prm[i].omega;
+    b.Qout = out[i].Q;
+    b.Lout = out[i].L;
+    b.Pout = out[i].P;
+    b.status = (DevStatus*)(base + bp.off_status) + i;
+    const int cnt[7] = {bgemm_tiles(b.m, b.d), bgemm_tiles(b.n, b.d),
+                        bgram_tiles(b.m, b.d, true, kMaxSplits),
+                        bgram_tiles(b.n, b.d, true, kMaxSplits),
+                        bgram_tiles(b.n, b.d, false, kMaxSplits), btrsm_blocks(b.m),
+                        btrsm_blocks(b.n)};
+    for (int k = 0; k < 7; ++k) bp.prefix[k][i + 1] = bp.prefix[k][i] + cnt[k];
+  }
+  cudaStream_t st = h->stream;
+  CK(cudaMemcpyAsync(base + bp.off_table, bp.table.data(), sizeof(BMat) * count,
+                     cudaMemcpyHostToDevice, st));
+  for (int k = 0; k < 7; ++k)
+    CK(cudaMemcpyAsync(base + bp.off_prefix[k], bp.prefix[k].data(), sizeof(int) * (count + 1),
+                       cudaMemcpyHostToDevice, st));
+  // graph cache: the launch sequence depends on shapes, q, dtype and the arena
+  std::vector<int64_t> key = {count, q0, (int64_t)ct0, (int64_t)(uintptr_t)h->arena};
+  for (int i = 0; i < count; ++i) {
+    key.push_back(bp.table[i].m);
+    key.push_back(bp.table[i].n);
+    key.push_back(bp.table[i].d);
+  }
+  ruqlp_ctx::BatchGraph* g = nullptr;
+  for (auto& c : h->graphs)
+    if (c.key == key) g = &c;
+  const bool graphs = h->batch_graphs && !h->profile;  // profiling runs eagerly
+  if (graphs && g && g->exec) {
+    CK(cudaGraphLaunch(g->exec, st));
+    g->uses++;
+  } else {
+    const bool capture = graphs && g != nullptr;  // second sighting: capture it
+    if (capture) {
+      if (!h->cap_stream) CK(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+      CK(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
+      s = batch_launches(h, bp, count, q0, ct0, h->cap_stream);
+      cudaGraph_t graph = nullptr;
+      const cudaError_t ec = cudaStreamEndCapture(h->cap_stream, &graph);
+      if (s != RUQLP_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return s;
+      }
+      CK(ec);
+      cudaGraphExec_t exec = nullptr;
+      const cudaError_t ei = cudaGraphInstantiate(&exec, graph, 0);
+      cudaGraphDestroy(graph);
+      CK(ei);
+      g->exec = exec;
+      CK(cudaGraphLaunch(exec, st));
+    } else {
+      s = batch_launches(h, bp, count, q0, ct0, st);
+      if (s != RUQLP_OK) return s;
+      if (graphs && g == nullptr) {
+        if (h->graphs.size() >= 8) {
+          if (h->graphs.front().exec) cudaGraphExecDestroy(h->graphs.front().exec);
+          h->graphs.erase(h->graphs.begin());
+        }
+        ruqlp_ctx::BatchGraph ng;
+        ng.key = key;
+        h->graphs.push_back(ng);
+      }
+    }
+  }
+  std::vector<DevStatus> stat(count);
+  CK(cudaMemcpyAsync(stat.data(), base + bp.off_status, sizeof(DevStatus) * count,
+                     cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  if (h->profile) prof_collect(h);
+  for (int i = 0; i < count; ++i) out[i].flags = (uint32_t)stat[i].flags;
+  return RUQLP_OK;
+}
 
 extern "C" {
 
@@ -561,6 +830,9 @@ ruqlp_status ruqlp_destroy(ruqlp_handle h) {
   if (!h) return RUQLP_ERR_INVALID;
   cudaSetDevice(h->device);
   cudaStreamSynchronize(h->stream);
+  for (auto& g : h->graphs)
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+  if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   if (h->arena) cudaFree(h->arena);
   if (h->status) cudaFree(h->status);
   if (h->status_host) cudaFreeHost(h->status_host);
@@ -576,6 +848,10 @@ ruqlp_status ruqlp_set_stream(ruqlp_handle h, void* stream) {
 
 ruqlp_status ruqlp_set_option(ruqlp_handle h, const char* name, int64_t value) {
   if (!h || !name) return RUQLP_ERR_INVALID;
+  if (strcmp(name, "batch_graph") == 0) {
+    h->batch_graphs = value ? 1 : 0;
+    return RUQLP_OK;
+  }
   if (strcmp(name, "orth_full") == 0) {
     h->orth_full = value ? 1 : 0;
     return RUQLP_OK;
@@ -631,8 +907,6 @@ ruqlp_status ruqlp_decompose(ruqlp_handle h, const ruqlp_matrix* A, const ruqlp_
   J.Qout = out->Q;
   J.Lout = out->L;
   J.Pout = out->P;
-  if (J.finish_paper)
-    return fail(h, RUQLP_ERR_INVALID, "finish_paper is not available in this build");
   J.use_tc = !J.csr && J.ct == Ty::BF16 && !h->bf16_simt && tc_supported(J.A, J.lda, J.dp);
   s = run_dense(h, J);
   if (s != RUQLP_OK) return s;
@@ -650,12 +924,10 @@ ruqlp_status ruqlp_decompose_host(ruqlp_handle h, const ruqlp_matrix* A,
   CK(cudaSetDevice(h->device));
   Job J{};
   fill_job(A, prm, out, m, n, d, J);
-  if (J.finish_paper)
-    return fail(h, RUQLP_ERR_INVALID, "finish_paper is not available in this build");
   const size_t oes = ty_size(J.ot);
   // the workspace first, then staging for A, Omega and the outputs
-  const Layout Lo = J.csr ? layout_of(m, n, d, J.ct, J.nnz, ty_size(J.tv))
-                          : layout_of(m, n, d, J.ct);
+  const Layout Lo = J.csr ? layout_of(m, n, d, J.ct, J.nnz, ty_size(J.tv), J.finish_paper)
+                          : layout_of(m, n, d, J.ct, -1, 0, J.finish_paper);
   size_t off = align_up(Lo.total, 256);
   auto take = [&](size_t bytes) {
     const size_t o = off;

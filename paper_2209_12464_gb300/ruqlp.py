@@ -66,6 +66,8 @@ _SIGS = {
     "ruqlp_workspace_bytes": (c_size_t, [c_int64, c_int64, c_int, c_int, c_int64]),
     "ruqlp_decompose": (c_int, [c_void_p, ctypes.POINTER(Matrix), ctypes.POINTER(Params),
                                 ctypes.POINTER(Outputs)]),
+    "ruqlp_decompose_batch": (c_int, [c_void_p, c_int, ctypes.POINTER(Matrix),
+                                      ctypes.POINTER(Params), ctypes.POINTER(Outputs)]),
     "ruqlp_decompose_host": (c_int, [c_void_p, ctypes.POINTER(Matrix), ctypes.POINTER(Params),
                                      ctypes.POINTER(Outputs)]),
     "ruqlp_last_error": (c_char_p, [c_void_p]),
@@ -135,6 +137,11 @@ def ruqlp_decompose(h, A, prm, out):
     return lib().ruqlp_decompose(h, ctypes.byref(A), ctypes.byref(prm), ctypes.byref(out))
 
 
+def ruqlp_decompose_batch(h, count, A, prm, out):
+    """A, prm, out: ctypes arrays (Matrix * count, ...)."""
+    return lib().ruqlp_decompose_batch(h, count, A, prm, out)
+
+
 def ruqlp_decompose_host(h, A, prm, out):
     return lib().ruqlp_decompose_host(h, ctypes.byref(A), ctypes.byref(prm), ctypes.byref(out))
 
@@ -184,6 +191,43 @@ class RuqlpError(RuntimeError):
 def _dtype_code(t):
     import torch
     return {torch.float64: F64, torch.float32: F32, torch.bfloat16: BF16}[t]
+
+
+class Batch:
+    """ctypes arrays of one batched call, built once and reusable."""
+
+    def __init__(self, handle, As, omegas, ks, p, q, out_dtype=None, ps=None, qs=None):
+        import torch
+        cnt = len(As)
+        od = out_dtype or torch.float32
+        ps = list(ps) if ps is not None else [p] * cnt
+        qs = list(qs) if qs is not None else [q] * cnt
+        self.handle, self.count = handle, cnt
+        self.M = (Matrix * cnt)()
+        self.P = (Params * cnt)()
+        self.O = (Outputs * cnt)()
+        self.keep = [As]
+        self.outs = []
+        for i, (A, om, k) in enumerate(zip(As, omegas, ks)):
+            if A.dim() != 2 or A.stride(1) != 1:
+                raise ValueError("batch matrices must be 2-D row-major tensors")
+            m, n = A.shape
+            d = k + ps[i]
+            om = om.contiguous()
+            self.keep.append(om)
+            Q = torch.empty(m, d, dtype=od, device=A.device)
+            L = torch.empty(d, d, dtype=od, device=A.device)
+            P = torch.empty(n, d, dtype=od, device=A.device)
+            self.M[i] = Matrix(0, Dense(m, n, A.stride(0), _dtype_code(A.dtype), A.data_ptr()),
+                               Csr())
+            self.P[i] = Params(k, ps[i], qs[i], _dtype_code(A.dtype), om.data_ptr(), 0)
+            self.O[i] = Outputs(Q.data_ptr(), L.data_ptr(), P.data_ptr(), _dtype_code(od), 0)
+            self.outs.append((Q, L, P))
+
+    def run(self):
+        self.handle.check(ruqlp_decompose_batch(self.handle.h, self.count, self.M, self.P,
+                                                self.O))
+        return [self.O[i].flags for i in range(self.count)]
 
 
 class Handle:
@@ -275,6 +319,19 @@ class Handle:
         out = Outputs(Q.data_ptr(), L.data_ptr(), P.data_ptr(), _dtype_code(out_dtype), 0)
         self.check(ruqlp_decompose(self.h, M, prm, out))
         return Q, L, P, out.flags
+
+    def prepare_batch(self, As, omegas, ks, p, q, out_dtype=None, ps=None, qs=None):
+        """Marshal a batch once (A_i, Omega_i, output tensors); the returned
+        object's run() calls ruqlp_decompose_batch and returns the flags."""
+        return Batch(self, As, omegas, ks, p, q, out_dtype, ps, qs)
+
+    def decompose_batch(self, As, omegas, ks, p, q, out_dtype=None, ps=None, qs=None):
+        """Batched RU-QLP of CUDA tensors As[i] (m_i x n_i, one dtype) with FP64
+        omegas[i] (n_i x (k_i + p_i)); p, q are shared unless ps / qs give one
+        per item.  Returns a list of (Q, L, P, flags)."""
+        b = Batch(self, As, omegas, ks, p, q, out_dtype, ps, qs)
+        flags = b.run()
+        return [(Q, L, P, f) for (Q, L, P), f in zip(b.outs, flags)]
 
     def decompose_csr(self, rowptr, colidx, values, shape, omega, k, p, q, out_dtype=None):
         """RU-QLP of a CSR matrix given as CUDA tensors (rowptr, colidx int32;

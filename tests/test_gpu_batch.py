@@ -1,0 +1,209 @@
+"""GPU tests of the batched path (ruqlp_decompose_batch): many independent
+RU-QLP decompositions (Section III-A, Algorithms 1-2) of uneven shapes in one
+call.
+
+  * parity: every item of an FP32 batch against the FP64 oracle with the FP32
+    tolerances of the single-matrix path (L and |diag(L)| within 1e-5 |L_11|,
+    residual within 1e-5, leading-k columns of Q and P within 1e-4);
+  * batch invariance: every item's Q, L, P are bitwise the single-matrix
+    result (FP32; BF16 against the CUDA-core BF16 single path), eagerly, under
+    graph capture and on graph replay;
+  * the full batched workload (512 matrices, m log-uniform in [256, 4096],
+    n in [128, 2048], k in [8, 64], p = 8, q = 1): invariance for all items,
+    the oracle on a sample.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2209_12464_gb300 import ruqlp
+from paper_2209_12464_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+# (m, n, k, p): single and several 64-column tiles, several 512-row Gram
+# slabs, m < n, p = 0, the largest batched d (256), a ragged d (5)
+MIX = [(64, 40, 2, 6), (900, 700, 30, 8), (2100, 300, 90, 10), (300, 1200, 20, 8),
+       (333, 129, 5, 0), (700, 520, 240, 16), (1500, 1500, 60, 8), (257, 2000, 8, 8),
+       (129, 65, 40, 8), (4100, 96, 12, 4)]
+Q_ITERS = 1
+
+
+@pytest.fixture(scope="module")
+def handle():
+    import __graft_entry__ as g
+    g.build()
+    h = ruqlp.Handle(0, torch.cuda.current_stream().cuda_stream)
+    yield h
+    h.close()
+
+
+def _mix(seed, shapes):
+    As, Oms = [], []
+    for i, (m, n, k, p) in enumerate(shapes):
+        sig = wl.spectrum_gap(min(m, n), k, 1e-2)
+        A, _, _, _ = wl.dense_spectral(seed + 17 * i, m, n, sig)
+        As.append(A)
+        Oms.append(wl.omega(seed + 17 * i + 1, n, k + p))
+    return As, Oms
+
+
+def _single(handle, A, om, k, p, q):
+    Q, L, P, f = handle.decompose(A, om, k, p, q, out_dtype=torch.float32)
+    return Q, L, P
+
+
+def test_batch_parity_with_oracle(handle):
+    As, Oms = _mix(wl.MASTER_SEED + 40, MIX)
+    Ag = [torch.from_numpy(A).float().cuda() for A in As]
+    Og = [torch.from_numpy(o).cuda() for o in Oms]
+    res = handle.decompose_batch(Ag, Og, [s[2] for s in MIX], None, Q_ITERS,
+                                 ps=[s[3] for s in MIX])
+    for (m, n, k, p), A, om, (Q, L, P, flags) in zip(MIX, Ag, Oms, res):
+        Aseen = A.double().cpu().numpy()
+        ref = oracle.ruqlp(Aseen, om, Q_ITERS)
+        Q, L, P = (t.double().cpu().numpy() for t in (Q, L, P))
+        l11 = abs(ref["L"][0, 0])
+        d = k + p
+        assert flags & ruqlp.FLAG_RANKDEF == 0
+        assert np.all(np.triu(L, 1) == 0.0)
+        assert np.max(np.abs(L - ref["L"])) <= 1e-5 * l11, (m, n, k, p)
+        r = oracle.residual_fro_small(Aseen, Q, L, P)
+        r0 = oracle.residual_fro_small(Aseen, ref["Q"], ref["L"], ref["P"])
+        assert abs(r - r0) <= 1e-5, (m, n, k, p, r, r0)
+        assert np.max(np.abs(Q[:, :k] - ref["Q"][:, :k])) <= 1e-4, (m, n, k, p)
+        assert np.max(np.abs(P[:, :k] - ref["P"][:, :k])) <= 1e-4, (m, n, k, p)
+        assert np.max(np.abs(Q.T @ Q - np.eye(d))) <= 2e-5
+        assert np.max(np.abs(P.T @ P - np.eye(d))) <= 2e-5
+
+
+@pytest.mark.parametrize("dtype", [torch.float32, torch.bfloat16], ids=["f32", "bf16"])
+def test_batch_items_bitwise_equal_single(handle, dtype):
+    As, Oms = _mix(wl.MASTER_SEED + 41, MIX)
+    Ag = [torch.from_numpy(A).to(dtype).cuda() for A in As]
+    Og = [torch.from_numpy(o).cuda() for o in Oms]
+    ks, ps = [s[2] for s in MIX], [s[3] for s in MIX]
+    runs = []
+    for _ in range(3):  # eager, captured into a graph, replayed
+        runs.append(handle.decompose_batch(Ag, Og, ks, None, Q_ITERS, ps=ps))
+    handle.set_option("bf16_simt", 1)
+    try:
+        for i, (A, om, k, p) in enumerate(zip(Ag, Og, ks, ps)):
+            one = _single(handle, A, om, k, p, Q_ITERS)
+            for run in runs:
+                for x, y in zip(run[i][:3], one):
+                    assert torch.equal(x, y), (i, MIX[i])
+    finally:
+        handle.set_option("bf16_simt", 0)
+
+
+def test_batch_graph_off_matches(handle):
+    As, Oms = _mix(wl.MASTER_SEED + 42, MIX[:4])
+    Ag = [torch.from_numpy(A).float().cuda() for A in As]
+    Og = [torch.from_numpy(o).cuda() for o in Oms]
+    ks, ps = [s[2] for s in MIX[:4]], [s[3] for s in MIX[:4]]
+    a = handle.decompose_batch(Ag, Og, ks, None, 2, ps=ps)
+    a2 = handle.decompose_batch(Ag, Og, ks, None, 2, ps=ps)
+    handle.set_option("batch_graph", 0)
+    try:
+        b = handle.decompose_batch(Ag, Og, ks, None, 2, ps=ps)
+    finally:
+        handle.set_option("batch_graph", 1)
+    for x, y, z in zip(a, a2, b):
+        for u, v, w in zip(x[:3], y[:3], z[:3]):
+            assert torch.equal(u, v) and torch.equal(u, w)
+
+
+def test_batch_new_inputs_same_shapes_replay(handle):
+    """A replayed graph reads the new call's A, Omega and outputs."""
+    shapes = MIX[:3]
+    ks, ps = [s[2] for s in shapes], [s[3] for s in shapes]
+    outs = []
+    for seed in (50, 51, 52):
+        As, Oms = _mix(wl.MASTER_SEED + seed, shapes)
+        Ag = [torch.from_numpy(A).float().cuda() for A in As]
+        Og = [torch.from_numpy(o).cuda() for o in Oms]
+        outs.append((Ag, Og, handle.decompose_batch(Ag, Og, ks, None, 1, ps=ps)))
+    for Ag, Og, res in outs:
+        for A, om, k, p, r in zip(Ag, Og, ks, ps, res):
+            one = _single(handle, A, om, k, p, 1)
+            for x, y in zip(r[:3], one):
+                assert torch.equal(x, y)
+
+
+@pytest.mark.parametrize("bad", ["mixed_dtype", "mixed_q", "d257", "empty", "f64"])
+def test_batch_invalid_rejected(handle, bad):
+    A1 = torch.randn(300, 280, device="cuda")
+    A2 = torch.randn(200, 150, device="cuda")
+    o1 = torch.randn(280, 10, dtype=torch.float64, device="cuda")
+    o2 = torch.randn(150, 10, dtype=torch.float64, device="cuda")
+    As, Os, ks, qs = [A1, A2], [o1, o2], [6, 6], None
+    if bad == "mixed_dtype":
+        As[1] = A2.bfloat16()
+    elif bad == "f64":
+        As = [A1.double(), A2.double()]
+    elif bad == "d257":
+        As[0] = torch.randn(600, 560, device="cuda")
+        Os[0] = torch.randn(560, 261, dtype=torch.float64, device="cuda")
+        ks[0] = 257
+    elif bad == "mixed_q":
+        qs = [1, 2]
+    if bad == "empty":
+        st = ruqlp.ruqlp_decompose_batch(handle.h, 0, None, None, None)
+        assert st == ruqlp.ERR_INVALID
+        return
+    with pytest.raises(ruqlp.RuqlpError) as ei:
+        handle.decompose_batch(As, Os, ks, 4, 1, qs=qs)
+    assert ei.value.status == ruqlp.ERR_INVALID
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("dtype", [torch.float32, torch.bfloat16], ids=["f32", "bf16"])
+def test_batched_workload_512(handle, dtype):
+    """The batched workload: all 512 items bitwise equal their single-matrix
+    results; 6 sampled items against the oracle.  FP32: the FP32 tolerances.
+    BF16: relative residual against the unrounded matrix within 1.05x the FP64
+    oracle's plus 2^-8 sqrt(d / m): each product rounds the skinny operand to
+    BF16 (relative 2^-9 per entry), and the last one, B^T = A^T bf16(Q), adds
+    Q dQ^T A with ||dQ^T A||_F about 2^-9 sqrt(d / m) ||A||_F for a random
+    rounding pattern dQ -- negligible for the 20000 x 20000 workload (d / m =
+    0.011), not for m = 256, d = 72."""
+    shapes = wl.batch_shapes(wl.MASTER_SEED + 4)
+    A32 = [wl.dense_spectral_torch(wl.MASTER_SEED + 400 + i, m, n,
+                                   wl.spectrum_gap(min(m, n), k, 1e-2))
+           for i, (m, n, k, p) in enumerate(shapes)]
+    Ag = [a.to(dtype) for a in A32]
+    Og = [wl.omega_torch(wl.MASTER_SEED + 1400 + i, n, k + p)
+          for i, (m, n, k, p) in enumerate(shapes)]
+    ks, ps = [s[2] for s in shapes], [s[3] for s in shapes]
+    res = handle.decompose_batch(Ag, Og, ks, None, 1, ps=ps)
+    handle.set_option("bf16_simt", 1)
+    try:
+        for i in range(len(shapes)):
+            one = _single(handle, Ag[i], Og[i], ks[i], ps[i], 1)
+            for x, y in zip(res[i][:3], one):
+                assert torch.equal(x, y), (i, shapes[i])
+    finally:
+        handle.set_option("bf16_simt", 0)
+    rng = np.random.default_rng(7)
+    for i in rng.choice(len(shapes), 6, replace=False):
+        m, n, k, p = shapes[i]
+        Aseen = Ag[i].double().cpu().numpy()
+        om = Og[i].cpu().numpy()
+        Q, L, P = (t.double().cpu().numpy() for t in res[i][:3])
+        if dtype == torch.float32:
+            ref = oracle.ruqlp(Aseen, om, 1)
+            l11 = abs(ref["L"][0, 0])
+            assert np.max(np.abs(L - ref["L"])) <= 1e-5 * l11
+            r = oracle.residual_fro_small(Aseen, Q, L, P)
+            r0 = oracle.residual_fro_small(Aseen, ref["Q"], ref["L"], ref["P"])
+            assert abs(r - r0) <= 1e-5
+        else:
+            A64 = A32[i].double().cpu().numpy()
+            ref = oracle.ruqlp(A64, om, 1)
+            r = oracle.residual_fro_small(A64, Q, L, P)
+            r0 = oracle.residual_fro_small(A64, ref["Q"], ref["L"], ref["P"])
+            assert r <= 1.05 * r0 + 2.0 ** -8 * np.sqrt((k + p) / m), (i, shapes[i], r, r0)

@@ -197,3 +197,26 @@ def test_light_and_full_intermediate_orth_agree(handle, case):
     l11 = abs(b[1][0, 0])
     assert np.max(np.abs(a[1] - b[1])) <= 1e-5 * l11
     assert np.max(np.abs(a[0][:, :k] - b[0][:, :k])) <= 1e-4
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32], ids=["f64", "f32"])
+@pytest.mark.parametrize("case", CASES[:3], ids=[c[0] for c in CASES[:3]])
+def test_finish_paper_matches_oracle(handle, case, dtype):
+    """finish_paper: Q P~ and R~ of [P~, R~] = qr(L) (Algorithm 1 step 5);
+    diag(R~) are the paper's L-values of A^T.  Same tolerances as the dense
+    parity test; A ~= (Q P~) R~ P^T."""
+    name, m, n, k, p, q, tail = case
+    A, Om = _case(*case, seed=wl.MASTER_SEED + 11 * m + n)
+    Ag = torch.from_numpy(A).to(dtype).cuda()
+    Aseen = Ag.double().cpu().numpy()
+    ref = oracle.ruqlp(Aseen, Om, q, finish_paper=True)
+    Qh, R, P, _ = handle.decompose(Ag, torch.from_numpy(Om).cuda(), k, p, q, finish_paper=True)
+    Qh, R, P = (t.double().cpu().numpy() for t in (Qh, R, P))
+    tol = TOL[dtype]
+    r11 = abs(ref["Rtilde"][0, 0])
+    assert np.all(np.tril(R, -1) == 0.0)
+    assert np.max(np.abs(R - ref["Rtilde"])) <= tol * r11
+    r = oracle.residual_fro_small(Aseen, Qh, R, P)
+    r0 = oracle.residual_fro_small(Aseen, ref["Qhat"], ref["Rtilde"], ref["P"])
+    assert abs(r - r0) <= tol
+    assert np.max(np.abs(Qh[:, :k] - ref["Qhat"][:, :k])) <= TOLQ[dtype] * 10
