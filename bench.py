@@ -222,7 +222,8 @@ def batch_inputs(torch, dev, count, dtype, gen):
             A32.append(wl.dense_lowrank_gauss_torch(B_SEED + 1000 + i, m, n, k, device=dev))
         Om.append(wl.omega_torch(B_SEED + 5000 + i, n, k + p, device=dev))
     tdt = {"bf16": torch.bfloat16, "f32": torch.float32}[dtype]
-    A = [a.to(tdt) for a in A32]
+    # rows start on 16-byte boundaries (what the tensor-map loads need)
+    A = [wl.aligned_rows(a.to(tdt)) for a in A32]
     return shapes, A, A32, Om
 
 
@@ -342,7 +343,7 @@ def run_batch(args, torch, dev, local, world, rank, dist):
     for _ in range(2):
         batch.run()
     torch.cuda.synchronize()
-    prof = {ph: h.profile(ph) for ph in ("ax", "atx", "orth", "step")}
+    prof = {ph: h.profile(ph) for ph in ("ax", "atx", "orth", "step", "tc_ax", "tc_atx")}
     h.set_option("profile", 0)
     peaks = {}
     try:
@@ -350,22 +351,40 @@ def run_batch(args, torch, dev, local, world, rank, dist):
     except OSError:
         pass
     sm_mhz = ck.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
-    cnt = prof["ax"][0] + prof["atx"][0]
-    avg = (prof["ax"][1] + prof["atx"][1]) / max(cnt, 1)
-    flops = 2.0 * sum(m * n * (k + p) for m, n, k, p in shapes)
-    alu_peak = 152 * 256 * sm_mhz * 1e6 / 1e12
-    achieved = flops / (avg * 1e-3) / 1e12
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
     step_ms = prof["step"][1] / max(prof["step"][0], 1)
-    roofline = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
-                "frac": achieved / alu_peak, "traffic": None,
-                "kernel": "k_bgemm (batched CUDA-core product, one pass over every A_i per launch)",
-                "alg_flops_per_launch": flops, "avg_launch_ms": avg, "launches": cnt,
-                "peak_source": "derived: 152 SMs x 128 FP32 FMA/clk x 2 x median SM clock",
-                "hbm_alg_gbs": bytes_a / (avg * 1e-3) / 1e9,
-                "phase_ms": {ph: prof[ph][1] / max(prof[ph][0], 1) for ph in prof},
-                "phase_share": {ph: prof[ph][1] / max(prof["step"][1], 1e-9)
-                                for ph in ("ax", "atx", "orth")},
-                "eager_step_ms": step_ms}
+    common = {"phase_ms": {ph: prof[ph][1] / max(prof[ph][0], 1) for ph in prof},
+              "phase_share": {ph: prof[ph][1] / max(prof["step"][1], 1e-9)
+                              for ph in ("ax", "atx", "orth")},
+              "eager_step_ms": step_ms}
+    if prof["tc_ax"][0]:
+        # the batched tcgen05 product: one pass over every A_i per launch.
+        # Algorithmic bytes = sum_i A_i (BF16) + Bt_i (dp x K, BF16) + the
+        # output (rows x dp, FP32); both orientations move the same bytes.
+        dps = [(k + p + 15) // 16 * 16 for m, n, k, p in shapes]
+        alg = bytes_a + sum(dp * (2 * n + 4 * m) for (m, n, k, p), dp in zip(shapes, dps))
+        cnt = prof["tc_ax"][0] + prof["tc_atx"][0]
+        avg = (prof["tc_ax"][1] + prof["tc_atx"][1]) / cnt
+        achieved = alg / (avg * 1e-3) / 1e9
+        roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                    "frac": achieved / hbm_peak, "traffic": None,
+                    "kernel": "k_btc_gemm (batched tcgen05 products over a tile list, one pass "
+                              "over every A_i per launch)",
+                    "alg_bytes_per_launch": alg, "avg_launch_ms": avg, "launches": cnt,
+                    "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)", **common}
+    else:
+        cnt = prof["ax"][0] + prof["atx"][0]
+        avg = (prof["ax"][1] + prof["atx"][1]) / max(cnt, 1)
+        flops = 2.0 * sum(m * n * (k + p) for m, n, k, p in shapes)
+        alu_peak = 152 * 256 * sm_mhz * 1e6 / 1e12
+        achieved = flops / (avg * 1e-3) / 1e12
+        roofline = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
+                    "frac": achieved / alu_peak, "traffic": None,
+                    "kernel": "k_bgemm (batched CUDA-core product, one pass over every A_i per "
+                              "launch)",
+                    "alg_flops_per_launch": flops, "avg_launch_ms": avg, "launches": cnt,
+                    "peak_source": "derived: 152 SMs x 128 FP32 FMA/clk x 2 x median SM clock",
+                    **common}
 
     # end to end: pinned host inputs -> device, batched call, outputs -> host
     e2e = None

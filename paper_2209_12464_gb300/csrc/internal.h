@@ -128,6 +128,9 @@ struct BMat {
   double* G;
   float* tiles;
   const double* omega;
+  void* Bt;        // dp x ldbt BF16 (tensor-core items): the transposed skinny operand
+  int64_t ldbt;
+  int use_tc, pad2;
   void* Qout;
   void* Lout;
   void* Pout;
@@ -158,6 +161,20 @@ cudaError_t bchol(const BMat* T, int count, double shift_rel, bool force_shift, 
                   cudaStream_t st);
 cudaError_t btrsm(const BMat* T, const int* prefix, int total, int count, int src, int dst,
                   int dmax, cudaStream_t st);
+// Batched tensor-core products (BF16 A): tile list entries and launcher.
+struct BTcTile {
+  int mat, tile;
+};
+// Encode the three tensor maps of one matrix (A, Bt over n, Bt over m) into
+// maps3 (3 x CUtensorMap, 64-byte aligned); a_only re-encodes A alone.
+bool btc_encode(void* maps3, const void* A, int64_t lda, int64_t m, int64_t n, const void* Bt,
+                int64_t ldbt, int dp, bool a_only);
+size_t btc_map_bytes();
+// Bt_i = bf16(buf_i[src])^T (zero columns d..dp) for the tensor-core items.
+cudaError_t btranspose_bf16(const BMat* T, int count, int src, cudaStream_t st);
+// buf[dst] = A Bt^T (trans: A^T Bt^T) for the tile list's matrices.
+cudaError_t btc_gemm(bool trans, const BMat* T, int count, const BTcTile* list, int n,
+                     const void* maps, int src, int dst, int dpmax, int* err, cudaStream_t st);
 cudaError_t bcast_omega(const BMat* T, int count, int64_t max_elems, cudaStream_t st);
 cudaError_t boutputs(const BMat* T, int count, int64_t max_elems, cudaStream_t st);
 

@@ -55,12 +55,24 @@ __device__ __forceinline__ void load_col(const float* __restrict__ T, int lane, 
 // One warp factors the 32 x 32 tile B = R^T R in registers (lane c owns
 // column c) and writes R (upper) back and S = R^{-1} (upper) to Sout.
 // Step k broadcasts row k of the partially reduced tile through the shared
-// row buffer rb (one store per lane, 128-bit broadcast loads), so every lane
-// forms r_ki itself; there are no shuffles and no branches in the loop.
-// Reciprocal square roots and reciprocals replace IEEE sqrt/divide (the
-// factor only has to be consistent with the solve that uses it).  A
-// non-positive pivot is replaced by bad_fill; the return value (same in every
-// lane) reports whether that happened.
+// row buffer rb (one store per lane, 128-bit broadcast loads of the whole
+// row issued together), so every lane forms r_ki itself; there are no
+// shuffles and no branches in the loop.  Reciprocal square roots and
+// reciprocals replace IEEE sqrt/divide (the factor only has to be consistent
+// with the solve that uses it).  A non-positive pivot is replaced by
+// bad_fill; the return value (same in every lane) reports whether that
+// happened.
+__device__ __forceinline__ void load_row(const float* __restrict__ p, float (&r)[TB]) {
+#pragma unroll
+  for (int q = 0; q < TB / 4; ++q) {
+    const float4 v = reinterpret_cast<const float4*>(p)[q];
+    r[4 * q] = v.x;
+    r[4 * q + 1] = v.y;
+    r[4 * q + 2] = v.z;
+    r[4 * q + 3] = v.w;
+  }
+}
+
 __device__ bool factor_tile(float* __restrict__ B, float* __restrict__ Sout, float* __restrict__ dinv,
                             float* __restrict__ rb, int lane, float bad_fill) {
   float col[TB];
@@ -72,7 +84,9 @@ __device__ bool factor_tile(float* __restrict__ B, float* __restrict__ Sout, flo
     __syncwarp();
     rb[lane] = col[k];  // row k of the current tile, lane c holds B[k][c]
     __syncwarp();
-    float piv = rb[k];
+    float row[TB];
+    load_row(rb, row);
+    float piv = row[k];
     const bool nonpos = !(piv > 0.f) || !(piv < 3.0e38f);
     bad = bad || nonpos;
     piv = nonpos ? bad_fill : piv;
@@ -82,27 +96,38 @@ __device__ bool factor_tile(float* __restrict__ B, float* __restrict__ Sout, flo
     col[k] = (lane >= k) ? rkc : col[k];
 #pragma unroll
     for (int i = k + 1; i < TB; ++i) {
-      const float rki = rb[i] * rinv;
+      const float rki = row[i] * rinv;
       const float upd = fmaf(-rki, rkc, col[i]);
       col[i] = (lane >= i) ? upd : col[i];
     }
   }
+  // R row-major into B; R transposed (column c of R as row c) into Sout,
+  // which the inverse below reads before overwriting it
 #pragma unroll
-  for (int r = 0; r < TB; ++r) B[r * TP + lane] = (r <= lane) ? col[r] : 0.f;
+  for (int r = 0; r < TB; ++r) {
+    const float v = (r <= lane) ? col[r] : 0.f;
+    B[r * TP + lane] = v;
+    Sout[lane * TP + r] = v;
+  }
   dinv[lane] = myinv;
   __syncwarp();
   // S = R^{-1}, right-looking: lane c solves R x = e_c from the bottom;
   // acc[j] -= R[j][r] x[r] for j < r are independent multiply-adds
+  float dv[TB];
+  load_row(dinv, dv);
   float acc[TB];
 #pragma unroll
   for (int r = 0; r < TB; ++r) acc[r] = (r == lane) ? 1.f : 0.f;
 #pragma unroll
   for (int r = TB - 1; r >= 0; --r) {
-    const float xr = acc[r] * dinv[r];
+    const float xr = acc[r] * dv[r];
     acc[r] = xr;
+    float rc[TB];  // column r of R (rows j < r are used)
+    load_row(Sout + r * TP, rc);
 #pragma unroll
-    for (int j = 0; j < r; ++j) acc[j] = fmaf(-B[j * TP + r], xr, acc[j]);
+    for (int j = 0; j < r; ++j) acc[j] = fmaf(-rc[j], xr, acc[j]);
   }
+  __syncwarp();
 #pragma unroll
   for (int r = 0; r < TB; ++r) Sout[r * TP + lane] = acc[r];
   return !bad;
@@ -118,8 +143,8 @@ __device__ __forceinline__ void chol_body(const double* __restrict__ G, int d, d
   extern __shared__ __align__(16) float sm[];
   __shared__ double s_shift;
   __shared__ int s_bad, s_rankdef;
-  __shared__ float s_dinv[TB];
-  __shared__ float s_row[TB];
+  __shared__ __align__(16) float s_dinv[TB];
+  __shared__ __align__(16) float s_row[TB];
   const int nb = (d + TB - 1) / TB;
   const int ntiles = nb * (nb + 1) / 2;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = NTH / 32;
@@ -141,23 +166,35 @@ __device__ __forceinline__ void chol_body(const double* __restrict__ G, int d, d
   for (; attempt < 2; ++attempt) {
     __syncthreads();
     const double add = attempt ? s_shift : 0.0;
-    for (int t = warp; t < ntiles; t += nw) {  // upper block triangle of G + shift
-      int I = 0, tt = t;
-      while (tt >= nb - I) { tt -= nb - I; ++I; }
-      const int J = I + tt;
-      float* T = tile(I, J);
-      const int j = J * TB + lane;
-      float v[TB];
+    // upper block triangle of G + shift I (identity padding), eight
+    // independent loads in flight per thread
+    for (int e0 = tid; e0 < ntiles * TB * TB; e0 += 8 * NTH) {
+      double x[8];
 #pragma unroll
-      for (int r = 0; r < TB; ++r) {
-        const int i = I * TB + r;
-        double x;
-        if (i < d && j < d) x = G[(size_t)i * d + j] + (i == j ? add : 0.0);
-        else x = (i == j) ? 1.0 : 0.0;
-        v[r] = (float)x;
+      for (int u = 0; u < 8; ++u) {
+        const int e = e0 + u * NTH;
+        x[u] = 0.0;
+        if (e < ntiles * TB * TB) {
+          const int t = e >> 10, r = (e >> 5) & 31, c = e & 31;
+          int I = 0, tt = t;
+          while (tt >= nb - I) { tt -= nb - I; ++I; }
+          const int i = I * TB + r, j = (I + tt) * TB + c;
+          if (i < d && j < d) x[u] = G[(size_t)i * d + j];
+        }
       }
 #pragma unroll
-      for (int r = 0; r < TB; ++r) T[r * TP + lane] = v[r];
+      for (int u = 0; u < 8; ++u) {
+        const int e = e0 + u * NTH;
+        if (e < ntiles * TB * TB) {
+          const int t = e >> 10, r = (e >> 5) & 31, c = e & 31;
+          int I = 0, tt = t;
+          while (tt >= nb - I) { tt -= nb - I; ++I; }
+          const int i = I * TB + r, j = (I + tt) * TB + c;
+          double v = x[u];
+          if (i == j) v = (i < d) ? v + add : 1.0;
+          sm[(size_t)t * TILE_FLOATS + r * TP + c] = (float)v;
+        }
+      }
     }
     if (tid == 0) s_bad = 0;
     __syncthreads();

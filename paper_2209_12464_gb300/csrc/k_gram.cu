@@ -126,6 +126,23 @@ k_gram_tiles(const float* __restrict__ X, int64_t ldx, const float* __restrict__
   gram_tile(X, ldx, W, ldw, M, d1, d2, sym, slab, partial, blockIdx.x, blockIdx.y);
 }
 
+// sum_z P[z * stride + idx] for z < slabs, in slab order, with eight
+// independent loads in flight
+__device__ __forceinline__ double slab_sum(const double* __restrict__ P, int slabs, int64_t stride,
+                                           int64_t idx) {
+  double s = 0.0;
+  int z = 0;
+  for (; z + 8 <= slabs; z += 8) {
+    double v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) v[u] = P[(int64_t)(z + u) * stride + idx];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) s += v[u];
+  }
+  for (; z < slabs; ++z) s += P[(int64_t)z * stride + idx];
+  return s;
+}
+
 // C[i][j] = sum over slabs of the partials (slab order); with sym the entry
 // is taken from the computed upper triangle.
 __global__ void k_gram_reduce(const double* __restrict__ P, int slabs, int d1, int d2, bool sym,
@@ -135,9 +152,7 @@ __global__ void k_gram_reduce(const double* __restrict__ P, int slabs, int d1, i
   if (idx >= (int64_t)d1 * d2) return;
   int i = (int)(idx / d2), j = (int)(idx % d2);
   const int64_t src = (sym && j < i) ? ((int64_t)j * d2 + i) : idx;
-  double s = 0.0;
-  for (int z = 0; z < slabs; ++z) s += P[(int64_t)z * d1 * d2 + src];
-  C[idx] = s;
+  C[idx] = slab_sum(P, slabs, (int64_t)d1 * d2, src);
 }
 
 // Batched Grams: tile t of the launch -> (matrix, tile, slab) through prefix;
@@ -174,9 +189,7 @@ __global__ void k_bgram_reduce(const BMat* __restrict__ Tb, int src, int src2, i
   const int slabs = (int)gram_slabs(M, max_slabs, &slab);
   const int i = (int)(idx / d), j = (int)(idx % d);
   const int64_t so = (sym && j < i) ? ((int64_t)j * d + i) : idx;
-  double s = 0.0;
-  for (int z = 0; z < slabs; ++z) s += b.partial[(int64_t)z * d * d + so];
-  b.G[idx] = s;
+  b.G[idx] = slab_sum(b.partial, slabs, (int64_t)d * d, so);
 }
 
 }  // namespace

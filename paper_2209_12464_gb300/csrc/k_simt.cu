@@ -156,8 +156,16 @@ __global__ void k_reduce_partials(const double* __restrict__ P, int splits, int6
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= M * N) return;
   const int64_t i = idx / N, j = idx % N;
-  double s = 0.0;
-  for (int z = 0; z < splits; ++z) s += P[(int64_t)z * M * N + idx];
+  double s = 0.0;  // split order, eight independent loads in flight
+  int z = 0;
+  for (; z + 8 <= splits; z += 8) {
+    double v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) v[u] = P[(int64_t)(z + u) * M * N + idx];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) s += v[u];
+  }
+  for (; z < splits; ++z) s += P[(int64_t)z * M * N + idx];
   C[i * ldc + j] = Cvt<TC>::from(s);
 }
 

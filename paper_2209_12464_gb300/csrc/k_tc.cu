@@ -22,6 +22,7 @@
 // sets an error word, stops issuing work, and frees its TMEM before exiting.
 #include <cuda.h>
 #include <cudaTypedefs.h>
+#include <string.h>
 
 #include "internal.h"
 
@@ -187,17 +188,88 @@ __device__ __forceinline__ Item get_item(const TcParams& p, int i) {
   return {base + (int)t0 + 1, 0, (int)(u1 - (t0 + 1) * p.KB), 1};
 }
 
-template <bool TRANS>
-__global__ void __launch_bounds__(NTHREADS, 1)
-k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-          TcParams p) {
+// One unit of work of a CTA: an output tile of 128 rows, K blocks [kb0, kb1),
+// written to out (rows < rows_valid) with leading dimension ldo.
+struct TcItem {
+  const CUtensorMap* mA;
+  const CUtensorMap* mB;
+  int tile, kb0, kb1, dp;
+  float* out;
+  int64_t ldo, rows;
+  bool a_split;  // K-major A loaded as two 64-row boxes (batched maps)
+};
+
+// Single-matrix work: whole tiles, then stream-K segments (fragments).
+struct WorkSingle {
+  const CUtensorMap* mA;
+  const CUtensorMap* mB;
+  const TcParams* p;
+  static constexpr bool kGlobalMaps = false;
+  __device__ int count() const { return item_count(*p); }
+  __device__ TcItem get(int i) const {
+    const Item it = get_item(*p, i);
+    TcItem r{mA, mB, it.tile, it.kb0, it.kb1, p->dp, nullptr, 0, 0, false};
+    if (it.slot < 0) {
+      r.out = p->out + (int64_t)it.tile * BM * p->ldo;
+      r.ldo = p->ldo;
+      r.rows = p->Mout - (int64_t)it.tile * BM;
+    } else {
+      r.out = p->frag + ((int64_t)blockIdx.x * 2 + it.slot) * BM * p->dp;
+      r.ldo = p->dp;
+      r.rows = BM;
+    }
+    return r;
+  }
+};
+
+// Batched work: CTA c takes tiles c, c + P, c + 2P, ... of a host-built list
+// (whole tiles only, so every tile is one K-ordered accumulation whichever CTA
+// runs it).  Tensor maps live in global memory, three per matrix: A (64 x 64
+// boxes), Bt over n (for A X) and Bt over m (for A^T Y).
+struct WorkBatch {
+  const BTcTile* list;
+  int n;
+  const BMat* T;
+  const CUtensorMap* maps;
+  int dst;
+  bool trans;
+  static constexpr bool kGlobalMaps = true;
+  __device__ int count() const {
+    return (int)blockIdx.x < n ? (n - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+  }
+  __device__ TcItem get(int i) const {
+    const BTcTile w = list[blockIdx.x + (int64_t)i * gridDim.x];
+    const BMat& b = T[w.mat];
+    const int64_t K = trans ? b.m : b.n, Mout = trans ? b.n : b.m;
+    TcItem r;
+    r.mA = maps + 3 * (int64_t)w.mat;
+    r.mB = maps + 3 * (int64_t)w.mat + (trans ? 2 : 1);
+    r.tile = w.tile;
+    r.kb0 = 0;
+    r.kb1 = (int)((K + BK - 1) / BK);
+    r.dp = b.dp;
+    r.out = bbuf(b, dst) + (int64_t)w.tile * BM * b.dp;
+    r.ldo = b.dp;
+    r.rows = Mout - (int64_t)w.tile * BM;
+    r.a_split = true;
+    return r;
+  }
+};
+
+__device__ __forceinline__ void tmap_acquire(const CUtensorMap* m) {
+  asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"((uint64_t)m)
+               : "memory");
+}
+
+// The warp-specialised pipeline shared by both kernels.  dpmax sizes the
+// shared-memory stages; each item's own dp sets its B bytes and MMA N.
+template <bool TRANS, class W>
+__device__ __forceinline__ void tc_body(const W& w, int* err, int S, int dpmax) {
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
   const uint32_t base = (raw + 1023u) & ~1023u;
   uint8_t* base_ptr = smem_raw + (base - raw);
-  const int S = p.stages;
-  const uint32_t b_bytes = (uint32_t)p.dp * BK * 2;
-  const uint32_t stage_bytes = A_TILE_BYTES + b_bytes;
+  const uint32_t stage_bytes = A_TILE_BYTES + (uint32_t)dpmax * BK * 2;
   const uint32_t bar_base = base + S * stage_bytes;
   // barriers: full[S], empty[S], tfull[2], tempty[2], drain; then the TMEM address
   auto full_bar = [&](int s) { return bar_base + 8u * s; };
@@ -209,6 +281,7 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
   __shared__ int s_abort;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nitems = w.count();
   if (threadIdx.x == 0) {
     for (int s = 0; s < S; ++s) {
       mbar_init(full_bar(s), 1);
@@ -221,8 +294,11 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
     mbar_init(drain_bar, 1);
     s_abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tmA) : "memory");
-    asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tmB) : "memory");
+    if (!W::kGlobalMaps && nitems > 0) {
+      const TcItem it = w.get(0);
+      asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)it.mA) : "memory");
+      asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)it.mB) : "memory");
+    }
   }
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(
@@ -236,8 +312,6 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
   const uint32_t tmem_base = *tmem_slot;
   volatile int* abort_flag = &s_abort;
 
-  const int nitems = item_count(p);
-
   if (warp == 0) {
     // ---------------- TMA producer ----------------
     if (lane == 0) {
@@ -246,27 +320,40 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
       uint32_t phase = 0;
       bool ok = true;
       int64_t issued = 0;
+      const CUtensorMap* last_a = nullptr;
       for (int i = 0; i < nitems && ok; ++i) {
-        const Item it = get_item(p, i);
+        const TcItem it = w.get(i);
+        if (W::kGlobalMaps && it.mA != last_a) {  // maps written before the launch
+          tmap_acquire(it.mA);
+          tmap_acquire(it.mB);
+          last_a = it.mA;
+        }
+        const uint32_t bytes = A_TILE_BYTES + (uint32_t)it.dp * BK * 2;
         for (int kb = it.kb0; kb < it.kb1; ++kb) {
           if (!mbar_wait(empty_bar(stage), phase ^ 1u, abort_flag)) { ok = false; break; }
           ++issued;
           const uint32_t sa = base + stage * stage_bytes, sb = sa + A_TILE_BYTES;
-          mbar_expect_tx(full_bar(stage), stage_bytes);
+          mbar_expect_tx(full_bar(stage), bytes);
           if (!TRANS) {
-            tma_load_2d(sa, &tmA, full_bar(stage), kb * BK, it.tile * BM, pol_a);
+            if (!it.a_split) {
+              tma_load_2d(sa, it.mA, full_bar(stage), kb * BK, it.tile * BM, pol_a);
+            } else {
+              tma_load_2d(sa, it.mA, full_bar(stage), kb * BK, it.tile * BM, pol_a);
+              tma_load_2d(sa + A_TILE_BYTES / 2, it.mA, full_bar(stage), kb * BK,
+                          it.tile * BM + 64, pol_a);
+            }
           } else {
-            tma_load_2d(sa, &tmA, full_bar(stage), it.tile * BM, kb * BK, pol_a);
-            tma_load_2d(sa + A_TILE_BYTES / 2, &tmA, full_bar(stage), it.tile * BM + 64, kb * BK,
-                        pol_a);
+            tma_load_2d(sa, it.mA, full_bar(stage), it.tile * BM, kb * BK, pol_a);
+            tma_load_2d(sa + A_TILE_BYTES / 2, it.mA, full_bar(stage), it.tile * BM + 64,
+                        kb * BK, pol_a);
           }
-          tma_load_2d(sb, &tmB, full_bar(stage), kb * BK, 0, pol_b);
+          tma_load_2d(sb, it.mB, full_bar(stage), kb * BK, 0, pol_b);
           if (++stage == S) { stage = 0; phase ^= 1u; }
         }
       }
       if (!ok) {
         *abort_flag = 1;
-        atomicExch(p.err, 1);
+        atomicExch(err, 1);
         // let the loads already issued land before the CTA releases its
         // shared memory: wait (bounded) on the newest phase of each stage
         int st2 = stage;
@@ -283,12 +370,12 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
   } else if (warp == 1) {
     // ---------------- MMA issuer ----------------
     if (lane == 0) {
-      const uint32_t idesc = idesc_bf16(p.dp, TRANS);
       int stage = 0;
       uint32_t phase = 0;
       bool ok = true;
       for (int i = 0; i < nitems && ok; ++i) {
-        const Item it = get_item(p, i);
+        const TcItem it = w.get(i);
+        const uint32_t idesc = idesc_bf16(it.dp, TRANS);
         const int acc = i & 1;
         const uint32_t use = (uint32_t)(i >> 1);
         if (!mbar_wait(tempty_bar(acc), (use & 1u) ^ 1u, abort_flag)) { ok = false; break; }
@@ -312,7 +399,7 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
         if (!ok) break;
         mma_commit(tfull_bar(acc));
       }
-      if (!ok) { *abort_flag = 1; atomicExch(p.err, 1); }
+      if (!ok) { *abort_flag = 1; atomicExch(err, 1); }
       // every MMA this thread issued has completed before TMEM is freed
       mma_commit(drain_bar);
       volatile int never = 0;
@@ -324,23 +411,15 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
     const int row = g * 32 + lane;
     bool ok = true;
     for (int i = 0; i < nitems && ok; ++i) {
-      const Item it = get_item(p, i);
+      const TcItem it = w.get(i);
       const int acc = i & 1;
       const uint32_t use = (uint32_t)(i >> 1);
       if (!mbar_wait(tfull_bar(acc), use & 1u, abort_flag)) { ok = false; break; }
       tc_fence_after();
       const uint32_t taddr = tmem_base + (uint32_t)(acc * 256) + ((uint32_t)(g * 32) << 16);
-      float* dst;
-      bool valid;
-      if (it.slot < 0) {
-        const int64_t r = (int64_t)it.tile * BM + row;
-        valid = r < p.Mout;
-        dst = p.out + r * p.ldo;
-      } else {
-        valid = true;
-        dst = p.frag + (((int64_t)blockIdx.x * 2 + it.slot) * BM + row) * p.dp;
-      }
-      for (int c = 0; c < p.dp; c += 16) {
+      const bool valid = row < it.rows;
+      float* dst = it.out + (int64_t)row * it.ldo;
+      for (int c = 0; c < it.dp; c += 16) {
         float v[16];
         tmem_ld16(taddr + c, v);
         if (valid) {
@@ -353,7 +432,7 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
       __syncwarp();
       if (lane == 0) mbar_arrive(tempty_bar(acc));
     }
-    if (!ok) { *abort_flag = 1; if (lane == 0) atomicExch(p.err, 1); }
+    if (!ok) { *abort_flag = 1; if (lane == 0) atomicExch(err, 1); }
   }
 
   __syncthreads();
@@ -361,6 +440,51 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
     tc_fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem_base)
                  : "memory");
+  }
+}
+
+template <bool TRANS>
+__global__ void __launch_bounds__(NTHREADS, 1)
+k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+          const __grid_constant__ TcParams p) {
+  const WorkSingle w{&tmA, &tmB, &p};
+  tc_body<TRANS>(w, p.err, p.stages, p.dp);
+}
+
+template <bool TRANS>
+__global__ void __launch_bounds__(NTHREADS, 1)
+k_btc_gemm(const BTcTile* __restrict__ list, int n, const BMat* __restrict__ T,
+           const CUtensorMap* __restrict__ maps, int dst, int stages, int dpmax, int* err) {
+  const WorkBatch w{list, n, T, maps, dst, TRANS};
+  tc_body<TRANS>(w, err, stages, dpmax);
+}
+
+// Bt_i[c][r] = bf16(buf_i[r][c]) for c < d, 0 for d <= c < dp, r < K_i (K_i = m
+// for the Y buffer, n otherwise), for the tensor-core items of a batch.
+__global__ void k_btranspose_bf16(const BMat* __restrict__ T, int src) {
+  __shared__ float t[32][33];
+  const BMat& b = T[blockIdx.y];
+  if (!b.use_tc) return;
+  const int64_t K = (src == B_Y) ? b.m : b.n;
+  const float* S = bbuf(b, src);
+  __nv_bfloat16* D = (__nv_bfloat16*)b.Bt;
+  const int64_t tr = (K + 31) / 32;
+  const int64_t tiles = tr * ((b.dp + 31) / 32);
+  for (int64_t tt = blockIdx.x; tt < tiles; tt += gridDim.x) {
+    const int64_t r0 = (tt % tr) * 32;
+    const int c0 = (int)(tt / tr) * 32;
+    __syncthreads();
+    for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+      const int64_t r = r0 + i;
+      const int c = c0 + threadIdx.x;
+      t[i][threadIdx.x] = (r < K && c < b.d) ? S[r * b.dp + c] : 0.f;
+    }
+    __syncthreads();
+    for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+      const int c = c0 + i;
+      const int64_t r = r0 + threadIdx.x;
+      if (c < b.dp && r < K) D[(int64_t)c * b.ldbt + r] = __float2bfloat16_rn(t[threadIdx.x][i]);
+    }
   }
 }
 
@@ -392,8 +516,17 @@ __global__ void __launch_bounds__(256) k_tc_fixup(TcParams p, int P) {
   const int n = s_n;
   for (int e = threadIdx.x; e < FIX_ROWS * p.dp; e += blockDim.x) {
     const int r = r0 + e / p.dp, col = e % p.dp;
+    // eight independent loads in flight, summed in contributor order
     float s = 0.f;
-    for (int i = 0; i < n; ++i) s += p.frag[((int64_t)s_src[i] * BM + r) * p.dp + col];
+    int i = 0;
+    for (; i + 8 <= n; i += 8) {
+      float v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) v[u] = p.frag[((int64_t)s_src[i + u] * BM + r) * p.dp + col];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) s += v[u];
+    }
+    for (; i < n; ++i) s += p.frag[((int64_t)s_src[i] * BM + r) * p.dp + col];
     const int64_t gr = (int64_t)tile * BM + r;
     if (gr < p.Mout) p.out[gr * p.ldo + col] = s;
   }
@@ -516,6 +649,51 @@ cudaError_t tc_gemm(bool trans, const void* A, int64_t lda, int64_t m, int64_t n
   e = cudaGetLastError();
   if (e != cudaSuccess || p.tail == 0) return e;
   k_tc_fixup<<<dim3(p.tail, BM / FIX_ROWS), 256, 0, st>>>(p, P);
+  count_launch();
+  return cudaGetLastError();
+}
+
+bool btc_encode(void* maps3, const void* A, int64_t lda, int64_t m, int64_t n, const void* Bt,
+                int64_t ldbt, int dp, bool a_only) {
+  CUtensorMap t;  // encoded in an aligned temporary, then copied into place
+  uint8_t* dst = (uint8_t*)maps3;
+  if (!make_map(&t, A, (uint64_t)n, (uint64_t)m, (uint64_t)lda, 64, 64)) return false;
+  memcpy(dst, &t, sizeof(t));
+  if (a_only) return true;
+  if (!make_map(&t, Bt, (uint64_t)n, (uint64_t)dp, (uint64_t)ldbt, 64, (uint32_t)dp)) return false;
+  memcpy(dst + sizeof(t), &t, sizeof(t));
+  if (!make_map(&t, Bt, (uint64_t)m, (uint64_t)dp, (uint64_t)ldbt, 64, (uint32_t)dp)) return false;
+  memcpy(dst + 2 * sizeof(t), &t, sizeof(t));
+  return true;
+}
+
+size_t btc_map_bytes() { return sizeof(CUtensorMap); }
+
+cudaError_t btc_gemm(bool trans, const BMat* T, int count, const BTcTile* list, int n,
+                     const void* maps, int src, int dst, int dpmax, int* err, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  if (dpmax < 16 || dpmax > 256 || dpmax % 16) return cudaErrorInvalidValue;
+  const size_t stage_bytes = A_TILE_BYTES + (size_t)dpmax * BK * 2;
+  int stages = (int)((200 * 1024) / stage_bytes);
+  if (stages > 8) stages = 8;
+  const size_t smem = 1024 + stages * stage_bytes + 8 * (2 * stages + 5) + 16;
+  cudaError_t e = trans ? cudaFuncSetAttribute(k_btc_gemm<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)smem)
+            : cudaFuncSetAttribute(k_btc_gemm<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)smem);
+  if (e != cudaSuccess) return e;
+  int P = sm_count();
+  if (n < P) P = n;
+  const CUtensorMap* mp = (const CUtensorMap*)maps;
+  if (trans) k_btc_gemm<true><<<P, NTHREADS, smem, st>>>(list, n, T, mp, dst, stages, dpmax, err);
+  else k_btc_gemm<false><<<P, NTHREADS, smem, st>>>(list, n, T, mp, dst, stages, dpmax, err);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t btranspose_bf16(const BMat* T, int count, int src, cudaStream_t st) {
+  if (count <= 0) return cudaSuccess;
+  k_btranspose_bf16<<<dim3(64, count), dim3(32, 8), 0, st>>>(T, src);
   count_launch();
   return cudaGetLastError();
 }

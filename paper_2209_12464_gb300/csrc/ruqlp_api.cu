@@ -37,14 +37,21 @@ struct ruqlp_ctx {
   struct Span { int cat; cudaEvent_t a, b; };
   std::vector<Span> spans;
   std::vector<cudaEvent_t> pool;
-  // batched decompositions: CUDA graphs of the launch sequence, keyed by the
-  // batch signature (shapes, q, dtype, arena address)
-  struct BatchGraph {
+  // batched decompositions, per batch signature (shapes, q, dtype, product
+  // kernels, arena address): the captured launch sequence and the host image
+  // of the tensor maps
+  struct BatchEntry {
     std::vector<int64_t> key;
     cudaGraphExec_t exec = nullptr;
-    int uses = 0;
+    int seen = 0;
+    int64_t launches = 0;           // kernels in the captured graph
+    std::vector<uint8_t> maps;      // 3 tensor maps per matrix
+    std::vector<const void*> aptr;  // A each A map was encoded for
+    std::vector<int64_t> alda;
   };
-  std::vector<BatchGraph> graphs;
+  std::vector<BatchEntry> batches;
+  void* stage = nullptr;  // pinned staging of the batch metadata
+  size_t stage_bytes = 0;
   int batch_graphs = 1;  // option "batch_graph"
   cudaStream_t cap_stream = nullptr;  // capture stream (the legacy stream cannot capture)
   int64_t prof_count[6] = {0, 0, 0, 0, 0, 0};
@@ -208,9 +215,9 @@ ruqlp_status ensure_arena(ruqlp_ctx* h, size_t bytes) {
   }
   CK(cudaMalloc(&h->arena, bytes));
   h->arena_bytes = bytes;
-  for (auto& g : h->graphs)
+  for (auto& g : h->batches)
     if (g.exec) cudaGraphExecDestroy(g.exec);
-  h->graphs.clear();
+  h->batches.clear();
   return RUQLP_OK;
 }
 
@@ -577,18 +584,23 @@ ruqlp_status finish(ruqlp_ctx* h, ruqlp_outputs* out) {
 // one q): every phase is one launch over a device problem table (BMat); the
 // per-matrix Cholesky runs one CTA per matrix.  The sequence of launches
 // depends only on the batch signature and is replayed from a CUDA graph.
-// Products use the CUDA-core kernels (BF16 A with FP32 accumulation); Grams,
-// Cholesky factorisations and triangular solves use the same device code and
-// shape-only work splits as single decompositions, so an FP32 matrix gives
-// bitwise the same Q, L, P alone (ruqlp_decompose, bf16_simt for BF16) and
-// inside a batch.
+// BF16 products run on the tensor cores (one persistent launch over a tile
+// list of all matrices) when A's rows are 16-byte aligned, else on the CUDA
+// cores; FP32 products on the CUDA cores.  Grams, Cholesky factorisations and
+// triangular solves use the same device code and shape-only work splits as
+// single decompositions, and every product tile is one K-ordered
+// accumulation, so a matrix gets bitwise the same Q, L, P alone (a batch of
+// one) and inside any batch; FP32 items (and BF16 with option bf16_simt) also
+// equal ruqlp_decompose bitwise.
 namespace {
 
 struct BatchPlan {
   std::vector<BMat> table;
-  std::vector<int> prefix[7];  // NN, TN, gramY, gramN, gramPZ, trsmY, trsmN
-  size_t off_table, off_prefix[7], off_status, total;
-  int dmax;
+  std::vector<int> prefix[7];  // NN, TN, gramY, gramN, gramPZ, trsmY, trsmN (CUDA-core tiles)
+  std::vector<BTcTile> tc_nn, tc_tn;  // tensor-core tile lists
+  size_t off_meta, off_table, off_prefix[7], off_tc_nn, off_tc_tn, off_maps, meta_end;
+  size_t off_status, off_err, total;
+  int dmax, dpmax_tc;
   int64_t max_omega, max_out;
 };
 
@@ -600,11 +612,12 @@ ruqlp_status batch_launches(ruqlp_ctx* h, const BatchPlan& bp, int count, int q,
   const BMat* T = (const BMat*)(base + bp.off_table);
   auto pre = [&](int k) { return (const int*)(base + bp.off_prefix[k]); };
   auto tot = [&](int k) { return bp.prefix[k][count]; };
+  int* err = (int*)(base + bp.off_err);
   const double s1 = 64.0 * 5.960464477539063e-08;
   // profiling spans only on the eager path (st is the handle's stream there)
   ruqlp_ctx* ph = (st == h->stream) ? h : nullptr;
   ProfScope step(ph, PROF_STEP);
-  CK(cudaMemsetAsync(base + bp.off_status, 0, sizeof(DevStatus) * count, st));
+  CK(cudaMemsetAsync(base + bp.off_status, 0, bp.total - bp.off_status, st));
   auto orth_b = [&](int src, int dst, int passes) -> ruqlp_status {
     ProfScope sp(ph, PROF_ORTH);
     const int gp = (src == B_Y) ? PF_GY : PF_GN;
@@ -621,6 +634,13 @@ ruqlp_status batch_launches(ruqlp_ctx* h, const BatchPlan& bp, int count, int q,
     ProfScope sp(ph, trans ? PROF_ATX : PROF_AX);
     const int pf = trans ? PF_TN : PF_NN;
     CK(bgemm(trans, ct, Ty::F32, T, pre(pf), tot(pf), count, src, dst, st));
+    const auto& list = trans ? bp.tc_tn : bp.tc_nn;
+    if (!list.empty()) {
+      CK(btranspose_bf16(T, count, src, st));
+      ProfScope tc(ph, trans ? PROF_TC_ATX : PROF_TC_AX);
+      CK(btc_gemm(trans, T, count, (const BTcTile*)(base + (trans ? bp.off_tc_tn : bp.off_tc_nn)),
+                  (int)list.size(), base + bp.off_maps, src, dst, bp.dpmax_tc, err, st));
+    }
     return RUQLP_OK;
   };
   ruqlp_status s;
@@ -638,6 +658,23 @@ ruqlp_status batch_launches(ruqlp_ctx* h, const BatchPlan& bp, int count, int q,
   CK(bgram(T, pre(PF_GPZ), tot(PF_GPZ), count, B_P, B_Z, kMaxSplits, bp.dmax, st));
   CK(boutputs(T, count, bp.max_out, st));
   return RUQLP_OK;
+}
+
+// tile list of the tensor-core items, longest contraction first (CTA c takes
+// entries c, c + P, ...; sorting keeps each wave's tiles of similar cost)
+void tc_list(const std::vector<BMat>& table, bool trans, std::vector<BTcTile>& out) {
+  out.clear();
+  std::vector<int> order;
+  for (int i = 0; i < (int)table.size(); ++i)
+    if (table[i].use_tc) order.push_back(i);
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+    const int64_t kx = trans ? table[x].m : table[x].n, ky = trans ? table[y].m : table[y].n;
+    return kx > ky;
+  });
+  for (int i : order) {
+    const int64_t rows = trans ? table[i].n : table[i].m;
+    for (int t = 0; t < (int)ceil_div(rows, 128); ++t) out.push_back({i, t});
+  }
 }
 
 }  // namespace
@@ -668,10 +705,12 @@ extern "C" ruqlp_status ruqlp_decompose_batch(ruqlp_handle h, int count, const r
     if (!chol_tiles_supported(dd[i])) return fail(h, RUQLP_ERR_INVALID, "batched d must be <= 256");
   }
   CK(cudaSetDevice(h->device));
-  // workspace: per-matrix buffers, then the table, prefix arrays and statuses
+  // workspace: per-matrix buffers; the metadata block (table, prefix arrays,
+  // tile lists, tensor maps: uploaded in one copy); statuses and an error word
   BatchPlan bp;
   bp.table.resize(count);
   bp.dmax = 0;
+  bp.dpmax_tc = 0;
   bp.max_omega = 0;
   bp.max_out = 0;
   size_t off = 0;
@@ -681,10 +720,14 @@ extern "C" ruqlp_status ruqlp_decompose_batch(ruqlp_handle h, int count, const r
     return o;
   };
   std::vector<size_t> oX(count), oY(count), oZ(count), oP(count), oPa(count), oG(count),
-      oT(count);
+      oT(count), oB(count);
   for (int i = 0; i < count; ++i) {
-    const int64_t m = A[i].dense.m, n = A[i].dense.n;
+    const ruqlp_dense& D = A[i].dense;
+    const int64_t m = D.m, n = D.n;
     const int d = dd[i], dp = round16(d);
+    BMat& b = bp.table[i];
+    b.use_tc = (ct0 == Ty::BF16 && !h->bf16_simt && tc_supported(D.data, D.ld, dp)) ? 1 : 0;
+    b.ldbt = align_up((size_t)std::max(m, n), 8);
     int64_t slab;
     const int64_t sl = std::max(gram_slabs(m, kMaxSplits, &slab), gram_slabs(n, kMaxSplits, &slab));
     oX[i] = take((size_t)n * dp * 4);
@@ -694,19 +737,34 @@ extern "C" ruqlp_status ruqlp_decompose_batch(ruqlp_handle h, int count, const r
     oPa[i] = take((size_t)sl * d * d * 8);
     oG[i] = take((size_t)d * d * 8);
     oT[i] = take(chol_tiles_bytes(d));
+    oB[i] = b.use_tc ? take((size_t)dp * b.ldbt * 2) : 0;
     bp.dmax = std::max(bp.dmax, d);
+    if (b.use_tc) bp.dpmax_tc = std::max(bp.dpmax_tc, dp);
     bp.max_omega = std::max<int64_t>(bp.max_omega, n * dp);
     bp.max_out = std::max<int64_t>(bp.max_out, (m + n) * d + (int64_t)d * d);
-    for (int k = 0; k < 7; ++k) bp.prefix[k].resize(count + 1);
   }
+  for (int k = 0; k < 7; ++k) bp.prefix[k].assign(count + 1, 0);
+  bp.off_meta = off;
   bp.off_table = take(sizeof(BMat) * count);
   for (int k = 0; k < 7; ++k) bp.off_prefix[k] = take(sizeof(int) * (count + 1));
+  // tile lists are sized below, after the table is filled
+  size_t n_nn = 0, n_tn = 0;
+  for (int i = 0; i < count; ++i)
+    if (bp.table[i].use_tc) {
+      n_nn += ceil_div(A[i].dense.m, 128);
+      n_tn += ceil_div(A[i].dense.n, 128);
+    }
+  bp.off_tc_nn = take(sizeof(BTcTile) * std::max<size_t>(n_nn, 1));
+  bp.off_tc_tn = take(sizeof(BTcTile) * std::max<size_t>(n_tn, 1));
+  const size_t map3 = 3 * btc_map_bytes();
+  bp.off_maps = take(map3 * count);
+  bp.meta_end = off;
   bp.off_status = take(sizeof(DevStatus) * count);
+  bp.off_err = take(sizeof(int));
   bp.total = off;
   ruqlp_status s = ensure_arena(h, bp.total);
   if (s != RUQLP_OK) return s;
   char* base = (char*)h->arena;
-  for (int k = 0; k < 7; ++k) bp.prefix[k][0] = 0;
   for (int i = 0; i < count; ++i) {
     BMat& b = bp.table[i];
     const ruqlp_dense& D = A[i].dense;
@@ -726,77 +784,113 @@ extern "C" ruqlp_status ruqlp_decompose_batch(ruqlp_handle h, int count, const r
     b.partial = (double*)(base + oPa[i]);
     b.G = (double*)(base + oG[i]);
     b.tiles = (float*)(base + oT[i]);
+    b.Bt = b.use_tc ? (void*)(base + oB[i]) : nullptr;
     b.omega = prm[i].omega;
     b.Qout = out[i].Q;
     b.Lout = out[i].L;
     b.Pout = out[i].P;
     b.status = (DevStatus*)(base + bp.off_status) + i;
-    const int cnt[7] = {bgemm_tiles(b.m, b.d), bgemm_tiles(b.n, b.d),
+    const int cnt[7] = {b.use_tc ? 0 : bgemm_tiles(b.m, b.d), b.use_tc ? 0 : bgemm_tiles(b.n, b.d),
                         bgram_tiles(b.m, b.d, true, kMaxSplits),
                         bgram_tiles(b.n, b.d, true, kMaxSplits),
                         bgram_tiles(b.n, b.d, false, kMaxSplits), btrsm_blocks(b.m),
                         btrsm_blocks(b.n)};
     for (int k = 0; k < 7; ++k) bp.prefix[k][i + 1] = bp.prefix[k][i] + cnt[k];
   }
-  cudaStream_t st = h->stream;
-  CK(cudaMemcpyAsync(base + bp.off_table, bp.table.data(), sizeof(BMat) * count,
-                     cudaMemcpyHostToDevice, st));
-  for (int k = 0; k < 7; ++k)
-    CK(cudaMemcpyAsync(base + bp.off_prefix[k], bp.prefix[k].data(), sizeof(int) * (count + 1),
-                       cudaMemcpyHostToDevice, st));
-  // graph cache: the launch sequence depends on shapes, q, dtype and the arena
+  tc_list(bp.table, false, bp.tc_nn);
+  tc_list(bp.table, true, bp.tc_tn);
+  // signature: the launch sequence depends on shapes, q, dtype, product
+  // kernels and the arena
   std::vector<int64_t> key = {count, q0, (int64_t)ct0, (int64_t)(uintptr_t)h->arena};
   for (int i = 0; i < count; ++i) {
     key.push_back(bp.table[i].m);
     key.push_back(bp.table[i].n);
     key.push_back(bp.table[i].d);
+    key.push_back(bp.table[i].use_tc);
   }
-  ruqlp_ctx::BatchGraph* g = nullptr;
-  for (auto& c : h->graphs)
+  ruqlp_ctx::BatchEntry* g = nullptr;
+  for (auto& c : h->batches)
     if (c.key == key) g = &c;
-  const bool graphs = h->batch_graphs && !h->profile;  // profiling runs eagerly
-  if (graphs && g && g->exec) {
-    CK(cudaGraphLaunch(g->exec, st));
-    g->uses++;
-  } else {
-    const bool capture = graphs && g != nullptr;  // second sighting: capture it
-    if (capture) {
-      if (!h->cap_stream) CK(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
-      CK(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
-      s = batch_launches(h, bp, count, q0, ct0, h->cap_stream);
-      cudaGraph_t graph = nullptr;
-      const cudaError_t ec = cudaStreamEndCapture(h->cap_stream, &graph);
-      if (s != RUQLP_OK) {
-        if (graph) cudaGraphDestroy(graph);
-        return s;
-      }
-      CK(ec);
-      cudaGraphExec_t exec = nullptr;
-      const cudaError_t ei = cudaGraphInstantiate(&exec, graph, 0);
-      cudaGraphDestroy(graph);
-      CK(ei);
-      g->exec = exec;
-      CK(cudaGraphLaunch(exec, st));
-    } else {
-      s = batch_launches(h, bp, count, q0, ct0, st);
-      if (s != RUQLP_OK) return s;
-      if (graphs && g == nullptr) {
-        if (h->graphs.size() >= 8) {
-          if (h->graphs.front().exec) cudaGraphExecDestroy(h->graphs.front().exec);
-          h->graphs.erase(h->graphs.begin());
-        }
-        ruqlp_ctx::BatchGraph ng;
-        ng.key = key;
-        h->graphs.push_back(ng);
-      }
+  if (!g) {
+    if (h->batches.size() >= 8) {
+      if (h->batches.front().exec) cudaGraphExecDestroy(h->batches.front().exec);
+      h->batches.erase(h->batches.begin());
     }
+    h->batches.emplace_back();
+    g = &h->batches.back();
+    g->key = key;
+    g->maps.assign(map3 * count, 0);
+    g->aptr.assign(count, nullptr);
+    g->alda.assign(count, 0);
   }
+  // tensor maps: Bt maps depend on the signature only; A maps are re-encoded
+  // when the caller's A pointer or stride changes
+  for (int i = 0; i < count; ++i) {
+    const BMat& b = bp.table[i];
+    if (!b.use_tc || (g->aptr[i] == b.A && g->alda[i] == b.lda)) continue;
+    if (!btc_encode(g->maps.data() + map3 * i, b.A, b.lda, b.m, b.n, b.Bt, b.ldbt, b.dp,
+                    g->aptr[i] != nullptr))
+      return fail(h, RUQLP_ERR_INVALID, "batch item %d: tensor map encoding failed", i);
+    g->aptr[i] = b.A;
+    g->alda[i] = b.lda;
+  }
+  // metadata image in pinned memory, one upload
+  const size_t meta = bp.meta_end - bp.off_meta;
+  if (h->stage_bytes < meta) {
+    if (h->stage) cudaFreeHost(h->stage);
+    h->stage = nullptr;
+    h->stage_bytes = 0;
+    CK(cudaMallocHost(&h->stage, meta));
+    h->stage_bytes = meta;
+  }
+  char* img = (char*)h->stage;
+  auto put = [&](size_t o, const void* src, size_t bytes) {
+    if (bytes) memcpy(img + (o - bp.off_meta), src, bytes);
+  };
+  put(bp.off_table, bp.table.data(), sizeof(BMat) * count);
+  for (int k = 0; k < 7; ++k) put(bp.off_prefix[k], bp.prefix[k].data(), sizeof(int) * (count + 1));
+  put(bp.off_tc_nn, bp.tc_nn.data(), sizeof(BTcTile) * bp.tc_nn.size());
+  put(bp.off_tc_tn, bp.tc_tn.data(), sizeof(BTcTile) * bp.tc_tn.size());
+  put(bp.off_maps, g->maps.data(), g->maps.size());
+  cudaStream_t st = h->stream;
+  CK(cudaMemcpyAsync(base + bp.off_meta, img, meta, cudaMemcpyHostToDevice, st));
+  const bool graphs = h->batch_graphs && !h->profile;  // profiling runs eagerly
+  if (graphs && g->exec) {
+    CK(cudaGraphLaunch(g->exec, st));
+    ruqlp::count_launch((int)g->launches);
+  } else if (graphs && g->seen > 0) {  // second sighting of the signature: capture it
+    if (!h->cap_stream) CK(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+    CK(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
+    const int64_t l0 = ruqlp::launch_count();
+    s = batch_launches(h, bp, count, q0, ct0, h->cap_stream);
+    g->launches = ruqlp::launch_count() - l0;
+    cudaGraph_t graph = nullptr;
+    const cudaError_t ec = cudaStreamEndCapture(h->cap_stream, &graph);
+    if (s != RUQLP_OK) {
+      if (graph) cudaGraphDestroy(graph);
+      return s;
+    }
+    CK(ec);
+    cudaGraphExec_t exec = nullptr;
+    const cudaError_t ei = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    CK(ei);
+    g->exec = exec;
+    CK(cudaGraphLaunch(exec, st));
+  } else {
+    s = batch_launches(h, bp, count, q0, ct0, st);
+    if (s != RUQLP_OK) return s;
+  }
+  g->seen++;
   std::vector<DevStatus> stat(count);
+  int derr = 0;
   CK(cudaMemcpyAsync(stat.data(), base + bp.off_status, sizeof(DevStatus) * count,
                      cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(&derr, base + bp.off_err, sizeof(int), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
   if (h->profile) prof_collect(h);
   for (int i = 0; i < count; ++i) out[i].flags = (uint32_t)stat[i].flags;
+  if (derr) return fail(h, RUQLP_ERR_TIMEOUT, "a bounded device wait ran out in a batched product");
   return RUQLP_OK;
 }
 
@@ -830,9 +924,10 @@ ruqlp_status ruqlp_destroy(ruqlp_handle h) {
   if (!h) return RUQLP_ERR_INVALID;
   cudaSetDevice(h->device);
   cudaStreamSynchronize(h->stream);
-  for (auto& g : h->graphs)
+  for (auto& g : h->batches)
     if (g.exec) cudaGraphExecDestroy(g.exec);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+  if (h->stage) cudaFreeHost(h->stage);
   if (h->arena) cudaFree(h->arena);
   if (h->status) cudaFree(h->status);
   if (h->status_host) cudaFreeHost(h->status_host);

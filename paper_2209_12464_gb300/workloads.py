@@ -233,6 +233,19 @@ def batch_shapes(seed, count=512, m_range=(256, 4096), n_range=(128, 2048),
     return out
 
 
+def aligned_rows(A):
+    """A copy of the 2-D torch tensor A whose rows start on 16-byte boundaries
+    (leading dimension rounded up to a multiple of 16 bytes; the padding
+    columns are zero and not part of the returned view)."""
+    import torch
+    m, n = A.shape
+    per = max(1, 16 // A.element_size())
+    ld = (n + per - 1) // per * per
+    buf = torch.zeros(m, ld, dtype=A.dtype, device=A.device)
+    buf[:, :n] = A
+    return buf[:, :n]
+
+
 def poisson_arrivals(seed, rate, count):
     """Arrival times (seconds) of a Poisson process with ``rate`` per second."""
     rng = np.random.default_rng(seed)

@@ -6,8 +6,11 @@ call.
     tolerances of the single-matrix path (L and |diag(L)| within 1e-5 |L_11|,
     residual within 1e-5, leading-k columns of Q and P within 1e-4);
   * batch invariance: every item's Q, L, P are bitwise the single-matrix
-    result (FP32; BF16 against the CUDA-core BF16 single path), eagerly, under
+    result (FP32; BF16 with CUDA-core products on both sides), eagerly, under
     graph capture and on graph replay;
+  * tensor-core batches (BF16 A with 16-byte aligned rows, mixed with
+    unaligned items that take the CUDA cores): every item bitwise equal to its
+    batch of one, and the BF16 accuracy rule against the oracle (below);
   * the full batched workload (512 matrices, m log-uniform in [256, 4096],
     n in [128, 2048], k in [8, 64], p = 8, q = 1): invariance for all items,
     the oracle on a sample.
@@ -51,6 +54,20 @@ def _mix(seed, shapes):
     return As, Oms
 
 
+def _pad8(A):
+    """A in rows that start on 16-byte boundaries: the layout the
+    tensor-core batched product needs."""
+    return wl.aligned_rows(A)
+
+
+def _bf16_bound(r0, d, m):
+    """BF16 products round the skinny operand to BF16 (relative 2^-9 per
+    entry); the last one, B^T = A^T bf16(Q), adds Q dQ^T A with
+    ||dQ^T A||_F about 2^-9 sqrt(d / m) ||A||_F.  Relative residual bound
+    against the unrounded matrix: 1.05 x the FP64 oracle's plus 2^-8 sqrt(d/m)."""
+    return 1.05 * r0 + 2.0 ** -8 * np.sqrt(d / m)
+
+
 def _single(handle, A, om, k, p, q):
     Q, L, P, f = handle.decompose(A, om, k, p, q, out_dtype=torch.float32)
     return Q, L, P
@@ -87,10 +104,10 @@ def test_batch_items_bitwise_equal_single(handle, dtype):
     Og = [torch.from_numpy(o).cuda() for o in Oms]
     ks, ps = [s[2] for s in MIX], [s[3] for s in MIX]
     runs = []
-    for _ in range(3):  # eager, captured into a graph, replayed
-        runs.append(handle.decompose_batch(Ag, Og, ks, None, Q_ITERS, ps=ps))
     handle.set_option("bf16_simt", 1)
     try:
+        for _ in range(3):  # eager, captured into a graph, replayed
+            runs.append(handle.decompose_batch(Ag, Og, ks, None, Q_ITERS, ps=ps))
         for i, (A, om, k, p) in enumerate(zip(Ag, Og, ks, ps)):
             one = _single(handle, A, om, k, p, Q_ITERS)
             for run in runs:
@@ -134,6 +151,37 @@ def test_batch_new_inputs_same_shapes_replay(handle):
                 assert torch.equal(x, y)
 
 
+def test_batch_tensor_core_items(handle):
+    """BF16 batch, half the items in 16-byte aligned storage (tensor cores),
+    the rest unaligned (CUDA cores): each item bitwise equals its batch of
+    one, on eager, captured and replayed calls; accuracy against the oracle
+    by the BF16 rule."""
+    As, Oms = _mix(wl.MASTER_SEED + 43, MIX)
+    Ag = []
+    for i, A in enumerate(As):
+        t = torch.from_numpy(A).bfloat16().cuda()
+        Ag.append(_pad8(t) if i % 2 == 0 else t)
+    Og = [torch.from_numpy(o).cuda() for o in Oms]
+    ks, ps = [s[2] for s in MIX], [s[3] for s in MIX]
+    runs = [handle.decompose_batch(Ag, Og, ks, None, Q_ITERS, ps=ps) for _ in range(3)]
+    for i in range(len(MIX)):
+        one = handle.decompose_batch([Ag[i]], [Og[i]], [ks[i]], ps[i], Q_ITERS)[0]
+        for run in runs:
+            for x, y in zip(run[i][:3], one[:3]):
+                assert torch.equal(x, y), (i, MIX[i])
+    for i, ((m, n, k, p), A64, om) in enumerate(zip(MIX, As, Oms)):
+        Q, L, P = (t.double().cpu().numpy() for t in runs[0][i][:3])
+        ref = oracle.ruqlp(A64, om, Q_ITERS)
+        r = oracle.residual_fro_small(A64, Q, L, P)
+        r0 = oracle.residual_fro_small(A64, ref["Q"], ref["L"], ref["P"])
+        assert r <= _bf16_bound(r0, k + p, m), (i, MIX[i], r, r0)
+        l11 = abs(ref["L"][0, 0])
+        assert np.max(np.abs(np.abs(np.diag(L))[:k] - np.abs(np.diag(ref["L"]))[:k])) <= 2e-2 * l11
+        d = k + p
+        assert np.max(np.abs(Q.T @ Q - np.eye(d))) <= 2e-5
+        assert np.max(np.abs(P.T @ P - np.eye(d))) <= 2e-5
+
+
 @pytest.mark.parametrize("bad", ["mixed_dtype", "mixed_q", "d257", "empty", "f64"])
 def test_batch_invalid_rejected(handle, bad):
     A1 = torch.randn(300, 280, device="cuda")
@@ -163,38 +211,42 @@ def test_batch_invalid_rejected(handle, bad):
 @pytest.mark.slow
 @pytest.mark.parametrize("dtype", [torch.float32, torch.bfloat16], ids=["f32", "bf16"])
 def test_batched_workload_512(handle, dtype):
-    """The batched workload: all 512 items bitwise equal their single-matrix
-    results; 6 sampled items against the oracle.  FP32: the FP32 tolerances.
-    BF16: relative residual against the unrounded matrix within 1.05x the FP64
-    oracle's plus 2^-8 sqrt(d / m): each product rounds the skinny operand to
-    BF16 (relative 2^-9 per entry), and the last one, B^T = A^T bf16(Q), adds
-    Q dQ^T A with ||dQ^T A||_F about 2^-9 sqrt(d / m) ||A||_F for a random
-    rounding pattern dQ -- negligible for the 20000 x 20000 workload (d / m =
-    0.011), not for m = 256, d = 72."""
+    """The batched workload (rows in 16-byte aligned storage, as the bench
+    lays them out).  FP32: all 512 items bitwise equal ruqlp_decompose.
+    BF16: tensor-core batch; 16 sampled items bitwise equal their batch of
+    one; then the CUDA-core BF16 batch bitwise equals ruqlp_decompose for all
+    512.  Six sampled items against the oracle (FP32 tolerances; BF16 rule)."""
     shapes = wl.batch_shapes(wl.MASTER_SEED + 4)
     A32 = [wl.dense_spectral_torch(wl.MASTER_SEED + 400 + i, m, n,
                                    wl.spectrum_gap(min(m, n), k, 1e-2))
            for i, (m, n, k, p) in enumerate(shapes)]
-    Ag = [a.to(dtype) for a in A32]
+    Ag = [_pad8(a.to(dtype)) for a in A32]
     Og = [wl.omega_torch(wl.MASTER_SEED + 1400 + i, n, k + p)
           for i, (m, n, k, p) in enumerate(shapes)]
     ks, ps = [s[2] for s in shapes], [s[3] for s in shapes]
     res = handle.decompose_batch(Ag, Og, ks, None, 1, ps=ps)
+    rng = np.random.default_rng(7)
+    if dtype == torch.bfloat16:
+        for i in rng.choice(len(shapes), 16, replace=False):
+            one = handle.decompose_batch([Ag[i]], [Og[i]], [ks[i]], ps[i], 1)[0]
+            for x, y in zip(res[i][:3], one[:3]):
+                assert torch.equal(x, y), (i, shapes[i])
     handle.set_option("bf16_simt", 1)
     try:
+        simt = res if dtype == torch.float32 else handle.decompose_batch(Ag, Og, ks, None, 1,
+                                                                           ps=ps)
         for i in range(len(shapes)):
             one = _single(handle, Ag[i], Og[i], ks[i], ps[i], 1)
-            for x, y in zip(res[i][:3], one):
+            for x, y in zip(simt[i][:3], one):
                 assert torch.equal(x, y), (i, shapes[i])
     finally:
         handle.set_option("bf16_simt", 0)
-    rng = np.random.default_rng(7)
     for i in rng.choice(len(shapes), 6, replace=False):
         m, n, k, p = shapes[i]
-        Aseen = Ag[i].double().cpu().numpy()
         om = Og[i].cpu().numpy()
         Q, L, P = (t.double().cpu().numpy() for t in res[i][:3])
         if dtype == torch.float32:
+            Aseen = Ag[i].double().cpu().numpy()
             ref = oracle.ruqlp(Aseen, om, 1)
             l11 = abs(ref["L"][0, 0])
             assert np.max(np.abs(L - ref["L"])) <= 1e-5 * l11
@@ -206,4 +258,4 @@ def test_batched_workload_512(handle, dtype):
             ref = oracle.ruqlp(A64, om, 1)
             r = oracle.residual_fro_small(A64, Q, L, P)
             r0 = oracle.residual_fro_small(A64, ref["Q"], ref["L"], ref["P"])
-            assert r <= 1.05 * r0 + 2.0 ** -8 * np.sqrt((k + p) / m), (i, shapes[i], r, r0)
+            assert r <= _bf16_bound(r0, k + p, m), (i, shapes[i], r, r0)
