@@ -12,6 +12,9 @@ every product, B^T = A^T Q and its QR.  The workload is the dense
   python bench.py --workload batch [--dtype bf16|f32]   (512 uneven matrices:
       m log-uniform in [256, 4096], n in [128, 2048], k uniform in [8, 64],
       p=8, q=1, same spectrum form; one ruqlp_decompose_batch call per step)
+  python bench.py --workload serve [--duration S] [--rate R]   (Poisson
+      arrivals at R/s: 95 % shaped like the batched workload, 5 % dense
+      16384 x 8192 with k=256, p=16, q=2; BF16; 150 GB budget; p50/p99)
 
 Under torchrun each rank runs its own replica of the workload (weak scaling,
 no data-path collective); rank 0 prints one JSON line.
@@ -49,9 +52,13 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--size", type=int, default=0, help="override m = n (testing only)")
-    ap.add_argument("--workload", default="dense", choices=["dense", "batch"],
+    ap.add_argument("--workload", default="dense", choices=["dense", "batch", "serve"],
                     help="dense: one 20000 x 20000 matrix (the metric's workload); batch: "
-                         "512 matrices of uneven shapes in one batched call")
+                         "512 matrices of uneven shapes in one batched call; serve: Poisson "
+                         "arrivals through ruqlp_submit / ruqlp_poll")
+    ap.add_argument("--duration", type=float, default=2.0,
+                    help="seconds of arrivals (serve workload)")
+    ap.add_argument("--rate", type=float, default=2000.0, help="arrivals per second (serve)")
     ap.add_argument("--count", type=int, default=512, help="batch size (batch workload)")
     ap.add_argument("--gen", default="haar", choices=["haar", "fast"],
                     help="haar: the workload's Haar U, V (torch.linalg.qr); fast: Gaussian "
@@ -441,6 +448,119 @@ def run_batch(args, torch, dev, local, world, rank, dist):
     return 0
 
 
+
+# ---------------------------------------------------------------------------
+# serving workload
+# ---------------------------------------------------------------------------
+S_SEED = 20260 + 4
+S_BIG = (16384, 8192, 256, 16, 2)
+S_BUDGET = 150 * 10 ** 9
+
+
+def run_serve(args, torch, dev, local, world, rank, dist):
+    import numpy as np
+    from paper_2209_12464_gb300 import ruqlp
+    from paper_2209_12464_gb300 import workloads as wl
+    # input pool (generation is not timed): 256 small matrices of the batched
+    # workload's shapes and 4 big ones
+    shapes = wl.batch_shapes(S_SEED, count=256, p=B_P)
+    small = []
+    for i, (m, n, k, p) in enumerate(shapes):
+        if args.gen == "haar":
+            A = wl.dense_spectral_torch(S_SEED + 100 + i, m, n, wl.spectrum_gap(min(m, n), k, TAIL),
+                                        device=dev)
+        else:
+            A = wl.dense_lowrank_gauss_torch(S_SEED + 100 + i, m, n, k, device=dev)
+        small.append((wl.aligned_rows(A.bfloat16()), wl.omega_torch(S_SEED + 600 + i, n, k + p,
+                                                                     device=dev), k, p, B_Q))
+    bm, bn, bk, bp, bq = S_BIG
+    big = []
+    for i in range(4):
+        if args.gen == "haar":
+            A = wl.dense_spectral_torch(S_SEED + 900 + i, bm, bn, wl.spectrum_gap(bn, bk, TAIL),
+                                        device=dev, dtype=torch.bfloat16)
+        else:
+            A = wl.dense_lowrank_gauss_torch(S_SEED + 900 + i, bm, bn, bk, device=dev).bfloat16()
+        big.append((A, wl.omega_torch(S_SEED + 950 + i, bn, bk + bp, device=dev), bk, bp, bq))
+    torch.cuda.synchronize()
+    h = ruqlp.Handle(local, torch.cuda.current_stream(dev).cuda_stream,
+                     hbm_budget_bytes=S_BUDGET, max_slots=4)
+    rng = np.random.default_rng(S_SEED)
+
+    def run(nreq, rate, seed):
+        arr = wl.poisson_arrivals(seed, rate, nreq)
+        kinds = rng.random(nreq) < 0.05
+        picks = rng.integers(0, 256, nreq)
+        bigs = rng.integers(0, 4, nreq)
+        tickets, pend = [], []
+        t0 = time.perf_counter()
+        for j in range(nreq):
+            while time.perf_counter() - t0 < arr[j]:
+                pend = [t for t in pend if not h.poll(t)]
+            A, om, k, p, q = big[bigs[j]] if kinds[j] else small[picks[j]]
+            t = h.submit(A, om, k, p, q)
+            t.big = bool(kinds[j])
+            t.bytes = A.shape[0] * A.shape[1] * 2 * (2 * q + 2)
+            tickets.append(t)
+            pend.append(t)
+        while pend:
+            pend = [t for t in pend if not h.poll(t)]
+        return tickets
+
+    run(max(100, int(0.1 * args.rate)), args.rate, S_SEED + 1)  # warm-up
+    nreq = max(1, int(args.duration * args.rate))
+    clocks = Clocks(local)
+    clocks.start()
+    time.sleep(0.3)
+    l0 = ruqlp.ruqlp_launch_count()
+    tickets = run(nreq, args.rate, S_SEED + 2)
+    launches = ruqlp.ruqlp_launch_count() - l0
+    ck = clocks.stop()
+    lat = np.array([(t.times[2] - t.times[0]) * 1e3 for t in tickets])
+    lat_b = np.array([(t.times[2] - t.times[0]) * 1e3 for t in tickets if t.big])
+    lat_s = np.array([(t.times[2] - t.times[0]) * 1e3 for t in tickets if not t.big])
+    wall = max(t.times[2] for t in tickets) - min(t.times[0] for t in tickets)
+    dps = len(tickets) / wall
+    gbs = sum(t.bytes for t in tickets) / wall / 1e9
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except OSError:
+        pass
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    pct = lambda a, q_: float(np.percentile(a, q_)) if len(a) else None
+    flags = 0
+    for t in tickets:
+        flags |= t.flags
+    out = {"metric": "RU-QLP serving: decompositions/s with p50/p99 latency", "value": dps,
+           "unit": "decompositions/s", "n_gpus": world, "steps": len(tickets),
+           "warmup": max(100, int(0.1 * args.rate)), "ms_per_step": 1e3 / dps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16",
+           "data": "synthetic",
+           "config": {"workload": "serving: Poisson arrivals %.0f/s for %.1f s; 95%% batched-"
+                                  "workload shapes (q=1, p=8), 5%% dense 16384x8192 k=256 p=16 "
+                                  "q=2; 150 GB budget, 4 slots" % (args.rate, args.duration),
+                      "pool": "256 small + 4 big device-resident inputs",
+                      "l2": "inputs larger than L2 (pool %.1f GB)" % (
+                          sum(a[0].numel() * 2 for a in small + big) / 1e9),
+                      "parallelism": f"replicas x{world}"},
+           "latency_ms": {"p50": pct(lat, 50), "p99": pct(lat, 99), "max": float(lat.max()),
+                          "small_p50": pct(lat_s, 50), "small_p99": pct(lat_s, 99),
+                          "big_p50": pct(lat_b, 50), "big_p99": pct(lat_b, 99),
+                          "n_small": int(len(lat_s)), "n_big": int(len(lat_b))},
+           "offered_rate": args.rate, "accuracy": {"flags": flags},
+           "roofline": {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s",
+                        "frac": gbs / hbm_peak, "traffic": None,
+                        "kernel": "all: A bytes streamed (passes x bytes(A)) over the run's wall "
+                                  "time (the load is latency-bound, not bandwidth-bound)",
+                        "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"},
+           "cpu_baseline": None, "e2e": None, "gpu_launches": launches, "clocks": ck}
+    if rank == 0:
+        print(json.dumps(out))
+    h.close()
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -455,8 +575,9 @@ def main():
     import __graft_entry__ as g
     g.build()
     from paper_2209_12464_gb300 import ruqlp
-    if args.workload == "batch":
-        rc = run_batch(args, torch, dev, local, world, rank, dist)
+    if args.workload in ("batch", "serve"):
+        fn = run_batch if args.workload == "batch" else run_serve
+        rc = fn(args, torch, dev, local, world, rank, dist)
         if world > 1:
             dist.destroy_process_group()
         return rc

@@ -108,7 +108,8 @@ typedef struct {
  * the FP64 path and FP32 (shifted CholeskyQR3) on the FP32/BF16 paths unless
  * the "orth_fp64" option is set.  compute must equal A's dtype.
  * BF16 inputs use the tensor cores when A's leading dimension is a multiple
- * of 8 elements, A is 16-byte aligned and d <= 256; otherwise CUDA cores.
+ * of 8 elements and A is 16-byte aligned (sketches wider than 256 columns
+ * run as column chunks, one pass over A each); otherwise CUDA cores.
  * omega: n x d row-major FP64 Gaussian test matrix (device memory for
  * ruqlp_decompose / ruqlp_submit; host memory for ruqlp_decompose_host).
  * finish_paper: 1 = also take the d x d QR of L, [P~, R~] = qr(L)
@@ -188,7 +189,7 @@ ruqlp_status ruqlp_decompose(ruqlp_handle h, const ruqlp_matrix* A,
 /* `count` independent decompositions in one call (the batched workload:
  * many dense matrices of uneven shapes).  A[i], prm[i], out[i] as for
  * ruqlp_decompose (device memory); every item must be dense, share one
- * compute dtype (F32 or BF16) and one q, have d <= 256 and finish_paper = 0.
+ * compute dtype (F32 or BF16) and one q, have d <= 288 and finish_paper = 0.
  * Each phase of the method (sketch products, Grams, Cholesky factorisations,
  * triangular solves) is one launch over all items; the launch sequence is
  * captured in a CUDA graph the second time a batch signature (shapes, q,
@@ -200,6 +201,40 @@ ruqlp_status ruqlp_decompose(ruqlp_handle h, const ruqlp_matrix* A,
  * BUDGET, CUDA. */
 ruqlp_status ruqlp_decompose_batch(ruqlp_handle h, int count, const ruqlp_matrix* A,
                                    const ruqlp_params* prm, ruqlp_outputs* out);
+
+/* Serving (the paper has no counterpart: a request loop around the
+ * decomposition of Section III).  ruqlp_submit queues one decomposition
+ * (arguments as for ruqlp_decompose, device memory) and returns at once with
+ * a ticket; A, omega, the output buffers and *out must stay valid until
+ * ruqlp_poll reports completion, and A and omega must already hold their
+ * values (the loop's streams do not wait on the caller's stream).  A scheduler thread of the handle admits
+ * queued requests in arrival order as execution slots (config.max_slots,
+ * each with its own stream and workspace) and HBM free up: the workspaces of
+ * all slots together stay within config.hbm_budget_bytes (0 = no limit).
+ * Consecutive batchable requests (dense, F32/BF16, d <= 256, at most 2^25
+ * elements, same compute dtype and q, no finish_paper) are launched together
+ * through the batched path; others run alone; requests arriving while earlier ones run are
+ * admitted into the next free slot, so their work overlaps on the device.
+ * A request's result is bitwise the one it gets alone (batch invariance).
+ * Errors at submit: INVALID (arguments), BUDGET (its workspace alone exceeds
+ * the budget).  ruqlp_submit and ruqlp_poll are thread-safe; ruqlp_destroy
+ * waits for every submitted request. */
+ruqlp_status ruqlp_submit(ruqlp_handle h, const ruqlp_matrix* A, const ruqlp_params* prm,
+                          ruqlp_outputs* out, uint64_t* ticket);
+
+/* Seconds since the handle's request loop started. */
+typedef struct {
+  double submit_s;  /* ruqlp_submit returned */
+  double start_s;   /* admitted and launched */
+  double done_s;    /* completion observed by the loop */
+} ruqlp_request_times;
+
+/* NOT_READY while the request is queued or running; afterwards its status
+ * (OK, or the error of its decomposition; out->flags set) -- once: the
+ * ticket is released.  ruqlp_poll_times also reports the request's times
+ * (times may be NULL).  Unknown tickets: INVALID. */
+ruqlp_status ruqlp_poll(ruqlp_handle h, uint64_t ticket);
+ruqlp_status ruqlp_poll_times(ruqlp_handle h, uint64_t ticket, ruqlp_request_times* times);
 
 /* The same decomposition with A, prm->omega and the outputs in HOST memory:
  * the library copies A and Omega into its arena, runs ruqlp_decompose's

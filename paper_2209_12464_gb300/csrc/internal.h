@@ -50,7 +50,7 @@ cudaError_t chol_upper(const double* G, int d, double shift_rel, double* R, void
 // trsm_tiles_f32 uses to form X = Y R^{-1} (X may alias Y).
 bool chol_tiles_supported(int d);
 size_t chol_tiles_bytes(int d);
-cudaError_t chol_tiles_f32(const double* G, int d, double shift_rel, bool force_shift,
+cudaError_t chol_tiles_f32(const float* G, int d, double shift_rel, bool force_shift,
                            float* tiles, DevStatus* status, const int32_t* gate, cudaStream_t st);
 cudaError_t trsm_tiles_f32(const float* Y, int64_t ldy, const float* tiles, float* X, int64_t ldx,
                            int64_t M, int d, cudaStream_t st);
@@ -58,10 +58,11 @@ cudaError_t trsm_tiles_f32(const float* Y, int64_t ldy, const float* tiles, floa
 // C (d1 x d2, FP64, ld d2) = X^T W for FP32 X (M x d1, ld ldx) and W (M x d2,
 // ld ldw): FP32 products summed in FP32 within a row slab, slabs summed in
 // FP64 in order.  X == W computes only the upper tiles and mirrors them.
-// partial: max_slabs * d1 * d2 doubles of scratch.
+// partial: max_slabs * d1 * d2 doubles of scratch.  Cf (optional): the same
+// result rounded to FP32 (the Cholesky's input).
 cudaError_t gram_f32(const float* X, int64_t ldx, const float* W, int64_t ldw, int64_t M, int d1,
                      int d2, double* C, double* partial, int max_slabs, const int32_t* gate,
-                     cudaStream_t st);
+                     cudaStream_t st, float* Cf = nullptr);
 
 // X[M x d] <- Y[M x d] R^{-1} for upper-triangular R (type ty, ld d): each
 // row solves x R = y by forward substitution.  X may alias Y.  A non-null
@@ -126,6 +127,7 @@ struct BMat {
   float* P;  // n x dp
   double* partial;
   double* G;
+  float* Gf;       // the Gram in FP32 (Cholesky input)
   float* tiles;
   const double* omega;
   void* Bt;        // dp x ldbt BF16 (tensor-core items): the transposed skinny operand

@@ -1,15 +1,18 @@
 // FP32 pieces of the shifted CholeskyQR3 orth() (Section II-A orth();
-// Fukaya, Kannan, Nakatsukasa, Yamamoto, Yanagisawa 2020) for d <= 256:
+// Fukaya, Kannan, Nakatsukasa, Yamamoto, Yanagisawa 2020) for d <= 288:
 //
 //  * k_chol_tiles: one CTA factors the d x d Gram G (+ shift I) = R^T R,
 //    blocked in 32 x 32 tiles held in shared memory (upper block triangle,
 //    padded to a multiple of 32 with the identity).  Each diagonal tile is
-//    factored and inverted by one warp in registers (shuffles); the panel
-//    solves (products with the tile inverse) and trailing updates are 32 x 32
-//    tile products spread over all warps with 128-bit broadcast loads, so the
-//    factorisation needs three block barriers per tile row, not per column.
+//    factored and inverted by one warp in registers (row broadcasts through
+//    shared memory); the panel solves (products with the tile inverse) and
+//    trailing updates are 32 x 32 tile products spread over all warps with
+//    128-bit broadcast loads, so the factorisation needs three block barriers
+//    per tile row, not per column.  The Gram arrives in FP32 (rounded by the
+//    slab reduction), so the kernel does no FP64 arithmetic.
 //  * k_trsm_tiles: Q = Y R^{-1} by blocked forward substitution with those
-//    tiles (rows of Y staged in shared memory, so Q may overwrite Y).
+//    tiles (rows of Y staged transposed in shared memory, so Q may overwrite
+//    Y).
 #include <math.h>
 
 #include "../../include/ruqlp.h"
@@ -21,7 +24,7 @@ namespace {
 
 constexpr int TB = 32;        // tile edge
 constexpr int TP = 36;        // row pitch: 16-byte aligned rows for 128-bit loads
-constexpr int MAXNB = 8;      // d <= 256
+constexpr int MAXNB = 9;      // d <= 288
 constexpr int NTH = 512;      // 16 warps; up to 128 registers for per-lane tile columns
 constexpr size_t TILE_FLOATS = (size_t)TB * TP;
 
@@ -137,11 +140,11 @@ __device__ bool factor_tile(float* __restrict__ B, float* __restrict__ Sout, flo
 // upper tiles R_IJ (I <= J) and the diagonal-tile inverses R_KK^{-1}, FP32,
 // 32 x 32 row-major each, to `tiles`: first the nb (nb+1)/2 R tiles in
 // row-of-tiles order, then the nb inverse tiles.
-__device__ __forceinline__ void chol_body(const double* __restrict__ G, int d, double shift_rel,
+__device__ __forceinline__ void chol_body(const float* __restrict__ G, int d, double shift_rel,
                                           int force_shift, float* __restrict__ tiles,
                                           DevStatus* __restrict__ status) {
   extern __shared__ __align__(16) float sm[];
-  __shared__ double s_shift;
+  __shared__ float s_shift;
   __shared__ int s_bad, s_rankdef;
   __shared__ __align__(16) float s_dinv[TB];
   __shared__ __align__(16) float s_row[TB];
@@ -149,15 +152,16 @@ __device__ __forceinline__ void chol_body(const double* __restrict__ G, int d, d
   const int ntiles = nb * (nb + 1) / 2;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = NTH / 32;
   auto tile = [&](int I, int J) { return sm + (size_t)bidx(I, J, nb) * TILE_FLOATS; };
-  auto dinv_s = [&](int K) { return sm + (size_t)(ntiles + K) * TILE_FLOATS; };  // shared
+  // the current diagonal tile's inverse (shared; copied out once formed)
+  float* const dinv_sm = sm + (size_t)ntiles * TILE_FLOATS;
 
   if (warp == 0) {  // shift = shift_rel * trace(G)
-    double t = 0.0;
+    float t = 0.f;
     for (int i = lane; i < d; i += 32) t += G[(size_t)i * d + i];
     for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
     if (lane == 0) {
-      double sh = shift_rel * t;
-      if (!(sh > 0.0)) sh = 1e-30;
+      float sh = (float)shift_rel * t;
+      if (!(sh > 0.f)) sh = 1e-30f;
       s_shift = sh;
       s_rankdef = 0;
     }
@@ -165,43 +169,37 @@ __device__ __forceinline__ void chol_body(const double* __restrict__ G, int d, d
   int attempt = force_shift ? 1 : 0;
   for (; attempt < 2; ++attempt) {
     __syncthreads();
-    const double add = attempt ? s_shift : 0.0;
-    // upper block triangle of G + shift I (identity padding), eight
-    // independent loads in flight per thread
-    for (int e0 = tid; e0 < ntiles * TB * TB; e0 += 8 * NTH) {
-      double x[8];
+    const float add = attempt ? s_shift : 0.f;
+    // upper block triangle of G + shift I (identity padding): one warp per
+    // tile, lane = column, all 32 row loads issued before the stores
+    for (int t = warp; t < ntiles; t += nw) {
+      int I = 0, tt = t;
+      while (tt >= nb - I) { tt -= nb - I; ++I; }
+      const int J = I + tt;
+      const int j = J * TB + lane;
+      float v[TB];
 #pragma unroll
-      for (int u = 0; u < 8; ++u) {
-        const int e = e0 + u * NTH;
-        x[u] = 0.0;
-        if (e < ntiles * TB * TB) {
-          const int t = e >> 10, r = (e >> 5) & 31, c = e & 31;
-          int I = 0, tt = t;
-          while (tt >= nb - I) { tt -= nb - I; ++I; }
-          const int i = I * TB + r, j = (I + tt) * TB + c;
-          if (i < d && j < d) x[u] = G[(size_t)i * d + j];
-        }
+      for (int r = 0; r < TB; ++r) {
+        const int i = I * TB + r;
+        v[r] = (i < d && j < d) ? G[(size_t)i * d + j] : 0.f;
       }
+      float* T = tile(I, J);
 #pragma unroll
-      for (int u = 0; u < 8; ++u) {
-        const int e = e0 + u * NTH;
-        if (e < ntiles * TB * TB) {
-          const int t = e >> 10, r = (e >> 5) & 31, c = e & 31;
-          int I = 0, tt = t;
-          while (tt >= nb - I) { tt -= nb - I; ++I; }
-          const int i = I * TB + r, j = (I + tt) * TB + c;
-          double v = x[u];
-          if (i == j) v = (i < d) ? v + add : 1.0;
-          sm[(size_t)t * TILE_FLOATS + r * TP + c] = (float)v;
-        }
+      for (int r = 0; r < TB; ++r) {
+        const int i = I * TB + r;
+        T[r * TP + lane] = (i == j) ? ((i < d) ? v[r] + add : 1.f) : v[r];
       }
     }
     if (tid == 0) s_bad = 0;
     __syncthreads();
     for (int K = 0; K < nb; ++K) {
       if (warp == 0) {  // (a) diagonal tile, its inverse (kept in shared memory)
-        const bool ok = factor_tile(tile(K, K), dinv_s(K), s_dinv, s_row, lane,
+        const bool ok = factor_tile(tile(K, K), dinv_sm, s_dinv, s_row, lane,
                                     attempt == 0 ? 1.f : (float)s_shift);
+        __syncwarp();
+        float* gi = tiles + (size_t)(ntiles + K) * TB * TB;
+#pragma unroll 8
+        for (int r = 0; r < TB; ++r) gi[r * TB + lane] = dinv_sm[r * TP + lane];
         if (lane == 0 && !ok) {
           if (attempt == 0) s_bad = 1;  // retry on G + shift I
           else s_rankdef = 1;           // pivots replaced by the shift
@@ -218,7 +216,7 @@ __device__ __forceinline__ void chol_body(const double* __restrict__ G, int d, d
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
           float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-          tile_tn8(dinv_s(K), q * 8, bc, acc);
+          tile_tn8(dinv_sm, q * 8, bc, acc);
 #pragma unroll
           for (int i = 0; i < 8; ++i) B[(q * 8 + i) * TP + lane] = acc[i];
         }
@@ -245,8 +243,8 @@ __device__ __forceinline__ void chol_body(const double* __restrict__ G, int d, d
     if (!s_bad) break;
   }
   __syncthreads();
-  // write R tiles and the diagonal-tile inverses (32 x 32 row-major each)
-  for (int t = warp; t < ntiles + nb; t += nw) {
+  // write the R tiles (32 x 32 row-major each; the inverses are out already)
+  for (int t = warp; t < ntiles; t += nw) {
     const float* src = sm + (size_t)t * TILE_FLOATS;
     float* dst = tiles + (size_t)t * TB * TB;
 #pragma unroll 8
@@ -262,7 +260,7 @@ __device__ __forceinline__ void chol_body(const double* __restrict__ G, int d, d
 }
 
 __global__ void __launch_bounds__(NTH)
-k_chol_tiles(const double* __restrict__ G, int d, double shift_rel, int force_shift,
+k_chol_tiles(const float* __restrict__ G, int d, double shift_rel, int force_shift,
              float* __restrict__ tiles, DevStatus* __restrict__ status,
              const int32_t* __restrict__ gate) {
   if (gate != nullptr && *gate == 0) return;
@@ -273,39 +271,43 @@ k_chol_tiles(const double* __restrict__ G, int d, double shift_rel, int force_sh
 __global__ void __launch_bounds__(NTH)
 k_bchol(const BMat* __restrict__ T, double shift_rel, int force_shift) {
   const BMat& b = T[blockIdx.x];
-  chol_body(b.G, b.d, shift_rel, force_shift, b.tiles, b.status);
+  chol_body(b.Gf, b.d, shift_rel, force_shift, b.tiles, b.status);
 }
 
 // X = Y R^{-1} by blocked forward substitution over 32-column tiles:
 //   X_J = (Y_J - sum_{K<J} X_K R_KJ) R_JJ^{-1}.
-// A CTA owns 32 rows, staged in shared memory (so X may alias Y).  R tiles
-// and diagonal-tile inverses come from k_chol_tiles' packed layout; they are
-// fetched with cp.async NPF tiles ahead of their use (L2 latency is long).
-constexpr int SR = 32;
-constexpr int NPF = 4;  // tile buffers (prefetch distance NPF - 1)
+// A CTA of 64 threads owns 32 rows, staged TRANSPOSED in shared memory
+// (ys[c][r], so X may alias Y); thread (rg, cg) keeps a 4 x 4 block (rows
+// 4rg.., columns 4cg.. of the current tile) in registers, and every step of a
+// tile product is two 128-bit loads (4 rows of X, 4 columns of R) for 16
+// multiply-adds.  R tiles and diagonal-tile inverses come from k_chol_tiles'
+// packed layout and are fetched with cp.async NPF - 1 tiles ahead.
+constexpr int SR = 32;        // rows per CTA
+constexpr int TT = 64;        // threads per CTA
+constexpr int YP = SR + 4;    // pitch of a transposed column (16-byte aligned)
+constexpr int NPF = 3;        // tile buffers (prefetch distance NPF - 1)
 __device__ __forceinline__ void trsm_body(const float* __restrict__ Y, int64_t ldy,
                                           const float* __restrict__ tiles, float* X, int64_t ldx,
                                           int64_t M, int d, int rb) {
-  extern __shared__ __align__(16) float ys[];  // SR x pitch
+  extern __shared__ __align__(16) float ys[];  // (nb * 32) x YP, ys[c * YP + r]
   __shared__ __align__(16) float Rt[NPF][TB][TB];
   const int nb = (d + TB - 1) / TB;
   const int ntiles = nb * (nb + 1) / 2;
-  const int pitch = nb * TB + 4;
   const int64_t r0 = (int64_t)rb * SR;
   const int nr = (int)min((int64_t)SR, M - r0);
   const int t = threadIdx.x;
-  // stage the rows (float4 when the row pitch allows it)
-  const int nv = nb * TB / 4;  // float4s per padded row
+  const int nv = nb * TB / 4;  // 4-column groups per padded row
   const bool vec = (ldy % 4 == 0) && (((uintptr_t)Y & 15) == 0);
-  // loads are issued in batches of 8 before their stores, so 8 are in flight
-  for (int e0 = t; e0 < SR * nv; e0 += 8 * 128) {
+  // stage: item e -> row e % SR, column group e / SR (a warp takes one group
+  // of 32 rows, so the transposed stores hit 32 banks); 8 loads in flight
+  for (int e0 = t; e0 < SR * nv; e0 += 8 * TT) {
     float4 v[8];
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
-      const int e = e0 + q * 128;
+      const int e = e0 + q * TT;
       v[q] = make_float4(0.f, 0.f, 0.f, 0.f);
       if (e < SR * nv) {
-        const int r = e / nv, c = (e % nv) * 4;
+        const int r = e % SR, c = (e / SR) * 4;
         if (r < nr) {
           const float* p = Y + (r0 + r) * ldy + c;
           if (vec && c + 3 < d) v[q] = *reinterpret_cast<const float4*>(p);
@@ -320,10 +322,13 @@ __device__ __forceinline__ void trsm_body(const float* __restrict__ Y, int64_t l
     }
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
-      const int e = e0 + q * 128;
+      const int e = e0 + q * TT;
       if (e < SR * nv) {
-        const int r = e / nv, c = (e % nv) * 4;
-        *reinterpret_cast<float4*>(ys + r * pitch + c) = v[q];
+        const int r = e % SR, c = (e / SR) * 4;
+        ys[(c + 0) * YP + r] = v[q].x;
+        ys[(c + 1) * YP + r] = v[q].y;
+        ys[(c + 2) * YP + r] = v[q].z;
+        ys[(c + 3) * YP + r] = v[q].w;
       }
     }
   }
@@ -332,18 +337,16 @@ __device__ __forceinline__ void trsm_body(const float* __restrict__ Y, int64_t l
     return (K < J) ? tiles + (size_t)bidx(K, J, nb) * TB * TB
                    : tiles + (size_t)(ntiles + J) * TB * TB;
   };
-  // asynchronous copy of one 4 KB tile (2 x 16 bytes per thread)
+  // asynchronous copy of one 4 KB tile (4 x 16 bytes per thread)
   auto fetch = [&](int b, const float* src) {
-    for (int e = t; e < TB * TB / 4; e += 128) {
+    for (int e = t; e < TB * TB / 4; e += TT) {
       const uint32_t dst = (uint32_t)__cvta_generic_to_shared(&Rt[b][0][0] + 4 * e);
       asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src + 4 * e)
                    : "memory");
     }
   };
-  const int row = t >> 2, c0 = (t & 3) * 8;
-  float* yr = ys + row * pitch;
+  const int rg = t & 7, cg = t >> 3;  // rows 4rg..4rg+3, tile columns 4cg..4cg+3
   // the tile sequence is (J=0: inv00), (J=1: R01, inv11), (J=2: R02, R12, inv22) ...
-  // step s -> (J, K) with K <= J; total nb (nb + 1) / 2 steps
   const int nsteps = nb * (nb + 1) / 2;
   auto step_tile = [&](int sidx) {
     int J = 0;
@@ -354,20 +357,28 @@ __device__ __forceinline__ void trsm_body(const float* __restrict__ Y, int64_t l
     if (q < nsteps) fetch(q % NPF, step_tile(q));
     asm volatile("cp.async.commit_group;" ::: "memory");
   }
+  auto col4 = [&](int c) { return reinterpret_cast<float4*>(ys + c * YP + rg * 4); };
   int sidx = 0;
   for (int J = 0; J < nb; ++J) {
-    float acc[8];
+    float acc[4][4];
     __syncthreads();
 #pragma unroll
-    for (int i = 0; i < 8; ++i) acc[i] = yr[J * TB + c0 + i];
+    for (int j = 0; j < 4; ++j) {
+      const float4 v = *col4(J * TB + cg * 4 + j);
+      acc[0][j] = v.x;
+      acc[1][j] = v.y;
+      acc[2][j] = v.z;
+      acc[3][j] = v.w;
+    }
     for (int K = 0; K <= J; ++K, ++sidx) {
       __syncthreads();  // everyone is done with the buffer about to be refilled
       if (sidx + NPF - 1 < nsteps) fetch((sidx + NPF - 1) % NPF, step_tile(sidx + NPF - 1));
       asm volatile("cp.async.commit_group;" ::: "memory");
       if (K == J) {
-        // stage the updated tile of this row, then multiply by R_JJ^{-1}
+        // stage the updated tile of this row block, then multiply by R_JJ^{-1}
 #pragma unroll
-        for (int i = 0; i < 8; ++i) yr[J * TB + c0 + i] = acc[i];
+        for (int j = 0; j < 4; ++j)
+          *col4(J * TB + cg * 4 + j) = make_float4(acc[0][j], acc[1][j], acc[2][j], acc[3][j]);
       }
       asm volatile("cp.async.wait_group %0;" ::"n"(NPF - 1) : "memory");  // step's tile landed
       __syncthreads();
@@ -375,47 +386,45 @@ __device__ __forceinline__ void trsm_body(const float* __restrict__ Y, int64_t l
       if (K < J) {
 #pragma unroll 8
         for (int k = 0; k < TB; ++k) {
-          const float x = yr[K * TB + k];
-          const float4 a0 = *reinterpret_cast<const float4*>(R + k * TB + c0);
-          const float4 a1 = *reinterpret_cast<const float4*>(R + k * TB + c0 + 4);
-          acc[0] = fmaf(-x, a0.x, acc[0]);
-          acc[1] = fmaf(-x, a0.y, acc[1]);
-          acc[2] = fmaf(-x, a0.z, acc[2]);
-          acc[3] = fmaf(-x, a0.w, acc[3]);
-          acc[4] = fmaf(-x, a1.x, acc[4]);
-          acc[5] = fmaf(-x, a1.y, acc[5]);
-          acc[6] = fmaf(-x, a1.z, acc[6]);
-          acc[7] = fmaf(-x, a1.w, acc[7]);
+          const float4 y = *col4(K * TB + k);
+          const float4 r = *reinterpret_cast<const float4*>(R + k * TB + cg * 4);
+          const float yv[4] = {y.x, y.y, y.z, y.w}, rv[4] = {r.x, r.y, r.z, r.w};
+#pragma unroll
+          for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(-yv[i], rv[j], acc[i][j]);
         }
       } else {
-        float out[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        float out[4][4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) out[i][j] = 0.f;
 #pragma unroll 8
         for (int k = 0; k < TB; ++k) {
-          const float x = yr[J * TB + k];
-          const float4 a0 = *reinterpret_cast<const float4*>(R + k * TB + c0);
-          const float4 a1 = *reinterpret_cast<const float4*>(R + k * TB + c0 + 4);
-          out[0] = fmaf(x, a0.x, out[0]);
-          out[1] = fmaf(x, a0.y, out[1]);
-          out[2] = fmaf(x, a0.z, out[2]);
-          out[3] = fmaf(x, a0.w, out[3]);
-          out[4] = fmaf(x, a1.x, out[4]);
-          out[5] = fmaf(x, a1.y, out[5]);
-          out[6] = fmaf(x, a1.z, out[6]);
-          out[7] = fmaf(x, a1.w, out[7]);
+          const float4 y = *col4(J * TB + k);
+          const float4 r = *reinterpret_cast<const float4*>(R + k * TB + cg * 4);
+          const float yv[4] = {y.x, y.y, y.z, y.w}, rv[4] = {r.x, r.y, r.z, r.w};
+#pragma unroll
+          for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) out[i][j] = fmaf(yv[i], rv[j], out[i][j]);
         }
         __syncthreads();
 #pragma unroll
-        for (int i = 0; i < 8; ++i) yr[J * TB + c0 + i] = out[i];
+        for (int j = 0; j < 4; ++j)
+          *col4(J * TB + cg * 4 + j) = make_float4(out[0][j], out[1][j], out[2][j], out[3][j]);
       }
     }
   }
   asm volatile("cp.async.wait_group 0;" ::: "memory");
   __syncthreads();
   const bool vecx = (ldx % 4 == 0) && (((uintptr_t)X & 15) == 0);
-  for (int e = t; e < SR * nv; e += 128) {
-    const int r = e / nv, c = (e % nv) * 4;
+  for (int e = t; e < SR * nv; e += TT) {
+    const int r = e % SR, c = (e / SR) * 4;
     if (r >= nr || c >= d) continue;
-    const float4 v = *reinterpret_cast<const float4*>(ys + r * pitch + c);
+    const float4 v = make_float4(ys[c * YP + r], ys[(c + 1) * YP + r], ys[(c + 2) * YP + r],
+                                 ys[(c + 3) * YP + r]);
     float* p = X + (r0 + r) * ldx + c;
     if (vecx && c + 3 < d) *reinterpret_cast<float4*>(p) = v;
     else {
@@ -427,14 +436,14 @@ __device__ __forceinline__ void trsm_body(const float* __restrict__ Y, int64_t l
   }
 }
 
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(TT)
 k_trsm_tiles(const float* __restrict__ Y, int64_t ldy, const float* __restrict__ tiles, float* X,
              int64_t ldx, int64_t M, int d) {
   trsm_body(Y, ldy, tiles, X, ldx, M, d, blockIdx.x);
 }
 
 // Batched: block t -> (matrix, 32-row block); M = rows of buf[src].
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(TT)
 k_btrsm(const BMat* __restrict__ T, const int* __restrict__ prefix, int count, int src, int dst) {
   const int t = blockIdx.x;
   int lo = 0, hi = count;
@@ -468,18 +477,18 @@ cudaError_t btrsm(const BMat* T, const int* prefix, int total, int count, int sr
                   int dmax, cudaStream_t st) {
   if (total <= 0) return cudaSuccess;
   const int nb = (dmax + TB - 1) / TB;
-  const size_t sm = (size_t)SR * (nb * TB + 4) * sizeof(float);
+  const size_t sm = (size_t)nb * TB * YP * sizeof(float);
   cudaError_t e =
       cudaFuncSetAttribute(k_btrsm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
-  k_btrsm<<<total, 128, sm, st>>>(T, prefix, count, src, dst);
+  k_btrsm<<<total, TT, sm, st>>>(T, prefix, count, src, dst);
   count_launch();
   return cudaGetLastError();
 }
 
 size_t chol_tiles_smem(int d) {
   const int nb = (d + TB - 1) / TB;
-  return ((size_t)nb * (nb + 1) / 2 + nb) * TILE_FLOATS * sizeof(float);
+  return ((size_t)nb * (nb + 1) / 2 + 1) * TILE_FLOATS * sizeof(float);
 }
 
 bool chol_tiles_supported(int d) {
@@ -491,7 +500,7 @@ size_t chol_tiles_bytes(int d) {
   return ((size_t)nb * (nb + 1) / 2 + nb) * TB * TB * sizeof(float);
 }
 
-cudaError_t chol_tiles_f32(const double* G, int d, double shift_rel, bool force_shift,
+cudaError_t chol_tiles_f32(const float* G, int d, double shift_rel, bool force_shift,
                            float* tiles, DevStatus* status, const int32_t* gate, cudaStream_t st) {
   if (!chol_tiles_supported(d)) return cudaErrorInvalidValue;
   const size_t sm = chol_tiles_smem(d);
@@ -507,11 +516,11 @@ cudaError_t trsm_tiles_f32(const float* Y, int64_t ldy, const float* tiles, floa
                            int64_t M, int d, cudaStream_t st) {
   if (M <= 0) return cudaSuccess;
   const int nb = (d + TB - 1) / TB;
-  const size_t sm = (size_t)SR * (nb * TB + 4) * sizeof(float);
+  const size_t sm = (size_t)nb * TB * YP * sizeof(float);
   cudaError_t e =
       cudaFuncSetAttribute(k_trsm_tiles, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
-  k_trsm_tiles<<<ceil_div(M, SR), 128, sm, st>>>(Y, ldy, tiles, X, ldx, M, d);
+  k_trsm_tiles<<<ceil_div(M, SR), TT, sm, st>>>(Y, ldy, tiles, X, ldx, M, d);
   count_launch();
   return cudaGetLastError();
 }

@@ -146,13 +146,16 @@ __device__ __forceinline__ double slab_sum(const double* __restrict__ P, int sla
 // C[i][j] = sum over slabs of the partials (slab order); with sym the entry
 // is taken from the computed upper triangle.
 __global__ void k_gram_reduce(const double* __restrict__ P, int slabs, int d1, int d2, bool sym,
-                              double* __restrict__ C, const int32_t* __restrict__ gate) {
+                              double* __restrict__ C, float* __restrict__ Cf,
+                              const int32_t* __restrict__ gate) {
   if (gate != nullptr && *gate == 0) return;
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= (int64_t)d1 * d2) return;
   int i = (int)(idx / d2), j = (int)(idx % d2);
   const int64_t src = (sym && j < i) ? ((int64_t)j * d2 + i) : idx;
-  C[idx] = slab_sum(P, slabs, (int64_t)d1 * d2, src);
+  const double s = slab_sum(P, slabs, (int64_t)d1 * d2, src);
+  C[idx] = s;
+  if (Cf != nullptr) Cf[idx] = (float)s;
 }
 
 // Batched Grams: tile t of the launch -> (matrix, tile, slab) through prefix;
@@ -189,7 +192,9 @@ __global__ void k_bgram_reduce(const BMat* __restrict__ Tb, int src, int src2, i
   const int slabs = (int)gram_slabs(M, max_slabs, &slab);
   const int i = (int)(idx / d), j = (int)(idx % d);
   const int64_t so = (sym && j < i) ? ((int64_t)j * d + i) : idx;
-  b.G[idx] = slab_sum(b.partial, slabs, (int64_t)d * d, so);
+  const double s = slab_sum(b.partial, slabs, (int64_t)d * d, so);
+  b.G[idx] = s;
+  b.Gf[idx] = (float)s;
 }
 
 }  // namespace
@@ -215,7 +220,7 @@ cudaError_t bgram(const BMat* T, const int* prefix, int total, int count, int sr
 
 cudaError_t gram_f32(const float* X, int64_t ldx, const float* W, int64_t ldw, int64_t M, int d1,
                      int d2, double* C, double* partial, int max_slabs, const int32_t* gate,
-                     cudaStream_t st) {
+                     cudaStream_t st, float* Cf) {
   if (M <= 0 || d1 <= 0 || d2 <= 0) return cudaSuccess;
   const bool sym = (X == W) && (ldx == ldw) && (d1 == d2);
   const int nb1 = (d1 + TM - 1) / TM, nb2 = (d2 + TM - 1) / TM;
@@ -229,7 +234,7 @@ cudaError_t gram_f32(const float* X, int64_t ldx, const float* W, int64_t ldw, i
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const int64_t tot = (int64_t)d1 * d2;
-  k_gram_reduce<<<ceil_div(tot, 256), 256, 0, st>>>(partial, (int)slabs, d1, d2, sym, C, gate);
+  k_gram_reduce<<<ceil_div(tot, 256), 256, 0, st>>>(partial, (int)slabs, d1, d2, sym, C, Cf, gate);
   count_launch();
   return cudaGetLastError();
 }

@@ -13,50 +13,10 @@
 #include <string>
 
 #include "../../include/ruqlp.h"
+#include "ctx.h"
 #include "internal.h"
 
 using namespace ruqlp;
-
-struct ruqlp_ctx {
-  int device = 0;
-  cudaStream_t stream = nullptr;
-  size_t budget = 0;
-  int max_slots = 8;
-  void* arena = nullptr;
-  size_t arena_bytes = 0;
-  DevStatus* status = nullptr;       // device
-  DevStatus* status_host = nullptr;  // pinned host
-  std::string err;
-  // policy knobs (ruqlp_set_option)
-  int orth_fp64 = 0;    // FP32/BF16 paths: CholeskyQR2 with FP64 Gram and Cholesky
-  int orth_full = 0;    // 1: every orth() takes three CholeskyQR passes (else the
-                        // intermediate ones take two)
-  int bf16_simt = 0;    // 1: BF16 products on CUDA cores instead of tensor cores
-  // phase timing with CUDA events on the handle's stream (option "profile")
-  bool profile = false;
-  struct Span { int cat; cudaEvent_t a, b; };
-  std::vector<Span> spans;
-  std::vector<cudaEvent_t> pool;
-  // batched decompositions, per batch signature (shapes, q, dtype, product
-  // kernels, arena address): the captured launch sequence and the host image
-  // of the tensor maps
-  struct BatchEntry {
-    std::vector<int64_t> key;
-    cudaGraphExec_t exec = nullptr;
-    int seen = 0;
-    int64_t launches = 0;           // kernels in the captured graph
-    std::vector<uint8_t> maps;      // 3 tensor maps per matrix
-    std::vector<const void*> aptr;  // A each A map was encoded for
-    std::vector<int64_t> alda;
-  };
-  std::vector<BatchEntry> batches;
-  void* stage = nullptr;  // pinned staging of the batch metadata
-  size_t stage_bytes = 0;
-  int batch_graphs = 1;  // option "batch_graph"
-  cudaStream_t cap_stream = nullptr;  // capture stream (the legacy stream cannot capture)
-  int64_t prof_count[6] = {0, 0, 0, 0, 0, 0};
-  double prof_ms[6] = {0, 0, 0, 0, 0, 0};
-};
 
 namespace ruqlp {
 static std::atomic<int64_t> g_launches{0};
@@ -156,7 +116,7 @@ constexpr int kMaxSplits = 64;
 
 // Workspace layout for one problem.
 struct Layout {
-  size_t X, Y, Z, P, partial, G, R, Rw, Bt, frag, colptr, rowidx, cvals, cscratch, T, total;
+  size_t X, Y, Z, P, partial, G, Gf, R, Rw, Bt, frag, colptr, rowidx, cvals, cscratch, T, total;
 };
 
 inline int64_t round8(int64_t x) { return (x + 7) / 8 * 8; }
@@ -180,6 +140,7 @@ Layout layout_of(int64_t m, int64_t n, int d, Ty ct, int64_t nnz = -1, size_t va
   L.P = take((size_t)n * dp * wes);
   L.partial = take((size_t)kMaxSplits * d * d * sizeof(double));
   L.G = take((size_t)d * d * sizeof(double));
+  L.Gf = take((size_t)d * d * sizeof(float));
   L.R = take((size_t)d * d * sizeof(double));
   {
     size_t rw = (size_t)d * d * sizeof(double);
@@ -188,7 +149,7 @@ Layout layout_of(int64_t m, int64_t n, int d, Ty ct, int64_t nnz = -1, size_t va
   }
   if (ct == Ty::BF16 && nnz < 0) {
     L.Bt = take((size_t)dp * round8(m > n ? m : n) * 2);
-    L.frag = take(dp <= 256 ? tc_frag_bytes(dp) : 0);
+    L.frag = take(tc_frag_bytes(dp <= 256 ? dp : 256));  // per column chunk
   }
   if (finish) L.T = take((size_t)m * dp * wes);
   if (nnz >= 0) {
@@ -315,6 +276,7 @@ ruqlp_status orth(ruqlp_ctx* h, const Layout& Lo, const Job& J, const void* Yin,
   char* base = (char*)h->arena;
   double* partial = (double*)(base + Lo.partial);
   double* G = (double*)(base + Lo.G);
+  float* Gf = (float*)(base + Lo.Gf);
   double* R = (double*)(base + Lo.R);
   void* Rw = base + Lo.Rw;
   const int d = J.d, dp = J.dp;
@@ -327,9 +289,9 @@ ruqlp_status orth(ruqlp_ctx* h, const Layout& Lo, const Job& J, const void* Yin,
     const int passes = (final_basis || h->orth_full) ? 3 : 2;
     for (int pass = 0; pass < passes; ++pass) {
       const float* src = (const float*)(pass == 0 ? Yin : Qout);
-      CK(gram_f32(src, dp, src, dp, M, d, d, G, partial, kMaxSplits, nullptr, st));
+      CK(gram_f32(src, dp, src, dp, M, d, d, G, partial, kMaxSplits, nullptr, st, Gf));
       if (blocked) {
-        CK(chol_tiles_f32(G, d, s1, pass == 0, (float*)Rw, h->status, nullptr, st));
+        CK(chol_tiles_f32(Gf, d, s1, pass == 0, (float*)Rw, h->status, nullptr, st));
         CK(trsm_tiles_f32(src, dp, (const float*)Rw, (float*)Qout, dp, M, d, st));
       } else {
         CK(chol_upper(G, d, s1, R, Rw, Ty::F32, h->status, nullptr, st, Ty::F32, pass == 0));
@@ -380,20 +342,30 @@ ruqlp_status product(ruqlp_ctx* h, const Layout& Lo, const Job& J, bool trans, T
     return RUQLP_OK;
   }
   if (J.use_tc) {
+    // the MMA's N is at most 256: wider sketches run as column chunks of
+    // equal width (multiples of 16), each one pass over A
     void* Bt = base + Lo.Bt;
     const int64_t ldb = round8(K);
-    CK(transpose_to_bf16(xt, Xin, ldx, K, J.d, J.dp, Bt, ldb, st));
-    CK(tc_gemm(trans, J.A, J.lda, J.m, J.n, Bt, ldb, J.dp, (float*)out, J.dp,
-               (float*)(base + Lo.frag), &h->status->timeout, st,
-               h->profile ? [&](bool begin) {
-                 static thread_local cudaEvent_t a;
-                 if (begin) { a = ev_get(h); cudaEventRecord(a, st); }
-                 else {
-                   cudaEvent_t b = ev_get(h);
-                   cudaEventRecord(b, st);
-                   h->spans.push_back({trans ? PROF_TC_ATX : PROF_TC_AX, a, b});
-                 }
-               } : std::function<void(bool)>()));
+    const int nch = (J.dp + 255) / 256;
+    const int w = round16((J.dp + nch - 1) / nch);
+    const size_t xes = ty_size(xt);
+    for (int c0 = 0; c0 < J.dp; c0 += w) {
+      const int wc = std::min(w, J.dp - c0);
+      const int cols = std::max(0, std::min(J.d - c0, wc));
+      CK(transpose_to_bf16(xt, (const char*)Xin + (size_t)c0 * xes, ldx, K, cols, wc, Bt, ldb,
+                           st));
+      CK(tc_gemm(trans, J.A, J.lda, J.m, J.n, Bt, ldb, wc, (float*)out + c0, J.dp,
+                 (float*)(base + Lo.frag), &h->status->timeout, st,
+                 h->profile ? [&](bool begin) {
+                   static thread_local cudaEvent_t a;
+                   if (begin) { a = ev_get(h); cudaEventRecord(a, st); }
+                   else {
+                     cudaEvent_t b = ev_get(h);
+                     cudaEventRecord(b, st);
+                     h->spans.push_back({trans ? PROF_TC_ATX : PROF_TC_AX, a, b});
+                   }
+                 } : std::function<void(bool)>()));
+    }
     return RUQLP_OK;
   }
   const Mul mul = (J.ct == Ty::F64) ? Mul::F64 : Mul::F32;
@@ -579,6 +551,77 @@ ruqlp_status finish(ruqlp_ctx* h, ruqlp_outputs* out) {
 }  // namespace
 
 
+namespace ruqlp {
+
+ruqlp_status single_begin(ruqlp_ctx* h, const ruqlp_matrix* A, const ruqlp_params* prm,
+                          const ruqlp_outputs* out) {
+  int64_t m, n;
+  int d;
+  ruqlp_status s = validate(h, A, prm, out, &m, &n, &d);
+  if (s != RUQLP_OK) return s;
+  CK(cudaSetDevice(h->device));
+  Job J{};
+  fill_job(A, prm, out, m, n, d, J);
+  J.Qout = out->Q;
+  J.Lout = out->L;
+  J.Pout = out->P;
+  J.use_tc = !J.csr && J.ct == Ty::BF16 && !h->bf16_simt &&
+             tc_supported(J.A, J.lda, std::min(J.dp, 256));
+  return run_dense(h, J);
+}
+
+ruqlp_status single_end(ruqlp_ctx* h, ruqlp_outputs* out) { return finish(h, out); }
+
+ruqlp_status check_request(ruqlp_ctx* h, const ruqlp_matrix* A, const ruqlp_params* prm,
+                           const ruqlp_outputs* out, int* d) {
+  int64_t m, n;
+  return validate(h, A, prm, out, &m, &n, d);
+}
+
+size_t single_bytes(const ruqlp_matrix* A, const ruqlp_params* prm) {
+  Ty ct;
+  if (!ty_of(prm->compute, &ct)) return 0;
+  const int d = prm->k + prm->p;
+  if (A->is_csr) {
+    Ty tv;
+    if (!ty_of(A->csr.dtype, &tv)) return 0;
+    return layout_of(A->csr.m, A->csr.n, d, ct, A->csr.nnz, ty_size(tv), prm->finish_paper != 0)
+        .total;
+  }
+  return layout_of(A->dense.m, A->dense.n, d, ct, -1, 0, prm->finish_paper != 0).total;
+}
+
+size_t batch_item_bytes(const ruqlp_matrix* A, const ruqlp_params* prm) {
+  const int64_t m = A->dense.m, n = A->dense.n;
+  const int d = prm->k + prm->p, dp = round16(d);
+  int64_t slab;
+  const int64_t sl = std::max(gram_slabs(m, kMaxSplits, &slab), gram_slabs(n, kMaxSplits, &slab));
+  const size_t per = (size_t)(3 * n + m) * dp * 4 + (size_t)sl * d * d * 8 + (size_t)d * d * 12 +
+                     chol_tiles_bytes(d) + (size_t)dp * std::max(m, n) * 2 + 8 * 256;
+  // plus its share of the metadata (table entry, prefixes, tile lists, maps)
+  return per + 4096 + (size_t)(ceil_div(m, 128) + ceil_div(n, 128)) * 8;
+}
+
+bool batchable(const ruqlp_matrix* A, const ruqlp_params* prm) {
+  Ty ct;
+  const int d = prm->k + prm->p;
+  return !A->is_csr && ty_of(prm->compute, &ct) && ct != Ty::F64 && !prm->finish_paper &&
+         round16(d) <= 256 && chol_tiles_supported(d) &&
+         A->dense.m * A->dense.n <= ((int64_t)1 << 25);
+}
+
+void copy_options(const ruqlp_ctx* from, ruqlp_ctx* to) {
+  to->orth_fp64 = from->orth_fp64;
+  to->orth_full = from->orth_full;
+  to->bf16_simt = from->bf16_simt;
+}
+
+ruqlp_status set_error(ruqlp_ctx* h, ruqlp_status s, const char* msg) {
+  return fail(h, s, "%s", msg);
+}
+
+}  // namespace ruqlp
+
 // ---------------------------------------------------------------------------
 // Batched decompositions (many dense matrices of uneven shapes, FP32 or BF16,
 // one q): every phase is one launch over a device problem table (BMat); the
@@ -679,10 +722,10 @@ void tc_list(const std::vector<BMat>& table, bool trans, std::vector<BTcTile>& o
 
 }  // namespace
 
-extern "C" ruqlp_status ruqlp_decompose_batch(ruqlp_handle h, int count, const ruqlp_matrix* A,
-                                              const ruqlp_params* prm, ruqlp_outputs* out) {
-  if (!h) return RUQLP_ERR_INVALID;
-  h->err.clear();
+namespace ruqlp {
+
+ruqlp_status batch_begin(ruqlp_ctx* h, int count, const ruqlp_matrix* A, const ruqlp_params* prm,
+                         const ruqlp_outputs* out, bool graphs_ok, BatchRun* run) {
   if (count < 1 || !A || !prm || !out) return fail(h, RUQLP_ERR_INVALID, "empty or NULL batch");
   Ty ct0 = Ty::F32;
   int q0 = 0;
@@ -702,7 +745,7 @@ extern "C" ruqlp_status ruqlp_decompose_batch(ruqlp_handle h, int count, const r
       return fail(h, RUQLP_ERR_INVALID, "all items of a batch need the same dtype and q");
     }
     if (prm[i].finish_paper) return fail(h, RUQLP_ERR_INVALID, "finish_paper is not batched");
-    if (!chol_tiles_supported(dd[i])) return fail(h, RUQLP_ERR_INVALID, "batched d must be <= 256");
+    if (!chol_tiles_supported(dd[i])) return fail(h, RUQLP_ERR_INVALID, "batched d must be <= 288");
   }
   CK(cudaSetDevice(h->device));
   // workspace: per-matrix buffers; the metadata block (table, prefix arrays,
@@ -720,7 +763,7 @@ extern "C" ruqlp_status ruqlp_decompose_batch(ruqlp_handle h, int count, const r
     return o;
   };
   std::vector<size_t> oX(count), oY(count), oZ(count), oP(count), oPa(count), oG(count),
-      oT(count), oB(count);
+      oT(count), oB(count), oGf(count);
   for (int i = 0; i < count; ++i) {
     const ruqlp_dense& D = A[i].dense;
     const int64_t m = D.m, n = D.n;
@@ -736,6 +779,7 @@ extern "C" ruqlp_status ruqlp_decompose_batch(ruqlp_handle h, int count, const r
     oP[i] = take((size_t)n * dp * 4);
     oPa[i] = take((size_t)sl * d * d * 8);
     oG[i] = take((size_t)d * d * 8);
+    oGf[i] = take((size_t)d * d * 4);
     oT[i] = take(chol_tiles_bytes(d));
     oB[i] = b.use_tc ? take((size_t)dp * b.ldbt * 2) : 0;
     bp.dmax = std::max(bp.dmax, d);
@@ -783,6 +827,7 @@ extern "C" ruqlp_status ruqlp_decompose_batch(ruqlp_handle h, int count, const r
     b.P = (float*)(base + oP[i]);
     b.partial = (double*)(base + oPa[i]);
     b.G = (double*)(base + oG[i]);
+    b.Gf = (float*)(base + oGf[i]);
     b.tiles = (float*)(base + oT[i]);
     b.Bt = b.use_tc ? (void*)(base + oB[i]) : nullptr;
     b.omega = prm[i].omega;
@@ -854,7 +899,7 @@ extern "C" ruqlp_status ruqlp_decompose_batch(ruqlp_handle h, int count, const r
   put(bp.off_maps, g->maps.data(), g->maps.size());
   cudaStream_t st = h->stream;
   CK(cudaMemcpyAsync(base + bp.off_meta, img, meta, cudaMemcpyHostToDevice, st));
-  const bool graphs = h->batch_graphs && !h->profile;  // profiling runs eagerly
+  const bool graphs = graphs_ok && h->batch_graphs && !h->profile;  // profiling runs eagerly
   if (graphs && g->exec) {
     CK(cudaGraphLaunch(g->exec, st));
     ruqlp::count_launch((int)g->launches);
@@ -882,16 +927,37 @@ extern "C" ruqlp_status ruqlp_decompose_batch(ruqlp_handle h, int count, const r
     if (s != RUQLP_OK) return s;
   }
   g->seen++;
-  std::vector<DevStatus> stat(count);
+  run->count = count;
+  run->off_status = bp.off_status;
+  run->off_err = bp.off_err;
+  return RUQLP_OK;
+}
+
+ruqlp_status batch_end(ruqlp_ctx* h, const BatchRun& run, ruqlp_outputs* out) {
+  char* base = (char*)h->arena;
+  cudaStream_t st = h->stream;
+  std::vector<DevStatus> stat(run.count);
   int derr = 0;
-  CK(cudaMemcpyAsync(stat.data(), base + bp.off_status, sizeof(DevStatus) * count,
+  CK(cudaMemcpyAsync(stat.data(), base + run.off_status, sizeof(DevStatus) * run.count,
                      cudaMemcpyDeviceToHost, st));
-  CK(cudaMemcpyAsync(&derr, base + bp.off_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(&derr, base + run.off_err, sizeof(int), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
   if (h->profile) prof_collect(h);
-  for (int i = 0; i < count; ++i) out[i].flags = (uint32_t)stat[i].flags;
+  for (int i = 0; i < run.count; ++i) out[i].flags = (uint32_t)stat[i].flags;
   if (derr) return fail(h, RUQLP_ERR_TIMEOUT, "a bounded device wait ran out in a batched product");
   return RUQLP_OK;
+}
+
+}  // namespace ruqlp
+
+extern "C" ruqlp_status ruqlp_decompose_batch(ruqlp_handle h, int count, const ruqlp_matrix* A,
+                                              const ruqlp_params* prm, ruqlp_outputs* out) {
+  if (!h) return RUQLP_ERR_INVALID;
+  h->err.clear();
+  BatchRun run;
+  ruqlp_status s = batch_begin(h, count, A, prm, out, true, &run);
+  if (s != RUQLP_OK) return s;
+  return batch_end(h, run, out);
 }
 
 extern "C" {
@@ -922,6 +988,7 @@ ruqlp_status ruqlp_create(ruqlp_handle* out, const ruqlp_config* cfg) {
 
 ruqlp_status ruqlp_destroy(ruqlp_handle h) {
   if (!h) return RUQLP_ERR_INVALID;
+  server_shutdown(h);
   cudaSetDevice(h->device);
   cudaStreamSynchronize(h->stream);
   for (auto& g : h->batches)
@@ -992,20 +1059,9 @@ ruqlp_status ruqlp_decompose(ruqlp_handle h, const ruqlp_matrix* A, const ruqlp_
                              ruqlp_outputs* out) {
   if (!h) return RUQLP_ERR_INVALID;
   h->err.clear();
-  int64_t m, n;
-  int d;
-  ruqlp_status s = validate(h, A, prm, out, &m, &n, &d);
+  ruqlp_status s = single_begin(h, A, prm, out);
   if (s != RUQLP_OK) return s;
-  CK(cudaSetDevice(h->device));
-  Job J{};
-  fill_job(A, prm, out, m, n, d, J);
-  J.Qout = out->Q;
-  J.Lout = out->L;
-  J.Pout = out->P;
-  J.use_tc = !J.csr && J.ct == Ty::BF16 && !h->bf16_simt && tc_supported(J.A, J.lda, J.dp);
-  s = run_dense(h, J);
-  if (s != RUQLP_OK) return s;
-  return finish(h, out);
+  return single_end(h, out);
 }
 
 ruqlp_status ruqlp_decompose_host(ruqlp_handle h, const ruqlp_matrix* A,
@@ -1072,7 +1128,8 @@ ruqlp_status ruqlp_decompose_host(ruqlp_handle h, const ruqlp_matrix* A,
   J.Qout = base + oQ;
   J.Lout = base + oL;
   J.Pout = base + oP;
-  J.use_tc = !J.csr && J.ct == Ty::BF16 && !h->bf16_simt && tc_supported(J.A, J.lda, J.dp);
+  J.use_tc = !J.csr && J.ct == Ty::BF16 && !h->bf16_simt &&
+             tc_supported(J.A, J.lda, std::min(J.dp, 256));
   s = run_dense(h, J);
   if (s != RUQLP_OK) return s;
   CK(cudaMemcpyAsync(out->Q, base + oQ, (size_t)m * d * oes, cudaMemcpyDeviceToHost, st));
@@ -1111,7 +1168,8 @@ ruqlp_status ruqlp_sketch(ruqlp_handle h, const ruqlp_matrix* A, int trans, cons
   fill_job(A, &prm, &o, m, n, 1, J);
   J.d = d;
   J.dp = round16(d);
-  J.use_tc = !J.csr && J.ct == Ty::BF16 && !h->bf16_simt && tc_supported(J.A, J.lda, J.dp);
+  J.use_tc = !J.csr && J.ct == Ty::BF16 && !h->bf16_simt &&
+             tc_supported(J.A, J.lda, std::min(J.dp, 256));
   const int64_t Mout = trans ? n : m;
   const Layout Lo = J.csr ? layout_of(m, n, d, J.ct, J.nnz, ty_size(J.tv))
                           : layout_of(m, n, d, J.ct);

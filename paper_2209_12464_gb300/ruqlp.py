@@ -54,6 +54,11 @@ class Outputs(ctypes.Structure):
                 ("flags", ctypes.c_uint32)]
 
 
+class RequestTimes(ctypes.Structure):
+    _fields_ = [("submit_s", ctypes.c_double), ("start_s", ctypes.c_double),
+                ("done_s", ctypes.c_double)]
+
+
 _lib = None
 _lock = threading.Lock()
 
@@ -70,6 +75,10 @@ _SIGS = {
                                       ctypes.POINTER(Params), ctypes.POINTER(Outputs)]),
     "ruqlp_decompose_host": (c_int, [c_void_p, ctypes.POINTER(Matrix), ctypes.POINTER(Params),
                                      ctypes.POINTER(Outputs)]),
+    "ruqlp_submit": (c_int, [c_void_p, ctypes.POINTER(Matrix), ctypes.POINTER(Params),
+                             ctypes.POINTER(Outputs), ctypes.POINTER(ctypes.c_uint64)]),
+    "ruqlp_poll": (c_int, [c_void_p, ctypes.c_uint64]),
+    "ruqlp_poll_times": (c_int, [c_void_p, ctypes.c_uint64, ctypes.POINTER(RequestTimes)]),
     "ruqlp_last_error": (c_char_p, [c_void_p]),
     "ruqlp_launch_count": (c_int64, []),
     "ruqlp_sketch": (c_int, [c_void_p, ctypes.POINTER(Matrix), c_int, c_void_p, c_int64, c_int,
@@ -144,6 +153,24 @@ def ruqlp_decompose_batch(h, count, A, prm, out):
 
 def ruqlp_decompose_host(h, A, prm, out):
     return lib().ruqlp_decompose_host(h, ctypes.byref(A), ctypes.byref(prm), ctypes.byref(out))
+
+
+def ruqlp_submit(h, A, prm, out):
+    """A, prm, out: ctypes structs the caller keeps alive until the poll."""
+    t = ctypes.c_uint64()
+    st = lib().ruqlp_submit(h, ctypes.byref(A), ctypes.byref(prm), ctypes.byref(out),
+                            ctypes.byref(t))
+    return st, t.value
+
+
+def ruqlp_poll(h, ticket):
+    return lib().ruqlp_poll(h, ticket)
+
+
+def ruqlp_poll_times(h, ticket):
+    tm = RequestTimes()
+    st = lib().ruqlp_poll_times(h, ticket, ctypes.byref(tm))
+    return st, (tm.submit_s, tm.start_s, tm.done_s)
 
 
 def ruqlp_last_error(h):
@@ -228,6 +255,16 @@ class Batch:
         self.handle.check(ruqlp_decompose_batch(self.handle.h, self.count, self.M, self.P,
                                                 self.O))
         return [self.O[i].flags for i in range(self.count)]
+
+
+class Ticket:
+    """A submitted request: its ticket id, the ctypes structs and tensors the
+    library reads until completion, and the output tensors."""
+
+    def __init__(self, tid, M, P, O, keep, outs):
+        self.id, self.M, self.P, self.O, self.keep, self.outs = tid, M, P, O, keep, outs
+        self.flags = None
+        self.times = None
 
 
 class Handle:
@@ -332,6 +369,38 @@ class Handle:
         b = Batch(self, As, omegas, ks, p, q, out_dtype, ps, qs)
         flags = b.run()
         return [(Q, L, P, f) for (Q, L, P), f in zip(b.outs, flags)]
+
+    def submit(self, A, omega, k, p, q, out_dtype=None, outs=None):
+        """Queue one decomposition (ruqlp_submit); returns a Ticket."""
+        import torch
+        m, n = A.shape
+        d = k + p
+        omega = omega.contiguous()
+        od = out_dtype or (torch.float64 if A.dtype == torch.float64 else torch.float32)
+        if outs is None:
+            outs = (torch.empty(m, d, dtype=od, device=A.device),
+                    torch.empty(d, d, dtype=od, device=A.device),
+                    torch.empty(n, d, dtype=od, device=A.device))
+        Q, L, P = outs
+        M = Matrix(0, Dense(m, n, A.stride(0), _dtype_code(A.dtype), A.data_ptr()), Csr())
+        prm = Params(k, p, q, _dtype_code(A.dtype), omega.data_ptr(), 0)
+        out = Outputs(Q.data_ptr(), L.data_ptr(), P.data_ptr(), _dtype_code(Q.dtype), 0)
+        st, tid = ruqlp_submit(self.h, M, prm, out)
+        self.check(st)
+        return Ticket(tid, M, prm, out, (A, omega), outs)
+
+    def poll(self, ticket):
+        """True once the request has completed (its outputs are then final,
+        ticket.flags and ticket.times set); raises on a failed request."""
+        if ticket.times is not None:
+            return True
+        st, times = ruqlp_poll_times(self.h, ticket.id)
+        if st == NOT_READY:
+            return False
+        ticket.times = times
+        ticket.flags = ticket.O.flags
+        self.check(st)
+        return True
 
     def decompose_csr(self, rowptr, colidx, values, shape, omega, k, p, q, out_dtype=None):
         """RU-QLP of a CSR matrix given as CUDA tensors (rowptr, colidx int32;

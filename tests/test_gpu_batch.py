@@ -182,7 +182,7 @@ def test_batch_tensor_core_items(handle):
         assert np.max(np.abs(P.T @ P - np.eye(d))) <= 2e-5
 
 
-@pytest.mark.parametrize("bad", ["mixed_dtype", "mixed_q", "d257", "empty", "f64"])
+@pytest.mark.parametrize("bad", ["mixed_dtype", "mixed_q", "d289", "empty", "f64"])
 def test_batch_invalid_rejected(handle, bad):
     A1 = torch.randn(300, 280, device="cuda")
     A2 = torch.randn(200, 150, device="cuda")
@@ -193,10 +193,10 @@ def test_batch_invalid_rejected(handle, bad):
         As[1] = A2.bfloat16()
     elif bad == "f64":
         As = [A1.double(), A2.double()]
-    elif bad == "d257":
+    elif bad == "d289":
         As[0] = torch.randn(600, 560, device="cuda")
-        Os[0] = torch.randn(560, 261, dtype=torch.float64, device="cuda")
-        ks[0] = 257
+        Os[0] = torch.randn(560, 293, dtype=torch.float64, device="cuda")
+        ks[0] = 289
     elif bad == "mixed_q":
         qs = [1, 2]
     if bad == "empty":

@@ -35,6 +35,7 @@ CASES = [
     ("k1-p0-200x150", 200, 150, 1, 0, 1, 1e-2),
     ("p0-500x400-q2", 500, 400, 30, 0, 2, 1e-2),
     ("tall-3000x200-d64", 3000, 200, 48, 16, 1, 1e-2),
+    ("d280-1500x1200", 1500, 1200, 256, 24, 1, 1e-2),
 ]
 
 

@@ -118,6 +118,41 @@ def test_bf16_decompose_structure_small(handle):
     assert np.max(np.abs(np.abs(np.diag(L)) - np.abs(np.diag(ref["L"])))) <= 2e-3 * abs(ref["L"][0, 0])
 
 
+def test_bf16_wide_sketch_column_chunks(handle):
+    """d = 272 > 256 (the MMA's widest N): products run as two column chunks,
+    orth() as a 9-tile Cholesky.  Bitwise equal to the CUDA-core product's
+    structure is not expected; the decomposition is checked against the
+    oracle by structure, orthonormality and the loose BF16 residual ratio."""
+    m, n, k, p, q = 3000, 2400, 256, 16, 1
+    A, _, s, _ = wl.dense_spectral(91, m, n, wl.spectrum_gap(n, k, 1e-2), noise_std=2e-6)
+    Om = wl.omega(92, n, k + p)
+    Ag = torch.from_numpy(A).to(torch.bfloat16).cuda()
+    Q, L, P, flags = handle.decompose(Ag, torch.from_numpy(Om).cuda(), k, p, q)
+    Q, L, P = (t.double().cpu().numpy() for t in (Q, L, P))
+    d = k + p
+    assert np.all(np.triu(L, 1) == 0.0)
+    assert np.max(np.abs(Q.T @ Q - np.eye(d))) <= 2e-5
+    assert np.max(np.abs(P.T @ P - np.eye(d))) <= 2e-5
+    ref = oracle.ruqlp(A, Om, q)
+    r = oracle.residual_fro(A, Q, L, P)
+    r0 = oracle.residual_fro(A, ref["Q"], ref["L"], ref["P"])
+    assert r <= 1.3 * r0 + 2.0 ** -8 * math.sqrt(d / m), (r, r0)
+    assert np.max(np.abs(np.abs(np.diag(L))[:k] - np.abs(np.diag(ref["L"]))[:k])) <= 2e-2
+
+
+def test_tc_wide_product_matches_halves(handle):
+    """A 272-column product equals the two products of its column halves
+    computed separately (the chunked launch is a column split)."""
+    m, n = 1000, 800
+    rng = np.random.default_rng(5)
+    A = torch.from_numpy(rng.standard_normal((m, n))).to(torch.bfloat16).cuda()
+    X = torch.from_numpy(rng.standard_normal((n, 272))).float().cuda()
+    Y = handle.sketch(A, X)
+    Y1 = handle.sketch(A, X[:, :144].contiguous())
+    Y2 = handle.sketch(A, X[:, 144:].contiguous())
+    assert torch.equal(Y[:, :144], Y1) and torch.equal(Y[:, 144:], Y2)
+
+
 def test_bf16_decompose_full_size_residual_vs_fp64_oracle(handle):
     """The bench workload (20000 x 20000, k=200, p=20, q=2, noise std 1e-6):
     BF16 tensor-core residual <= 1.05x the FP64 oracle's on the same A."""
