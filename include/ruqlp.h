@@ -313,7 +313,9 @@ int64_t ruqlp_launch_count(void);
  *   "orth" whole orth() calls (Gram, Cholesky, triangular solve passes),
  *   "step" whole decompositions,
  *   "tc_ax" / "tc_atx" the tensor-core product kernel launches alone
- *   (BF16 path; without operand transposes and the stream-K fix-up).
+ *   (BF16 path; without operand transposes and the stream-K fix-up),
+ *   "gram" / "chol" / "trsm" the FP32 orth() passes' Gram (with its slab
+ *   reduction), blocked Cholesky and triangular solve (single-matrix path).
  * Errors: INVALID (unknown phase, NULL pointers). */
 ruqlp_status ruqlp_profile(ruqlp_handle h, const char* phase, int64_t* count, double* total_ms);
 

@@ -51,8 +51,8 @@ struct ruqlp_ctx {
   size_t stage_bytes = 0;
   int batch_graphs = 1;  // option "batch_graph"
   cudaStream_t cap_stream = nullptr;  // capture stream (the legacy stream cannot capture)
-  int64_t prof_count[6] = {0, 0, 0, 0, 0, 0};
-  double prof_ms[6] = {0, 0, 0, 0, 0, 0};
+  int64_t prof_count[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+  double prof_ms[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
   // request loop of ruqlp_submit / ruqlp_poll (created on the first submit)
   ruqlp::Server* server = nullptr;
   std::mutex server_mu;

@@ -161,8 +161,10 @@ cudaError_t bgram(const BMat* T, const int* prefix, int total, int count, int sr
 int btrsm_blocks(int64_t M);
 cudaError_t bchol(const BMat* T, int count, double shift_rel, bool force_shift, int dmax,
                   cudaStream_t st);
+// make_bt: also write the result transposed in BF16 to each tensor-core
+// item's Bt (the next product's B operand).
 cudaError_t btrsm(const BMat* T, const int* prefix, int total, int count, int src, int dst,
-                  int dmax, cudaStream_t st);
+                  int dmax, cudaStream_t st, bool make_bt = false);
 // Batched tensor-core products (BF16 A): tile list entries and launcher.
 struct BTcTile {
   int mat, tile;
@@ -172,8 +174,6 @@ struct BTcTile {
 bool btc_encode(void* maps3, const void* A, int64_t lda, int64_t m, int64_t n, const void* Bt,
                 int64_t ldbt, int dp, bool a_only);
 size_t btc_map_bytes();
-// Bt_i = bf16(buf_i[src])^T (zero columns d..dp) for the tensor-core items.
-cudaError_t btranspose_bf16(const BMat* T, int count, int src, cudaStream_t st);
 // buf[dst] = A Bt^T (trans: A^T Bt^T) for the tile list's matrices.
 cudaError_t btc_gemm(bool trans, const BMat* T, int count, const BTcTile* list, int n,
                      const void* maps, int src, int dst, int dpmax, int* err, cudaStream_t st);

@@ -116,14 +116,12 @@ __device__ bool factor_tile(float* __restrict__ B, float* __restrict__ Sout, flo
   __syncwarp();
   // S = R^{-1}, right-looking: lane c solves R x = e_c from the bottom;
   // acc[j] -= R[j][r] x[r] for j < r are independent multiply-adds
-  float dv[TB];
-  load_row(dinv, dv);
   float acc[TB];
 #pragma unroll
   for (int r = 0; r < TB; ++r) acc[r] = (r == lane) ? 1.f : 0.f;
 #pragma unroll
   for (int r = TB - 1; r >= 0; --r) {
-    const float xr = acc[r] * dv[r];
+    const float xr = acc[r] * dinv[r];
     acc[r] = xr;
     float rc[TB];  // column r of R (rows j < r are used)
     load_row(Sout + r * TP, rc);
@@ -136,10 +134,12 @@ __device__ bool factor_tile(float* __restrict__ B, float* __restrict__ Sout, flo
   return !bad;
 }
 
-// Blocked Cholesky G (+ shift I) = R^T R, d <= 256, one CTA.  Writes the
-// upper tiles R_IJ (I <= J) and the diagonal-tile inverses R_KK^{-1}, FP32,
-// 32 x 32 row-major each, to `tiles`: first the nb (nb+1)/2 R tiles in
-// row-of-tiles order, then the nb inverse tiles.
+// Blocked Cholesky G (+ shift I) = R^T R, d <= 288, one CTA of NT threads
+// (NT >= 128; each tile operation is done by one warp, so the result does not
+// depend on NT).  Writes the upper tiles R_IJ (I <= J) and the diagonal-tile
+// inverses R_KK^{-1}, FP32, 32 x 32 row-major each, to `tiles`: first the
+// nb (nb+1)/2 R tiles in row-of-tiles order, then the nb inverse tiles.
+template <int NT>
 __device__ __forceinline__ void chol_body(const float* __restrict__ G, int d, double shift_rel,
                                           int force_shift, float* __restrict__ tiles,
                                           DevStatus* __restrict__ status) {
@@ -150,7 +150,7 @@ __device__ __forceinline__ void chol_body(const float* __restrict__ G, int d, do
   __shared__ __align__(16) float s_row[TB];
   const int nb = (d + TB - 1) / TB;
   const int ntiles = nb * (nb + 1) / 2;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = NTH / 32;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = NT / 32;
   auto tile = [&](int I, int J) { return sm + (size_t)bidx(I, J, nb) * TILE_FLOATS; };
   // the current diagonal tile's inverse (shared; copied out once formed)
   float* const dinv_sm = sm + (size_t)ntiles * TILE_FLOATS;
@@ -177,23 +177,26 @@ __device__ __forceinline__ void chol_body(const float* __restrict__ G, int d, do
       while (tt >= nb - I) { tt -= nb - I; ++I; }
       const int J = I + tt;
       const int j = J * TB + lane;
-      float v[TB];
-#pragma unroll
-      for (int r = 0; r < TB; ++r) {
-        const int i = I * TB + r;
-        v[r] = (i < d && j < d) ? G[(size_t)i * d + j] : 0.f;
-      }
       float* T = tile(I, J);
 #pragma unroll
-      for (int r = 0; r < TB; ++r) {
-        const int i = I * TB + r;
-        T[r * TP + lane] = (i == j) ? ((i < d) ? v[r] + add : 1.f) : v[r];
+      for (int h = 0; h < TB; h += 16) {  // 16 loads in flight per lane
+        float v[16];
+#pragma unroll
+        for (int r = 0; r < 16; ++r) {
+          const int i = I * TB + h + r;
+          v[r] = (i < d && j < d) ? G[(size_t)i * d + j] : 0.f;
+        }
+#pragma unroll
+        for (int r = 0; r < 16; ++r) {
+          const int i = I * TB + h + r;
+          T[(h + r) * TP + lane] = (i == j) ? ((i < d) ? v[r] + add : 1.f) : v[r];
+        }
       }
     }
     if (tid == 0) s_bad = 0;
     __syncthreads();
     for (int K = 0; K < nb; ++K) {
-      if (warp == 0) {  // (a) diagonal tile, its inverse (kept in shared memory)
+      if (warp == 0) {  // (a) diagonal tile: factor, inverse (shared), inverse out
         const bool ok = factor_tile(tile(K, K), dinv_sm, s_dinv, s_row, lane,
                                     attempt == 0 ? 1.f : (float)s_shift);
         __syncwarp();
@@ -264,14 +267,16 @@ k_chol_tiles(const float* __restrict__ G, int d, double shift_rel, int force_shi
              float* __restrict__ tiles, DevStatus* __restrict__ status,
              const int32_t* __restrict__ gate) {
   if (gate != nullptr && *gate == 0) return;
-  chol_body(G, d, shift_rel, force_shift, tiles, status);
+  chol_body<NTH>(G, d, shift_rel, force_shift, tiles, status);
 }
 
-// One CTA per matrix of the problem table.
-__global__ void __launch_bounds__(NTH)
+// One CTA per matrix of the problem table; small batches of small d take
+// 128-thread CTAs, four per SM.
+template <int NT>
+__global__ void __launch_bounds__(NT, NT == 128 ? 4 : 1)
 k_bchol(const BMat* __restrict__ T, double shift_rel, int force_shift) {
   const BMat& b = T[blockIdx.x];
-  chol_body(b.Gf, b.d, shift_rel, force_shift, b.tiles, b.status);
+  chol_body<NT>(b.Gf, b.d, shift_rel, force_shift, b.tiles, b.status);
 }
 
 // X = Y R^{-1} by blocked forward substitution over 32-column tiles:
@@ -282,13 +287,20 @@ k_bchol(const BMat* __restrict__ T, double shift_rel, int force_shift) {
 // tile product is two 128-bit loads (4 rows of X, 4 columns of R) for 16
 // multiply-adds.  R tiles and diagonal-tile inverses come from k_chol_tiles'
 // packed layout and are fetched with cp.async NPF - 1 tiles ahead.
-constexpr int SR = 32;        // rows per CTA
-constexpr int TT = 64;        // threads per CTA
-constexpr int YP = SR + 4;    // pitch of a transposed column (16-byte aligned)
+// SR rows per CTA (32 for single matrices, 128 for batches of small ones;
+// the arithmetic of every element is the same either way), TT = 2 SR threads,
+// YP = pitch of a transposed column (16-byte aligned).
+constexpr int SR1 = 32, SRB = 128;
 constexpr int NPF = 3;        // tile buffers (prefetch distance NPF - 1)
+// Bt (optional): also write X^T in BF16 (dp x ldbt, K-major: the next
+// tensor-core product's B operand), zero in the padding rows d..dp.
+template <int SR>
 __device__ __forceinline__ void trsm_body(const float* __restrict__ Y, int64_t ldy,
                                           const float* __restrict__ tiles, float* X, int64_t ldx,
-                                          int64_t M, int d, int rb) {
+                                          int64_t M, int d, int rb,
+                                          __nv_bfloat16* __restrict__ Bt = nullptr,
+                                          int64_t ldbt = 0) {
+  constexpr int TT = 2 * SR, YP = SR + 4, RG = SR / 4;
   extern __shared__ __align__(16) float ys[];  // (nb * 32) x YP, ys[c * YP + r]
   __shared__ __align__(16) float Rt[NPF][TB][TB];
   const int nb = (d + TB - 1) / TB;
@@ -345,7 +357,7 @@ __device__ __forceinline__ void trsm_body(const float* __restrict__ Y, int64_t l
                    : "memory");
     }
   };
-  const int rg = t & 7, cg = t >> 3;  // rows 4rg..4rg+3, tile columns 4cg..4cg+3
+  const int rg = t % RG, cg = t / RG;  // rows 4rg..4rg+3, tile columns 4cg..4cg+3
   // the tile sequence is (J=0: inv00), (J=1: R01, inv11), (J=2: R02, R12, inv22) ...
   const int nsteps = nb * (nb + 1) / 2;
   auto step_tile = [&](int sidx) {
@@ -434,17 +446,25 @@ __device__ __forceinline__ void trsm_body(const float* __restrict__ Y, int64_t l
       if (c + 3 < d) p[3] = v.w;
     }
   }
+  if (Bt != nullptr) {  // rows of X^T are columns of the staged block: contiguous in r
+    const int dp = (d + 15) / 16 * 16;
+    for (int e = t; e < SR * dp; e += TT) {
+      const int r = e % SR, c = e / SR;
+      if (r < nr) Bt[(int64_t)c * ldbt + r0 + r] = __float2bfloat16_rn(c < d ? ys[c * YP + r] : 0.f);
+    }
+  }
 }
 
-__global__ void __launch_bounds__(TT)
+__global__ void __launch_bounds__(2 * SR1)
 k_trsm_tiles(const float* __restrict__ Y, int64_t ldy, const float* __restrict__ tiles, float* X,
              int64_t ldx, int64_t M, int d) {
-  trsm_body(Y, ldy, tiles, X, ldx, M, d, blockIdx.x);
+  trsm_body<SR1>(Y, ldy, tiles, X, ldx, M, d, blockIdx.x);
 }
 
-// Batched: block t -> (matrix, 32-row block); M = rows of buf[src].
-__global__ void __launch_bounds__(TT)
-k_btrsm(const BMat* __restrict__ T, const int* __restrict__ prefix, int count, int src, int dst) {
+// Batched: block t -> (matrix, 128-row block); M = rows of buf[src].
+__global__ void __launch_bounds__(2 * SRB)
+k_btrsm(const BMat* __restrict__ T, const int* __restrict__ prefix, int count, int src, int dst,
+        int make_bt) {
   const int t = blockIdx.x;
   int lo = 0, hi = count;
   while (hi - lo > 1) {
@@ -453,35 +473,43 @@ k_btrsm(const BMat* __restrict__ T, const int* __restrict__ prefix, int count, i
   }
   const BMat& b = T[lo];
   const int64_t M = (src == B_Y) ? b.m : b.n;
-  trsm_body(bbuf(b, src), b.dp, b.tiles, bbuf(b, dst), b.dp, M, b.d, t - prefix[lo]);
+  trsm_body<SRB>(bbuf(b, src), b.dp, b.tiles, bbuf(b, dst), b.dp, M, b.d, t - prefix[lo],
+            (make_bt && b.use_tc) ? (__nv_bfloat16*)b.Bt : nullptr, b.ldbt);
 }
 
 }  // namespace
 
-int btrsm_blocks(int64_t M) { return ceil_div(M, SR); }
+int btrsm_blocks(int64_t M) { return ceil_div(M, SRB); }
 
 cudaError_t bchol(const BMat* T, int count, double shift_rel, bool force_shift, int dmax,
                   cudaStream_t st) {
   if (count <= 0) return cudaSuccess;
   if (!chol_tiles_supported(dmax)) return cudaErrorInvalidValue;
   const size_t sm = chol_tiles_smem(dmax);
-  cudaError_t e =
-      cudaFuncSetAttribute(k_bchol, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  if (e != cudaSuccess) return e;
-  k_bchol<<<count, NTH, sm, st>>>(T, shift_rel, force_shift ? 1 : 0);
+  if (dmax <= 96) {
+    cudaError_t e =
+        cudaFuncSetAttribute(k_bchol<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    k_bchol<128><<<count, 128, sm, st>>>(T, shift_rel, force_shift ? 1 : 0);
+  } else {
+    cudaError_t e =
+        cudaFuncSetAttribute(k_bchol<NTH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    k_bchol<NTH><<<count, NTH, sm, st>>>(T, shift_rel, force_shift ? 1 : 0);
+  }
   count_launch();
   return cudaGetLastError();
 }
 
 cudaError_t btrsm(const BMat* T, const int* prefix, int total, int count, int src, int dst,
-                  int dmax, cudaStream_t st) {
+                  int dmax, cudaStream_t st, bool make_bt) {
   if (total <= 0) return cudaSuccess;
   const int nb = (dmax + TB - 1) / TB;
-  const size_t sm = (size_t)nb * TB * YP * sizeof(float);
+  const size_t sm = (size_t)nb * TB * (SRB + 4) * sizeof(float);
   cudaError_t e =
       cudaFuncSetAttribute(k_btrsm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
-  k_btrsm<<<total, TT, sm, st>>>(T, prefix, count, src, dst);
+  k_btrsm<<<total, 2 * SRB, sm, st>>>(T, prefix, count, src, dst, make_bt ? 1 : 0);
   count_launch();
   return cudaGetLastError();
 }
@@ -516,11 +544,11 @@ cudaError_t trsm_tiles_f32(const float* Y, int64_t ldy, const float* tiles, floa
                            int64_t M, int d, cudaStream_t st) {
   if (M <= 0) return cudaSuccess;
   const int nb = (d + TB - 1) / TB;
-  const size_t sm = (size_t)nb * TB * YP * sizeof(float);
+  const size_t sm = (size_t)nb * TB * (SR1 + 4) * sizeof(float);
   cudaError_t e =
       cudaFuncSetAttribute(k_trsm_tiles, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
-  k_trsm_tiles<<<ceil_div(M, SR), TT, sm, st>>>(Y, ldy, tiles, X, ldx, M, d);
+  k_trsm_tiles<<<ceil_div(M, SR1), 2 * SR1, sm, st>>>(Y, ldy, tiles, X, ldx, M, d);
   count_launch();
   return cudaGetLastError();
 }

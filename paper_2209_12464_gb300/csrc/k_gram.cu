@@ -118,6 +118,96 @@ __device__ __forceinline__ void gram_tile(const float* __restrict__ X, int64_t l
   }
 }
 
+// Small-d variant for batches: one dp x dp tile (dp = 8 TPT <= 80) per slab,
+// thread (ty, tx) of an 8 x 8 grid owns a TPT x TPT block; both triangles
+// are computed (the FP32 products commute, so the lower triangle equals the
+// mirror of the upper bitwise).  Every entry is the same sequential FP32 sum
+// over the slab's rows as in gram_tile, so results match it bitwise.
+constexpr int SMALL_MAX = 80;  // largest dp of the small variant
+template <int TPT>
+__device__ __forceinline__ void gram_small(const float* __restrict__ X, const float* __restrict__ W,
+                                           int64_t ld, int64_t M, int d, bool sym, int64_t slab,
+                                           double* __restrict__ partial, int slab_id,
+                                           float* __restrict__ sbuf) {
+  constexpr int E = 8 * TPT;
+  float(*Xs)[E] = reinterpret_cast<float(*)[E]>(sbuf);  // TK x E each
+  float(*Ws)[E] = reinterpret_cast<float(*)[E]>(sbuf + TK * E);
+  const int64_t r_begin = (int64_t)slab_id * slab;
+  const int64_t r_end = min(M, r_begin + slab);
+  const int t = threadIdx.x, ty = t >> 3, tx = t & 7;
+  float acc[TPT][TPT];
+#pragma unroll
+  for (int i = 0; i < TPT; ++i)
+#pragma unroll
+    for (int j = 0; j < TPT; ++j) acc[i][j] = 0.f;
+  constexpr int NV = TK * E / 4 / NT;  // float4s per thread per chunk (= TPT)
+  auto load = [&](const float* S, int64_t r0, float4 (&v)[NV]) {
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+      const int e = (q * NT + t) * 4;
+      const int rr = e / E, cc = e % E;
+      const int64_t r = r0 + rr;
+      v[q] = (r < r_end) ? *reinterpret_cast<const float4*>(S + r * ld + cc)
+                         : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+  };
+  auto store = [&](float (*Ss)[E], const float4 (&v)[NV]) {
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+      const int e = (q * NT + t) * 4;
+      *reinterpret_cast<float4*>(&Ss[e / E][e % E]) = v[q];
+    }
+  };
+  float4 vx[NV], vw[NV];
+  int64_t r0 = r_begin;
+  if (r0 < r_end) {
+    load(X, r0, vx);
+    if (!sym) load(W, r0, vw);
+  }
+  for (; r0 < r_end; r0 += TK) {
+    store(Xs, vx);
+    if (!sym) store(Ws, vw);
+    __syncthreads();
+    if (r0 + TK < r_end) {
+      load(X, r0 + TK, vx);
+      if (!sym) load(W, r0 + TK, vw);
+    }
+    const float(*Bs)[E] = sym ? Xs : Ws;
+#pragma unroll 4
+    for (int k = 0; k < TK; ++k) {
+      float a[TPT], b[TPT];
+#pragma unroll
+      for (int i = 0; i < TPT; i += 2) {
+        const float2 x2 = *reinterpret_cast<const float2*>(&Xs[k][ty * TPT + i]);
+        const float2 w2 = *reinterpret_cast<const float2*>(&Bs[k][tx * TPT + i]);
+        a[i] = x2.x;
+        a[i + 1] = x2.y;
+        b[i] = w2.x;
+        b[i + 1] = w2.y;
+      }
+#pragma unroll
+      for (int i = 0; i < TPT; ++i)
+#pragma unroll
+        for (int j = 0; j < TPT; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+  double* P = partial + (int64_t)slab_id * d * d;
+#pragma unroll
+  for (int i = 0; i < TPT; ++i) {
+    const int r = ty * TPT + i;
+    if (r >= d) continue;
+#pragma unroll
+    for (int j = 0; j < TPT; ++j) {
+      const int c = tx * TPT + j;
+      if (c < d) P[(int64_t)r * d + c] = (double)acc[i][j];
+    }
+  }
+}
+
+// Batched Grams take the small-d variant when dp <= 80.
+__host__ __device__ inline bool gram_is_small(int dp) { return dp <= SMALL_MAX; }
+
 __global__ void __launch_bounds__(NT)
 k_gram_tiles(const float* __restrict__ X, int64_t ldx, const float* __restrict__ W, int64_t ldw,
              int64_t M, int d1, int d2, bool sym, int64_t slab, double* __restrict__ partial,
@@ -175,6 +265,19 @@ k_bgram(const BMat* __restrict__ Tb, const int* __restrict__ prefix, int count, 
   const int64_t M = (src == B_Y) ? b.m : b.n;
   int64_t slab;
   gram_slabs(M, max_slabs, &slab);
+  if (gram_is_small(b.dp)) {
+    __shared__ __align__(16) float sbuf[2 * TK * SMALL_MAX];
+    const float* X = bbuf(b, src);
+    const float* W = bbuf(b, src2);
+    switch (b.dp / 8) {
+      case 2: gram_small<2>(X, W, b.dp, M, b.d, sym, slab, b.partial, local, sbuf); break;
+      case 4: gram_small<4>(X, W, b.dp, M, b.d, sym, slab, b.partial, local, sbuf); break;
+      case 6: gram_small<6>(X, W, b.dp, M, b.d, sym, slab, b.partial, local, sbuf); break;
+      case 8: gram_small<8>(X, W, b.dp, M, b.d, sym, slab, b.partial, local, sbuf); break;
+      default: gram_small<10>(X, W, b.dp, M, b.d, sym, slab, b.partial, local, sbuf); break;
+    }
+    return;
+  }
   const int nb = (b.d + TM - 1) / TM;
   const int tiles = sym ? nb * (nb + 1) / 2 : nb * nb;
   gram_tile(bbuf(b, src), b.dp, bbuf(b, src2), b.dp, M, b.d, b.d, sym, slab, b.partial,
@@ -202,7 +305,9 @@ __global__ void k_bgram_reduce(const BMat* __restrict__ Tb, int src, int src2, i
 int bgram_tiles(int64_t M, int d, bool sym, int max_slabs) {
   const int nb = (d + TM - 1) / TM;
   int64_t slab;
-  return (sym ? nb * (nb + 1) / 2 : nb * nb) * (int)gram_slabs(M, max_slabs, &slab);
+  const int slabs = (int)gram_slabs(M, max_slabs, &slab);
+  if (gram_is_small((d + 15) / 16 * 16)) return slabs;
+  return (sym ? nb * (nb + 1) / 2 : nb * nb) * slabs;
 }
 
 cudaError_t bgram(const BMat* T, const int* prefix, int total, int count, int src, int src2,

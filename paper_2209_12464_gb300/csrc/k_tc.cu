@@ -459,38 +459,9 @@ k_btc_gemm(const BTcTile* __restrict__ list, int n, const BMat* __restrict__ T,
   tc_body<TRANS>(w, err, stages, dpmax);
 }
 
-// Bt_i[c][r] = bf16(buf_i[r][c]) for c < d, 0 for d <= c < dp, r < K_i (K_i = m
-// for the Y buffer, n otherwise), for the tensor-core items of a batch.
-__global__ void k_btranspose_bf16(const BMat* __restrict__ T, int src) {
-  __shared__ float t[32][33];
-  const BMat& b = T[blockIdx.y];
-  if (!b.use_tc) return;
-  const int64_t K = (src == B_Y) ? b.m : b.n;
-  const float* S = bbuf(b, src);
-  __nv_bfloat16* D = (__nv_bfloat16*)b.Bt;
-  const int64_t tr = (K + 31) / 32;
-  const int64_t tiles = tr * ((b.dp + 31) / 32);
-  for (int64_t tt = blockIdx.x; tt < tiles; tt += gridDim.x) {
-    const int64_t r0 = (tt % tr) * 32;
-    const int c0 = (int)(tt / tr) * 32;
-    __syncthreads();
-    for (int i = threadIdx.y; i < 32; i += blockDim.y) {
-      const int64_t r = r0 + i;
-      const int c = c0 + threadIdx.x;
-      t[i][threadIdx.x] = (r < K && c < b.d) ? S[r * b.dp + c] : 0.f;
-    }
-    __syncthreads();
-    for (int i = threadIdx.y; i < 32; i += blockDim.y) {
-      const int c = c0 + i;
-      const int64_t r = r0 + threadIdx.x;
-      if (c < b.dp && r < K) D[(int64_t)c * b.ldbt + r] = __float2bfloat16_rn(t[threadIdx.x][i]);
-    }
-  }
-}
-
 // Sum the stream-K fragments of each tail tile in CTA order into the output.
-// Thread 0 lists the tile's contributing CTAs and fragment slots once.
-constexpr int FIX_ROWS = 4;
+// One block per (tail tile, row), one thread per column; thread 0 lists the
+// tile's contributing CTAs and fragment slots first.
 __global__ void __launch_bounds__(256) k_tc_fixup(TcParams p, int P) {
   __shared__ int s_src[512];
   __shared__ int s_n;
@@ -512,23 +483,23 @@ __global__ void __launch_bounds__(256) k_tc_fixup(TcParams p, int P) {
   }
   __syncthreads();
   const int tile = p.full_waves * P + tt;
-  const int r0 = blockIdx.y * FIX_ROWS;
+  const int r = blockIdx.y;
   const int n = s_n;
-  for (int e = threadIdx.x; e < FIX_ROWS * p.dp; e += blockDim.x) {
-    const int r = r0 + e / p.dp, col = e % p.dp;
-    // eight independent loads in flight, summed in contributor order
+  const int64_t gr = (int64_t)tile * BM + r;
+  if (gr >= p.Mout) return;
+  for (int col = threadIdx.x; col < p.dp; col += blockDim.x) {
+    // sixteen independent loads in flight, summed in contributor order
     float s = 0.f;
     int i = 0;
-    for (; i + 8 <= n; i += 8) {
-      float v[8];
+    for (; i + 16 <= n; i += 16) {
+      float v[16];
 #pragma unroll
-      for (int u = 0; u < 8; ++u) v[u] = p.frag[((int64_t)s_src[i + u] * BM + r) * p.dp + col];
+      for (int u = 0; u < 16; ++u) v[u] = p.frag[((int64_t)s_src[i + u] * BM + r) * p.dp + col];
 #pragma unroll
-      for (int u = 0; u < 8; ++u) s += v[u];
+      for (int u = 0; u < 16; ++u) s += v[u];
     }
     for (; i < n; ++i) s += p.frag[((int64_t)s_src[i] * BM + r) * p.dp + col];
-    const int64_t gr = (int64_t)tile * BM + r;
-    if (gr < p.Mout) p.out[gr * p.ldo + col] = s;
+    p.out[gr * p.ldo + col] = s;
   }
 }
 
@@ -648,7 +619,7 @@ cudaError_t tc_gemm(bool trans, const void* A, int64_t lda, int64_t m, int64_t n
   count_launch();
   e = cudaGetLastError();
   if (e != cudaSuccess || p.tail == 0) return e;
-  k_tc_fixup<<<dim3(p.tail, BM / FIX_ROWS), 256, 0, st>>>(p, P);
+  k_tc_fixup<<<dim3(p.tail, BM), 256, 0, st>>>(p, P);
   count_launch();
   return cudaGetLastError();
 }
@@ -687,13 +658,6 @@ cudaError_t btc_gemm(bool trans, const BMat* T, int count, const BTcTile* list, 
   const CUtensorMap* mp = (const CUtensorMap*)maps;
   if (trans) k_btc_gemm<true><<<P, NTHREADS, smem, st>>>(list, n, T, mp, dst, stages, dpmax, err);
   else k_btc_gemm<false><<<P, NTHREADS, smem, st>>>(list, n, T, mp, dst, stages, dpmax, err);
-  count_launch();
-  return cudaGetLastError();
-}
-
-cudaError_t btranspose_bf16(const BMat* T, int count, int src, cudaStream_t st) {
-  if (count <= 0) return cudaSuccess;
-  k_btranspose_bf16<<<dim3(64, count), dim3(32, 8), 0, st>>>(T, src);
   count_launch();
   return cudaGetLastError();
 }

@@ -52,9 +52,13 @@ ruqlp_status fail(ruqlp_ctx* h, ruqlp_status s, const char* fmt, ...) {
 // product phases), orth(), the whole decomposition, and the tensor-core
 // product kernel launches alone (k_tc_gemm, without operand transposes or the
 // stream-K fix-up) for A X and A^T Y.
-enum { PROF_AX = 0, PROF_ATX = 1, PROF_ORTH = 2, PROF_STEP = 3, PROF_TC_AX = 4, PROF_TC_ATX = 5 };
-const int kProfN = 6;
-const char* kProfNames[kProfN] = {"ax", "atx", "orth", "step", "tc_ax", "tc_atx"};
+enum {
+  PROF_AX = 0, PROF_ATX = 1, PROF_ORTH = 2, PROF_STEP = 3, PROF_TC_AX = 4, PROF_TC_ATX = 5,
+  PROF_GRAM = 6, PROF_CHOL = 7, PROF_TRSM = 8
+};
+const int kProfN = 9;
+const char* kProfNames[kProfN] = {"ax", "atx", "orth", "step", "tc_ax", "tc_atx",
+                                  "gram", "chol", "trsm"};
 
 cudaEvent_t ev_get(ruqlp_ctx* h) {
   if (!h->pool.empty()) {
@@ -289,9 +293,16 @@ ruqlp_status orth(ruqlp_ctx* h, const Layout& Lo, const Job& J, const void* Yin,
     const int passes = (final_basis || h->orth_full) ? 3 : 2;
     for (int pass = 0; pass < passes; ++pass) {
       const float* src = (const float*)(pass == 0 ? Yin : Qout);
-      CK(gram_f32(src, dp, src, dp, M, d, d, G, partial, kMaxSplits, nullptr, st, Gf));
+      {
+        ProfScope pg(h, PROF_GRAM);
+        CK(gram_f32(src, dp, src, dp, M, d, d, G, partial, kMaxSplits, nullptr, st, Gf));
+      }
       if (blocked) {
-        CK(chol_tiles_f32(Gf, d, s1, pass == 0, (float*)Rw, h->status, nullptr, st));
+        {
+          ProfScope pc(h, PROF_CHOL);
+          CK(chol_tiles_f32(Gf, d, s1, pass == 0, (float*)Rw, h->status, nullptr, st));
+        }
+        ProfScope pt(h, PROF_TRSM);
         CK(trsm_tiles_f32(src, dp, (const float*)Rw, (float*)Qout, dp, M, d, st));
       } else {
         CK(chol_upper(G, d, s1, R, Rw, Ty::F32, h->status, nullptr, st, Ty::F32, pass == 0));
@@ -661,7 +672,9 @@ ruqlp_status batch_launches(ruqlp_ctx* h, const BatchPlan& bp, int count, int q,
   ruqlp_ctx* ph = (st == h->stream) ? h : nullptr;
   ProfScope step(ph, PROF_STEP);
   CK(cudaMemsetAsync(base + bp.off_status, 0, bp.total - bp.off_status, st));
-  auto orth_b = [&](int src, int dst, int passes) -> ruqlp_status {
+  // make_bt: the last solve also writes the BF16 transposed operand of the
+  // next tensor-core product (so that product needs no transpose launch)
+  auto orth_b = [&](int src, int dst, int passes, bool make_bt) -> ruqlp_status {
     ProfScope sp(ph, PROF_ORTH);
     const int gp = (src == B_Y) ? PF_GY : PF_GN;
     const int tp = (src == B_Y) ? PF_TY : PF_TN2;
@@ -669,7 +682,7 @@ ruqlp_status batch_launches(ruqlp_ctx* h, const BatchPlan& bp, int count, int q,
       const int from = pass == 0 ? src : dst;
       CK(bgram(T, pre(gp), tot(gp), count, from, from, kMaxSplits, bp.dmax, st));
       CK(bchol(T, count, s1, pass == 0, bp.dmax, st));
-      CK(btrsm(T, pre(tp), tot(tp), count, from, dst, bp.dmax, st));
+      CK(btrsm(T, pre(tp), tot(tp), count, from, dst, bp.dmax, st, make_bt && pass == passes - 1));
     }
     return RUQLP_OK;
   };
@@ -678,8 +691,7 @@ ruqlp_status batch_launches(ruqlp_ctx* h, const BatchPlan& bp, int count, int q,
     const int pf = trans ? PF_TN : PF_NN;
     CK(bgemm(trans, ct, Ty::F32, T, pre(pf), tot(pf), count, src, dst, st));
     const auto& list = trans ? bp.tc_tn : bp.tc_nn;
-    if (!list.empty()) {
-      CK(btranspose_bf16(T, count, src, st));
+    if (!list.empty()) {  // Bt was written by the step that produced buf[src]
       ProfScope tc(ph, trans ? PROF_TC_ATX : PROF_TC_AX);
       CK(btc_gemm(trans, T, count, (const BTcTile*)(base + (trans ? bp.off_tc_tn : bp.off_tc_nn)),
                   (int)list.size(), base + bp.off_maps, src, dst, bp.dpmax_tc, err, st));
@@ -689,15 +701,15 @@ ruqlp_status batch_launches(ruqlp_ctx* h, const BatchPlan& bp, int count, int q,
   ruqlp_status s;
   CK(bcast_omega(T, count, bp.max_omega, st));
   if ((s = prod(false, B_X, B_Y)) != RUQLP_OK) return s;
-  if ((s = orth_b(B_Y, B_Y, q == 0 ? 3 : 2)) != RUQLP_OK) return s;
+  if ((s = orth_b(B_Y, B_Y, q == 0 ? 3 : 2, true)) != RUQLP_OK) return s;
   for (int it = 0; it < q; ++it) {
     if ((s = prod(true, B_Y, B_Z)) != RUQLP_OK) return s;
-    if ((s = orth_b(B_Z, B_Z, 2)) != RUQLP_OK) return s;
+    if ((s = orth_b(B_Z, B_Z, 2, true)) != RUQLP_OK) return s;
     if ((s = prod(false, B_Z, B_Y)) != RUQLP_OK) return s;
-    if ((s = orth_b(B_Y, B_Y, it == q - 1 ? 3 : 2)) != RUQLP_OK) return s;
+    if ((s = orth_b(B_Y, B_Y, it == q - 1 ? 3 : 2, true)) != RUQLP_OK) return s;
   }
   if ((s = prod(true, B_Y, B_Z)) != RUQLP_OK) return s;
-  if ((s = orth_b(B_Z, B_P, 3)) != RUQLP_OK) return s;
+  if ((s = orth_b(B_Z, B_P, 3, false)) != RUQLP_OK) return s;
   CK(bgram(T, pre(PF_GPZ), tot(PF_GPZ), count, B_P, B_Z, kMaxSplits, bp.dmax, st));
   CK(boutputs(T, count, bp.max_out, st));
   return RUQLP_OK;
