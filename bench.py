@@ -12,6 +12,9 @@ every product, B^T = A^T Q and its QR.  The workload is the dense
   python bench.py --workload batch [--dtype bf16|f32]   (512 uneven matrices:
       m log-uniform in [256, 4096], n in [128, 2048], k uniform in [8, 64],
       p=8, q=1, same spectrum form; one ruqlp_decompose_batch call per step)
+  python bench.py --workload csr [--dtype f32|bf16]   (CSR 200000 x 100000,
+      0.1 % uniform pattern, N(0,1) values + planted rank-100 term of scale 10,
+      k=100, p=10, q=1; values in FP32 or BF16)
   python bench.py --workload serve [--duration S] [--rate R]   (Poisson
       arrivals at R/s: 95 % shaped like the batched workload, 5 % dense
       16384 x 8192 with k=256, p=16, q=2; BF16; 150 GB budget; p50/p99)
@@ -52,7 +55,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--size", type=int, default=0, help="override m = n (testing only)")
-    ap.add_argument("--workload", default="dense", choices=["dense", "batch", "serve"],
+    ap.add_argument("--workload", default="dense", choices=["dense", "batch", "serve", "csr"],
                     help="dense: one 20000 x 20000 matrix (the metric's workload); batch: "
                          "512 matrices of uneven shapes in one batched call; serve: Poisson "
                          "arrivals through ruqlp_submit / ruqlp_poll")
@@ -575,6 +578,156 @@ def run_serve(args, torch, dev, local, world, rank, dist):
     return 0
 
 
+
+# ---------------------------------------------------------------------------
+# sparse workload
+# ---------------------------------------------------------------------------
+C_SEED = 20260 + 2
+C_SHAPE = (200000, 100000, 1e-3, 100, 10, 1)  # m, n, density, k, p, q
+
+
+def run_csr(args, torch, dev, local, world, rank, dist):
+    import numpy as np
+    from paper_2209_12464_gb300 import ruqlp
+    from paper_2209_12464_gb300 import workloads as wl
+    if args.dtype not in ("bf16", "f32"):
+        raise SystemExit("the sparse workload runs with FP32 or BF16 values")
+    m, n, dens, k, p, q = C_SHAPE
+    A = wl.csr_uniform(C_SEED, m, n, dens, planted_rank=100, planted_scale=10.0)
+    vdt = torch.bfloat16 if args.dtype == "bf16" else torch.float32
+    rp = torch.from_numpy(A["rowptr"]).to(dev)
+    ci = torch.from_numpy(A["colidx"]).to(dev)
+    va = torch.from_numpy(A["values"]).to(vdt).to(dev)
+    Om = wl.omega_torch(C_SEED + 1, n, k + p, device=dev)
+    nnz = int(va.numel())
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream(dev)
+    h = ruqlp.Handle(local, stream.cuda_stream)
+
+    def step():
+        return h.decompose_csr(rp, ci, va, (m, n), Om, k, p, q)
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    clocks = Clocks(local)
+    clocks.start()
+    time.sleep(0.3)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    l0 = ruqlp.ruqlp_launch_count()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    flags = 0
+    for _ in range(args.steps):
+        flags |= step()[3]
+    e1.record(stream)
+    torch.cuda.synchronize()
+    launches = (ruqlp.ruqlp_launch_count() - l0) // max(args.steps, 1)
+    if world > 1:
+        dist.barrier()
+    ck = clocks.stop()
+    ms = e0.elapsed_time(e1) / max(args.steps, 1)
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    passes = 2 * q + 2
+    vbytes = va.element_size()
+    bytes_a = nnz * (4 + vbytes) + (m + 1) * 4  # CSR of A (the CSC copy of A^T is the same size)
+    value = world * passes * bytes_a / (ms * 1e-3) / 1e9
+    h.set_option("profile", 1)
+    for _ in range(2):
+        step()
+    torch.cuda.synchronize()
+    prof = {ph: h.profile(ph) for ph in ("ax", "atx", "orth", "step")}
+    h.set_option("profile", 0)
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except OSError:
+        pass
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    d = k + p
+    dp = (d + 15) // 16 * 16
+    # one SpMM launch streams the CSR (or CSC) once and writes rows x dp FP32;
+    # the gathered skinny operand (n x dp or m x dp FP32) is read once from HBM
+    # and then served from L2
+    alg_ax = bytes_a + m * dp * 4 + n * dp * 4
+    alg_atx = nnz * (4 + vbytes) + (n + 1) * 4 + n * dp * 4 + m * dp * 4
+    cnt = prof["ax"][0] + prof["atx"][0]
+    avg = (prof["ax"][1] + prof["atx"][1]) / max(cnt, 1)
+    achieved = (alg_ax + alg_atx) / 2 / (avg * 1e-3) / 1e9
+    gather = nnz * dp * 4  # each nonzero gathers one dp-row of the skinny operand (L2)
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                "frac": achieved / hbm_peak, "traffic": None,
+                "kernel": "k_spmm (warp-per-row CSR/CSC product, one pass over A per launch)",
+                "l2_gather_bytes_per_launch": gather,
+                "l2_gather_gbs": gather / (avg * 1e-3) / 1e9,
+                "note": "the skinny operand (<= 45 MB) stays in L2; every nonzero gathers a "
+                        "dp-row of it, so the launch is bound by L2 gather bandwidth, not HBM",
+                "alg_bytes_per_launch": (alg_ax + alg_atx) / 2, "avg_launch_ms": avg,
+                "launches": cnt, "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)",
+                "phase_ms": {ph: prof[ph][1] / max(prof[ph][0], 1) for ph in prof},
+                "phase_share": {ph: prof[ph][1] / max(prof["step"][1], 1e-9)
+                                for ph in ("ax", "atx", "orth")}}
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = csr_cpu_baseline(args.dtype)
+    if rank == 0:
+        out = {"metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world,
+               "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+               "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+               "dtype": args.dtype, "data": "synthetic",
+               "config": {"workload": "CSR 200000x100000, uniform 0.1% pattern, N(0,1) values + "
+                                      "planted rank-100 term of scale 10; k=100 p=10 q=1",
+                          "nnz": nnz, "passes": passes, "bytes_A": bytes_a,
+                          "values": args.dtype,
+                          "l2": "inputs larger than L2 (CSR %.0f MB vs 129 MB L2)" % (bytes_a / 1e6),
+                          "parallelism": f"replicas x{world}"},
+               "accuracy": {"flags": flags},
+               "roofline": roofline, "cpu_baseline": cpu, "e2e": None,
+               "gpu_launches": launches, "clocks": ck}
+        print(json.dumps(out))
+    h.close()
+    return 0
+
+
+def csr_cpu_baseline(dtype):
+    """The FP64 oracle (scipy.sparse products) on a 20000-row sample of the
+    sparse workload's form, in a spawned process."""
+    code = r"""
+import sys, time, json
+sys.path.insert(0, %r)
+import oracle
+from paper_2209_12464_gb300 import workloads as wl
+A = wl.csr_uniform(7, 20000, 100000, 1e-3, planted_rank=100, planted_scale=10.0)
+Om = wl.omega(8, 100000, 110)
+t0 = time.perf_counter()
+oracle.ruqlp(A, Om, 1)
+t = time.perf_counter() - t0
+print(json.dumps({"seconds": t, "nnz": int(A["values"].shape[0])}))
+""" % (ROOT,)
+    env = dict(os.environ)
+    cores = os.cpu_count() or 1
+    for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        env[v] = str(cores)
+    env["CUDA_VISIBLE_DEVICES"] = ""
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env,
+                       timeout=900)
+    if r.returncode != 0:
+        return {"value": None, "error": r.stderr[-400:]}
+    j = json.loads(r.stdout.strip().splitlines()[-1])
+    vb = 2 if dtype == "bf16" else 4
+    gbytes = 4 * (j["nnz"] * (4 + vb) + 20001 * 4) / 1e9
+    return {"value": gbytes / j["seconds"], "unit": "GB/s", "cores": cores, "kind": "oracle",
+            "seconds": j["seconds"],
+            "sample": "oracle.ruqlp (FP64, scipy.sparse products, own Householder QR) on a "
+                      "20000 x 100000 CSR of the same form (k=100, p=10, q=1)"}
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -589,8 +742,8 @@ def main():
     import __graft_entry__ as g
     g.build()
     from paper_2209_12464_gb300 import ruqlp
-    if args.workload in ("batch", "serve"):
-        fn = run_batch if args.workload == "batch" else run_serve
+    if args.workload in ("batch", "serve", "csr"):
+        fn = {"batch": run_batch, "serve": run_serve, "csr": run_csr}[args.workload]
         rc = fn(args, torch, dev, local, world, rank, dist)
         if world > 1:
             dist.destroy_process_group()
