@@ -111,7 +111,9 @@ typedef struct {
  * of 8 elements and A is 16-byte aligned (sketches wider than 256 columns
  * run as column chunks, one pass over A each); otherwise CUDA cores.
  * omega: n x d row-major FP64 Gaussian test matrix (device memory for
- * ruqlp_decompose / ruqlp_submit; host memory for ruqlp_decompose_host).
+ * ruqlp_decompose / ruqlp_submit; host memory for ruqlp_decompose_host), or
+ * NULL: then the library generates it on the device from omega_seed with
+ * the counter-based generator of ruqlp_omega (no host copy of Omega).
  * finish_paper: 1 = also take the d x d QR of L, [P~, R~] = qr(L)
  * (Algorithm 1, step 5, in the paper's orientation).  On return Q holds
  * Q P~ and L holds R~ (UPPER triangular), so A ~= Q L P^T still holds and
@@ -121,6 +123,7 @@ typedef struct {
   ruqlp_dtype compute;
   const double* omega;
   int finish_paper;
+  uint64_t omega_seed;
 } ruqlp_params;
 
 /* Q: m x d, L: d x d (dense, zero upper triangle), P: n x d, all row-major
@@ -302,6 +305,14 @@ ruqlp_status ruqlp_gram_noalloc(const void* Y, int64_t M, int d, int64_t ldy,
 
 /* Message of the last error on this handle (never NULL; "" if none). */
 const char* ruqlp_last_error(ruqlp_handle h);
+
+/* Omega for a NULL params.omega (Section III-A step 1: iid N(0,1)), written
+ * to out (device, n x d row-major FP64, ld d): Philox4x32-10 (Salmon et al.,
+ * SC 2011) with key (seed mod 2^32, seed / 2^32) and counter
+ * (j, i mod 2^32, i / 2^32, 0) for entry (i, j); its words x0, x1 give
+ * u = (x + 1/2) 2^-32 and Omega_ij = sqrt(-2 ln u1) cos(2 pi u2) in FP64.
+ * Errors: INVALID (n < 1, d < 1, NULL out), CUDA. */
+ruqlp_status ruqlp_omega(ruqlp_handle h, int64_t n, int d, uint64_t seed, double* out);
 
 /* Kernels launched by this library in this process so far (all handles). */
 int64_t ruqlp_launch_count(void);

@@ -129,7 +129,8 @@ struct BMat {
   double* G;
   float* Gf;       // the Gram in FP32 (Cholesky input)
   float* tiles;
-  const double* omega;
+  const double* omega;  // NULL: generated from seed (philox.cuh)
+  uint64_t seed;
   void* Bt;        // dp x ldbt BF16 (tensor-core items): the transposed skinny operand
   int64_t ldbt;
   int use_tc, pad2;
@@ -165,6 +166,18 @@ cudaError_t bchol(const BMat* T, int count, double shift_rel, bool force_shift, 
 // item's Bt (the next product's B operand).
 cudaError_t btrsm(const BMat* T, const int* prefix, int total, int count, int src, int dst,
                   int dmax, cudaStream_t st, bool make_bt = false);
+// Tensor-core Gram C = Y^T Y of a tall FP32 Y (M >= 8192, d <= 256, ld a
+// multiple of 4, 16-byte aligned) via a three-way BF16 split; part holds
+// gram_tc_ctas(M) * d * d FP32 slab sums; C (FP64) and Cf (FP32) the result.
+bool gram_tc_supported(int64_t M, int d, int64_t ldy, const void* Y);
+int gram_tc_ctas(int64_t M);
+cudaError_t gram_tc(const float* Y, int64_t ldy, int64_t M, int d, float* part, double* C,
+                    float* Cf, int* err, cudaStream_t st);
+// Omega (n x d, FP64, row-major with ld ldo) from the counter-based generator
+// of philox.cuh.
+cudaError_t omega_philox(uint64_t seed, int64_t n, int d, double* out, int64_t ldo,
+                         cudaStream_t st);
+
 // Batched tensor-core products (BF16 A): tile list entries and launcher.
 struct BTcTile {
   int mat, tile;

@@ -2,6 +2,7 @@
 // Omega intake (Section III-A step 1) and the output writes (Q, L = R_B^T, P),
 // one launch over every matrix of the problem table (blockIdx.y = matrix).
 #include "internal.h"
+#include "philox.cuh"
 
 namespace ruqlp {
 namespace {
@@ -22,7 +23,8 @@ __global__ void __launch_bounds__(256) k_bcast_omega(const BMat* __restrict__ T)
         const int64_t r = r0 + i;
         const int c = c0 + tx;
         float v = 0.f;
-        if (r < b.n && c < b.d) v = (float)b.omega[r * b.d + c];
+        if (r < b.n && c < b.d)
+          v = (float)(b.omega != nullptr ? b.omega[r * b.d + c] : omega_entry(b.seed, r, c));
         t[i][tx] = v;
         if (r < b.n && c < b.dp) b.X[r * b.dp + c] = v;
       }

@@ -20,6 +20,7 @@
 // order by a fix-up kernel (deterministic; no atomics).
 // Every mbarrier wait is bounded (~2 s of %globaltimer); on timeout the CTA
 // sets an error word, stops issuing work, and frees its TMEM before exiting.
+#include <algorithm>
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <string.h>
@@ -414,7 +415,11 @@ __device__ __forceinline__ void tc_body(const W& w, int* err, int S, int dpmax) 
       const TcItem it = w.get(i);
       const int acc = i & 1;
       const uint32_t use = (uint32_t)(i >> 1);
-      if (!mbar_wait(tfull_bar(acc), use & 1u, abort_flag)) { ok = false; break; }
+      // the warp agrees on the outcome before its collective TMEM loads
+      if (!__all_sync(0xffffffffu, mbar_wait(tfull_bar(acc), use & 1u, abort_flag))) {
+        ok = false;
+        break;
+      }
       tc_fence_after();
       const uint32_t taddr = tmem_base + (uint32_t)(acc * 256) + ((uint32_t)(g * 32) << 16);
       const bool valid = row < it.rows;
@@ -562,6 +567,249 @@ int sm_count() {
   return n;
 }
 
+// ---------------------------------------------------------------------------
+// Gram of a tall FP32 matrix on the tensor cores (orth()'s Y^T Y, Section II-A):
+// Y (M x dp, FP32, dp <= 256) is split on the fly into three BF16 parts,
+// y = h + m + l with h = bf16(y), m = bf16(y - h), l = bf16(y - h - m)
+// (|y - h - m - l| <= 2^-27 |y|), and
+//   Y^T Y ~= h'h + h'm + m'h + m'm + h'l + l'h
+// (the dropped m'l, l'm, l'l terms are below 2^-26 of |y_i||y_j|).  Products
+// of BF16 parts are exact in FP32, so the result matches an FP32 Gram.
+// Each CTA (256 threads) owns a slab of rows; per 64-row chunk all threads
+// write the three parts into a 128B-swizzled shared-memory stage (both
+// operands MN-major: rows of Y are the contraction), and thread 0 issues
+// 2 (M tiles of 128 Gram rows) x 6 (part pairs) x 4 (K = 16 rows) MMAs with
+// N = dp into TMEM, while the threads convert the next chunk into the other
+// stage.  Slab sums (FP32) go to part[c]; k_gram_tc_reduce adds them in CTA
+// order in FP64.
+constexpr int GT_THREADS = 256;
+constexpr int GT_ROWS = 64;                      // rows per chunk
+constexpr uint32_t GT_BOX = 64 * 128;            // [64 rows][64 BF16] box, 8 KB
+constexpr uint32_t GT_SPLIT = 4 * GT_BOX;        // 256 columns
+constexpr uint32_t GT_STAGE = 3 * GT_SPLIT;      // h, m, l: 96 KB
+
+__device__ __forceinline__ uint32_t pack_bf16x2(float a, float b) {
+  const uint32_t lo = __bfloat16_as_ushort(__float2bfloat16_rn(a));
+  const uint32_t hi = __bfloat16_as_ushort(__float2bfloat16_rn(b));
+  return lo | (hi << 16);
+}
+
+__global__ void __launch_bounds__(GT_THREADS, 1)
+k_gram_tc(const float* __restrict__ Y, int64_t ldy, int64_t M, int d, int dp, int64_t slab_rows,
+          float* __restrict__ part, int* err) {
+  extern __shared__ uint8_t smem_raw[];
+  const uint32_t raw = smem_u32(smem_raw);
+  const uint32_t base = (raw + 1023u) & ~1023u;
+  uint8_t* base_ptr = smem_raw + (base - raw);
+  const uint32_t bar = base + 2 * GT_STAGE;  // done[0], done[1], drain
+  uint32_t* tmem_slot = (uint32_t*)(base_ptr + 2 * GT_STAGE + 32);
+  __shared__ int s_abort;
+  const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+  if (t == 0) {
+    mbar_init(bar, 1);
+    mbar_init(bar + 8, 1);
+    mbar_init(bar + 16, 1);
+    s_abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(
+                     smem_u32(tmem_slot))
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+  volatile int* abort_flag = &s_abort;
+  const int64_t r_begin = (int64_t)blockIdx.x * slab_rows;
+  const int64_t r_end = min(M, r_begin + slab_rows);
+  const int nchunks = r_end > r_begin ? (int)((r_end - r_begin + GT_ROWS - 1) / GT_ROWS) : 0;
+  // kind::f16, BF16 x BF16 -> FP32, A and B MN-major, M = 128, N = dp
+  const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | (1u << 15) | (1u << 16) |
+                         ((uint32_t)(dp >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+  const int n1 = dp > 128 ? dp - 128 : 16;  // M tile 1: columns 128..dp-1
+  const uint32_t idesc1 = (idesc & ~(0x3Fu << 17)) | ((uint32_t)(n1 >> 3) << 17);
+  bool ok = true;
+  for (int i = 0; i < nchunks && ok; ++i) {
+    const int st = i & 1;
+    const uint32_t stage = base + st * GT_STAGE;
+    if (i >= 2) {  // chunk i - 2's MMAs have read this stage (all threads agree)
+      const bool w = mbar_wait(bar + 8 * st, (uint32_t)(((i >> 1) - 1) & 1), abort_flag);
+      if (__syncthreads_or(!w)) {
+        ok = false;
+        break;
+      }
+    }
+    const int64_t r0 = r_begin + (int64_t)i * GT_ROWS;
+    // 64 rows x 64 groups of 4 columns (256 columns, zero beyond d); each
+    // thread issues all of its 16 loads before converting
+    constexpr int PER = GT_ROWS * 64 / GT_THREADS;
+    float4 xv[PER];
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+      const int e = t + q * GT_THREADS;
+      const int row = e >> 6, c = (e & 63) * 4;
+      xv[q] = (r0 + row < r_end && c < dp)
+                  ? *reinterpret_cast<const float4*>(Y + (r0 + row) * ldy + c)
+                  : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+      const int e = t + q * GT_THREADS;
+      const int row = e >> 6, c = (e & 63) * 4;
+      float v[4] = {(c < d) ? xv[q].x : 0.f, (c + 1 < d) ? xv[q].y : 0.f,
+                    (c + 2 < d) ? xv[q].z : 0.f, (c + 3 < d) ? xv[q].w : 0.f};
+      float hv[4], mv[4], lv[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        hv[j] = __bfloat162float(__float2bfloat16_rn(v[j]));
+        const float r1 = v[j] - hv[j];
+        mv[j] = __bfloat162float(__float2bfloat16_rn(r1));
+        lv[j] = r1 - mv[j];
+      }
+      const int box = c >> 6, cb = c & 63;
+      const uint32_t off = (uint32_t)box * GT_BOX + (uint32_t)row * 128 +
+                           ((uint32_t)((cb >> 3) ^ (row & 7)) << 4) + (uint32_t)((cb & 7) * 2);
+      const uint32_t a = stage + off;
+      asm volatile("st.shared.v2.b32 [%0], {%1, %2};" ::"r"(a), "r"(pack_bf16x2(hv[0], hv[1])),
+                   "r"(pack_bf16x2(hv[2], hv[3]))
+                   : "memory");
+      asm volatile("st.shared.v2.b32 [%0], {%1, %2};" ::"r"(a + GT_SPLIT),
+                   "r"(pack_bf16x2(mv[0], mv[1])), "r"(pack_bf16x2(mv[2], mv[3]))
+                   : "memory");
+      asm volatile("st.shared.v2.b32 [%0], {%1, %2};" ::"r"(a + 2 * GT_SPLIT),
+                   "r"(pack_bf16x2(lv[0], lv[1])), "r"(pack_bf16x2(lv[2], lv[3]))
+                   : "memory");
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    if (t == 0) {
+      tc_fence_after();
+      // part pairs (A part, B part): hh, hm, mh, mm, hl, lh.  M tile 0 is
+      // Gram rows 0..127 against all dp columns; M tile 1 (rows 128..) only
+      // needs the columns from 128 on (the upper triangle)
+      const int pa[6] = {0, 0, 1, 1, 0, 2}, pb[6] = {0, 1, 0, 1, 2, 0};
+#pragma unroll
+      for (int kk = 0; kk < GT_ROWS / 16; ++kk) {
+#pragma unroll
+        for (int mt = 0; mt < 2; ++mt) {
+          if (mt == 1 && dp <= 128) break;
+          const uint32_t id = mt == 0 ? idesc : idesc1;
+#pragma unroll
+          for (int q = 0; q < 6; ++q) {
+            const uint64_t ad = sdesc(stage + pa[q] * GT_SPLIT + 2 * mt * GT_BOX + kk * 2048,
+                                      GT_BOX, 1024);
+            const uint64_t bd = sdesc(stage + pb[q] * GT_SPLIT + 2 * mt * GT_BOX + kk * 2048,
+                                      GT_BOX, 1024);
+            mma_bf16(tmem_base + (uint32_t)(mt * 256), ad, bd, id,
+                     (i > 0 || kk > 0 || q > 0) ? 1u : 0u);
+          }
+        }
+      }
+      mma_commit(bar + 8 * st);
+    }
+  }
+  // wait for the last chunk's MMAs (they complete in issue order)
+  if (ok && nchunks > 0) {
+    const int last = nchunks - 1;
+    const bool w = mbar_wait(bar + 8 * (last & 1), (uint32_t)((last >> 1) & 1), abort_flag);
+    if (__syncthreads_or(!w)) ok = false;
+  }
+  if (!ok && t == 0) atomicExch(err, 1);
+  __syncthreads();
+  tc_fence_after();
+  // epilogue: warp w reads TMEM lanes 32 (w % 4) .. +31 of M tile w / 4
+  // (Gram rows (w / 4) * 128 + 32 (w % 4) + lane) and stores the upper
+  // triangle (row <= column) of its slab sum
+  float* P = part + (int64_t)blockIdx.x * d * d;
+  {
+    const int mt = warp >> 2, g = warp & 3;
+    const int row = mt * 128 + g * 32 + lane;
+    const int c0 = mt * 128, ncol = mt == 0 ? dp : n1;
+    if (mt == 0 || dp > 128) {
+      for (int c = 0; c < ncol; c += 16) {
+        float v[16];
+        if (ok && nchunks > 0) {
+          tmem_ld16(tmem_base + (uint32_t)(mt * 256 + c) + ((uint32_t)(g * 32) << 16), v);
+        } else {
+#pragma unroll
+          for (int j = 0; j < 16; ++j) v[j] = 0.f;
+        }
+        if (row < d) {
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            const int col = c0 + c + j;
+            if (col < d && col >= row) P[(int64_t)row * d + col] = v[j];
+          }
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (t == 0) {  // every MMA this CTA issued has completed before TMEM is freed
+    tc_fence_after();
+    mma_commit(bar + 16);
+    volatile int never = 0;
+    mbar_wait(bar + 16, 0, &never);
+  }
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem_base)
+                 : "memory");
+  }
+}
+
+// C = sum over CTAs of the slab sums, FP64, mirrored from the upper
+// triangle; Cf its FP32 copy.  A block takes 32 consecutive upper-triangle
+// entries (row-major order, so the reads are coalesced); warp w adds the
+// slab sums z = w, w + 8, ... in order, then the 8 warp sums are added in
+// warp order (a fixed, deterministic order).
+__global__ void __launch_bounds__(256) k_gram_tc_reduce(const float* __restrict__ part, int P,
+                                                        int d, double* __restrict__ C,
+                                                        float* __restrict__ Cf) {
+  __shared__ double ws[8][33];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int64_t nu = (int64_t)d * (d + 1) / 2;
+  const int64_t u = (int64_t)blockIdx.x * 32 + lane;  // upper-triangle entry
+  int i = 0, j = 0;
+  if (u < nu) {  // row i holds entries (i, i..d-1): find i by walking rows
+    int64_t rem = u;
+    while (rem >= d - i) { rem -= d - i; ++i; }
+    j = i + (int)rem;
+  }
+  const int64_t dd = (int64_t)d * d, src = (int64_t)i * d + j;
+  double s = 0.0;
+  if (u < nu) {
+    int z = w;
+    for (; z + 8 * 3 < P; z += 8 * 4) {
+      const float a = part[(int64_t)z * dd + src], b = part[(int64_t)(z + 8) * dd + src];
+      const float c = part[(int64_t)(z + 16) * dd + src], e = part[(int64_t)(z + 24) * dd + src];
+      s += (double)a;
+      s += (double)b;
+      s += (double)c;
+      s += (double)e;
+    }
+    for (; z < P; z += 8) s += (double)part[(int64_t)z * dd + src];
+  }
+  ws[w][lane] = s;
+  __syncthreads();
+  if (w == 0 && u < nu) {
+    double t = 0.0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) t += ws[k][lane];
+    C[(int64_t)i * d + j] = t;
+    C[(int64_t)j * d + i] = t;
+    if (Cf != nullptr) {
+      Cf[(int64_t)i * d + j] = (float)t;
+      Cf[(int64_t)j * d + i] = (float)t;
+    }
+  }
+}
+
 }  // namespace
 
 bool tc_supported(const void* A, int64_t lda, int dp) {
@@ -570,6 +818,45 @@ bool tc_supported(const void* A, int64_t lda, int dp) {
 }
 
 size_t tc_frag_bytes(int dp) { return (size_t)sm_count() * 2 * BM * dp * sizeof(float); }
+
+// Rows per CTA (a multiple of the 64-row chunk) and the number of CTAs, every
+// one of which gets rows; functions of M (and the SM count) only.
+static int64_t gram_tc_slab(int64_t M) {
+  const int64_t chunks = (M + GT_ROWS - 1) / GT_ROWS;
+  const int64_t p0 = std::min<int64_t>(sm_count(), std::max<int64_t>(chunks, 1));
+  const int64_t slab = (M + p0 - 1) / p0;
+  return (slab + GT_ROWS - 1) / GT_ROWS * GT_ROWS;
+}
+
+int gram_tc_ctas(int64_t M) {
+  const int64_t slab = gram_tc_slab(M);
+  return (int)std::max<int64_t>(1, (M + slab - 1) / slab);
+}
+
+bool gram_tc_supported(int64_t M, int d, int64_t ldy, const void* Y) {
+  const int dp = (d + 15) / 16 * 16;
+  return M >= 8192 && d >= 1 && dp <= 256 && ldy % 4 == 0 && ((uintptr_t)Y & 15) == 0 &&
+         ldy >= dp;
+}
+
+cudaError_t gram_tc(const float* Y, int64_t ldy, int64_t M, int d, float* part, double* C,
+                    float* Cf, int* err, cudaStream_t st) {
+  if (!gram_tc_supported(M, d, ldy, Y)) return cudaErrorInvalidValue;
+  const int dp = (d + 15) / 16 * 16;
+  const int P = gram_tc_ctas(M);
+  const int64_t slab = gram_tc_slab(M);
+  const size_t smem = 1024 + 2 * (size_t)GT_STAGE + 64;
+  cudaError_t e =
+      cudaFuncSetAttribute(k_gram_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k_gram_tc<<<P, GT_THREADS, smem, st>>>(Y, ldy, M, d, dp, slab, part, err);
+  count_launch();
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_gram_tc_reduce<<<ceil_div((int64_t)d * (d + 1) / 2, 32), 256, 0, st>>>(part, P, d, C, Cf);
+  count_launch();
+  return cudaGetLastError();
+}
 
 cudaError_t tc_gemm(bool trans, const void* A, int64_t lda, int64_t m, int64_t n, const void* Bt,
                     int64_t ldb, int dp, float* out, int64_t ldo, float* frag, int* err,

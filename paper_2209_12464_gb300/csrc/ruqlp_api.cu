@@ -120,7 +120,8 @@ constexpr int kMaxSplits = 64;
 
 // Workspace layout for one problem.
 struct Layout {
-  size_t X, Y, Z, P, partial, G, Gf, R, Rw, Bt, frag, colptr, rowidx, cvals, cscratch, T, total;
+  size_t X, Y, Z, P, partial, G, Gf, R, Rw, Bt, frag, colptr, rowidx, cvals, cscratch, T, Om,
+      total;
 };
 
 inline int64_t round8(int64_t x) { return (x + 7) / 8 * 8; }
@@ -128,7 +129,7 @@ inline int64_t round8(int64_t x) { return (x + 7) / 8 * 8; }
 // nnz >= 0: A is CSR with nnz nonzeros of val_bytes each (CSC copy kept too).
 // finish: room for Algorithm 1 step 5 (an m x dp buffer for Q P~).
 Layout layout_of(int64_t m, int64_t n, int d, Ty ct, int64_t nnz = -1, size_t val_bytes = 0,
-                 bool finish = false) {
+                 bool finish = false, bool gen_omega = false) {
   Layout L{};
   const int dp = round16(d);
   const size_t wes = ty_size(work_ty(ct));
@@ -142,7 +143,9 @@ Layout layout_of(int64_t m, int64_t n, int d, Ty ct, int64_t nnz = -1, size_t va
   L.Y = take((size_t)m * dp * wes);
   L.Z = take((size_t)n * dp * wes);
   L.P = take((size_t)n * dp * wes);
-  L.partial = take((size_t)kMaxSplits * d * d * sizeof(double));
+  // Gram scratch: FP64 slab partials (SIMT Gram) or FP32 slab sums of the
+  // tensor-core Gram (one per SM, at most 160)
+  L.partial = take((size_t)d * d * std::max<size_t>(kMaxSplits * sizeof(double), 160 * sizeof(float)));
   L.G = take((size_t)d * d * sizeof(double));
   L.Gf = take((size_t)d * d * sizeof(float));
   L.R = take((size_t)d * d * sizeof(double));
@@ -156,6 +159,7 @@ Layout layout_of(int64_t m, int64_t n, int d, Ty ct, int64_t nnz = -1, size_t va
     L.frag = take(tc_frag_bytes(dp <= 256 ? dp : 256));  // per column chunk
   }
   if (finish) L.T = take((size_t)m * dp * wes);
+  if (gen_omega) L.Om = take((size_t)n * d * sizeof(double));
   if (nnz >= 0) {
     L.colptr = take((size_t)(n + 1) * sizeof(int32_t));
     L.rowidx = take((size_t)(nnz > 0 ? nnz : 1) * sizeof(int32_t));
@@ -200,7 +204,6 @@ ruqlp_status validate_params(ruqlp_ctx* h, int64_t m, int64_t n, Ty at, const ru
                 (long long)dd, (long long)(m < n ? m : n));
   if (dd > 512) return fail(h, RUQLP_ERR_INVALID, "d = %lld exceeds the maximum of 512",
                             (long long)dd);
-  if (!prm->omega) return fail(h, RUQLP_ERR_INVALID, "omega is NULL");
   if (!out->Q || !out->L || !out->P) return fail(h, RUQLP_ERR_INVALID, "NULL output buffer");
   if (out->out_dtype != RUQLP_F64 && out->out_dtype != RUQLP_F32)
     return fail(h, RUQLP_ERR_INVALID, "out_dtype must be F64 or F32");
@@ -244,7 +247,8 @@ struct Job {
   int64_t lda, m, n;
   int d, dp, q;
   Ty ct, wt;
-  const double* omega;  // device, n x d
+  const double* omega;  // device, n x d; NULL: generated from seed
+  uint64_t seed = 0;
   void* Qout;
   void* Lout;
   void* Pout;
@@ -295,7 +299,10 @@ ruqlp_status orth(ruqlp_ctx* h, const Layout& Lo, const Job& J, const void* Yin,
       const float* src = (const float*)(pass == 0 ? Yin : Qout);
       {
         ProfScope pg(h, PROF_GRAM);
-        CK(gram_f32(src, dp, src, dp, M, d, d, G, partial, kMaxSplits, nullptr, st, Gf));
+        if (gram_tc_supported(M, d, dp, src))
+          CK(gram_tc(src, dp, M, d, (float*)partial, G, Gf, &h->status->timeout, st));
+        else
+          CK(gram_f32(src, dp, src, dp, M, d, d, G, partial, kMaxSplits, nullptr, st, Gf));
       }
       if (blocked) {
         {
@@ -408,6 +415,7 @@ void fill_job(const ruqlp_matrix* A, const ruqlp_params* prm, const ruqlp_output
   ty_of(prm->compute, &J.ct);
   J.wt = work_ty(J.ct);
   J.omega = prm->omega;
+  J.seed = prm->omega_seed;
   ty_of(out->out_dtype, &J.ot);
   J.finish_paper = prm->finish_paper != 0;
   if (A->is_csr) {
@@ -451,11 +459,18 @@ ruqlp_status prepare_csr(ruqlp_ctx* h, const Layout& Lo, Job& J) {
 
 ruqlp_status run_dense(ruqlp_ctx* h, const Job& J0) {
   Job J = J0;
-  const Layout Lo = J.csr ? layout_of(J.m, J.n, J.d, J.ct, J.nnz, ty_size(J.tv), J.finish_paper)
-                          : layout_of(J.m, J.n, J.d, J.ct, -1, 0, J.finish_paper);
+  const bool gen = J.omega == nullptr;
+  const Layout Lo = J.csr ? layout_of(J.m, J.n, J.d, J.ct, J.nnz, ty_size(J.tv), J.finish_paper,
+                                      gen)
+                          : layout_of(J.m, J.n, J.d, J.ct, -1, 0, J.finish_paper, gen);
   ruqlp_status s = ensure_arena(h, Lo.total);
   if (s != RUQLP_OK) return s;
   CK(status_reset(h->status, h->stream));
+  if (gen) {  // a1: Omega from the counter-based generator, on the device
+    double* Om = (double*)((char*)h->arena + Lo.Om);
+    CK(omega_philox(J.seed, J.n, J.d, Om, J.d, h->stream));
+    J.omega = Om;
+  }
   if (J.csr) {
     s = prepare_csr(h, Lo, J);
     if (s != RUQLP_OK) return s;
@@ -596,10 +611,13 @@ size_t single_bytes(const ruqlp_matrix* A, const ruqlp_params* prm) {
   if (A->is_csr) {
     Ty tv;
     if (!ty_of(A->csr.dtype, &tv)) return 0;
-    return layout_of(A->csr.m, A->csr.n, d, ct, A->csr.nnz, ty_size(tv), prm->finish_paper != 0)
+    return layout_of(A->csr.m, A->csr.n, d, ct, A->csr.nnz, ty_size(tv), prm->finish_paper != 0,
+                     prm->omega == nullptr)
         .total;
   }
-  return layout_of(A->dense.m, A->dense.n, d, ct, -1, 0, prm->finish_paper != 0).total;
+  return layout_of(A->dense.m, A->dense.n, d, ct, -1, 0, prm->finish_paper != 0,
+                   prm->omega == nullptr)
+      .total;
 }
 
 size_t batch_item_bytes(const ruqlp_matrix* A, const ruqlp_params* prm) {
@@ -843,6 +861,7 @@ ruqlp_status batch_begin(ruqlp_ctx* h, int count, const ruqlp_matrix* A, const r
     b.tiles = (float*)(base + oT[i]);
     b.Bt = b.use_tc ? (void*)(base + oB[i]) : nullptr;
     b.omega = prm[i].omega;
+    b.seed = prm[i].omega_seed;
     b.Qout = out[i].Q;
     b.Lout = out[i].L;
     b.Pout = out[i].P;
@@ -1089,8 +1108,9 @@ ruqlp_status ruqlp_decompose_host(ruqlp_handle h, const ruqlp_matrix* A,
   fill_job(A, prm, out, m, n, d, J);
   const size_t oes = ty_size(J.ot);
   // the workspace first, then staging for A, Omega and the outputs
-  const Layout Lo = J.csr ? layout_of(m, n, d, J.ct, J.nnz, ty_size(J.tv), J.finish_paper)
-                          : layout_of(m, n, d, J.ct, -1, 0, J.finish_paper);
+  const bool gen = prm->omega == nullptr;  // run_dense's layout, which comes first
+  const Layout Lo = J.csr ? layout_of(m, n, d, J.ct, J.nnz, ty_size(J.tv), J.finish_paper, gen)
+                          : layout_of(m, n, d, J.ct, -1, 0, J.finish_paper, gen);
   size_t off = align_up(Lo.total, 256);
   auto take = [&](size_t bytes) {
     const size_t o = off;
@@ -1107,7 +1127,7 @@ ruqlp_status ruqlp_decompose_host(ruqlp_handle h, const ruqlp_matrix* A,
     lds = (J.ct == Ty::BF16) ? round8(n) : n;  // TMA needs a 16-byte row pitch
     oA = take((size_t)m * lds * ty_size(J.ct));
   }
-  const size_t oOm = take((size_t)n * d * sizeof(double));
+  const size_t oOm = prm->omega ? take((size_t)n * d * sizeof(double)) : 0;
   const size_t oQ = take((size_t)m * d * oes);
   const size_t oL = take((size_t)d * d * oes);
   const size_t oP = take((size_t)n * d * oes);
@@ -1134,9 +1154,11 @@ ruqlp_status ruqlp_decompose_host(ruqlp_handle h, const ruqlp_matrix* A,
     J.A = base + oA;
     J.lda = lds;
   }
-  CK(cudaMemcpyAsync(base + oOm, prm->omega, (size_t)n * d * sizeof(double),
-                     cudaMemcpyHostToDevice, st));
-  J.omega = (const double*)(base + oOm);
+  if (prm->omega) {
+    CK(cudaMemcpyAsync(base + oOm, prm->omega, (size_t)n * d * sizeof(double),
+                       cudaMemcpyHostToDevice, st));
+    J.omega = (const double*)(base + oOm);
+  }  // else generated on the device by run_dense
   J.Qout = base + oQ;
   J.Lout = base + oL;
   J.Pout = base + oP;
@@ -1148,6 +1170,16 @@ ruqlp_status ruqlp_decompose_host(ruqlp_handle h, const ruqlp_matrix* A,
   CK(cudaMemcpyAsync(out->L, base + oL, (size_t)d * d * oes, cudaMemcpyDeviceToHost, st));
   CK(cudaMemcpyAsync(out->P, base + oP, (size_t)n * d * oes, cudaMemcpyDeviceToHost, st));
   return finish(h, out);
+}
+
+ruqlp_status ruqlp_omega(ruqlp_handle h, int64_t n, int d, uint64_t seed, double* out) {
+  if (!h) return RUQLP_ERR_INVALID;
+  h->err.clear();
+  if (n < 1 || d < 1 || !out) return fail(h, RUQLP_ERR_INVALID, "invalid arguments to ruqlp_omega");
+  CK(cudaSetDevice(h->device));
+  CK(omega_philox(seed, n, d, out, d, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  return RUQLP_OK;
 }
 
 const char* ruqlp_last_error(ruqlp_handle h) { return h ? h->err.c_str() : "NULL handle"; }

@@ -46,7 +46,7 @@ class Matrix(ctypes.Structure):
 
 class Params(ctypes.Structure):
     _fields_ = [("k", c_int), ("p", c_int), ("q", c_int), ("compute", c_int),
-                ("omega", c_void_p), ("finish_paper", c_int)]
+                ("omega", c_void_p), ("finish_paper", c_int), ("omega_seed", ctypes.c_uint64)]
 
 
 class Outputs(ctypes.Structure):
@@ -79,6 +79,7 @@ _SIGS = {
                              ctypes.POINTER(Outputs), ctypes.POINTER(ctypes.c_uint64)]),
     "ruqlp_poll": (c_int, [c_void_p, ctypes.c_uint64]),
     "ruqlp_poll_times": (c_int, [c_void_p, ctypes.c_uint64, ctypes.POINTER(RequestTimes)]),
+    "ruqlp_omega": (c_int, [c_void_p, c_int64, c_int, ctypes.c_uint64, c_void_p]),
     "ruqlp_last_error": (c_char_p, [c_void_p]),
     "ruqlp_launch_count": (c_int64, []),
     "ruqlp_sketch": (c_int, [c_void_p, ctypes.POINTER(Matrix), c_int, c_void_p, c_int64, c_int,
@@ -173,6 +174,10 @@ def ruqlp_poll_times(h, ticket):
     return st, (tm.submit_s, tm.start_s, tm.done_s)
 
 
+def ruqlp_omega(h, n, d, seed, out):
+    return lib().ruqlp_omega(h, n, d, seed, out)
+
+
 def ruqlp_last_error(h):
     return lib().ruqlp_last_error(h).decode()
 
@@ -223,9 +228,11 @@ def _dtype_code(t):
 class Batch:
     """ctypes arrays of one batched call, built once and reusable."""
 
-    def __init__(self, handle, As, omegas, ks, p, q, out_dtype=None, ps=None, qs=None):
+    def __init__(self, handle, As, omegas, ks, p, q, out_dtype=None, ps=None, qs=None,
+                 seeds=None):
         import torch
         cnt = len(As)
+        seeds = list(seeds) if seeds is not None else [0] * cnt
         od = out_dtype or torch.float32
         ps = list(ps) if ps is not None else [p] * cnt
         qs = list(qs) if qs is not None else [q] * cnt
@@ -240,14 +247,15 @@ class Batch:
                 raise ValueError("batch matrices must be 2-D row-major tensors")
             m, n = A.shape
             d = k + ps[i]
-            om = om.contiguous()
+            om = om.contiguous() if om is not None else None
             self.keep.append(om)
             Q = torch.empty(m, d, dtype=od, device=A.device)
             L = torch.empty(d, d, dtype=od, device=A.device)
             P = torch.empty(n, d, dtype=od, device=A.device)
             self.M[i] = Matrix(0, Dense(m, n, A.stride(0), _dtype_code(A.dtype), A.data_ptr()),
                                Csr())
-            self.P[i] = Params(k, ps[i], qs[i], _dtype_code(A.dtype), om.data_ptr(), 0)
+            self.P[i] = Params(k, ps[i], qs[i], _dtype_code(A.dtype),
+                               om.data_ptr() if om is not None else None, 0, int(seeds[i]))
             self.O[i] = Outputs(Q.data_ptr(), L.data_ptr(), P.data_ptr(), _dtype_code(od), 0)
             self.outs.append((Q, L, P))
 
@@ -334,15 +342,25 @@ class Handle:
         except Exception:
             pass
 
-    def decompose(self, A, omega, k, p, q, out_dtype=None, outs=None, finish_paper=False):
+    def omega(self, n, d, seed):
+        """The library's Gaussian test matrix for a seed (ruqlp_omega): an
+        n x d FP64 CUDA tensor."""
+        import torch
+        out = torch.empty(n, d, dtype=torch.float64, device="cuda")
+        self.check(ruqlp_omega(self.h, n, d, seed, out.data_ptr()))
+        return out
+
+    def decompose(self, A, omega, k, p, q, out_dtype=None, outs=None, finish_paper=False,
+                  seed=0):
         """RU-QLP of the CUDA tensor A (m x n, row-major) with the FP64 CUDA
-        tensor omega (n x d).  Returns (Q, L, P, flags) as torch tensors."""
+        tensor omega (n x d), or omega=None: Omega generated on the device from
+        seed.  Returns (Q, L, P, flags) as torch tensors."""
         import torch
         if A.dim() != 2 or A.stride(1) != 1:
             raise ValueError("A must be a 2-D row-major tensor")
         m, n = A.shape
         d = k + p
-        omega = omega.contiguous()
+        omega = omega.contiguous() if omega is not None else None
         if out_dtype is None:
             out_dtype = torch.float64 if A.dtype == torch.float64 else torch.float32
         if outs is None:
@@ -352,21 +370,25 @@ class Handle:
         else:
             Q, L, P = outs
         M = Matrix(0, Dense(m, n, A.stride(0), _dtype_code(A.dtype), A.data_ptr()), Csr())
-        prm = Params(k, p, q, _dtype_code(A.dtype), omega.data_ptr(), int(finish_paper))
+        prm = Params(k, p, q, _dtype_code(A.dtype), omega.data_ptr() if omega is not None else None,
+                     int(finish_paper), int(seed))
         out = Outputs(Q.data_ptr(), L.data_ptr(), P.data_ptr(), _dtype_code(out_dtype), 0)
         self.check(ruqlp_decompose(self.h, M, prm, out))
         return Q, L, P, out.flags
 
-    def prepare_batch(self, As, omegas, ks, p, q, out_dtype=None, ps=None, qs=None):
+    def prepare_batch(self, As, omegas, ks, p, q, out_dtype=None, ps=None, qs=None,
+                      seeds=None):
         """Marshal a batch once (A_i, Omega_i, output tensors); the returned
         object's run() calls ruqlp_decompose_batch and returns the flags."""
-        return Batch(self, As, omegas, ks, p, q, out_dtype, ps, qs)
+        return Batch(self, As, omegas, ks, p, q, out_dtype, ps, qs, seeds)
 
-    def decompose_batch(self, As, omegas, ks, p, q, out_dtype=None, ps=None, qs=None):
+    def decompose_batch(self, As, omegas, ks, p, q, out_dtype=None, ps=None, qs=None,
+                        seeds=None):
         """Batched RU-QLP of CUDA tensors As[i] (m_i x n_i, one dtype) with FP64
-        omegas[i] (n_i x (k_i + p_i)); p, q are shared unless ps / qs give one
-        per item.  Returns a list of (Q, L, P, flags)."""
-        b = Batch(self, As, omegas, ks, p, q, out_dtype, ps, qs)
+        omegas[i] (n_i x (k_i + p_i)) or None (generated from seeds[i]); p, q
+        are shared unless ps / qs give one per item.  Returns a list of
+        (Q, L, P, flags)."""
+        b = Batch(self, As, omegas, ks, p, q, out_dtype, ps, qs, seeds)
         flags = b.run()
         return [(Q, L, P, f) for (Q, L, P), f in zip(b.outs, flags)]
 
@@ -433,12 +455,14 @@ class Handle:
                                 Y.data_ptr(), d))
         return Y
 
-    def decompose_host(self, A, omega, k, p, q, outs):
-        """Same with CPU tensors (pinned or pageable); outs = (Q, L, P) CPU tensors."""
+    def decompose_host(self, A, omega, k, p, q, outs, seed=0):
+        """Same with CPU tensors (pinned or pageable); outs = (Q, L, P) CPU
+        tensors; omega=None generates Omega on the device from seed."""
         m, n = A.shape
         Q, L, P = outs
         M = Matrix(0, Dense(m, n, A.stride(0), _dtype_code(A.dtype), A.data_ptr()), Csr())
-        prm = Params(k, p, q, _dtype_code(A.dtype), omega.data_ptr(), 0)
+        prm = Params(k, p, q, _dtype_code(A.dtype), omega.data_ptr() if omega is not None else None,
+                     0, int(seed))
         out = Outputs(Q.data_ptr(), L.data_ptr(), P.data_ptr(), _dtype_code(Q.dtype), 0)
         self.check(ruqlp_decompose_host(self.h, M, prm, out))
         return Q, L, P, out.flags

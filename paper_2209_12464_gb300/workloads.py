@@ -158,6 +158,45 @@ def omega(seed, n, d):
     return np.random.default_rng(seed).standard_normal((n, d))
 
 
+def philox4x32_10(c, k):
+    """Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC 2011) on numpy uint32
+    arrays: counter words c = (c0, c1, c2, c3), key k = (k0, k1); ten rounds of
+    (hi0, lo0) = 0xD2511F53 c0, (hi1, lo1) = 0xCD9E8D57 c2,
+    c <- (hi1 ^ c1 ^ k0, lo1, hi0 ^ c3 ^ k1, lo0), key += (0x9E3779B9,
+    0xBB67AE85).  Returns the four output words."""
+    m0, m1 = np.uint64(0xD2511F53), np.uint64(0xCD9E8D57)
+    mask = np.uint64(0xFFFFFFFF)
+    c = [np.asarray(x, dtype=np.uint32) for x in c]
+    k0 = np.asarray(k[0], dtype=np.uint64)
+    k1 = np.asarray(k[1], dtype=np.uint64)
+    for _ in range(10):
+        p0 = m0 * c[0].astype(np.uint64)
+        p1 = m1 * c[2].astype(np.uint64)
+        hi0, lo0 = (p0 >> np.uint64(32)).astype(np.uint32), (p0 & mask).astype(np.uint32)
+        hi1, lo1 = (p1 >> np.uint64(32)).astype(np.uint32), (p1 & mask).astype(np.uint32)
+        c = [hi1 ^ c[1] ^ k0.astype(np.uint32), lo1, hi0 ^ c[3] ^ k1.astype(np.uint32), lo0]
+        k0 = (k0 + np.uint64(0x9E3779B9)) & mask
+        k1 = (k1 + np.uint64(0xBB67AE85)) & mask
+    return c
+
+
+def omega_philox(seed, n, d):
+    """Host twin of the library's device-generated Omega (float64 n x d):
+    entry (i, j) takes counter (j, i mod 2^32, i >> 32, 0) and key
+    (seed mod 2^32, seed >> 32); u = (x + 1/2) 2^-32 from the first two
+    words; Omega_ij = sqrt(-2 ln u1) cos(2 pi u2)."""
+    i = np.repeat(np.arange(n, dtype=np.uint64), d)
+    j = np.tile(np.arange(d, dtype=np.uint64), n)
+    s = np.uint64(seed)
+    c = (j.astype(np.uint32), (i & np.uint64(0xFFFFFFFF)).astype(np.uint32),
+         (i >> np.uint64(32)).astype(np.uint32), np.zeros(n * d, dtype=np.uint32))
+    x = philox4x32_10(c, (np.full(n * d, int(s & np.uint64(0xFFFFFFFF)), dtype=np.uint32),
+                          np.full(n * d, int(s >> np.uint64(32)), dtype=np.uint32)))
+    u1 = (x[0].astype(np.float64) + 0.5) * 2.3283064365386963e-10
+    u2 = (x[1].astype(np.float64) + 0.5) * 2.3283064365386963e-10
+    return (np.sqrt(-2.0 * np.log(u1)) * np.cos(6.283185307179586 * u2)).reshape(n, d)
+
+
 def omega_torch(seed, n, d, device="cuda"):
     """Device twin of ``omega`` for large n (float64 on ``device``)."""
     import torch

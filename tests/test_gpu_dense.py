@@ -36,6 +36,7 @@ CASES = [
     ("p0-500x400-q2", 500, 400, 30, 0, 2, 1e-2),
     ("tall-3000x200-d64", 3000, 200, 48, 16, 1, 1e-2),
     ("d280-1500x1200", 1500, 1200, 256, 24, 1, 1e-2),
+    ("tall-9000x700-tcgram", 9000, 700, 100, 20, 1, 1e-2),
 ]
 
 
@@ -107,7 +108,7 @@ def test_repeat_is_bitwise_deterministic(handle):
         assert torch.equal(x, y)
 
 
-@pytest.mark.parametrize("bad", ["k0", "pneg", "qneg", "dbig", "nullomega", "d513"])
+@pytest.mark.parametrize("bad", ["k0", "pneg", "qneg", "dbig", "nullout", "d513"])
 def test_invalid_arguments_rejected(handle, bad):
     m, n = 64, 48
     A = torch.randn(m, n, dtype=torch.float64, device="cuda")
@@ -130,8 +131,9 @@ def test_invalid_arguments_rejected(handle, bad):
     P = torch.empty(A.shape[1], d, dtype=torch.float64, device="cuda")
     M = ruqlp.Matrix(0, ruqlp.Dense(A.shape[0], A.shape[1], A.shape[1], ruqlp.F64,
                                     A.data_ptr()), ruqlp.Csr())
-    prm = ruqlp.Params(k, p, q, ruqlp.F64, 0 if bad == "nullomega" else om.data_ptr(), 0)
-    out = ruqlp.Outputs(Q.data_ptr(), L.data_ptr(), P.data_ptr(), ruqlp.F64, 0)
+    prm = ruqlp.Params(k, p, q, ruqlp.F64, om.data_ptr(), 0)
+    out = ruqlp.Outputs(0 if bad == "nullout" else Q.data_ptr(), L.data_ptr(), P.data_ptr(),
+                        ruqlp.F64, 0)
     st = ruqlp.ruqlp_decompose(handle.h, M, prm, out)
     assert st == ruqlp.ERR_INVALID
     assert ruqlp.ruqlp_last_error(handle.h) != ""
@@ -153,7 +155,7 @@ def test_gram_entry_matches_fp64_products(handle, shape, dtype):
 
 ORTH_CASES = [  # M, d, log10 kappa
     (1000, 30, 1), (1000, 30, 5), (20011, 220, 3), (5003, 64, 6), (300, 300, 2), (129, 1, 0),
-    (777, 37, 4), (4096, 272, 3),
+    (777, 37, 4), (4096, 272, 3), (9000, 100, 5), (16384, 256, 2), (8192, 17, 3),
 ]
 
 
