@@ -92,10 +92,24 @@ typedef struct {
   ruqlp_dtype dtype;
 } ruqlp_csr;
 
+/* Low-rank term of a sparse input (is_csr = 2): A = S + X D Y^T with S the
+ * CSR part, X (m x r), D (r x r), Y (n x r), FP32, row-major with leading
+ * dimension r, device memory, 1 <= r <= 4096.  The term is applied through
+ * products -- A W = S W + X (D (Y^T W)), A^T W = S^T W + Y (D^T (X^T W)) --
+ * and never formed, keeping the sparse path's O(sd) cost (Section III-D)
+ * plus O((m + n) r d).  Not accepted by ruqlp_decompose_host. */
 typedef struct {
-  int is_csr;          /* 0: dense, 1: csr */
+  int64_t r;
+  const float* X;
+  const float* D;
+  const float* Y;
+} ruqlp_lowrank;
+
+typedef struct {
+  int is_csr;          /* 0: dense, 1: csr, 2: csr plus a low-rank term */
   ruqlp_dense dense;
   ruqlp_csr csr;
+  ruqlp_lowrank lr;
 } ruqlp_matrix;
 
 /* k >= 1 (target rank), p >= 0 (oversampling), d = k + p with

@@ -167,14 +167,37 @@ def _as_operator(A):
     return np.asarray(A, dtype=np.float64)
 
 
+def _lowrank(A):
+    """The (X, D, Y) of a low-rank term A = S + X D Y^T attached to a CSR dict
+    under "lowrank" (float64), or None."""
+    if isinstance(A, dict) and A.get("lowrank") is not None:
+        lr = A["lowrank"]
+        return tuple(np.asarray(lr[k], dtype=np.float64) for k in ("X", "D", "Y"))
+    return None
+
+
 def apply_A(A, X):
-    """A X in float64 (sketch step Y = A Omega, Algorithm 1 step 3 / Section III-A)."""
-    return np.asarray(_as_operator(A) @ np.asarray(X, dtype=np.float64))
+    """A X in float64 (sketch step Y = A Omega, Algorithm 1 step 3 / Section III-A).
+    For A = S + X_l D Y_l^T: S X + X_l (D (Y_l^T X))."""
+    X = np.asarray(X, dtype=np.float64)
+    out = np.asarray(_as_operator(A) @ X)
+    lr = _lowrank(A)
+    if lr is not None:
+        Xl, D, Yl = lr
+        out = out + Xl @ (D @ (Yl.T @ X))
+    return out
 
 
 def apply_At(A, Y):
-    """A^T Y in float64 (the transposed products of Algorithm 2 and B^T = A^T Q)."""
-    return np.asarray(_as_operator(A).T @ np.asarray(Y, dtype=np.float64))
+    """A^T Y in float64 (the transposed products of Algorithm 2 and B^T = A^T Q).
+    For A = S + X_l D Y_l^T: S^T Y + Y_l (D^T (X_l^T Y))."""
+    Y = np.asarray(Y, dtype=np.float64)
+    out = np.asarray(_as_operator(A).T @ Y)
+    lr = _lowrank(A)
+    if lr is not None:
+        Xl, D, Yl = lr
+        out = out + Yl @ (D.T @ (Xl.T @ Y))
+    return out
 
 
 # ---------------------------------------------------------------------------
@@ -192,7 +215,8 @@ def ruqlp(A, Omega, q, finish_paper=False):
     A ~= Qhat R~ P^T and diag(R~) are the paper's L-values of A^T.
 
     A is a float64-convertible m x n array or a CSR dict (rowptr, colidx,
-    values, m, n).  Returns a dict with Q (m x d), L (d x d lower triangular),
+    values, m, n), optionally with a low-rank term "lowrank" = {X, D, Y}
+    (A = S + X D Y^T, applied as products, never formed).  Returns a dict with Q (m x d), L (d x d lower triangular),
     P (n x d), RB (d x d) and, with finish_paper, Qhat and Rtilde.
     """
     Op = _as_operator(A)
@@ -205,14 +229,14 @@ def ruqlp(A, Omega, q, finish_paper=False):
         raise ValueError("need 1 <= d <= min(m, n)")
     if q < 0:
         raise ValueError("q must be >= 0")
-    Y = np.asarray(Op @ Omega)
+    Y = apply_A(A, Omega)
     Q = orth(Y)
     for _ in range(q):
-        Z = np.asarray(Op.T @ Q)
+        Z = apply_At(A, Q)
         Qt = orth(Z)
-        Y = np.asarray(Op @ Qt)
+        Y = apply_A(A, Qt)
         Q = orth(Y)
-    Bt = np.asarray(Op.T @ Q)
+    Bt = apply_At(A, Q)
     P, RB = householder_qr(Bt)
     out = {"Q": Q, "L": RB.T.copy(), "P": P, "RB": RB}
     if finish_paper:
@@ -266,7 +290,20 @@ def residual_fro(A, Q, L, P):
         a2 = float(np.sum(Op * Op))
     else:
         a2 = float(np.sum(Op.data * Op.data))
-    QtAP = np.asarray(Op.T @ Q).T @ P
+    lr = _lowrank(A)
+    if lr is not None:
+        # ||S + X D Y^T||^2 = ||S||^2 + 2 sum_{(i,j) in S} s_ij (X D Y^T)_ij
+        #                     + trace(D^T (X^T X) D (Y^T Y))
+        Xl, D, Yl = lr
+        coo = Op.tocoo()
+        XD = Xl @ D
+        cross = 0.0
+        for s0 in range(0, coo.nnz, 1 << 20):
+            s1 = min(coo.nnz, s0 + (1 << 20))
+            r, c = coo.row[s0:s1], coo.col[s0:s1]
+            cross += float(np.sum(coo.data[s0:s1] * np.einsum("ij,ij->i", XD[r], Yl[c])))
+        a2 = a2 + 2.0 * cross + float(np.trace(D.T @ (Xl.T @ Xl) @ D @ (Yl.T @ Yl)))
+    QtAP = Q.T @ apply_A(A, P)
     am = float(np.sum(QtAP * L))
     m2 = float(np.sum((L.T @ (Q.T @ Q) @ L) * (P.T @ P)))
     r2 = max(a2 - 2.0 * am + m2, 0.0)

@@ -52,8 +52,11 @@ bool chol_tiles_supported(int d);
 size_t chol_tiles_bytes(int d);
 cudaError_t chol_tiles_f32(const float* G, int d, double shift_rel, bool force_shift,
                            float* tiles, DevStatus* status, const int32_t* gate, cudaStream_t st);
+// Bt (optional): also X^T in BF16 (dp x ldbt, zero rows d..dp), the next
+// tensor-core product's B operand.
 cudaError_t trsm_tiles_f32(const float* Y, int64_t ldy, const float* tiles, float* X, int64_t ldx,
-                           int64_t M, int d, cudaStream_t st);
+                           int64_t M, int d, cudaStream_t st, void* Bt = nullptr,
+                           int64_t ldbt = 0);
 
 // C (d1 x d2, FP64, ld d2) = X^T W for FP32 X (M x d1, ld ldx) and W (M x d2,
 // ld ldw): FP32 products summed in FP32 within a row slab, slabs summed in
@@ -173,6 +176,10 @@ bool gram_tc_supported(int64_t M, int d, int64_t ldy, const void* Y);
 int gram_tc_ctas(int64_t M);
 cudaError_t gram_tc(const float* Y, int64_t ldy, int64_t M, int d, float* part, double* C,
                     float* Cf, int* err, cudaStream_t st);
+// out += t for a rows x d FP32 block (the low-rank term of a CSR input).
+cudaError_t add_rows_f32(float* out, int64_t ldo, const float* t, int64_t ldt, int64_t rows, int d,
+                         cudaStream_t st);
+
 // Omega (n x d, FP64, row-major with ld ldo) from the counter-based generator
 // of philox.cuh.
 cudaError_t omega_philox(uint64_t seed, int64_t n, int d, double* out, int64_t ldo,

@@ -457,8 +457,8 @@ __device__ __forceinline__ void trsm_body(const float* __restrict__ Y, int64_t l
 
 __global__ void __launch_bounds__(2 * SR1)
 k_trsm_tiles(const float* __restrict__ Y, int64_t ldy, const float* __restrict__ tiles, float* X,
-             int64_t ldx, int64_t M, int d) {
-  trsm_body<SR1>(Y, ldy, tiles, X, ldx, M, d, blockIdx.x);
+             int64_t ldx, int64_t M, int d, __nv_bfloat16* __restrict__ Bt, int64_t ldbt) {
+  trsm_body<SR1>(Y, ldy, tiles, X, ldx, M, d, blockIdx.x, Bt, ldbt);
 }
 
 // Batched: block t -> (matrix, 128-row block); M = rows of buf[src].
@@ -541,14 +541,15 @@ cudaError_t chol_tiles_f32(const float* G, int d, double shift_rel, bool force_s
 }
 
 cudaError_t trsm_tiles_f32(const float* Y, int64_t ldy, const float* tiles, float* X, int64_t ldx,
-                           int64_t M, int d, cudaStream_t st) {
+                           int64_t M, int d, cudaStream_t st, void* Bt, int64_t ldbt) {
   if (M <= 0) return cudaSuccess;
   const int nb = (d + TB - 1) / TB;
   const size_t sm = (size_t)nb * TB * (SR1 + 4) * sizeof(float);
   cudaError_t e =
       cudaFuncSetAttribute(k_trsm_tiles, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
-  k_trsm_tiles<<<ceil_div(M, SR1), 2 * SR1, sm, st>>>(Y, ldy, tiles, X, ldx, M, d);
+  k_trsm_tiles<<<ceil_div(M, SR1), 2 * SR1, sm, st>>>(Y, ldy, tiles, X, ldx, M, d,
+                                                      (__nv_bfloat16*)Bt, ldbt);
   count_launch();
   return cudaGetLastError();
 }

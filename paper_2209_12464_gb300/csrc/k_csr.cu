@@ -12,6 +12,8 @@
 // deterministic.  The transpose is made deterministic too: nonzeros are
 // scattered to their column (atomic cursors), then each column's entries are
 // sorted by row index, the unique order of the CSC.
+#include <algorithm>
+
 #include "../../include/ruqlp.h"
 #include "internal.h"
 
@@ -199,7 +201,22 @@ k_spmm(const int32_t* __restrict__ ptr, const int32_t* __restrict__ idx, const T
   }
 }
 
+// out[r][c] += t[r][c], r < rows, c < d (FP32).
+__global__ void k_add_rows(float* __restrict__ out, int64_t ldo, const float* __restrict__ t,
+                           int64_t ldt, int64_t rows, int d) {
+  for (int64_t r = blockIdx.x; r < rows; r += gridDim.x)
+    for (int c = threadIdx.x; c < d; c += blockDim.x) out[r * ldo + c] += t[r * ldt + c];
+}
+
 }  // namespace
+
+cudaError_t add_rows_f32(float* out, int64_t ldo, const float* t, int64_t ldt, int64_t rows, int d,
+                         cudaStream_t st) {
+  if (rows <= 0 || d <= 0) return cudaSuccess;
+  k_add_rows<<<(int)std::min<int64_t>(rows, 152 * 16), 128, 0, st>>>(out, ldo, t, ldt, rows, d);
+  count_launch();
+  return cudaGetLastError();
+}
 
 cudaError_t csr_validate(const int32_t* rowptr, const int32_t* colidx, int64_t m, int64_t n,
                          int64_t nnz, int* flag, cudaStream_t st) {

@@ -121,7 +121,7 @@ constexpr int kMaxSplits = 64;
 // Workspace layout for one problem.
 struct Layout {
   size_t X, Y, Z, P, partial, G, Gf, R, Rw, Bt, frag, colptr, rowidx, cvals, cscratch, T, Om,
-      total;
+      lrT1, lrT2, lrTmp, lrPart, total;
 };
 
 inline int64_t round8(int64_t x) { return (x + 7) / 8 * 8; }
@@ -129,7 +129,7 @@ inline int64_t round8(int64_t x) { return (x + 7) / 8 * 8; }
 // nnz >= 0: A is CSR with nnz nonzeros of val_bytes each (CSC copy kept too).
 // finish: room for Algorithm 1 step 5 (an m x dp buffer for Q P~).
 Layout layout_of(int64_t m, int64_t n, int d, Ty ct, int64_t nnz = -1, size_t val_bytes = 0,
-                 bool finish = false, bool gen_omega = false) {
+                 bool finish = false, bool gen_omega = false, int64_t lr_r = 0) {
   Layout L{};
   const int dp = round16(d);
   const size_t wes = ty_size(work_ty(ct));
@@ -160,6 +160,12 @@ Layout layout_of(int64_t m, int64_t n, int d, Ty ct, int64_t nnz = -1, size_t va
   }
   if (finish) L.T = take((size_t)m * dp * wes);
   if (gen_omega) L.Om = take((size_t)n * d * sizeof(double));
+  if (lr_r > 0) {  // low-rank term of a CSR input
+    L.lrT1 = take((size_t)lr_r * dp * sizeof(float));
+    L.lrT2 = take((size_t)lr_r * dp * sizeof(float));
+    L.lrTmp = take((size_t)(m > n ? m : n) * dp * sizeof(float));
+    L.lrPart = take((size_t)kMaxSplits * lr_r * dp * sizeof(double));
+  }
   if (nnz >= 0) {
     L.colptr = take((size_t)(n + 1) * sizeof(int32_t));
     L.rowidx = take((size_t)(nnz > 0 ? nnz : 1) * sizeof(int32_t));
@@ -226,6 +232,13 @@ ruqlp_status validate(ruqlp_ctx* h, const ruqlp_matrix* A, const ruqlp_params* p
       return fail(h, RUQLP_ERR_INVALID, "NULL CSR array");
     if (!ty_of(C.dtype, &at) || at == Ty::F64)
       return fail(h, RUQLP_ERR_INVALID, "CSR values must be F32 or BF16");
+    if (A->is_csr == 2) {
+      const ruqlp_lowrank& R = A->lr;
+      if (R.r < 1 || R.r > 4096) return fail(h, RUQLP_ERR_INVALID, "low-rank r must be in [1, 4096]");
+      if (!R.X || !R.D || !R.Y) return fail(h, RUQLP_ERR_INVALID, "NULL low-rank factor");
+    } else if (A->is_csr != 1) {
+      return fail(h, RUQLP_ERR_INVALID, "is_csr must be 0, 1 or 2");
+    }
     *m = C.m;
     *n = C.n;
   } else {
@@ -265,6 +278,11 @@ struct Job {
   int32_t* colptr = nullptr;
   int32_t* rowidx = nullptr;
   void* cvals = nullptr;
+  // low-rank term A = S + X D Y^T of a CSR input (lr_r = 0: none)
+  int64_t lr_r = 0;
+  const float* lrX = nullptr;
+  const float* lrD = nullptr;
+  const float* lrY = nullptr;
 };
 
 // orth() of Section II-A: Q = Yin R^{-1} with R from Cholesky factorisations
@@ -278,8 +296,12 @@ struct Job {
 //    passes restore orthonormality.  FP32 Grams are summed in FP64 across row
 //    slabs.  (A single-SM FP64 Cholesky of a 220 x 220 Gram costs ~0.45 ms on
 //    GB300, whose FP64 rate is 1/58 of FP32.)
+// make_bt: the last solve also writes Q^T in BF16 to the arena's Bt (the
+// next tensor-core product's operand); returns whether it did.
 ruqlp_status orth(ruqlp_ctx* h, const Layout& Lo, const Job& J, const void* Yin, void* Qout,
-                  int64_t M, bool final_basis = true) {
+                  int64_t M, bool final_basis = true, bool make_bt = false,
+                  bool* bt_made = nullptr) {
+  if (bt_made) *bt_made = false;
   ProfScope ps(h, PROF_ORTH);
   char* base = (char*)h->arena;
   double* partial = (double*)(base + Lo.partial);
@@ -310,7 +332,10 @@ ruqlp_status orth(ruqlp_ctx* h, const Layout& Lo, const Job& J, const void* Yin,
           CK(chol_tiles_f32(Gf, d, s1, pass == 0, (float*)Rw, h->status, nullptr, st));
         }
         ProfScope pt(h, PROF_TRSM);
-        CK(trsm_tiles_f32(src, dp, (const float*)Rw, (float*)Qout, dp, M, d, st));
+        const bool bt = make_bt && pass == passes - 1;
+        CK(trsm_tiles_f32(src, dp, (const float*)Rw, (float*)Qout, dp, M, d, st,
+                          bt ? base + Lo.Bt : nullptr, round8(M)));
+        if (bt && bt_made) *bt_made = true;
       } else {
         CK(chol_upper(G, d, s1, R, Rw, Ty::F32, h->status, nullptr, st, Ty::F32, pass == 0));
         CK(trsm_right_upper(Ty::F32, src, dp, Rw, Qout, dp, M, d, nullptr, st));
@@ -343,7 +368,7 @@ ruqlp_status orth(ruqlp_ctx* h, const Layout& Lo, const Job& J, const void* Yin,
 //   trans = true:  out[n x dp] = A^T Xin, Xin m x d;
 // Xin has type xt and leading dimension ldx; out is the work type, ld dp.
 ruqlp_status product(ruqlp_ctx* h, const Layout& Lo, const Job& J, bool trans, Ty xt,
-                     const void* Xin, int64_t ldx, void* out) {
+                     const void* Xin, int64_t ldx, void* out, bool bt_ready = false) {
   ProfScope p(h, trans ? PROF_ATX : PROF_AX);
   cudaStream_t st = h->stream;
   char* base = (char*)h->arena;
@@ -357,6 +382,28 @@ ruqlp_status product(ruqlp_ctx* h, const Layout& Lo, const Job& J, bool trans, T
     else
       CK(spmm_csr(J.tv, J.colptr, J.rowidx, J.cvals, J.n, (const float*)Xin, ldx, J.d,
                   (float*)out, J.dp, st));
+    if (J.lr_r > 0) {
+      // + X (D (Y^T W))  or  + Y (D^T (X^T W)): two thin products and a
+      // K = r product, FP32 with FP64 split-K partials over the long dimension
+      const int64_t r = J.lr_r;
+      const float* F1 = trans ? J.lrX : J.lrY;  // contracted with W
+      const float* F2 = trans ? J.lrY : J.lrX;  // expands back to rows
+      float* T1 = (float*)(base + Lo.lrT1);
+      float* T2 = (float*)(base + Lo.lrT2);
+      float* tmp = (float*)(base + Lo.lrTmp);
+      double* lrp = (double*)(base + Lo.lrPart);
+      CK(simt_gemm_tn(Ty::F32, Ty::F32, Ty::F32, Mul::F32, F1, r, Xin, ldx, T1, J.dp, r, K, J.d,
+                      tn_splits(r, K, J.d, kMaxSplits), lrp, nullptr, st));
+      if (!trans)
+        CK(simt_gemm_nn(Ty::F32, Ty::F32, Ty::F32, Mul::F32, J.lrD, r, T1, J.dp, T2, J.dp, r, r,
+                        J.d, st));
+      else
+        CK(simt_gemm_tn(Ty::F32, Ty::F32, Ty::F32, Mul::F32, J.lrD, r, T1, J.dp, T2, J.dp, r, r,
+                        J.d, 1, nullptr, nullptr, st));
+      CK(simt_gemm_nn(Ty::F32, Ty::F32, Ty::F32, Mul::F32, F2, r, T2, J.dp, tmp, J.dp, Mout, r,
+                      J.d, st));
+      CK(add_rows_f32((float*)out, J.dp, tmp, J.dp, Mout, J.d, st));
+    }
     return RUQLP_OK;
   }
   if (J.use_tc) {
@@ -370,8 +417,9 @@ ruqlp_status product(ruqlp_ctx* h, const Layout& Lo, const Job& J, bool trans, T
     for (int c0 = 0; c0 < J.dp; c0 += w) {
       const int wc = std::min(w, J.dp - c0);
       const int cols = std::max(0, std::min(J.d - c0, wc));
-      CK(transpose_to_bf16(xt, (const char*)Xin + (size_t)c0 * xes, ldx, K, cols, wc, Bt, ldb,
-                           st));
+      if (!(bt_ready && nch == 1))  // else the last solve of orth() wrote it
+        CK(transpose_to_bf16(xt, (const char*)Xin + (size_t)c0 * xes, ldx, K, cols, wc, Bt, ldb,
+                             st));
       CK(tc_gemm(trans, J.A, J.lda, J.m, J.n, Bt, ldb, wc, (float*)out + c0, J.dp,
                  (float*)(base + Lo.frag), &h->status->timeout, st,
                  h->profile ? [&](bool begin) {
@@ -426,6 +474,12 @@ void fill_job(const ruqlp_matrix* A, const ruqlp_params* prm, const ruqlp_output
     J.nnz = A->csr.nnz;
     ty_of(A->csr.dtype, &J.tv);
     J.wt = Ty::F32;
+    if (A->is_csr == 2) {
+      J.lr_r = A->lr.r;
+      J.lrX = A->lr.X;
+      J.lrD = A->lr.D;
+      J.lrY = A->lr.Y;
+    }
   } else {
     J.A = A->dense.data;
     J.lda = A->dense.ld;
@@ -461,7 +515,7 @@ ruqlp_status run_dense(ruqlp_ctx* h, const Job& J0) {
   Job J = J0;
   const bool gen = J.omega == nullptr;
   const Layout Lo = J.csr ? layout_of(J.m, J.n, J.d, J.ct, J.nnz, ty_size(J.tv), J.finish_paper,
-                                      gen)
+                                      gen, J.lr_r)
                           : layout_of(J.m, J.n, J.d, J.ct, -1, 0, J.finish_paper, gen);
   ruqlp_status s = ensure_arena(h, Lo.total);
   if (s != RUQLP_OK) return s;
@@ -504,21 +558,24 @@ ruqlp_status run_dense(ruqlp_ctx* h, const Job& J0) {
   // exact arithmetic.  On the FP32/BF16 paths those take two CholeskyQR
   // passes (shifted, then plain: orthonormal to about kappa(Y)^2 u, enough to
   // keep the next sketch well conditioned); the last Q and P take three.
-  s = orth(h, Lo, J, Y, Y, J.m, J.q == 0);
+  // the orth() before a tensor-core product hands it the transposed BF16 Q
+  const bool fuse_bt = J.use_tc && J.dp <= 256;
+  bool btY = false, btZ = false;
+  s = orth(h, Lo, J, Y, Y, J.m, J.q == 0, fuse_bt, &btY);
   if (s != RUQLP_OK) return s;
   // a4: power iteration with orthonormalisation (Algorithm 2)
   for (int it = 0; it < J.q; ++it) {
-    s = product(h, Lo, J, true, wt, Y, dp, Z);
+    s = product(h, Lo, J, true, wt, Y, dp, Z, btY);
     if (s != RUQLP_OK) return s;
-    s = orth(h, Lo, J, Z, Z, J.n, false);
+    s = orth(h, Lo, J, Z, Z, J.n, false, fuse_bt, &btZ);
     if (s != RUQLP_OK) return s;
-    s = product(h, Lo, J, false, wt, Z, dp, Y);
+    s = product(h, Lo, J, false, wt, Z, dp, Y, btZ);
     if (s != RUQLP_OK) return s;
-    s = orth(h, Lo, J, Y, Y, J.m, it == J.q - 1);
+    s = orth(h, Lo, J, Y, Y, J.m, it == J.q - 1, fuse_bt, &btY);
     if (s != RUQLP_OK) return s;
   }
   // a5: B^T = A^T Q
-  s = product(h, Lo, J, true, wt, Y, dp, Z);
+  s = product(h, Lo, J, true, wt, Y, dp, Z, btY);
   if (s != RUQLP_OK) return s;
   // a6: [P, R_B] = qr(B^T): P = orth(B^T), R_B = P^T B^T
   s = orth(h, Lo, J, Z, Pb, J.n);
@@ -612,7 +669,7 @@ size_t single_bytes(const ruqlp_matrix* A, const ruqlp_params* prm) {
     Ty tv;
     if (!ty_of(A->csr.dtype, &tv)) return 0;
     return layout_of(A->csr.m, A->csr.n, d, ct, A->csr.nnz, ty_size(tv), prm->finish_paper != 0,
-                     prm->omega == nullptr)
+                     prm->omega == nullptr, A->is_csr == 2 ? A->lr.r : 0)
         .total;
   }
   return layout_of(A->dense.m, A->dense.n, d, ct, -1, 0, prm->finish_paper != 0,
@@ -1103,6 +1160,8 @@ ruqlp_status ruqlp_decompose_host(ruqlp_handle h, const ruqlp_matrix* A,
   int d;
   ruqlp_status s = validate(h, A, prm, out, &m, &n, &d);
   if (s != RUQLP_OK) return s;
+  if (A->is_csr == 2)
+    return fail(h, RUQLP_ERR_INVALID, "a low-rank term needs the device entry points");
   CK(cudaSetDevice(h->device));
   Job J{};
   fill_job(A, prm, out, m, n, d, J);
@@ -1215,7 +1274,7 @@ ruqlp_status ruqlp_sketch(ruqlp_handle h, const ruqlp_matrix* A, int trans, cons
   J.use_tc = !J.csr && J.ct == Ty::BF16 && !h->bf16_simt &&
              tc_supported(J.A, J.lda, std::min(J.dp, 256));
   const int64_t Mout = trans ? n : m;
-  const Layout Lo = J.csr ? layout_of(m, n, d, J.ct, J.nnz, ty_size(J.tv))
+  const Layout Lo = J.csr ? layout_of(m, n, d, J.ct, J.nnz, ty_size(J.tv), false, false, J.lr_r)
                           : layout_of(m, n, d, J.ct);
   s = ensure_arena(h, Lo.total);
   if (s != RUQLP_OK) return s;

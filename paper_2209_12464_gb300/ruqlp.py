@@ -40,8 +40,12 @@ class Csr(ctypes.Structure):
                 ("colidx", c_void_p), ("values", c_void_p), ("dtype", c_int)]
 
 
+class LowRank(ctypes.Structure):
+    _fields_ = [("r", c_int64), ("X", c_void_p), ("D", c_void_p), ("Y", c_void_p)]
+
+
 class Matrix(ctypes.Structure):
-    _fields_ = [("is_csr", c_int), ("dense", Dense), ("csr", Csr)]
+    _fields_ = [("is_csr", c_int), ("dense", Dense), ("csr", Csr), ("lr", LowRank)]
 
 
 class Params(ctypes.Structure):
@@ -424,9 +428,12 @@ class Handle:
         self.check(st)
         return True
 
-    def decompose_csr(self, rowptr, colidx, values, shape, omega, k, p, q, out_dtype=None):
+    def decompose_csr(self, rowptr, colidx, values, shape, omega, k, p, q, out_dtype=None,
+                      lowrank=None):
         """RU-QLP of a CSR matrix given as CUDA tensors (rowptr, colidx int32;
-        values float32 or bfloat16).  Returns (Q, L, P, flags)."""
+        values float32 or bfloat16), optionally plus a low-rank term
+        lowrank = (X, D, Y) (FP32 CUDA tensors, A = S + X D Y^T).  Returns
+        (Q, L, P, flags)."""
         import torch
         m, n = shape
         d = k + p
@@ -437,13 +444,18 @@ class Handle:
         P = torch.empty(n, d, dtype=od, device=dev)
         M = Matrix(1, Dense(), Csr(m, n, values.numel(), rowptr.data_ptr(), colidx.data_ptr(),
                                    values.data_ptr(), _dtype_code(values.dtype)))
+        if lowrank is not None:
+            X, D, Y = (t.contiguous() for t in lowrank)
+            M.is_csr = 2
+            M.lr = LowRank(X.shape[1], X.data_ptr(), D.data_ptr(), Y.data_ptr())
         prm = Params(k, p, q, _dtype_code(values.dtype), omega.contiguous().data_ptr(), 0)
         out = Outputs(Q.data_ptr(), L.data_ptr(), P.data_ptr(), _dtype_code(od), 0)
         self.check(ruqlp_decompose(self.h, M, prm, out))
         return Q, L, P, out.flags
 
-    def sketch_csr(self, rowptr, colidx, values, shape, X, trans=False):
-        """Y = A X (or A^T X) for a CSR A on the device; X float32."""
+    def sketch_csr(self, rowptr, colidx, values, shape, X, trans=False, lowrank=None):
+        """Y = A X (or A^T X) for a CSR A (plus an optional low-rank term
+        (Xl, D, Yl), A = S + Xl D Yl^T) on the device; X float32."""
         import torch
         m, n = shape
         K, Mout = (m, n) if trans else (n, m)
@@ -451,6 +463,10 @@ class Handle:
         Y = torch.empty(Mout, d, dtype=torch.float32, device=X.device)
         M = Matrix(1, Dense(), Csr(m, n, values.numel(), rowptr.data_ptr(), colidx.data_ptr(),
                                    values.data_ptr(), _dtype_code(values.dtype)))
+        if lowrank is not None:
+            Xl, Dl, Yl = (t.contiguous() for t in lowrank)
+            M.is_csr = 2
+            M.lr = LowRank(Xl.shape[1], Xl.data_ptr(), Dl.data_ptr(), Yl.data_ptr())
         self.check(ruqlp_sketch(self.h, M, int(trans), X.data_ptr(), X.stride(0), d,
                                 Y.data_ptr(), d))
         return Y

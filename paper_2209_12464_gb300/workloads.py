@@ -245,6 +245,24 @@ def csr_uniform(seed, m, n, density, planted_rank=0, planted_scale=0.0,
             "values": vals, "m": int(m), "n": int(n)}
 
 
+def csr_lowrank(seed, m, n, density, r, scale, noise_values=1.0):
+    """Sparse-plus-low-rank input A = S + X D Y^T: S a uniform CSR pattern
+    (csr_uniform) with N(0, noise_values^2) values, X (m x r) and Y (n x r)
+    with Haar-distributed orthonormal columns, D = diag(scale * (1, ..., 1/r))
+    (linearly decreasing from scale to scale / r).  The low-rank term's
+    singular values are D's; with scale well above ||S||_2 (about
+    noise_values * sqrt(density) (sqrt(m) + sqrt(n))) the spectrum has a gap
+    after r.  Returns the CSR dict with "lowrank" = {X, D, Y} (float64)."""
+    A = csr_uniform(seed, m, n, density)
+    A["values"] = A["values"] * noise_values
+    rng = np.random.default_rng(seed + 101)
+    X = haar(rng, m, r)
+    Y = haar(rng, n, r)
+    D = np.diag(scale * np.linspace(1.0, 1.0 / r, r))
+    A["lowrank"] = {"X": X, "D": D, "Y": Y}
+    return A
+
+
 def csr_to_dense(A):
     """Dense float64 copy of a small CSR dict (test helper)."""
     D = np.zeros((A["m"], A["n"]))

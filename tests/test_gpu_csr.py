@@ -151,3 +151,55 @@ def test_csr_full_size_workload_against_oracle(handle):
     r0 = oracle.residual_fro(As, ref["Q"], ref["L"], ref["P"])
     assert abs(r_gpu - r0) <= 1e-5
     assert np.max(np.abs(Q.T @ Q - np.eye(k + p))) <= 2e-5
+
+
+def _lowrank_dev(A):
+    lr = A["lowrank"]
+    return tuple(torch.from_numpy(np.ascontiguousarray(lr[k])).float().cuda() for k in ("X", "D", "Y"))
+
+
+def _seen_lr(A, vals_dev, lr_dev):
+    B = _seen(A, vals_dev)
+    B["lowrank"] = {k: t.double().cpu().numpy() for k, t in zip(("X", "D", "Y"), lr_dev)}
+    return B
+
+
+@pytest.mark.parametrize("trans", [False, True], ids=["AX", "AtX"])
+def test_csr_lowrank_product_parity(handle, trans):
+    """Products with A = S + X D Y^T (CSR plus low-rank term) against the
+    oracle's FP64 products of the same FP32 values: the SpMM bound for S plus
+    FP32 accumulation over n (or m) terms for the thin products."""
+    m, n, r, d = 3000, 2000, 24, 40
+    A = wl.csr_lowrank(71, m, n, 0.01, r, 60.0)
+    rp, ci, va = _dev(A, torch.float32)
+    lr = _lowrank_dev(A)
+    K = m if trans else n
+    X = torch.from_numpy(np.random.default_rng(3).standard_normal((K, d))).float().cuda()
+    Y = handle.sketch_csr(rp, ci, va, (m, n), X, trans=trans, lowrank=lr).double().cpu().numpy()
+    As = _seen_lr(A, va, lr)
+    Xh = X.double().cpu().numpy()
+    ref = oracle.apply_At(As, Xh) if trans else oracle.apply_A(As, Xh)
+    assert np.max(np.abs(Y - ref)) <= 64 * math.sqrt(K) * U32 * np.max(np.abs(ref))
+
+
+@pytest.mark.parametrize("vdtype", [torch.float32, torch.bfloat16], ids=["f32", "bf16"])
+def test_csr_lowrank_decompose_parity(handle, vdtype):
+    """RU-QLP of a sparse-plus-low-rank input: the FP32 tolerances of the
+    sparse path, and the gap after r visible in |diag(L)|."""
+    m, n, r, k, p, q = 4000, 2500, 12, 12, 8, 1
+    A = wl.csr_lowrank(72, m, n, 0.005, r, 600.0)
+    rp, ci, va = _dev(A, vdtype)
+    lr = _lowrank_dev(A)
+    Om = wl.omega(73, n, k + p)
+    Q, L, P, flags = handle.decompose_csr(rp, ci, va, (m, n), torch.from_numpy(Om).cuda(), k, p, q,
+                                          lowrank=lr)
+    Q, L, P = (t.double().cpu().numpy() for t in (Q, L, P))
+    As = _seen_lr(A, va, lr)
+    ref = oracle.ruqlp(As, Om, q)
+    l11 = abs(ref["L"][0, 0])
+    assert np.max(np.abs(L - ref["L"])) <= 1e-5 * l11
+    r_gpu = oracle.residual_fro(As, Q, L, P)
+    r0 = oracle.residual_fro(As, ref["Q"], ref["L"], ref["P"])
+    assert abs(r_gpu - r0) <= 1e-5
+    Ld = np.abs(np.diag(L))
+    assert np.min(Ld[:r]) > 3.0 * np.max(Ld[r:])
