@@ -131,7 +131,11 @@ typedef struct {
  * finish_paper: 1 = also take the d x d QR of L, [P~, R~] = qr(L)
  * (Algorithm 1, step 5, in the paper's orientation).  On return Q holds
  * Q P~ and L holds R~ (UPPER triangular), so A ~= Q L P^T still holds and
- * diag(L) are the paper's L-values of A^T (Corollary 1). */
+ * diag(L) are the paper's L-values of A^T (Corollary 1).
+ * 2 = the SVD-like finish of Section III-C (Remark 1): L = U S V^T by
+ * one-sided Jacobi (in the work precision, on one SM); on return Q holds
+ * Q U, P holds P V and L holds diag(S) (descending), so A ~= Q L P^T is an
+ * approximate truncated SVD.  d <= 512. */
 typedef struct {
   int k, p, q;
   ruqlp_dtype compute;

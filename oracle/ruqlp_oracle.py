@@ -212,7 +212,9 @@ def ruqlp(A, Omega, q, finish_paper=False):
       B^T = A^T Q;  [P, R_B] = qr(B^T);  L = R_B^T.
     With ``finish_paper`` also [P~, R~] = qr(L) (Algorithm 1 step 5, the d x d
     QR of R^T in the paper's orientation), returning Qhat = Q P~ and R~, so that
-    A ~= Qhat R~ P^T and diag(R~) are the paper's L-values of A^T.
+    A ~= Qhat R~ P^T and diag(R~) are the paper's L-values of A^T.  With
+    ``finish_paper=2`` (or "svd") instead the SVD of L (Section III-C, Remark
+    1): Qsvd = Q U, Sigma, Psvd = P V with L = U diag(Sigma) V^T.
 
     A is a float64-convertible m x n array or a CSR dict (rowptr, colidx,
     values, m, n), optionally with a low-rank term "lowrank" = {X, D, Y}
@@ -239,7 +241,13 @@ def ruqlp(A, Omega, q, finish_paper=False):
     Bt = apply_At(A, Q)
     P, RB = householder_qr(Bt)
     out = {"Q": Q, "L": RB.T.copy(), "P": P, "RB": RB}
-    if finish_paper:
+    if finish_paper == 2 or finish_paper == "svd":
+        # Section III-C, Remark 1: L = U S V^T, A ~= (Q U) S (P V)^T
+        U, sv, V = jacobi_svd(out["L"])
+        out["Qsvd"] = Q @ U
+        out["Sigma"] = sv
+        out["Psvd"] = P @ V
+    elif finish_paper:
         Pt, Rt = householder_qr(out["L"])
         out["Qhat"] = Q @ Pt
         out["Rtilde"] = Rt

@@ -176,6 +176,15 @@ bool gram_tc_supported(int64_t M, int d, int64_t ldy, const void* Y);
 int gram_tc_ctas(int64_t M);
 cudaError_t gram_tc(const float* Y, int64_t ldy, int64_t M, int d, float* part, double* C,
                     float* Cf, int* err, cudaStream_t st);
+// SVD of a d x d matrix by one-sided Jacobi in one CTA (type t: F32/F64):
+// W (column-major) holds the matrix on entry; outputs Uo, Vo (d x d row-major,
+// ld ldo, columns sorted by decreasing singular value) and s (descending).
+cudaError_t svd_jacobi(Ty t, void* W, void* V, void* s, int d, int max_sweeps, int* order,
+                       void* tmpcol, int* sweeps, void* Uo, void* Vo, int64_t ldo,
+                       cudaStream_t st);
+// L (d x d, type to) = diag(s) (s of type t).
+cudaError_t write_diag(Ty t, const void* s, int d, Ty to, void* L, cudaStream_t st);
+
 // out += t for a rows x d FP32 block (the low-rank term of a CSR input).
 cudaError_t add_rows_f32(float* out, int64_t ldo, const float* t, int64_t ldt, int64_t rows, int d,
                          cudaStream_t st);

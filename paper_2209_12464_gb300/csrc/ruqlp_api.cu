@@ -121,7 +121,7 @@ constexpr int kMaxSplits = 64;
 // Workspace layout for one problem.
 struct Layout {
   size_t X, Y, Z, P, partial, G, Gf, R, Rw, Bt, frag, colptr, rowidx, cvals, cscratch, T, Om,
-      lrT1, lrT2, lrTmp, lrPart, total;
+      lrT1, lrT2, lrTmp, lrPart, svdW, svdV, svdS, svdOrd, svdTmp, svdU, svdVs, total;
 };
 
 inline int64_t round8(int64_t x) { return (x + 7) / 8 * 8; }
@@ -129,7 +129,7 @@ inline int64_t round8(int64_t x) { return (x + 7) / 8 * 8; }
 // nnz >= 0: A is CSR with nnz nonzeros of val_bytes each (CSC copy kept too).
 // finish: room for Algorithm 1 step 5 (an m x dp buffer for Q P~).
 Layout layout_of(int64_t m, int64_t n, int d, Ty ct, int64_t nnz = -1, size_t val_bytes = 0,
-                 bool finish = false, bool gen_omega = false, int64_t lr_r = 0) {
+                 int finish = 0, bool gen_omega = false, int64_t lr_r = 0) {
   Layout L{};
   const int dp = round16(d);
   const size_t wes = ty_size(work_ty(ct));
@@ -159,6 +159,15 @@ Layout layout_of(int64_t m, int64_t n, int d, Ty ct, int64_t nnz = -1, size_t va
     L.frag = take(tc_frag_bytes(dp <= 256 ? dp : 256));  // per column chunk
   }
   if (finish) L.T = take((size_t)m * dp * wes);
+  if (finish == 2) {  // Jacobi SVD of L: W, V, S, order, norms, sweep count, sorted U and V
+    L.svdW = take((size_t)d * d * wes);
+    L.svdV = take((size_t)d * d * wes);
+    L.svdS = take((size_t)d * wes);
+    L.svdOrd = take((size_t)d * sizeof(int) + 16);
+    L.svdTmp = take((size_t)d * wes);
+    L.svdU = take((size_t)d * dp * wes);
+    L.svdVs = take((size_t)d * dp * wes);
+  }
   if (gen_omega) L.Om = take((size_t)n * d * sizeof(double));
   if (lr_r > 0) {  // low-rank term of a CSR input
     L.lrT1 = take((size_t)lr_r * dp * sizeof(float));
@@ -204,6 +213,8 @@ ruqlp_status validate_params(ruqlp_ctx* h, int64_t m, int64_t n, Ty at, const ru
   if (prm->k < 1) return fail(h, RUQLP_ERR_INVALID, "k must be >= 1 (got %d)", prm->k);
   if (prm->p < 0) return fail(h, RUQLP_ERR_INVALID, "p must be >= 0 (got %d)", prm->p);
   if (prm->q < 0) return fail(h, RUQLP_ERR_INVALID, "q must be >= 0 (got %d)", prm->q);
+  if (prm->finish_paper < 0 || prm->finish_paper > 2)
+    return fail(h, RUQLP_ERR_INVALID, "finish_paper must be 0, 1 or 2");
   const int64_t dd = (int64_t)prm->k + prm->p;
   if (dd > m || dd > n)
     return fail(h, RUQLP_ERR_INVALID, "d = k + p = %lld exceeds min(m, n) = %lld",
@@ -266,7 +277,7 @@ struct Job {
   void* Lout;
   void* Pout;
   Ty ot;
-  bool finish_paper;
+  int finish_paper;  // 0 none, 1 qr(L) (Algorithm 1 step 5), 2 SVD of L (Remark 1)
   bool use_tc;  // BF16 products on the tensor cores (k_tc.cu)
   // CSR input (work type FP32): A's arrays and the CSC copy in the arena
   bool csr = false;
@@ -465,7 +476,7 @@ void fill_job(const ruqlp_matrix* A, const ruqlp_params* prm, const ruqlp_output
   J.omega = prm->omega;
   J.seed = prm->omega_seed;
   ty_of(out->out_dtype, &J.ot);
-  J.finish_paper = prm->finish_paper != 0;
+  J.finish_paper = prm->finish_paper;
   if (A->is_csr) {
     J.csr = true;
     J.rowptr = A->csr.rowptr;
@@ -586,6 +597,25 @@ ruqlp_status run_dense(ruqlp_ctx* h, const Job& J0) {
   else
     CK(gram_f32((const float*)Pb, dp, (const float*)Z, dp, J.n, d, d, G, partial, kMaxSplits,
                 nullptr, st));
+  if (J.finish_paper == 2) {
+    // Remark 1: L = U S V^T (one-sided Jacobi on one SM), A ~= (Q U) S (P V)^T;
+    // the column-major copy of L is R_B row-major
+    void* W = base + Lo.svdW;
+    void* Us = base + Lo.svdU;
+    void* Vs = base + Lo.svdVs;
+    void* QP = base + Lo.T;
+    const Mul mm = wt == Ty::F64 ? Mul::F64 : Mul::F32;
+    CK(copy_cast_2d(Ty::F64, G, d, wt, W, d, d, d, st));
+    CK(svd_jacobi(wt, W, base + Lo.svdV, base + Lo.svdS, d, 40, (int*)(base + Lo.svdOrd),
+                  base + Lo.svdTmp, (int*)(base + Lo.svdOrd + (size_t)d * sizeof(int)), Us, Vs,
+                  dp, st));
+    CK(simt_gemm_nn(wt, wt, wt, mm, Y, dp, Us, dp, QP, dp, J.m, d, d, st));
+    CK(simt_gemm_nn(wt, wt, wt, mm, Pb, dp, Vs, dp, X, dp, J.n, d, d, st));
+    CK(write_diag(wt, base + Lo.svdS, d, J.ot, J.Lout, st));
+    CK(copy_cast_2d(wt, QP, dp, J.ot, J.Qout, d, J.m, d, st));
+    CK(copy_cast_2d(wt, X, dp, J.ot, J.Pout, d, J.n, d, st));
+    return RUQLP_OK;
+  }
   if (J.finish_paper) {
     // Algorithm 1 step 5 in this orientation: [P~, R~] = qr(L), L = R_B^T;
     // Q <- Q P~, middle factor R~ (upper triangular): A ~= (Q P~) R~ P^T.
@@ -668,11 +698,11 @@ size_t single_bytes(const ruqlp_matrix* A, const ruqlp_params* prm) {
   if (A->is_csr) {
     Ty tv;
     if (!ty_of(A->csr.dtype, &tv)) return 0;
-    return layout_of(A->csr.m, A->csr.n, d, ct, A->csr.nnz, ty_size(tv), prm->finish_paper != 0,
+    return layout_of(A->csr.m, A->csr.n, d, ct, A->csr.nnz, ty_size(tv), prm->finish_paper,
                      prm->omega == nullptr, A->is_csr == 2 ? A->lr.r : 0)
         .total;
   }
-  return layout_of(A->dense.m, A->dense.n, d, ct, -1, 0, prm->finish_paper != 0,
+  return layout_of(A->dense.m, A->dense.n, d, ct, -1, 0, prm->finish_paper,
                    prm->omega == nullptr)
       .total;
 }

@@ -223,3 +223,37 @@ def test_finish_paper_matches_oracle(handle, case, dtype):
     r0 = oracle.residual_fro_small(Aseen, ref["Qhat"], ref["Rtilde"], ref["P"])
     assert abs(r - r0) <= tol
     assert np.max(np.abs(Qh[:, :k] - ref["Qhat"][:, :k])) <= TOLQ[dtype] * 10
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32], ids=["f64", "f32"])
+@pytest.mark.parametrize("case", [CASES[0], CASES[1], CASES[6]], ids=[CASES[0][0], CASES[1][0],
+                                                                     CASES[6][0]])
+def test_svd_finish_matches_oracle(handle, case, dtype):
+    """finish_paper = 2 (Section III-C, Remark 1): L = diag(S) descending,
+    S against the oracle's Jacobi SVD of its L (FP64: 1e-10 |L_11|, FP32:
+    1e-5), Q and P orthonormal, residual equal to the oracle's; singular
+    vectors of well-separated values match up to sign."""
+    name, m, n, k, p, q, tail = case
+    A, Om = _case(*case, seed=wl.MASTER_SEED + 7 * m + n)
+    Ag = torch.from_numpy(A).to(dtype).cuda()
+    Aseen = Ag.double().cpu().numpy()
+    ref = oracle.ruqlp(Aseen, Om, q, finish_paper=2)
+    Q, L, P, flags = handle.decompose(Ag, torch.from_numpy(Om).cuda(), k, p, q, finish_paper=2)
+    Q, L, P = (t.double().cpu().numpy() for t in (Q, L, P))
+    d = k + p
+    tol = TOL[dtype]
+    S = np.diag(L)
+    assert np.all(L - np.diag(S) == 0.0)
+    assert np.all(np.diff(S) <= 0.0)
+    assert np.max(np.abs(S - ref["Sigma"])) <= tol * ref["Sigma"][0]
+    assert np.max(np.abs(Q.T @ Q - np.eye(d))) <= TOLO[dtype] * 10
+    assert np.max(np.abs(P.T @ P - np.eye(d))) <= TOLO[dtype] * 10
+    r = oracle.residual_fro_small(Aseen, Q, L, P)
+    r0 = oracle.residual_fro_small(Aseen, ref["Qsvd"], np.diag(ref["Sigma"]), ref["Psvd"])
+    assert abs(r - r0) <= tol
+    # tail singular values are distinct: their vectors are determined up to sign
+    sv = ref["Sigma"]
+    for j in range(k, d - 1):
+        if min(sv[j - 1] - sv[j], sv[j] - sv[j + 1]) > 1e-3 * sv[j]:
+            c = abs(np.dot(Q[:, j], ref["Qsvd"][:, j]))
+            assert c >= 1.0 - (1e-6 if dtype == torch.float64 else 1e-2), (j, c)

@@ -127,3 +127,23 @@ def test_sparse_plus_lowrank_operator_equals_dense_form():
     s = np.linalg.svd(Dn, compute_uv=False)
     Ld = np.abs(np.diag(a["L"]))
     assert np.all(Ld[:6] >= 0.5 * s[5]) and np.all(Ld[6:] <= 2.0 * s[6])
+
+
+def test_svd_like_finish_is_an_exact_refactoring():
+    """Section III-C, Remark 1: L = U S V^T gives A ~= (Q U) S (P V)^T with the
+    same residual; S are L's singular values (LAPACK after sorting), and for
+    a gapped spectrum the leading ones approximate A's."""
+    A, U0, s0, V0 = wl.dense_spectral(21, 300, 200, wl.spectrum_gap(200, 10, 1e-3))
+    Om = wl.omega(22, 200, 16)
+    o = oracle.ruqlp(A, Om, 1, finish_paper=2)
+    sv = np.linalg.svd(o["L"], compute_uv=False)
+    assert np.max(np.abs(o["Sigma"] - sv)) <= 1e-13 * sv[0]
+    r1 = oracle.residual_fro_small(A, o["Q"], o["L"], o["P"])
+    r2 = oracle.residual_fro_small(A, o["Qsvd"], np.diag(o["Sigma"]), o["Psvd"])
+    assert abs(r1 - r2) <= 1e-13
+    assert np.max(np.abs(o["Qsvd"].T @ o["Qsvd"] - np.eye(16))) <= 1e-13
+    assert np.max(np.abs(o["Sigma"][:10] - s0[:10])) <= 1e-6
+    # the leading singular subspaces are the generator's (sigma_1..10 are
+    # equal, so only the subspace is determined)
+    assert np.max(oracle.principal_sines(o["Qsvd"][:, :10], U0[:, :10])) <= 1e-5
+    assert np.max(oracle.principal_sines(o["Psvd"][:, :10], V0[:, :10])) <= 1e-5
