@@ -15,6 +15,8 @@ every product, B^T = A^T Q and its QR.  The workload is the dense
   python bench.py --workload csr [--dtype f32|bf16]   (CSR 200000 x 100000,
       0.1 % uniform pattern, N(0,1) values + planted rank-100 term of scale 10,
       k=100, p=10, q=1; values in FP32 or BF16)
+  python bench.py --workload csrlr   (the same pattern with N(0,1) values plus
+      a rank-100 term X D Y^T kept as factors, D from 200 down to 2)
   python bench.py --workload serve [--duration S] [--rate R]   (Poisson
       arrivals at R/s: 95 % shaped like the batched workload, 5 % dense
       16384 x 8192 with k=256, p=16, q=2; BF16; 150 GB budget; p50/p99)
@@ -55,7 +57,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--size", type=int, default=0, help="override m = n (testing only)")
-    ap.add_argument("--workload", default="dense", choices=["dense", "batch", "serve", "csr"],
+    ap.add_argument("--workload", default="dense",
+                    choices=["dense", "batch", "serve", "csr", "csrlr"],
                     help="dense: one 20000 x 20000 matrix (the metric's workload); batch: "
                          "512 matrices of uneven shapes in one batched call; serve: Poisson "
                          "arrivals through ruqlp_submit / ruqlp_poll")
@@ -593,7 +596,11 @@ def run_csr(args, torch, dev, local, world, rank, dist):
     if args.dtype not in ("bf16", "f32"):
         raise SystemExit("the sparse workload runs with FP32 or BF16 values")
     m, n, dens, k, p, q = C_SHAPE
-    A = wl.csr_uniform(C_SEED, m, n, dens, planted_rank=100, planted_scale=10.0)
+    lowrank = args.workload == "csrlr"
+    if lowrank:
+        A = wl.csr_lowrank(C_SEED, m, n, dens, 100, 200.0)
+    else:
+        A = wl.csr_uniform(C_SEED, m, n, dens, planted_rank=100, planted_scale=10.0)
     vdt = torch.bfloat16 if args.dtype == "bf16" else torch.float32
     rp = torch.from_numpy(A["rowptr"]).to(dev)
     ci = torch.from_numpy(A["colidx"]).to(dev)
@@ -604,8 +611,14 @@ def run_csr(args, torch, dev, local, world, rank, dist):
     stream = torch.cuda.current_stream(dev)
     h = ruqlp.Handle(local, stream.cuda_stream)
 
+    lr = None
+    if lowrank:
+        lr = tuple(torch.from_numpy(np.ascontiguousarray(A["lowrank"][key])).float().to(dev)
+                   for key in ("X", "D", "Y"))
+        torch.cuda.synchronize()
+
     def step():
-        return h.decompose_csr(rp, ci, va, (m, n), Om, k, p, q)
+        return h.decompose_csr(rp, ci, va, (m, n), Om, k, p, q, lowrank=lr)
 
     for _ in range(max(args.warmup, 3)):
         step()
@@ -674,15 +687,18 @@ def run_csr(args, torch, dev, local, world, rank, dist):
                 "phase_share": {ph: prof[ph][1] / max(prof["step"][1], 1e-9)
                                 for ph in ("ax", "atx", "orth")}}
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and not lowrank:
         cpu = csr_cpu_baseline(args.dtype)
     if rank == 0:
         out = {"metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world,
                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                "dtype": args.dtype, "data": "synthetic",
-               "config": {"workload": "CSR 200000x100000, uniform 0.1% pattern, N(0,1) values + "
-                                      "planted rank-100 term of scale 10; k=100 p=10 q=1",
+               "config": {"workload": ("CSR 200000x100000, uniform 0.1% pattern, N(0,1) values, "
+                                       "plus a rank-100 term X D Y^T (D 200..2) as factors; "
+                                       "k=100 p=10 q=1") if lowrank else
+                                      ("CSR 200000x100000, uniform 0.1% pattern, N(0,1) values + "
+                                       "planted rank-100 term of scale 10; k=100 p=10 q=1"),
                           "nnz": nnz, "passes": passes, "bytes_A": bytes_a,
                           "values": args.dtype,
                           "l2": "inputs larger than L2 (CSR %.0f MB vs 129 MB L2)" % (bytes_a / 1e6),
@@ -742,8 +758,9 @@ def main():
     import __graft_entry__ as g
     g.build()
     from paper_2209_12464_gb300 import ruqlp
-    if args.workload in ("batch", "serve", "csr"):
-        fn = {"batch": run_batch, "serve": run_serve, "csr": run_csr}[args.workload]
+    if args.workload in ("batch", "serve", "csr", "csrlr"):
+        fn = {"batch": run_batch, "serve": run_serve, "csr": run_csr,
+              "csrlr": run_csr}[args.workload]
         rc = fn(args, torch, dev, local, world, rank, dist)
         if world > 1:
             dist.destroy_process_group()

@@ -40,8 +40,7 @@ struct TcParams {
   int64_t Mout;   // output rows
   int64_t K;      // contraction length
   int dp;         // N (multiple of 16, <= 256)
-  int stages;     // A ring depth
-  int bstages;    // B ring depth
+  int stages;
   float* out;
   int64_t ldo;
   float* frag;    // [P][2][BM][dp]
@@ -266,39 +265,28 @@ __device__ __forceinline__ void tmap_acquire(const CUtensorMap* m) {
 // The warp-specialised pipeline shared by both kernels.  dpmax sizes the
 // shared-memory stages; each item's own dp sets its B bytes and MMA N.
 template <bool TRANS, class W>
-__device__ __forceinline__ void tc_body(const W& w, int* err, int SA, int SB, int dpmax) {
+__device__ __forceinline__ void tc_body(const W& w, int* err, int S, int dpmax) {
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
   const uint32_t base = (raw + 1023u) & ~1023u;
   uint8_t* base_ptr = smem_raw + (base - raw);
-  // A and B have rings of their own: A (streamed from HBM) gets the deep one,
-  // B (the skinny operand, an L2 hit re-read by every CTA) a shallow one
-  const uint32_t b_stage = (uint32_t)dpmax * BK * 2;
-  const uint32_t b_base = base + SA * A_TILE_BYTES;
-  const uint32_t bar_base = b_base + SB * b_stage;
-  // barriers: afull[SA], aempty[SA], bfull[SB], bempty[SB], tfull[2],
-  // tempty[2], drain; then the TMEM address
-  auto afull_bar = [&](int s) { return bar_base + 8u * s; };
-  auto aempty_bar = [&](int s) { return bar_base + 8u * (SA + s); };
-  auto bfull_bar = [&](int s) { return bar_base + 8u * (2 * SA + s); };
-  auto bempty_bar = [&](int s) { return bar_base + 8u * (2 * SA + SB + s); };
-  const int NB = 2 * SA + 2 * SB;
-  auto tfull_bar = [&](int a) { return bar_base + 8u * (NB + a); };
-  auto tempty_bar = [&](int a) { return bar_base + 8u * (NB + 2 + a); };
-  const uint32_t drain_bar = bar_base + 8u * (NB + 4);
-  uint32_t* tmem_slot = (uint32_t*)(base_ptr + (bar_base - base) + 8 * (NB + 5));
+  const uint32_t stage_bytes = A_TILE_BYTES + (uint32_t)dpmax * BK * 2;
+  const uint32_t bar_base = base + S * stage_bytes;
+  // barriers: full[S], empty[S], tfull[2], tempty[2], drain; then the TMEM address
+  auto full_bar = [&](int s) { return bar_base + 8u * s; };
+  auto empty_bar = [&](int s) { return bar_base + 8u * (S + s); };
+  auto tfull_bar = [&](int a) { return bar_base + 8u * (2 * S + a); };
+  auto tempty_bar = [&](int a) { return bar_base + 8u * (2 * S + 2 + a); };
+  const uint32_t drain_bar = bar_base + 8u * (2 * S + 4);
+  uint32_t* tmem_slot = (uint32_t*)(base_ptr + S * stage_bytes + 8 * (2 * S + 5));
   __shared__ int s_abort;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nitems = w.count();
   if (threadIdx.x == 0) {
-    for (int s = 0; s < SA; ++s) {
-      mbar_init(afull_bar(s), 1);
-      mbar_init(aempty_bar(s), 1);
-    }
-    for (int s = 0; s < SB; ++s) {
-      mbar_init(bfull_bar(s), 1);
-      mbar_init(bempty_bar(s), 1);
+    for (int s = 0; s < S; ++s) {
+      mbar_init(full_bar(s), 1);
+      mbar_init(empty_bar(s), 1);
     }
     for (int a = 0; a < 2; ++a) {
       mbar_init(tfull_bar(a), 1);
@@ -326,48 +314,41 @@ __device__ __forceinline__ void tc_body(const W& w, int* err, int SA, int SB, in
   volatile int* abort_flag = &s_abort;
 
   if (warp == 0) {
-    // ---------------- TMA producers: lane 0 loads A, lane 1 loads B ------
-    if (lane < 2) {
-      const bool is_a = lane == 0;
-      const int S = is_a ? SA : SB;
-      const uint64_t pol = is_a ? policy_evict_first() : policy_evict_last();
+    // ---------------- TMA producer ----------------
+    if (lane == 0) {
+      const uint64_t pol_a = policy_evict_first(), pol_b = policy_evict_last();
       int stage = 0;
       uint32_t phase = 0;
       bool ok = true;
       int64_t issued = 0;
-      const CUtensorMap* last = nullptr;
+      const CUtensorMap* last_a = nullptr;
       for (int i = 0; i < nitems && ok; ++i) {
         const TcItem it = w.get(i);
-        const CUtensorMap* map = is_a ? it.mA : it.mB;
-        if (W::kGlobalMaps && map != last) {  // maps written before the launch
-          tmap_acquire(map);
-          last = map;
+        if (W::kGlobalMaps && it.mA != last_a) {  // maps written before the launch
+          tmap_acquire(it.mA);
+          tmap_acquire(it.mB);
+          last_a = it.mA;
         }
-        const uint32_t bytes = is_a ? A_TILE_BYTES : (uint32_t)it.dp * BK * 2;
+        const uint32_t bytes = A_TILE_BYTES + (uint32_t)it.dp * BK * 2;
         for (int kb = it.kb0; kb < it.kb1; ++kb) {
-          const uint32_t full = is_a ? afull_bar(stage) : bfull_bar(stage);
-          if (!mbar_wait(is_a ? aempty_bar(stage) : bempty_bar(stage), phase ^ 1u, abort_flag)) {
-            ok = false;
-            break;
-          }
+          if (!mbar_wait(empty_bar(stage), phase ^ 1u, abort_flag)) { ok = false; break; }
           ++issued;
-          mbar_expect_tx(full, bytes);
-          if (is_a) {
-            const uint32_t sa = base + stage * A_TILE_BYTES;
-            if (!TRANS) {
-              if (!it.a_split) {
-                tma_load_2d(sa, map, full, kb * BK, it.tile * BM, pol);
-              } else {
-                tma_load_2d(sa, map, full, kb * BK, it.tile * BM, pol);
-                tma_load_2d(sa + A_TILE_BYTES / 2, map, full, kb * BK, it.tile * BM + 64, pol);
-              }
+          const uint32_t sa = base + stage * stage_bytes, sb = sa + A_TILE_BYTES;
+          mbar_expect_tx(full_bar(stage), bytes);
+          if (!TRANS) {
+            if (!it.a_split) {
+              tma_load_2d(sa, it.mA, full_bar(stage), kb * BK, it.tile * BM, pol_a);
             } else {
-              tma_load_2d(sa, map, full, it.tile * BM, kb * BK, pol);
-              tma_load_2d(sa + A_TILE_BYTES / 2, map, full, it.tile * BM + 64, kb * BK, pol);
+              tma_load_2d(sa, it.mA, full_bar(stage), kb * BK, it.tile * BM, pol_a);
+              tma_load_2d(sa + A_TILE_BYTES / 2, it.mA, full_bar(stage), kb * BK,
+                          it.tile * BM + 64, pol_a);
             }
           } else {
-            tma_load_2d(b_base + stage * b_stage, map, full, kb * BK, 0, pol);
+            tma_load_2d(sa, it.mA, full_bar(stage), it.tile * BM, kb * BK, pol_a);
+            tma_load_2d(sa + A_TILE_BYTES / 2, it.mA, full_bar(stage), it.tile * BM + 64,
+                        kb * BK, pol_a);
           }
+          tma_load_2d(sb, it.mB, full_bar(stage), kb * BK, 0, pol_b);
           if (++stage == S) { stage = 0; phase ^= 1u; }
         }
       }
@@ -383,15 +364,15 @@ __device__ __forceinline__ void tc_body(const W& w, int* err, int SA, int SB, in
           if (st2 == 0) { st2 = S; ph2 ^= 1u; }
           --st2;
           volatile int never = 0;
-          mbar_wait(is_a ? afull_bar(st2) : bfull_bar(st2), ph2, &never);
+          mbar_wait(full_bar(st2), ph2, &never);
         }
       }
     }
   } else if (warp == 1) {
     // ---------------- MMA issuer ----------------
     if (lane == 0) {
-      int sa_i = 0, sb_i = 0;
-      uint32_t pa = 0, pb = 0;
+      int stage = 0;
+      uint32_t phase = 0;
       bool ok = true;
       for (int i = 0; i < nitems && ok; ++i) {
         const TcItem it = w.get(i);
@@ -402,13 +383,9 @@ __device__ __forceinline__ void tc_body(const W& w, int* err, int SA, int SB, in
         tc_fence_after();
         const uint32_t tmem_d = tmem_base + (uint32_t)(acc * 256);
         for (int kb = it.kb0; kb < it.kb1; ++kb) {
-          if (!mbar_wait(afull_bar(sa_i), pa, abort_flag) ||
-              !mbar_wait(bfull_bar(sb_i), pb, abort_flag)) {
-            ok = false;
-            break;
-          }
+          if (!mbar_wait(full_bar(stage), phase, abort_flag)) { ok = false; break; }
           tc_fence_after();
-          const uint32_t sa = base + sa_i * A_TILE_BYTES, sb = b_base + sb_i * b_stage;
+          const uint32_t sa = base + stage * stage_bytes, sb = sa + A_TILE_BYTES;
 #pragma unroll
           for (int kk = 0; kk < BK / 16; ++kk) {
             uint64_t ad, bd;
@@ -417,10 +394,8 @@ __device__ __forceinline__ void tc_body(const W& w, int* err, int SA, int SB, in
             bd = sdesc(sb + kk * 32, 16, 1024);
             mma_bf16(tmem_d, ad, bd, idesc, (kb > it.kb0 || kk > 0) ? 1u : 0u);
           }
-          mma_commit(aempty_bar(sa_i));
-          mma_commit(bempty_bar(sb_i));
-          if (++sa_i == SA) { sa_i = 0; pa ^= 1u; }
-          if (++sb_i == SB) { sb_i = 0; pb ^= 1u; }
+          mma_commit(empty_bar(stage));
+          if (++stage == S) { stage = 0; phase ^= 1u; }
         }
         if (!ok) break;
         mma_commit(tfull_bar(acc));
@@ -478,16 +453,15 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
           const __grid_constant__ TcParams p) {
   const WorkSingle w{&tmA, &tmB, &p};
-  tc_body<TRANS>(w, p.err, p.stages, p.bstages, p.dp);
+  tc_body<TRANS>(w, p.err, p.stages, p.dp);
 }
 
 template <bool TRANS>
 __global__ void __launch_bounds__(NTHREADS, 1)
 k_btc_gemm(const BTcTile* __restrict__ list, int n, const BMat* __restrict__ T,
-           const CUtensorMap* __restrict__ maps, int dst, int stages, int bstages, int dpmax,
-           int* err) {
+           const CUtensorMap* __restrict__ maps, int dst, int stages, int dpmax, int* err) {
   const WorkBatch w{list, n, T, maps, dst, TRANS};
-  tc_body<TRANS>(w, err, stages, bstages, dpmax);
+  tc_body<TRANS>(w, err, stages, dpmax);
 }
 
 // Sum the stream-K fragments of each tail tile in CTA order into the output.
@@ -836,22 +810,6 @@ __global__ void __launch_bounds__(256) k_gram_tc_reduce(const float* __restrict_
   }
 }
 
-// Ring depths of the product kernels for a B tile of dpmax columns: three B
-// stages (L2 hits), as many A stages as fit in 212 KB (at most 12); the
-// dynamic shared memory size including alignment slack and barriers.
-bool ring_sizes(int dpmax, int* SA, int* SB, size_t* smem) {
-  const size_t b_stage = (size_t)dpmax * BK * 2;
-  const size_t budget = 212 * 1024;
-  *SB = 3;
-  if (3 * b_stage >= budget) return false;
-  int sa = (int)((budget - 3 * b_stage) / A_TILE_BYTES);
-  if (sa > 12) sa = 12;
-  if (sa < 2) return false;
-  *SA = sa;
-  *smem = 1024 + (size_t)sa * A_TILE_BYTES + 3 * b_stage + 8 * (2 * sa + 2 * 3 + 5) + 16;
-  return true;
-}
-
 }  // namespace
 
 bool tc_supported(const void* A, int64_t lda, int dp) {
@@ -928,8 +886,12 @@ cudaError_t tc_gemm(bool trans, const void* A, int64_t lda, int64_t m, int64_t n
   p.full_waves = p.T / P;
   p.tail = p.T - p.full_waves * P;
   p.U = (int64_t)p.tail * p.KB;
-  size_t smem;
-  if (!ring_sizes(dp, &p.stages, &p.bstages, &smem)) return cudaErrorInvalidValue;
+  const size_t stage_bytes = A_TILE_BYTES + (size_t)dp * BK * 2;
+  int stages = (int)((200 * 1024) / stage_bytes);
+  if (stages > 8) stages = 8;
+  if (stages < 2) return cudaErrorInvalidValue;
+  p.stages = stages;
+  const size_t smem = 1024 + stages * stage_bytes + 8 * (2 * stages + 5) + 16;
   cudaError_t e = trans ? cudaFuncSetAttribute(k_tc_gemm<true>,
                                                cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                (int)smem)
@@ -969,9 +931,10 @@ cudaError_t btc_gemm(bool trans, const BMat* T, int count, const BTcTile* list, 
                      const void* maps, int src, int dst, int dpmax, int* err, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
   if (dpmax < 16 || dpmax > 256 || dpmax % 16) return cudaErrorInvalidValue;
-  int stages, bstages;
-  size_t smem;
-  if (!ring_sizes(dpmax, &stages, &bstages, &smem)) return cudaErrorInvalidValue;
+  const size_t stage_bytes = A_TILE_BYTES + (size_t)dpmax * BK * 2;
+  int stages = (int)((200 * 1024) / stage_bytes);
+  if (stages > 8) stages = 8;
+  const size_t smem = 1024 + stages * stage_bytes + 8 * (2 * stages + 5) + 16;
   cudaError_t e = trans ? cudaFuncSetAttribute(k_btc_gemm<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    (int)smem)
             : cudaFuncSetAttribute(k_btc_gemm<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -980,10 +943,8 @@ cudaError_t btc_gemm(bool trans, const BMat* T, int count, const BTcTile* list, 
   int P = sm_count();
   if (n < P) P = n;
   const CUtensorMap* mp = (const CUtensorMap*)maps;
-  if (trans)
-    k_btc_gemm<true><<<P, NTHREADS, smem, st>>>(list, n, T, mp, dst, stages, bstages, dpmax, err);
-  else
-    k_btc_gemm<false><<<P, NTHREADS, smem, st>>>(list, n, T, mp, dst, stages, bstages, dpmax, err);
+  if (trans) k_btc_gemm<true><<<P, NTHREADS, smem, st>>>(list, n, T, mp, dst, stages, dpmax, err);
+  else k_btc_gemm<false><<<P, NTHREADS, smem, st>>>(list, n, T, mp, dst, stages, dpmax, err);
   count_launch();
   return cudaGetLastError();
 }
