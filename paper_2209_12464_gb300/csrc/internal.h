@@ -1,6 +1,7 @@
 // Internal launchers of the RU-QLP CUDA library (not part of the C ABI).
 #pragma once
 
+#include <cuda.h>
 #include <functional>
 
 #include "common.cuh"
@@ -171,9 +172,16 @@ cudaError_t btrsm(const BMat* T, const int* prefix, int total, int count, int sr
                   int dmax, cudaStream_t st, bool make_bt = false);
 // Tensor-core Gram C = Y^T Y of a tall FP32 Y (M >= 8192, d <= 256, ld a
 // multiple of 4, 16-byte aligned) via a three-way BF16 split; part holds
-// gram_tc_ctas(M) * d * d FP32 slab sums; C (FP64) and Cf (FP32) the result.
+// the FP32 slab sums (gram_tc_part_bytes(d) bytes at most); C (FP64) and Cf
+// (FP32) the result.
 bool gram_tc_supported(int64_t M, int d, int64_t ldy, const void* Y);
 int gram_tc_ctas(int64_t M);
+size_t gram_tc_part_bytes(int d);
+// 2-D BF16 tensor map (128-byte swizzle) over a row-major [outer][inner]
+// array with leading dimension ld_elems; box box_inner x box_outer.
+bool make_map(CUtensorMap* m, const void* ptr, uint64_t inner, uint64_t outer, uint64_t ld_elems,
+              uint32_t box_inner, uint32_t box_outer);
+int sm_count();
 cudaError_t gram_tc(const float* Y, int64_t ldy, int64_t M, int d, float* part, double* C,
                     float* Cf, int* err, cudaStream_t st);
 // SVD of a d x d matrix by one-sided Jacobi in one CTA (type t: F32/F64):

@@ -3,13 +3,13 @@
 //
 //  * k_chol_tiles: one CTA factors the d x d Gram G (+ shift I) = R^T R,
 //    blocked in 32 x 32 tiles held in shared memory (upper block triangle,
-//    padded to a multiple of 32 with the identity).  Each diagonal tile is
-//    factored and inverted by one warp in registers (row broadcasts through
-//    shared memory); the panel solves (products with the tile inverse) and
-//    trailing updates are 32 x 32 tile products spread over all warps with
-//    128-bit broadcast loads, so the factorisation needs three block barriers
-//    per tile row, not per column.  The Gram arrives in FP32 (rounded by the
-//    slab reduction), so the kernel does no FP64 arithmetic.
+//    padded to a multiple of 32 with the identity; loaded with cp.async).
+//    Each diagonal tile is factored and inverted by one warp in registers
+//    (row broadcasts through shared memory); the panel solves (products with
+//    the tile inverse) and trailing updates are 32 x 16 half-tile products,
+//    one per warp, 4 x 4 outputs per lane, so the factorisation needs three
+//    block barriers per tile row, not per column.  The Gram arrives in FP32
+//    (rounded by the slab reduction), so the kernel does no FP64 arithmetic.
 //  * k_trsm_tiles: Q = Y R^{-1} by blocked forward substitution with those
 //    tiles (rows of Y staged transposed in shared memory, so Q may overwrite
 //    Y).
@@ -30,23 +30,24 @@ constexpr size_t TILE_FLOATS = (size_t)TB * TP;
 
 __device__ __forceinline__ int bidx(int I, int J, int nb) { return I * nb - (I * (I - 1)) / 2 + (J - I); }
 
-// acc[r] (r = r0..r0+7) += sum_k A[k][r] * bcol[k] for one lane's column
-// bcol (in registers).  A is a 32 x 32 tile in shared memory (pitch TP); each
-// 128-bit load of A serves 4 rows, and the 8 rows are independent chains.
-__device__ __forceinline__ void tile_tn8(const float* __restrict__ A, int r0, const float (&bcol)[TB],
-                                         float (&acc)[8]) {
+// acc[i][j] = sum_k A[k][r0 + i] B[k][c0 + j] for a lane's 4 x 4 block of a
+// 32 x 32 tile product A^T B (tiles in shared memory, pitch TP), k ascending
+// from zero; two 128-bit loads feed 16 multiply-adds.
+__device__ __forceinline__ void tile_tn44(const float* __restrict__ A, const float* __restrict__ B,
+                                          int r0, int c0, float (&acc)[4][4]) {
 #pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+#pragma unroll 8
   for (int k = 0; k < TB; ++k) {
-    const float4 a0 = *reinterpret_cast<const float4*>(A + k * TP + r0);
-    const float4 a1 = *reinterpret_cast<const float4*>(A + k * TP + r0 + 4);
-    acc[0] = fmaf(a0.x, bcol[k], acc[0]);
-    acc[1] = fmaf(a0.y, bcol[k], acc[1]);
-    acc[2] = fmaf(a0.z, bcol[k], acc[2]);
-    acc[3] = fmaf(a0.w, bcol[k], acc[3]);
-    acc[4] = fmaf(a1.x, bcol[k], acc[4]);
-    acc[5] = fmaf(a1.y, bcol[k], acc[5]);
-    acc[6] = fmaf(a1.z, bcol[k], acc[6]);
-    acc[7] = fmaf(a1.w, bcol[k], acc[7]);
+    const float4 a = *reinterpret_cast<const float4*>(A + k * TP + r0);
+    const float4 b = *reinterpret_cast<const float4*>(B + k * TP + c0);
+    const float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
   }
 }
 
@@ -56,15 +57,18 @@ __device__ __forceinline__ void load_col(const float* __restrict__ T, int lane, 
 }
 
 // One warp factors the 32 x 32 tile B = R^T R in registers (lane c owns
-// column c) and writes R (upper) back and S = R^{-1} (upper) to Sout.
-// Step k broadcasts row k of the partially reduced tile through the shared
-// row buffer rb (one store per lane, 128-bit broadcast loads of the whole
-// row issued together), so every lane forms r_ki itself; there are no
-// shuffles and no branches in the loop.  Reciprocal square roots and
-// reciprocals replace IEEE sqrt/divide (the factor only has to be consistent
-// with the solve that uses it).  A non-positive pivot is replaced by
-// bad_fill; the return value (same in every lane) reports whether that
-// happened.
+// column c) and writes R (upper) back and S = R^{-1} (upper, row-major) to
+// Sout.  Step k broadcasts row k of the partially reduced tile through the
+// shared row buffer rb (one store per lane, 128-bit broadcast loads of the
+// whole row issued together) and the pivot by a shuffle, so every lane forms
+// r_ki itself; there are no branches or masks in the loop.  The inverse comes
+// out of the same elimination: the row operations that reduce B (row i -=
+// (b_ki / b_kk) row k) are applied to the identity too, which leaves the
+// inverse of the unit lower factor; lane c's copy of column c, scaled by
+// 1 / r_jj as pivot j is formed, is row c of S.  Reciprocal square roots
+// replace IEEE sqrt/divide (the factor only has to be consistent with the
+// solve that uses it).  A non-positive pivot is replaced by bad_fill; the
+// return value (same in every lane) reports whether that happened.
 __device__ __forceinline__ void load_row(const float* __restrict__ p, float (&r)[TB]) {
 #pragma unroll
   for (int q = 0; q < TB / 4; ++q) {
@@ -76,61 +80,47 @@ __device__ __forceinline__ void load_row(const float* __restrict__ p, float (&r)
   }
 }
 
-__device__ bool factor_tile(float* __restrict__ B, float* __restrict__ Sout, float* __restrict__ dinv,
-                            float* __restrict__ rb, int lane, float bad_fill) {
-  float col[TB];
+__device__ __noinline__ bool factor_tile(float* __restrict__ B, float* __restrict__ Sout,
+                                         float* __restrict__ rb, int lane, float bad_fill) {
+  float col[TB], ecol[TB];
   load_col(B, lane, col);
-  float myinv = 0.f;  // 1 / R[lane][lane]
+#pragma unroll
+  for (int i = 0; i < TB; ++i) ecol[i] = (i == lane) ? 1.f : 0.f;
   bool bad = false;
 #pragma unroll
   for (int k = 0; k < TB; ++k) {
     __syncwarp();
     rb[lane] = col[k];  // row k of the current tile, lane c holds B[k][c]
+    float piv = __shfl_sync(0xffffffffu, col[k], k);
     __syncwarp();
     float row[TB];
     load_row(rb, row);
-    float piv = row[k];
     const bool nonpos = !(piv > 0.f) || !(piv < 3.0e38f);
     bad = bad || nonpos;
     piv = nonpos ? bad_fill : piv;
     const float rinv = rsqrtf(piv);
-    const float rkc = (lane == k) ? piv * rinv : col[k] * rinv;  // r_kc for c >= k
-    myinv = (lane == k) ? rinv : myinv;
-    col[k] = (lane >= k) ? rkc : col[k];
+    const float rkc = ((lane == k) ? piv : col[k]) * rinv;  // r_kc for c >= k
+    col[k] = rkc;
+    const float skc = ecol[k] * rinv;  // S[c][k]
+    ecol[k] = skc;
+    // b_ic -= r_ki r_kc with r_ki = b_ki / sqrt(piv), and the same row
+    // operation on the identity: one multiply-add per entry each.  The
+    // entries of B below the diagonal (i > c) are updated too, without a
+    // mask: they are never read as row values (step k reads only lanes >= k)
+    // and are zeroed on the way out.
+    const float tkc = rkc * rinv, tec = skc * rinv;
 #pragma unroll
     for (int i = k + 1; i < TB; ++i) {
-      const float rki = row[i] * rinv;
-      const float upd = fmaf(-rki, rkc, col[i]);
-      col[i] = (lane >= i) ? upd : col[i];
+      col[i] = fmaf(-row[i], tkc, col[i]);
+      ecol[i] = fmaf(-row[i], tec, ecol[i]);
     }
   }
-  // R row-major into B; R transposed (column c of R as row c) into Sout,
-  // which the inverse below reads before overwriting it
 #pragma unroll
   for (int r = 0; r < TB; ++r) {
-    const float v = (r <= lane) ? col[r] : 0.f;
-    B[r * TP + lane] = v;
-    Sout[lane * TP + r] = v;
-  }
-  dinv[lane] = myinv;
-  __syncwarp();
-  // S = R^{-1}, right-looking: lane c solves R x = e_c from the bottom;
-  // acc[j] -= R[j][r] x[r] for j < r are independent multiply-adds
-  float acc[TB];
-#pragma unroll
-  for (int r = 0; r < TB; ++r) acc[r] = (r == lane) ? 1.f : 0.f;
-#pragma unroll
-  for (int r = TB - 1; r >= 0; --r) {
-    const float xr = acc[r] * dinv[r];
-    acc[r] = xr;
-    float rc[TB];  // column r of R (rows j < r are used)
-    load_row(Sout + r * TP, rc);
-#pragma unroll
-    for (int j = 0; j < r; ++j) acc[j] = fmaf(-rc[j], xr, acc[j]);
+    B[r * TP + lane] = (r <= lane) ? col[r] : 0.f;
+    Sout[lane * TP + r] = (r >= lane) ? ecol[r] : 0.f;
   }
   __syncwarp();
-#pragma unroll
-  for (int r = 0; r < TB; ++r) Sout[r * TP + lane] = acc[r];
   return !bad;
 }
 
@@ -146,100 +136,152 @@ __device__ __forceinline__ void chol_body(const float* __restrict__ G, int d, do
   extern __shared__ __align__(16) float sm[];
   __shared__ float s_shift;
   __shared__ int s_bad, s_rankdef;
-  __shared__ __align__(16) float s_dinv[TB];
   __shared__ __align__(16) float s_row[TB];
+  __shared__ unsigned char s_tI[MAXNB * (MAXNB + 1) / 2], s_tJ[MAXNB * (MAXNB + 1) / 2];
   const int nb = (d + TB - 1) / TB;
   const int ntiles = nb * (nb + 1) / 2;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = NT / 32;
   auto tile = [&](int I, int J) { return sm + (size_t)bidx(I, J, nb) * TILE_FLOATS; };
-  // the current diagonal tile's inverse (shared; copied out once formed)
+  // the current diagonal tile's inverse (shared; copied out once used)
   float* const dinv_sm = sm + (size_t)ntiles * TILE_FLOATS;
+  // a lane's 4 x 4 block within a 32 x 16 half tile: rows 4 rg.., columns 4 cg..
+  const int rg = lane >> 2, cg = lane & 3;
 
-  if (warp == 0) {  // shift = shift_rel * trace(G)
-    float t = 0.f;
-    for (int i = lane; i < d; i += 32) t += G[(size_t)i * d + i];
-    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-    if (lane == 0) {
-      float sh = (float)shift_rel * t;
-      if (!(sh > 0.f)) sh = 1e-30f;
-      s_shift = sh;
-      s_rankdef = 0;
-    }
+  if (tid == 0) s_rankdef = 0;
+  if (tid < ntiles) {  // packed tile index -> (I, J)
+    int I = 0, tt = tid;
+    while (tt >= nb - I) { tt -= nb - I; ++I; }
+    s_tI[tid] = (unsigned char)I;
+    s_tJ[tid] = (unsigned char)(I + tt);
   }
+  // rows of G start on 16 bytes when d % 4 == 0: then whole 4-column chunks
+  // are either inside G or past its edge
+  const bool vec = (d % 4 == 0) && (((uintptr_t)G & 15) == 0);
+  // item u of a step's trailing update (rem tile rows left): tile (I, J),
+  // K < I <= J, column half u & 1
+  auto update = [&](int K, int rem, int u) {
+    int I = 0, tt = u >> 1;
+    while (tt >= rem - I) { tt -= rem - I; ++I; }
+    I += K + 1;
+    const int J = I + tt, c0 = (u & 1) * 16 + cg * 4;
+    float acc[4][4];
+    tile_tn44(tile(K, I), tile(K, J), rg * 4, c0, acc);
+    float* C = tile(I, J);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      float4* pc = reinterpret_cast<float4*>(C + (rg * 4 + i) * TP + c0);
+      float4 v = *pc;
+      v.x -= acc[i][0];
+      v.y -= acc[i][1];
+      v.z -= acc[i][2];
+      v.w -= acc[i][3];
+      *pc = v;
+    }
+  };
   int attempt = force_shift ? 1 : 0;
   for (; attempt < 2; ++attempt) {
     __syncthreads();
-    const float add = attempt ? s_shift : 0.f;
-    // upper block triangle of G + shift I (identity padding): one warp per
-    // tile, lane = column, all 32 row loads issued before the stores
-    for (int t = warp; t < ntiles; t += nw) {
-      int I = 0, tt = t;
-      while (tt >= nb - I) { tt -= nb - I; ++I; }
-      const int J = I + tt;
-      const int j = J * TB + lane;
-      float* T = tile(I, J);
+    // upper block triangle of G
+    if (vec) {
+      // 16-byte cp.async chunks (zero-filled past the edge), all in flight at once
+      for (int e = tid; e < ntiles * TB * 8; e += NT) {
+        const int t = e >> 8, r = (e >> 3) & 31, c4 = (e & 7) * 4;
+        const int I = s_tI[t], J = s_tJ[t];
+        const int i = I * TB + r, j = J * TB + c4;
+        const bool in = i < d && j < d;
+        const float* src = in ? G + (size_t)i * d + j : G;
+        const uint32_t dst = (uint32_t)__cvta_generic_to_shared(tile(I, J) + r * TP + c4);
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src),
+                     "r"(in ? 16 : 0)
+                     : "memory");
+      }
+      asm volatile("cp.async.commit_group;" ::: "memory");
+      asm volatile("cp.async.wait_group 0;" ::: "memory");
+    } else {
+      // one warp per tile, lane = column, 16 row loads in flight per lane
+      for (int t = warp; t < ntiles; t += nw) {
+        const int I = s_tI[t], J = s_tJ[t];
+        const int j = J * TB + lane;
+        float* T = tile(I, J);
 #pragma unroll
-      for (int h = 0; h < TB; h += 16) {  // 16 loads in flight per lane
-        float v[16];
+        for (int h = 0; h < TB; h += 16) {
+          float v[16];
 #pragma unroll
-        for (int r = 0; r < 16; ++r) {
-          const int i = I * TB + h + r;
-          v[r] = (i < d && j < d) ? G[(size_t)i * d + j] : 0.f;
-        }
+          for (int r = 0; r < 16; ++r) {
+            const int i = I * TB + h + r;
+            v[r] = (i < d && j < d) ? G[(size_t)i * d + j] : 0.f;
+          }
 #pragma unroll
-        for (int r = 0; r < 16; ++r) {
-          const int i = I * TB + h + r;
-          T[(h + r) * TP + lane] = (i == j) ? ((i < d) ? v[r] + add : 1.f) : v[r];
+          for (int r = 0; r < 16; ++r) T[(h + r) * TP + lane] = v[r];
         }
       }
     }
-    if (tid == 0) s_bad = 0;
     __syncthreads();
-    for (int K = 0; K < nb; ++K) {
-      if (warp == 0) {  // (a) diagonal tile: factor, inverse (shared), inverse out
-        const bool ok = factor_tile(tile(K, K), dinv_sm, s_dinv, s_row, lane,
-                                    attempt == 0 ? 1.f : (float)s_shift);
-        __syncwarp();
-        float* gi = tiles + (size_t)(ntiles + K) * TB * TB;
+    if (warp == 0) {  // shift = shift_rel * trace(G), from the loaded tiles
+      float t = 0.f;
+      for (int i = lane; i < d; i += 32) t += tile(i / TB, i / TB)[(i % TB) * (TP + 1)];
+      for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+      if (lane == 0) {
+        float sh = (float)shift_rel * t;
+        if (!(sh > 0.f)) sh = 1e-30f;
+        s_shift = sh;
+        s_bad = 0;
+      }
+    }
+    __syncthreads();
+    const float add = attempt ? s_shift : 0.f;
+    for (int i = tid; i < nb * TB; i += NT) {  // + shift I; identity padding
+      float* p = tile(i / TB, i / TB) + (i % TB) * (TP + 1);
+      *p = (i < d) ? *p + add : 1.f;
+    }
+    __syncthreads();
+    const float fill = attempt == 0 ? 1.f : add;
+    // Step K = -1 only factors the first diagonal tile; step K >= 0 does the
+    // panel of tile row K, the trailing update, then the next diagonal tile.
+    // (Overlapping that factorisation with the trailing update measured no
+    // faster: the one-warp chain slows down as much as the overlap saves.)
+    // The factorisation has one call site (its unrolled code is large).
+    for (int K = -1; K < nb; ++K) {
+      if (K >= 0) {
+        if (s_bad) break;
+        // (b) panel B_KJ <- R_KK^{-T} B_KJ, items (J, column half): each item
+        // reads and writes only its own 32 x 16 block, so a warp barrier
+        // separates its reads from its writes.  The last warp also copies
+        // the diagonal inverse out.
+        const int npan = 2 * (nb - K - 1);
+        for (int u = warp; u < npan; u += nw) {
+          float* B = tile(K, K + 1 + (u >> 1));
+          const int c0 = (u & 1) * 16 + cg * 4;
+          float acc[4][4];
+          tile_tn44(dinv_sm, B, rg * 4, c0, acc);
+          __syncwarp();
+#pragma unroll
+          for (int i = 0; i < 4; ++i)
+            *reinterpret_cast<float4*>(B + (rg * 4 + i) * TP + c0) =
+                make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
+          __syncwarp();
+        }
+        if (warp == nw - 1) {
+          float* gi = tiles + (size_t)(ntiles + K) * TB * TB;
 #pragma unroll 8
-        for (int r = 0; r < TB; ++r) gi[r * TB + lane] = dinv_sm[r * TP + lane];
-        if (lane == 0 && !ok) {
-          if (attempt == 0) s_bad = 1;  // retry on G + shift I
-          else s_rankdef = 1;           // pivots replaced by the shift
+          for (int r = 0; r < TB; ++r) gi[r * TB + lane] = dinv_sm[r * TP + lane];
         }
+        __syncthreads();
       }
-      __syncthreads();
-      if (s_bad) break;
-      // (b) panel B_KJ <- R_KK^{-T} B_KJ: one warp per tile; each lane reads
-      // and writes only its own column
-      for (int J = K + 1 + warp; J < nb; J += nw) {
-        float* B = tile(K, J);
-        float bc[TB];
-        load_col(B, lane, bc);
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-          tile_tn8(dinv_sm, q * 8, bc, acc);
-#pragma unroll
-          for (int i = 0; i < 8; ++i) B[(q * 8 + i) * TP + lane] = acc[i];
-        }
-      }
-      __syncthreads();
-      // (c) trailing update B_IJ -= B_KI^T B_KJ, items (I, J, 8-row slice)
+      // (c) trailing update B_IJ -= B_KI^T B_KJ, then the next diagonal tile
       const int rem = nb - K - 1;
-      const int nupd = rem * (rem + 1) / 2 * 4;
-      for (int u = warp; u < nupd; u += nw) {
-        int I = 0, tt = u / 4;
-        while (tt >= rem - I) { tt -= rem - I; ++I; }
-        I += K + 1;
-        const int J = I + tt, r0 = (u % 4) * 8;
-        float bc[TB];
-        load_col(tile(K, J), lane, bc);
-        float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-        tile_tn8(tile(K, I), r0, bc, acc);
-        float* C = tile(I, J);
-#pragma unroll
-        for (int i = 0; i < 8; ++i) C[(r0 + i) * TP + lane] -= acc[i];
+      if (rem > 0) {
+        if (K >= 0) {
+          for (int u = warp; u < rem * (rem + 1); u += nw) update(K, rem, u);
+          __syncthreads();
+        }
+        if (warp == 0) {
+          const bool ok = factor_tile(tile(K + 1, K + 1), dinv_sm, s_row, lane, fill);
+          if (lane == 0 && !ok) {
+            if (attempt == 0) s_bad = 1;  // retry on G + shift I
+            else s_rankdef = 1;           // pivots replaced by the shift
+          }
+        }
       }
       __syncthreads();
     }

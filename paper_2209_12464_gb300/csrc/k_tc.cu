@@ -26,6 +26,7 @@
 #include <string.h>
 
 #include "internal.h"
+#include "tcgen05.cuh"
 
 namespace ruqlp {
 namespace {
@@ -34,7 +35,6 @@ constexpr int BM = 128;       // rows of an output tile (MMA M)
 constexpr int BK = 64;        // K per stage (one 128-byte swizzle row of BF16)
 constexpr int NTHREADS = 192;
 constexpr int A_TILE_BYTES = BM * BK * 2;  // 16 KB
-constexpr uint64_t WAIT_NS = 2000000000ull;
 
 struct TcParams {
   int64_t Mout;   // output rows
@@ -48,117 +48,6 @@ struct TcParams {
   int64_t U;      // stream-K units = tail * KB
   int* err;
 };
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
-__device__ __forceinline__ uint64_t gtimer() {
-  uint64_t t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
-               : "memory");
-}
-__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}"
-      : "=r"(ok)
-      : "r"(bar), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-// Bounded wait on an mbarrier phase; false on timeout or when another role
-// of the CTA has already given up.
-__device__ __noinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag) {
-  if (mbar_try_wait(bar, parity)) return true;
-  const uint64_t t0 = gtimer();
-  for (uint32_t it = 1;; ++it) {
-    if (mbar_try_wait(bar, parity)) return true;
-    if ((it & 63) == 0) {
-      if (*abort_flag) return false;
-      if (gtimer() - t0 > WAIT_NS) return false;
-    }
-  }
-}
-
-__device__ __forceinline__ uint64_t policy_evict_first() {
-  uint64_t p;
-  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
-  return p;
-}
-__device__ __forceinline__ uint64_t policy_evict_last() {
-  uint64_t p;
-  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
-  return p;
-}
-__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, uint32_t bar,
-                                            int x, int y, uint64_t policy) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint"
-      " [%0], [%1, {%3, %4}], [%2], %5;" ::"r"(dst),
-      "l"((uint64_t)map), "r"(bar), "r"(x), "r"(y), "l"(policy)
-      : "memory");
-}
-
-__device__ __forceinline__ void tc_fence_before() {
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-}
-__device__ __forceinline__ void tc_fence_after() {
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-}
-
-// Shared-memory matrix descriptor (tcgen05): start address, leading and
-// stride byte offsets, version 1, 128-byte swizzle.
-__device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
-  return (uint64_t)((saddr & 0x3FFFF) >> 4) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
-         ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | (1ull << 46) | (2ull << 61);
-}
-
-// Instruction descriptor, kind::f16: BF16 x BF16 -> FP32, M = 128, N = n.
-__device__ __forceinline__ uint32_t idesc_bf16(int n, bool a_mn_major) {
-  return (1u << 4) | (1u << 7) | (1u << 10) | ((a_mn_major ? 1u : 0u) << 15) |
-         ((uint32_t)(n >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
-}
-
-__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc,
-                                         uint32_t idesc, uint32_t accumulate) {
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "setp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
-      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
-      : "memory");
-}
-__device__ __forceinline__ void mma_commit(uint32_t bar) {
-  asm volatile(
-      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
-      : "memory");
-}
-
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
-  uint32_t r[16];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
-      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
-        "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
-}
 
 // A CTA's work, generated on the fly: items 0..full_waves-1 are whole tiles
 // (data parallel), then at most two stream-K segments of tail tiles.
@@ -465,8 +354,9 @@ k_btc_gemm(const BTcTile* __restrict__ list, int n, const BMat* __restrict__ T,
 }
 
 // Sum the stream-K fragments of each tail tile in CTA order into the output.
-// One block per (tail tile, row), one thread per column; thread 0 lists the
-// tile's contributing CTAs and fragment slots first.
+// One block per (tail tile, 4 rows), one thread per 4 columns (16-byte loads,
+// up to 16 contributors in flight); thread 0 lists the tile's contributing
+// CTAs and fragment slots first.
 __global__ void __launch_bounds__(256) k_tc_fixup(TcParams p, int P) {
   __shared__ int s_src[512];
   __shared__ int s_n;
@@ -487,25 +377,31 @@ __global__ void __launch_bounds__(256) k_tc_fixup(TcParams p, int P) {
     s_n = n;
   }
   __syncthreads();
+  // block (tt, y): rows 4 y .. 4 y + 3 of the tile, a thread per 4 columns
   const int tile = p.full_waves * P + tt;
-  const int r = blockIdx.y;
+  const int q4 = p.dp / 4;
+  const int r = blockIdx.y * 4 + threadIdx.x / 64, c4 = threadIdx.x % 64;
   const int n = s_n;
   const int64_t gr = (int64_t)tile * BM + r;
-  if (gr >= p.Mout) return;
-  for (int col = threadIdx.x; col < p.dp; col += blockDim.x) {
-    // sixteen independent loads in flight, summed in contributor order
-    float s = 0.f;
-    int i = 0;
-    for (; i + 16 <= n; i += 16) {
-      float v[16];
+  if (gr >= p.Mout || c4 >= q4) return;
+  const float4* frag = reinterpret_cast<const float4*>(p.frag);
+  // sixteen 16-byte loads in flight, summed in contributor order
+  float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
+  for (int i = 0; i < n; i += 16) {
+    float4 v[16];
 #pragma unroll
-      for (int u = 0; u < 16; ++u) v[u] = p.frag[((int64_t)s_src[i + u] * BM + r) * p.dp + col];
+    for (int u = 0; u < 16; ++u)
+      if (i + u < n) v[u] = frag[((int64_t)s_src[i + u] * BM + r) * q4 + c4];
 #pragma unroll
-      for (int u = 0; u < 16; ++u) s += v[u];
-    }
-    for (; i < n; ++i) s += p.frag[((int64_t)s_src[i] * BM + r) * p.dp + col];
-    p.out[gr * p.ldo + col] = s;
+    for (int u = 0; u < 16; ++u)
+      if (i + u < n) {
+        s.x += v[u].x;
+        s.y += v[u].y;
+        s.z += v[u].z;
+        s.w += v[u].w;
+      }
   }
+  *reinterpret_cast<float4*>(p.out + gr * p.ldo + 4 * c4) = s;
 }
 
 // dst[c][r] = bf16(src[r][c]) for c < cols, 0 for cols <= c < dp (r < rows).
@@ -529,6 +425,8 @@ __global__ void k_transpose_bf16(const TS* __restrict__ src, int64_t lds, int64_
     if (c < dp && r < rows) dst[(int64_t)c * ldd + r] = __float2bfloat16_rn(t[threadIdx.x][i]);
   }
 }
+
+}  // namespace
 
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
@@ -567,6 +465,8 @@ int sm_count() {
   return n;
 }
 
+namespace {
+
 // ---------------------------------------------------------------------------
 // Gram of a tall FP32 matrix on the tensor cores (orth()'s Y^T Y, Section II-A):
 // Y (M x dp, FP32, dp <= 256) is split on the fly into three BF16 parts,
@@ -575,24 +475,18 @@ int sm_count() {
 //   Y^T Y ~= h'h + h'm + m'h + m'm + h'l + l'h
 // (the dropped m'l, l'm, l'l terms are below 2^-26 of |y_i||y_j|).  Products
 // of BF16 parts are exact in FP32, so the result matches an FP32 Gram.
-// Each CTA (256 threads) owns a slab of rows; per 64-row chunk all threads
+// Each CTA (512 threads) owns a slab of rows; per 64-row chunk all threads
 // write the three parts into a 128B-swizzled shared-memory stage (both
 // operands MN-major: rows of Y are the contraction), and thread 0 issues
 // 2 (M tiles of 128 Gram rows) x 6 (part pairs) x 4 (K = 16 rows) MMAs with
 // N = dp into TMEM, while the threads convert the next chunk into the other
 // stage.  Slab sums (FP32) go to part[c]; k_gram_tc_reduce adds them in CTA
-// order in FP64.
-constexpr int GT_THREADS = 256;
+// order with compensated FP32 summation.
+constexpr int GT_THREADS = 512;
 constexpr int GT_ROWS = 64;                      // rows per chunk
 constexpr uint32_t GT_BOX = 64 * 128;            // [64 rows][64 BF16] box, 8 KB
 constexpr uint32_t GT_SPLIT = 4 * GT_BOX;        // 256 columns
 constexpr uint32_t GT_STAGE = 3 * GT_SPLIT;      // h, m, l: 96 KB
-
-__device__ __forceinline__ uint32_t pack_bf16x2(float a, float b) {
-  const uint32_t lo = __bfloat16_as_ushort(__float2bfloat16_rn(a));
-  const uint32_t hi = __bfloat16_as_ushort(__float2bfloat16_rn(b));
-  return lo | (hi << 16);
-}
 
 __global__ void __launch_bounds__(GT_THREADS, 1)
 k_gram_tc(const float* __restrict__ Y, int64_t ldy, int64_t M, int d, int dp, int64_t slab_rows,
@@ -632,6 +526,22 @@ k_gram_tc(const float* __restrict__ Y, int64_t ldy, int64_t M, int d, int dp, in
   const int n1 = dp > 128 ? dp - 128 : 16;  // M tile 1: columns 128..dp-1
   const uint32_t idesc1 = (idesc & ~(0x3Fu << 17)) | ((uint32_t)(n1 >> 3) << 17);
   bool ok = true;
+  // 64 rows x 64 groups of 4 columns (256 columns, zero beyond d) per chunk;
+  // chunk i + 1's loads are in flight while chunk i is converted
+  constexpr int PER = GT_ROWS * 64 / GT_THREADS;
+  auto load = [&](int i, float4 (&x)[PER]) {
+    const int64_t r0 = r_begin + (int64_t)i * GT_ROWS;
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+      const int e = t + q * GT_THREADS;
+      const int row = e >> 6, c = (e & 63) * 4;
+      x[q] = (r0 + row < r_end && c < dp)
+                 ? *reinterpret_cast<const float4*>(Y + (r0 + row) * ldy + c)
+                 : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+  };
+  float4 xv[PER];
+  if (nchunks > 0) load(0, xv);
   for (int i = 0; i < nchunks && ok; ++i) {
     const int st = i & 1;
     const uint32_t stage = base + st * GT_STAGE;
@@ -642,19 +552,8 @@ k_gram_tc(const float* __restrict__ Y, int64_t ldy, int64_t M, int d, int dp, in
         break;
       }
     }
-    const int64_t r0 = r_begin + (int64_t)i * GT_ROWS;
-    // 64 rows x 64 groups of 4 columns (256 columns, zero beyond d); each
-    // thread issues all of its 16 loads before converting
-    constexpr int PER = GT_ROWS * 64 / GT_THREADS;
-    float4 xv[PER];
-#pragma unroll
-    for (int q = 0; q < PER; ++q) {
-      const int e = t + q * GT_THREADS;
-      const int row = e >> 6, c = (e & 63) * 4;
-      xv[q] = (r0 + row < r_end && c < dp)
-                  ? *reinterpret_cast<const float4*>(Y + (r0 + row) * ldy + c)
-                  : make_float4(0.f, 0.f, 0.f, 0.f);
-    }
+    float4 xn[PER];
+    if (i + 1 < nchunks) load(i + 1, xn);
 #pragma unroll
     for (int q = 0; q < PER; ++q) {
       const int e = t + q * GT_THREADS;
@@ -683,6 +582,8 @@ k_gram_tc(const float* __restrict__ Y, int64_t ldy, int64_t M, int d, int dp, in
                    "r"(pack_bf16x2(lv[0], lv[1])), "r"(pack_bf16x2(lv[2], lv[3]))
                    : "memory");
     }
+#pragma unroll
+    for (int q = 0; q < PER; ++q) xv[q] = xn[q];
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     __syncthreads();
     if (t == 0) {
@@ -720,30 +621,29 @@ k_gram_tc(const float* __restrict__ Y, int64_t ldy, int64_t M, int d, int dp, in
   if (!ok && t == 0) atomicExch(err, 1);
   __syncthreads();
   tc_fence_after();
-  // epilogue: warp w reads TMEM lanes 32 (w % 4) .. +31 of M tile w / 4
-  // (Gram rows (w / 4) * 128 + 32 (w % 4) + lane) and stores the upper
-  // triangle (row <= column) of its slab sum
-  float* P = part + (int64_t)blockIdx.x * d * d;
+  // epilogue: warp w reads TMEM lanes 32 (w % 4) .. +31 of M tile w / 4,
+  // Gram rows 32 g .. 32 g + 31 with g = w (row block), and stores the
+  // columns from 32 g on (the upper block triangle) of its slab sum in the
+  // lane-major layout part[c][g][col][32]: lane l of the warp writes row
+  // 32 g + l, so each store is one contiguous 128-byte line.
+  const int nbr = (dp + 31) / 32;
+  float* P = part + (int64_t)blockIdx.x * nbr * dp * 32;
   {
-    const int mt = warp >> 2, g = warp & 3;
-    const int row = mt * 128 + g * 32 + lane;
+    const int mt = warp >> 2, g4 = warp & 3, g = warp;
     const int c0 = mt * 128, ncol = mt == 0 ? dp : n1;
-    if (mt == 0 || dp > 128) {
-      for (int c = 0; c < ncol; c += 16) {
+    if (warp < 8 && g < nbr && (mt == 0 || dp > 128)) {
+      for (int c = 32 * g4; c < ncol; c += 16) {
         float v[16];
         if (ok && nchunks > 0) {
-          tmem_ld16(tmem_base + (uint32_t)(mt * 256 + c) + ((uint32_t)(g * 32) << 16), v);
+          tmem_ld16(tmem_base + (uint32_t)(mt * 256 + c) + ((uint32_t)(g4 * 32) << 16), v);
         } else {
 #pragma unroll
           for (int j = 0; j < 16; ++j) v[j] = 0.f;
         }
-        if (row < d) {
+        float* dst = P + ((int64_t)g * dp + c0 + c) * 32 + lane;
 #pragma unroll
-          for (int j = 0; j < 16; ++j) {
-            const int col = c0 + c + j;
-            if (col < d && col >= row) P[(int64_t)row * d + col] = v[j];
-          }
-        }
+        for (int j = 0; j < 16; ++j)
+          if (c0 + c + j < dp) dst[j * 32] = v[j];
       }
     }
   }
@@ -763,49 +663,59 @@ k_gram_tc(const float* __restrict__ Y, int64_t ldy, int64_t M, int d, int dp, in
   }
 }
 
-// C = sum over CTAs of the slab sums, FP64, mirrored from the upper
-// triangle; Cf its FP32 copy.  A block takes 32 consecutive upper-triangle
-// entries (row-major order, so the reads are coalesced); warp w adds the
-// slab sums z = w, w + 8, ... in order, then the 8 warp sums are added in
-// warp order (a fixed, deterministic order).
+// s + c accumulates x: Knuth's TwoSum of s and x, its rounding error
+// collected in c (compensated summation in FP32; GB300's FP64 rate is a
+// small fraction of its FP32 rate, so the slab sums are not added in FP64).
+__device__ __forceinline__ void two_sum_acc(float& s, float& c, float x) {
+  const float t = s + x;
+  const float bp = t - s;
+  c += (s - (t - bp)) + (x - bp);
+  s = t;
+}
+
+// C = sum over CTAs of the slab sums, mirrored from the upper triangle, as
+// FP64 (s + c of the compensated FP32 sum) and Cf = fl32(s + c).  Block
+// (col, g) adds entries (32 g + l, col), l = lane, of the P slab sums (one
+// 128-byte line each in the lane-major layout); warp w adds the slab sums
+// z = w, w + 8, ... in order, then the 8 warp sums are added in warp order
+// (a fixed, deterministic order).
 __global__ void __launch_bounds__(256) k_gram_tc_reduce(const float* __restrict__ part, int P,
-                                                        int d, double* __restrict__ C,
+                                                        int d, int dp, double* __restrict__ C,
                                                         float* __restrict__ Cf) {
-  __shared__ double ws[8][33];
+  __shared__ float ws[8][33], wc[8][33];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int64_t nu = (int64_t)d * (d + 1) / 2;
-  const int64_t u = (int64_t)blockIdx.x * 32 + lane;  // upper-triangle entry
-  int i = 0, j = 0;
-  if (u < nu) {  // row i holds entries (i, i..d-1): find i by walking rows
-    int64_t rem = u;
-    while (rem >= d - i) { rem -= d - i; ++i; }
-    j = i + (int)rem;
+  const int col = blockIdx.x, g = blockIdx.y, nbr = gridDim.y;
+  if (col >= d || col < 32 * g) return;  // block-uniform
+  const int i = 32 * g + lane;
+  const int64_t slab = (int64_t)nbr * dp * 32, src = ((int64_t)g * dp + col) * 32 + lane;
+  float s = 0.f, c = 0.f;
+  int z = w;
+  for (; z + 8 * 3 < P; z += 8 * 4) {
+    const float a = part[z * slab + src], b = part[(z + 8) * slab + src];
+    const float x = part[(z + 16) * slab + src], e = part[(z + 24) * slab + src];
+    two_sum_acc(s, c, a);
+    two_sum_acc(s, c, b);
+    two_sum_acc(s, c, x);
+    two_sum_acc(s, c, e);
   }
-  const int64_t dd = (int64_t)d * d, src = (int64_t)i * d + j;
-  double s = 0.0;
-  if (u < nu) {
-    int z = w;
-    for (; z + 8 * 3 < P; z += 8 * 4) {
-      const float a = part[(int64_t)z * dd + src], b = part[(int64_t)(z + 8) * dd + src];
-      const float c = part[(int64_t)(z + 16) * dd + src], e = part[(int64_t)(z + 24) * dd + src];
-      s += (double)a;
-      s += (double)b;
-      s += (double)c;
-      s += (double)e;
-    }
-    for (; z < P; z += 8) s += (double)part[(int64_t)z * dd + src];
-  }
+  for (; z < P; z += 8) two_sum_acc(s, c, part[z * slab + src]);
   ws[w][lane] = s;
+  wc[w][lane] = c;
   __syncthreads();
-  if (w == 0 && u < nu) {
-    double t = 0.0;
+  if (w == 0 && i <= col && i < d) {
+    float t = 0.f, tc = 0.f;
 #pragma unroll
-    for (int k = 0; k < 8; ++k) t += ws[k][lane];
-    C[(int64_t)i * d + j] = t;
-    C[(int64_t)j * d + i] = t;
+    for (int k = 0; k < 8; ++k) {
+      two_sum_acc(t, tc, ws[k][lane]);
+      tc += wc[k][lane];
+    }
+    const double v = (double)t + (double)tc;
+    C[(int64_t)col * d + i] = v;
+    C[(int64_t)i * d + col] = v;
     if (Cf != nullptr) {
-      Cf[(int64_t)i * d + j] = (float)t;
-      Cf[(int64_t)j * d + i] = (float)t;
+      const float f = t + tc;
+      Cf[(int64_t)col * d + i] = f;
+      Cf[(int64_t)i * d + col] = f;
     }
   }
 }
@@ -833,6 +743,11 @@ int gram_tc_ctas(int64_t M) {
   return (int)std::max<int64_t>(1, (M + slab - 1) / slab);
 }
 
+size_t gram_tc_part_bytes(int d) {
+  const int dp = (d + 15) / 16 * 16;
+  return (size_t)sm_count() * ((dp + 31) / 32) * dp * 32 * sizeof(float);
+}
+
 bool gram_tc_supported(int64_t M, int d, int64_t ldy, const void* Y) {
   const int dp = (d + 15) / 16 * 16;
   return M >= 8192 && d >= 1 && dp <= 256 && ldy % 4 == 0 && ((uintptr_t)Y & 15) == 0 &&
@@ -853,7 +768,7 @@ cudaError_t gram_tc(const float* Y, int64_t ldy, int64_t M, int d, float* part, 
   count_launch();
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  k_gram_tc_reduce<<<ceil_div((int64_t)d * (d + 1) / 2, 32), 256, 0, st>>>(part, P, d, C, Cf);
+  k_gram_tc_reduce<<<dim3(d, (dp + 31) / 32), 256, 0, st>>>(part, P, d, dp, C, Cf);
   count_launch();
   return cudaGetLastError();
 }
@@ -906,7 +821,7 @@ cudaError_t tc_gemm(bool trans, const void* A, int64_t lda, int64_t m, int64_t n
   count_launch();
   e = cudaGetLastError();
   if (e != cudaSuccess || p.tail == 0) return e;
-  k_tc_fixup<<<dim3(p.tail, BM), 256, 0, st>>>(p, P);
+  k_tc_fixup<<<dim3(p.tail, BM / 4), 256, 0, st>>>(p, P);
   count_launch();
   return cudaGetLastError();
 }

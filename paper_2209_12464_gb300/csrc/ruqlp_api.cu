@@ -145,7 +145,8 @@ Layout layout_of(int64_t m, int64_t n, int d, Ty ct, int64_t nnz = -1, size_t va
   L.P = take((size_t)n * dp * wes);
   // Gram scratch: FP64 slab partials (SIMT Gram) or FP32 slab sums of the
   // tensor-core Gram (one per SM, at most 160)
-  L.partial = take((size_t)d * d * std::max<size_t>(kMaxSplits * sizeof(double), 160 * sizeof(float)));
+  L.partial = take(std::max((size_t)d * d * std::max<size_t>(kMaxSplits * sizeof(double), 160 * sizeof(float)),
+                             gram_tc_part_bytes(d)));
   L.G = take((size_t)d * d * sizeof(double));
   L.Gf = take((size_t)d * d * sizeof(float));
   L.R = take((size_t)d * d * sizeof(double));
@@ -304,8 +305,9 @@ struct Job {
 //  * FP32 work type (default for FP32/BF16): shifted CholeskyQR3 in FP32 --
 //    the first Cholesky always factors G + s I, s = 64 u_32 trace(G), so it
 //    cannot break down for kappa(Y) up to about 1/u_32; two more unshifted
-//    passes restore orthonormality.  FP32 Grams are summed in FP64 across row
-//    slabs.  (A single-SM FP64 Cholesky of a 220 x 220 Gram costs ~0.45 ms on
+//    passes restore orthonormality.  FP32 Grams are summed across row slabs
+//    in FP64 (CUDA-core Gram) or with compensated FP32 sums (tensor-core
+//    Gram).  (A single-SM FP64 Cholesky of a 220 x 220 Gram costs ~0.45 ms on
 //    GB300, whose FP64 rate is 1/58 of FP32.)
 // make_bt: the last solve also writes Q^T in BF16 to the arena's Bt (the
 // next tensor-core product's operand); returns whether it did.
@@ -332,7 +334,7 @@ ruqlp_status orth(ruqlp_ctx* h, const Layout& Lo, const Job& J, const void* Yin,
       const float* src = (const float*)(pass == 0 ? Yin : Qout);
       {
         ProfScope pg(h, PROF_GRAM);
-        if (gram_tc_supported(M, d, dp, src))
+        if (!h->orth_simt && gram_tc_supported(M, d, dp, src))
           CK(gram_tc(src, dp, M, d, (float*)partial, G, Gf, &h->status->timeout, st));
         else
           CK(gram_f32(src, dp, src, dp, M, d, d, G, partial, kMaxSplits, nullptr, st, Gf));
@@ -730,6 +732,7 @@ void copy_options(const ruqlp_ctx* from, ruqlp_ctx* to) {
   to->orth_fp64 = from->orth_fp64;
   to->orth_full = from->orth_full;
   to->bf16_simt = from->bf16_simt;
+  to->orth_simt = from->orth_simt;
 }
 
 ruqlp_status set_error(ruqlp_ctx* h, ruqlp_status s, const char* msg) {
@@ -1142,6 +1145,10 @@ ruqlp_status ruqlp_set_option(ruqlp_handle h, const char* name, int64_t value) {
   }
   if (strcmp(name, "bf16_simt") == 0) {
     h->bf16_simt = value ? 1 : 0;
+    return RUQLP_OK;
+  }
+  if (strcmp(name, "orth_simt") == 0) {
+    h->orth_simt = value ? 1 : 0;
     return RUQLP_OK;
   }
   if (strcmp(name, "profile") == 0) {

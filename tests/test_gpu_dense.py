@@ -202,6 +202,47 @@ def test_light_and_full_intermediate_orth_agree(handle, case):
     assert np.max(np.abs(a[0][:, :k] - b[0][:, :k])) <= 1e-4
 
 
+@pytest.mark.parametrize("shape", [(9000, 700, 100, 20, 1), (12288, 8500, 120, 16, 2),
+                                   (8192, 8192, 230, 26, 1)],
+                         ids=["Ytall", "YZtall-q2", "d256"])
+def test_tensor_core_orth_matches_cuda_core_orth(handle, shape):
+    """orth() of tall Y and Z with tensor-core Grams (three-way BF16 split)
+    against the CUDA-core FP32 Gram (option orth_simt).  Compared where the
+    results are well determined whatever the rounding: the singular values of L (those of Q^T A P depend
+    on the spans of Q and P only), the leading-k subspaces of Q and P (largest
+    principal-angle sine), orthonormality, and the relative residual.  Single
+    columns of Q and entries of L are basis-dependent: Y after the power step
+    has kappa ~ 1e3, so they move by ~ kappa u between any two FP32
+    orthogonalisations."""
+    m, n, k, p, q = shape
+    A = wl.dense_lowrank_gauss_torch(wl.MASTER_SEED + m + n, m, n, k, noise_std=1e-4)
+    Ag = wl.aligned_rows(A.bfloat16())
+    Og = wl.omega_torch(wl.MASTER_SEED + 5 * m, n, k + p)
+    a = handle.decompose(Ag, Og, k, p, q)[:3]
+    handle.set_option("orth_simt", 1)
+    try:
+        b = handle.decompose(Ag, Og, k, p, q)[:3]
+    finally:
+        handle.set_option("orth_simt", 0)
+    d = k + p
+    A64 = Ag.double()
+    res = []
+    for Q, L, P in (a, b):
+        R = A64 - Q.double() @ L.double() @ P.double().T
+        res.append(float(torch.linalg.norm(R) / torch.linalg.norm(A64)))
+    a = [t.double().cpu().numpy() for t in a]
+    b = [t.double().cpu().numpy() for t in b]
+    sa, sb = np.linalg.svd(a[1], compute_uv=False), np.linalg.svd(b[1], compute_uv=False)
+    ds = np.max(np.abs(sa - sb)) / sb[0]
+    assert ds <= 1e-5, ds
+    for x, y in ((a[0], b[0]), (a[2], b[2])):
+        U, V = x[:, :k], y[:, :k]
+        sin = np.linalg.norm(V - U @ (U.T @ V), 2)
+        assert sin <= 1e-4, sin
+        assert np.max(np.abs(x.T @ x - np.eye(d))) <= 50 * d * 2.0 ** -24
+    assert abs(res[0] - res[1]) <= 1e-5 * max(res[1], 1e-3), res
+
+
 @pytest.mark.parametrize("dtype", [torch.float64, torch.float32], ids=["f64", "f32"])
 @pytest.mark.parametrize("case", CASES[:3], ids=[c[0] for c in CASES[:3]])
 def test_finish_paper_matches_oracle(handle, case, dtype):
