@@ -180,9 +180,9 @@ ruqlp_status ruqlp_set_stream(ruqlp_handle h, void* cuda_stream);
  *   "bf16_simt": 1 = run BF16 products on the CUDA cores instead of the
  *   tensor cores (comparison baseline); 0 (default) = tensor cores.
  *   "orth_simt": 1 = orth() of tall matrices (>= 8192 rows) forms its Grams
- *   on the CUDA cores (FP32 Gram tiles); 0 (default) = on the tensor cores
- *   (three-way BF16 split of the FP32 operand, FP32 accumulation:
- *   FP32-level results).
+ *   and Q = Y R^{-1} on the CUDA cores (FP32 Gram tiles, blocked triangular
+ *   solve); 0 (default) = on the tensor cores (three-way BF16 split of the
+ *   FP32 operands, FP32 accumulation: FP32-level results).
  *   "profile": 1 = bracket every phase with CUDA events on the handle's
  *   stream and accumulate their durations (read with ruqlp_profile); setting
  *   it (to 0 or 1) also zeroes the accumulators.

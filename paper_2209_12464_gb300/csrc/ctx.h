@@ -29,7 +29,7 @@ struct ruqlp_ctx {
   int orth_full = 0;    // 1: every orth() takes three CholeskyQR passes (else the
                         // intermediate ones take two)
   int bf16_simt = 0;    // 1: BF16 products on CUDA cores instead of tensor cores
-  int orth_simt = 0;    // 1: orth() Grams on CUDA cores
+  int orth_simt = 0;    // 1: orth() Grams and Q = Y R^{-1} on CUDA cores
   // phase timing with CUDA events on the handle's stream (option "profile")
   bool profile = false;
   struct Span { int cat; cudaEvent_t a, b; };

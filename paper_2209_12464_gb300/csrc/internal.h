@@ -177,6 +177,14 @@ cudaError_t btrsm(const BMat* T, const int* prefix, int total, int count, int sr
 bool gram_tc_supported(int64_t M, int d, int64_t ldy, const void* Y);
 int gram_tc_ctas(int64_t M);
 size_t gram_tc_part_bytes(int d);
+// Q = Y R^{-1} on the tensor cores (tall FP32 Y, M >= 8192, d <= 256): the
+// blocked Cholesky's tiles are inverted into St (qmul_st_bytes(d) bytes,
+// S^T as three BF16 parts), then Q (may alias Y) = Y S; Bt (optional)
+// receives Q^T in BF16 with leading dimension ldbt.  err: timeout word.
+size_t qmul_st_bytes(int d);
+bool qmul_supported(int64_t M, int d, int64_t ldy, const void* Y, int64_t ldq, const void* Q);
+cudaError_t qmul_tc(const float* Y, int64_t ldy, const float* tiles, int64_t M, int d, void* St,
+                    float* Q, int64_t ldq, void* Bt, int64_t ldbt, int* err, cudaStream_t st);
 // 2-D BF16 tensor map (128-byte swizzle) over a row-major [outer][inner]
 // array with leading dimension ld_elems; box box_inner x box_outer.
 bool make_map(CUtensorMap* m, const void* ptr, uint64_t inner, uint64_t outer, uint64_t ld_elems,

@@ -1,0 +1,502 @@
+// Q = Y R^{-1} of orth() (Section II-A, CholeskyQR) on the tensor cores, for
+// tall FP32 Y (M >= 8192 rows, d <= 256):
+//
+//  * k_trinv: S = R^{-1} (upper triangular, d x d) from the blocked Cholesky's
+//    R tiles and diagonal-tile inverses, one CTA per 32-column block J (all
+//    its tiles loaded at once):
+//    S_JJ is given, and for K = J down to 1
+//        acc_I += R_IK S_KJ          (all I < K, one tile product each)
+//        S_{K-1,J} = -S_{K-1,K-1} acc_{K-1},
+//    which is back substitution on R S_{:,J} = E_J.  S^T is written as three
+//    BF16 parts s = h + m + l (h = bf16(s), m = bf16(s - h), l = bf16(s - h - m)),
+//    K-major ([part][n][k], k padded to 256 with zeros): the B operand below.
+//  * k_qmul_tc: Q = Y S with tcgen05.mma (BF16 x BF16 -> FP32 in TMEM).  Y is
+//    split the same way on the fly; of the nine part products the six above
+//    2^-24 are kept (hh, hm, mh, mm, hl, lh), so Q matches an FP32 product.
+//    One CTA per SM takes 128-row tiles; a tile is accumulated over 64-wide
+//    K chunks, chunk c only into the columns n >= 64 c (S is upper
+//    triangular).  Converter warps write the Y chunk's parts into one of two
+//    128B-swizzled stages while a producer warp loads the S parts with TMA
+//    and an MMA warp issues 6 x 4 MMAs per chunk; the epilogue of a tile
+//    drains TMEM (two accumulators) while the next tile's MMAs run, and
+//    stores Q (and optionally Q^T in BF16, the next product's operand).  A
+//    tile's rows are read in full before they are written, so Q may
+//    overwrite Y.
+// Every mbarrier wait is bounded; on timeout the CTA sets the error word,
+// waits for its own copies and MMAs, frees TMEM and returns.
+#include <cuda.h>
+
+#include "internal.h"
+#include "tcgen05.cuh"
+
+namespace ruqlp {
+namespace {
+
+constexpr int TB = 32;   // tile edge of the Cholesky's blocking
+constexpr int TP = 36;   // shared-memory row pitch (16-byte aligned rows)
+constexpr int KP = 256;  // padded K of the S^T parts
+constexpr size_t TILE_F = (size_t)TB * TP;
+
+__device__ __forceinline__ int bidx(int I, int J, int nb) { return I * nb - (I * (I - 1)) / 2 + (J - I); }
+
+// acc[i][j] += sum_k A[rg + 8 i][k] B[k][c0 + j] for a lane's 4 x 4 block
+// of a 32 x 32 tile product A B (row-major tiles, pitch TP).  Rows rg + 8 i
+// keep the four 128-bit loads of A conflict-free.
+__device__ __forceinline__ void tile_nn44(const float* __restrict__ A, const float* __restrict__ B,
+                                          int rg, int c0, float (&acc)[4][4]) {
+#pragma unroll 2
+  for (int k = 0; k < TB; k += 4) {
+    float4 a[4], b[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) a[i] = *reinterpret_cast<const float4*>(A + (rg + 8 * i) * TP + k);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) b[q] = *reinterpret_cast<const float4*>(B + (k + q) * TP + c0);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const float av[4] = {a[i].x, a[i].y, a[i].z, a[i].w};
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        acc[i][0] = fmaf(av[q], b[q].x, acc[i][0]);
+        acc[i][1] = fmaf(av[q], b[q].y, acc[i][1]);
+        acc[i][2] = fmaf(av[q], b[q].z, acc[i][2]);
+        acc[i][3] = fmaf(av[q], b[q].w, acc[i][3]);
+      }
+    }
+  }
+}
+
+// 32 x 32 tile (pitch 32, global) -> shared (pitch TP) with cp.async
+__device__ __forceinline__ void fetch_tile(float* dst, const float* src, int t, int nt) {
+  for (int e = t; e < TB * 8; e += nt) {
+    const int r = e >> 3, c4 = (e & 7) * 4;
+    const uint32_t a = (uint32_t)__cvta_generic_to_shared(dst + r * TP + c4);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(a), "l"(src + r * TB + c4)
+                 : "memory");
+  }
+}
+
+constexpr int TI_THREADS = 512;
+
+// grid = nb CTAs (block column J = blockIdx.x).  tiles: the Cholesky's R
+// tiles (packed upper block triangle, 32 x 32 row-major each) followed by
+// the nb diagonal-tile inverses.  Writes rows n = 32 J .. of St[3][dp][KP].
+// Every tile the column needs (R_IK for I < K <= J, S_KK for K <= J) is
+// loaded at once; acc_I is accumulated in the slot of S_IJ and turned into
+// S_IJ in place.
+__global__ void __launch_bounds__(TI_THREADS)
+k_trinv(const float* __restrict__ tiles, int d, int dp, __nv_bfloat16* __restrict__ St) {
+  extern __shared__ __align__(16) float sm[];
+  const int nb = (d + TB - 1) / TB, ntiles = nb * (nb + 1) / 2;
+  const int J = blockIdx.x;
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5, nw = TI_THREADS / 32;
+  const int rg = lane >> 2, cg = lane & 3;
+  // shared: Scol[K] (K <= J), R_IK at Rs[K (K - 1) / 2 + I] (I < K <= J),
+  // diagonal inverses Ds[K] (K < J)
+  float* Scol = sm;
+  float* Rs = Scol + (size_t)nb * TILE_F;
+  float* Ds = Rs + (size_t)nb * (nb - 1) / 2 * TILE_F;
+  auto rtile = [&](int I, int K) { return tiles + (size_t)bidx(I, K, nb) * TB * TB; };
+  auto dtile = [&](int K) { return tiles + (size_t)(ntiles + K) * TB * TB; };
+  fetch_tile(Scol + (size_t)J * TILE_F, dtile(J), t, TI_THREADS);
+  for (int K = 1; K <= J; ++K)
+    for (int I = 0; I < K; ++I)
+      fetch_tile(Rs + ((size_t)K * (K - 1) / 2 + I) * TILE_F, rtile(I, K), t, TI_THREADS);
+  for (int K = 0; K < J; ++K) fetch_tile(Ds + (size_t)K * TILE_F, dtile(K), t, TI_THREADS);
+  asm volatile("cp.async.commit_group;" ::: "memory");
+  for (int e = t; e < J * TB * TB; e += TI_THREADS) {  // acc_I = 0, I < J
+    const int I = e >> 10, r = (e >> 5) & 31, c = e & 31;
+    Scol[I * TILE_F + r * TP + c] = 0.f;
+  }
+  asm volatile("cp.async.wait_group 0;" ::: "memory");
+  __syncthreads();
+  for (int K = J; K >= 1; --K) {
+    const float* SKJ = Scol + (size_t)K * TILE_F;
+    // acc_I += R_IK S_KJ, items (I, column half)
+    for (int u = warp; u < 2 * K; u += nw) {
+      const int I = u >> 1, c0 = (u & 1) * 16 + cg * 4;
+      float* C = Scol + (size_t)I * TILE_F;
+      float a4[4][4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const float4 v = *reinterpret_cast<const float4*>(C + (rg + 8 * i) * TP + c0);
+        a4[i][0] = v.x;
+        a4[i][1] = v.y;
+        a4[i][2] = v.z;
+        a4[i][3] = v.w;
+      }
+      tile_nn44(Rs + ((size_t)K * (K - 1) / 2 + I) * TILE_F, SKJ, rg, c0, a4);
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+        *reinterpret_cast<float4*>(C + (rg + 8 * i) * TP + c0) =
+            make_float4(a4[i][0], a4[i][1], a4[i][2], a4[i][3]);
+    }
+    __syncthreads();
+    // S_{K-1,J} = -S_{K-1,K-1} acc_{K-1}, in place: a warp per column half
+    // reads its whole strip before writing it
+    if (warp < 2) {
+      const int c0 = warp * 16 + cg * 4;
+      float o[4][4] = {};
+      float* D = Scol + (size_t)(K - 1) * TILE_F;
+      tile_nn44(Ds + (size_t)(K - 1) * TILE_F, D, rg, c0, o);
+      __syncwarp();
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+        *reinterpret_cast<float4*>(D + (rg + 8 * i) * TP + c0) =
+            make_float4(-o[i][0], -o[i][1], -o[i][2], -o[i][3]);
+    }
+    __syncthreads();
+  }
+  // St[p][n][k] = part p of S[k][n], n = 32 J + c: lane = k within a
+  // 32-row block, so a warp writes 64 contiguous bytes per row n
+  for (int e = warp; e < TB * (KP / TB); e += nw) {
+    const int c = e / (KP / TB), kb = e % (KP / TB);
+    const int n = J * TB + c, k = kb * TB + lane;
+    if (n >= dp) continue;
+    float v = 0.f;
+    if (kb <= J && k < d && n < d) v = Scol[(size_t)kb * TILE_F + lane * TP + c];
+    const __nv_bfloat16 h = __float2bfloat16_rn(v);
+    const float r1 = v - __bfloat162float(h);
+    const __nv_bfloat16 m = __float2bfloat16_rn(r1);
+    const __nv_bfloat16 l = __float2bfloat16_rn(r1 - __bfloat162float(m));
+    const size_t o = (size_t)n * KP + k;
+    St[o] = h;
+    St[(size_t)dp * KP + o] = m;
+    St[2 * (size_t)dp * KP + o] = l;
+  }
+}
+
+constexpr int QM_CONV = 8;                      // converter / epilogue warps
+constexpr int QM_PROD = QM_CONV;                // TMA producer warp
+constexpr int QM_MMA = QM_CONV + 1;             // MMA warp
+constexpr int QM_THREADS = 32 * (QM_CONV + 2);
+constexpr int QM_PER = 128 * 16 / (QM_CONV * 32);  // float4 of a chunk per thread
+constexpr int QM_BM = 128;
+constexpr uint32_t QM_APART = QM_BM * 128;       // A part: [128 rows][64 BF16], 16 KB
+constexpr uint32_t QM_ASTAGE = 3 * QM_APART;     // 48 KB
+constexpr uint32_t QM_BPART = 256 * 128;         // B part: [256 rows][64 BF16], 32 KB
+constexpr uint32_t QM_B = 3 * QM_BPART;          // 96 KB
+constexpr int QM_SP = 20;                        // epilogue staging pitch (floats)
+constexpr uint32_t QM_STG = QM_CONV * 32 * QM_SP * 4;  // 20 KB
+constexpr uint32_t QM_BAR = 2 * QM_ASTAGE + QM_B + QM_STG;
+constexpr size_t QM_SMEM = 1024 + (size_t)QM_BAR + 128;
+
+struct QmParams {
+  const float* Y;
+  int64_t ldy;
+  float* Q;
+  int64_t ldq;
+  __nv_bfloat16* Bt;  // optional Q^T (dp x ldbt)
+  int64_t ldbt;
+  int64_t M;
+  int d, dp;
+  int* err;
+};
+
+// Per 128-row tile, K chunk c (k in [64 c, 64 c + 64)) contributes to the
+// output columns n >= 64 c only: one MMA chain of width N = dp - 64 c.
+// Warps 0..7 convert Y chunks into two A stages and drain finished
+// accumulators (the epilogue of tile i - 1 runs after the first chunk of
+// tile i, while its MMAs proceed); warp 8 loads the S parts of each chunk
+// with TMA into one B buffer; warp 9 issues the MMAs.  Two TMEM
+// accumulators (2 x 256 columns).
+__global__ void __launch_bounds__(QM_THREADS, 1)
+k_qmul_tc(const __grid_constant__ CUtensorMap tmS, const __grid_constant__ QmParams p) {
+  extern __shared__ uint8_t smem_raw[];
+  const uint32_t raw = smem_u32(smem_raw);
+  const uint32_t base = (raw + 1023u) & ~1023u;
+  uint8_t* base_ptr = smem_raw + (base - raw);
+  const uint32_t sB = base + 2 * QM_ASTAGE;
+  float* stg_all = (float*)(base_ptr + 2 * QM_ASTAGE + QM_B);
+  // barriers: a_full[2] (8 arrivals), a_empty[2] (MMA commit), b_full (TMA),
+  // b_empty (MMA commit), acc_full[2] (MMA commit), acc_empty[2] (8
+  // arrivals), drain
+  const uint32_t bar = base + QM_BAR;
+  auto a_full = [&](int s) { return bar + 8u * s; };
+  auto a_empty = [&](int s) { return bar + 16u + 8u * s; };
+  const uint32_t b_full = bar + 32, b_empty = bar + 40;
+  auto acc_full = [&](int s) { return bar + 48u + 8u * s; };
+  auto acc_empty = [&](int s) { return bar + 64u + 8u * s; };
+  const uint32_t drain = bar + 80;
+  uint32_t* tmem_slot = (uint32_t*)(base_ptr + QM_BAR + 96);
+  __shared__ int s_abort;
+  const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+  if (t == 0) {
+    mbar_init(a_full(0), QM_CONV);
+    mbar_init(a_full(1), QM_CONV);
+    mbar_init(a_empty(0), 1);
+    mbar_init(a_empty(1), 1);
+    mbar_init(b_full, 1);
+    mbar_init(b_empty, 1);
+    mbar_init(acc_full(0), 1);
+    mbar_init(acc_full(1), 1);
+    mbar_init(acc_empty(0), QM_CONV);
+    mbar_init(acc_empty(1), QM_CONV);
+    mbar_init(drain, 1);
+    s_abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tmS) : "memory");
+  }
+  if (warp == QM_MMA) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(
+                     smem_u32(tmem_slot))
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+  volatile int* abort_flag = &s_abort;
+
+  const int dp = p.dp, d = p.d;
+  const int nsteps = (dp + 63) / 64;  // K chunks per tile
+  const int64_t ntiles = (p.M + QM_BM - 1) / QM_BM;
+  const int my_tiles =
+      (int64_t)blockIdx.x < ntiles ? (int)((ntiles - 1 - blockIdx.x) / gridDim.x + 1) : 0;
+  const int total = my_tiles * nsteps;
+
+  if (warp == QM_PROD) {
+    // ---------------- TMA producer: S^T parts, rows 64 c .. ----------------
+    if (lane == 0) {
+      const uint64_t pol = policy_evict_last();
+      bool pending = false;
+      uint32_t pend_par = 0;
+      for (int g = 0; g < total; ++g) {
+        const int c = g % nsteps;
+        if (g >= 1 && !mbar_wait(b_empty, (uint32_t)((g - 1) & 1), abort_flag)) {
+          s_abort = 1;
+          break;
+        }
+        mbar_expect_tx(b_full, 3 * QM_BPART);
+#pragma unroll
+        for (int q = 0; q < 3; ++q)
+          tma_load_2d(sB + q * QM_BPART, &tmS, b_full, 64 * c, q * dp + 64 * c, pol);
+        pending = true;
+        pend_par = (uint32_t)(g & 1);
+      }
+      volatile int never = 0;
+      // the last copy must land before the CTA exits (the MMA warp waited for
+      // the others)
+      if (pending) mbar_wait(b_full, pend_par, &never);
+    }
+  } else if (warp == QM_MMA) {
+    // ---------------- MMA issuer (one lane) ----------------
+    if (lane == 0) {
+      bool ok = true;
+      const int pa[6] = {0, 0, 1, 1, 0, 2}, pb[6] = {0, 1, 0, 1, 2, 0};
+      int g = 0;
+      for (int i = 0; i < my_tiles && ok; ++i) {
+        const int set = i & 1;
+        if (i >= 2 && !mbar_wait(acc_empty(set), (uint32_t)(((i >> 1) - 1) & 1), abort_flag)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        for (int c = 0; c < nsteps; ++c, ++g) {
+          const int st = g & 1;
+          const uint32_t stA = base + st * QM_ASTAGE;
+          if (!mbar_wait(a_full(st), (uint32_t)((g >> 1) & 1), abort_flag) ||
+              !mbar_wait(b_full, (uint32_t)(g & 1), abort_flag)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const int n = dp - 64 * c;
+          const uint32_t id = idesc_bf16(n, false);
+          const uint32_t dcol = tmem_base + (uint32_t)(256 * set + 64 * c);
+          const uint64_t ad0 = sdesc(stA, 16, 1024), bd0 = sdesc(sB, 16, 1024);
+#pragma unroll
+          for (int kk = 0; kk < 4; ++kk) {
+#pragma unroll
+            for (int q = 0; q < 6; ++q) {
+              const uint64_t ad = ad0 + (uint64_t)((pa[q] * QM_APART + kk * 32) >> 4);
+              const uint64_t bd = bd0 + (uint64_t)((pb[q] * QM_BPART + kk * 32) >> 4);
+              mma_bf16(dcol, ad, bd, id, (c > 0 || kk > 0 || q > 0) ? 1u : 0u);
+            }
+          }
+          mma_commit(a_empty(st));
+          mma_commit(b_empty);
+          if (c == nsteps - 1) mma_commit(acc_full(set));
+        }
+      }
+      if (!ok) s_abort = 1;
+    }
+  } else {
+    // ---------------- converters + epilogue (warps 0..7) ----------------
+    const int ct = t;  // 0..255
+    // the A chunk of (tile i, chunk c): 128 rows x 64 columns of Y
+    auto load_a = [&](int i, int c, float4 (&x)[QM_PER]) {
+      const int64_t r0 = ((int64_t)blockIdx.x + (int64_t)i * gridDim.x) * QM_BM;
+#pragma unroll
+      for (int q = 0; q < QM_PER; ++q) {
+        const int e = ct + q * QM_CONV * 32;
+        const int row = e >> 4, k = c * 64 + (e & 15) * 4;
+        x[q] = (r0 + row < p.M && k < d)
+                   ? *reinterpret_cast<const float4*>(p.Y + (r0 + row) * p.ldy + k)
+                   : make_float4(0.f, 0.f, 0.f, 0.f);
+        if (k + 3 >= d && k < d) {  // zero the columns past d
+          if (k + 1 >= d) x[q].y = 0.f;
+          if (k + 2 >= d) x[q].z = 0.f;
+          if (k + 3 >= d) x[q].w = 0.f;
+        }
+      }
+    };
+    bool ok = true;
+    // one chunk step: wait for the A stage, start the next chunk's loads into
+    // nxt, convert cur into the stage, signal the MMA warp
+    auto step = [&](int g, int i, int c, float4 (&cur)[QM_PER], float4 (&nxt)[QM_PER]) {
+      const int st = g & 1;
+      const uint32_t stA = base + st * QM_ASTAGE;
+      if (g >= 2 && !mbar_wait(a_empty(st), (uint32_t)(((g >> 1) - 1) & 1), abort_flag)) {
+        ok = false;
+        return;
+      }
+      int ni = i, nc = c + 1;
+      if (nc == nsteps) {
+        nc = 0;
+        ++ni;
+      }
+      if (ni < my_tiles) load_a(ni, nc, nxt);
+      asm volatile("" ::: "memory");  // the loads are issued before the conversion
+#pragma unroll
+      for (int q = 0; q < QM_PER; ++q) {
+        const int e = ct + q * QM_CONV * 32;
+        const int row = e >> 4, kc = (e & 15) * 4;
+        const float v[4] = {cur[q].x, cur[q].y, cur[q].z, cur[q].w};
+        uint32_t hp[2], mp[2], lp[2];
+        split3_bf16x4(v, hp, mp, lp);
+        const uint32_t off = (uint32_t)row * 128 + ((uint32_t)((kc >> 3) ^ (row & 7)) << 4) +
+                             (uint32_t)((kc & 7) * 2);
+        const uint32_t a = stA + off;
+        asm volatile("st.shared.v2.b32 [%0], {%1, %2};" ::"r"(a), "r"(hp[0]), "r"(hp[1])
+                     : "memory");
+        asm volatile("st.shared.v2.b32 [%0], {%1, %2};" ::"r"(a + QM_APART), "r"(mp[0]),
+                     "r"(mp[1])
+                     : "memory");
+        asm volatile("st.shared.v2.b32 [%0], {%1, %2};" ::"r"(a + 2 * QM_APART), "r"(lp[0]),
+                     "r"(lp[1])
+                     : "memory");
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) mbar_arrive(a_full(st));
+    };
+    // drain accumulator set j & 1 (tile j): warp w reads TMEM lanes
+    // 32 (w % 4) + lane (tile rows) and columns 128 (w / 4) .. + 127, stages
+    // 16 columns at a time and stores 64-byte row segments
+    float* stg = stg_all + warp * 32 * QM_SP;
+    auto epilogue = [&](int j) {
+      const int set = j & 1;
+      if (!mbar_wait(acc_full(set), (uint32_t)((j >> 1) & 1), abort_flag)) {
+        ok = false;
+        return;
+      }
+      tc_fence_after();
+      const int h = warp >> 2, q4 = warp & 3;
+      const int64_t rbase = ((int64_t)blockIdx.x + (int64_t)j * gridDim.x) * QM_BM + q4 * 32;
+      const int c1 = min(dp, 128 * h + 128);
+      for (int col = 128 * h; col < c1; col += 16) {
+        float v[16];
+        tmem_ld16(tmem_base + (uint32_t)(256 * set + col) + ((uint32_t)(q4 * 32) << 16), v);
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+          *reinterpret_cast<float4*>(stg + lane * QM_SP + 4 * u) =
+              make_float4(v[4 * u], v[4 * u + 1], v[4 * u + 2], v[4 * u + 3]);
+        if (p.Bt != nullptr && rbase + lane < p.M) {
+#pragma unroll
+          for (int u = 0; u < 16; ++u)
+            p.Bt[(int64_t)(col + u) * p.ldbt + rbase + lane] = __float2bfloat16_rn(v[u]);
+        }
+        __syncwarp();
+#pragma unroll
+        for (int rr = 0; rr < 4; ++rr) {
+          const int row = rr * 8 + (lane >> 2), c4 = lane & 3;
+          if (rbase + row < p.M)
+            *reinterpret_cast<float4*>(p.Q + (rbase + row) * p.ldq + col + 4 * c4) =
+                *reinterpret_cast<const float4*>(stg + row * QM_SP + 4 * c4);
+        }
+        __syncwarp();
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(acc_empty(set));
+    };
+    float4 x0[QM_PER], x1[QM_PER];
+    if (my_tiles > 0) load_a(0, 0, x0);
+    int g = 0;
+    for (int i = 0; i < my_tiles && ok; ++i) {
+      for (int c = 0; c < nsteps && ok; ++c, ++g) {
+        if (g & 1) step(g, i, c, x1, x0);
+        else step(g, i, c, x0, x1);
+        if (c == 0 && i > 0 && ok) epilogue(i - 1);
+      }
+    }
+    if (ok && my_tiles > 0) epilogue(my_tiles - 1);
+    if (!ok) s_abort = 1;
+  }
+  __syncthreads();
+  if (warp == QM_MMA) {
+    if (lane == 0) {
+      volatile int never = 0;
+      tc_fence_after();
+      mma_commit(drain);  // every MMA this CTA issued has completed before TMEM is freed
+      mbar_wait(drain, 0, &never);
+    }
+    __syncwarp();
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem_base)
+                 : "memory");
+  }
+  if (t == 0 && *abort_flag) atomicExch(p.err, 1);
+}
+
+}  // namespace
+
+size_t qmul_st_bytes(int d) {
+  const int dp = (d + 15) / 16 * 16;
+  return (size_t)3 * dp * KP * sizeof(__nv_bfloat16);
+}
+
+bool qmul_supported(int64_t M, int d, int64_t ldy, const void* Y, int64_t ldq, const void* Q) {
+  const int dp = (d + 15) / 16 * 16;
+  return M >= 8192 && d >= 1 && dp <= 256 && ldy % 4 == 0 && ldq % 4 == 0 && ldy >= dp &&
+         ldq >= dp && ((uintptr_t)Y & 15) == 0 && ((uintptr_t)Q & 15) == 0;
+}
+
+cudaError_t qmul_tc(const float* Y, int64_t ldy, const float* tiles, int64_t M, int d, void* St,
+                    float* Q, int64_t ldq, void* Bt, int64_t ldbt, int* err, cudaStream_t st) {
+  if (!qmul_supported(M, d, ldy, Y, ldq, Q) || ((uintptr_t)St & 15) != 0)
+    return cudaErrorInvalidValue;
+  const int dp = (d + 15) / 16 * 16;
+  const int nb = (d + TB - 1) / TB;
+  const size_t ti_smem = (size_t)(nb + nb * (nb - 1) / 2 + nb) * TILE_F * sizeof(float);
+  cudaError_t e =
+      cudaFuncSetAttribute(k_trinv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ti_smem);
+  if (e != cudaSuccess) return e;
+  k_trinv<<<nb, TI_THREADS, ti_smem, st>>>(tiles, d, dp, (__nv_bfloat16*)St);
+  count_launch();
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  CUtensorMap map;
+  if (!make_map(&map, St, KP, (uint64_t)3 * dp, KP, 64, 256)) return cudaErrorInvalidValue;
+  QmParams p;
+  p.Y = Y;
+  p.ldy = ldy;
+  p.Q = Q;
+  p.ldq = ldq;
+  p.Bt = (__nv_bfloat16*)Bt;
+  p.ldbt = ldbt;
+  p.M = M;
+  p.d = d;
+  p.dp = dp;
+  p.err = err;
+  e = cudaFuncSetAttribute(k_qmul_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)QM_SMEM);
+  if (e != cudaSuccess) return e;
+  const int64_t ntiles = (M + QM_BM - 1) / QM_BM;
+  const int P = (int)std::min<int64_t>(ntiles, sm_count());
+  k_qmul_tc<<<P, QM_THREADS, QM_SMEM, st>>>(map, p);
+  count_launch();
+  return cudaGetLastError();
+}
+
+}  // namespace ruqlp

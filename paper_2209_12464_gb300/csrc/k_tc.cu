@@ -355,33 +355,42 @@ k_btc_gemm(const BTcTile* __restrict__ list, int n, const BMat* __restrict__ T,
 
 // Sum the stream-K fragments of each tail tile in CTA order into the output.
 // One block per (tail tile, 4 rows), one thread per 4 columns (16-byte loads,
-// up to 16 contributors in flight); thread 0 lists the tile's contributing
-// CTAs and fragment slots first.
+// up to 16 contributors in flight), after the block lists the tile's
+// contributing CTAs and fragment slots.
 __global__ void __launch_bounds__(256) k_tc_fixup(TcParams p, int P) {
-  __shared__ int s_src[512];
-  __shared__ int s_n;
+  __shared__ int s_src[256];
+  __shared__ int s_cnt[8];
   const int tt = blockIdx.x;  // tail tile index
   const int64_t KB = p.KB;
   const int64_t lo = tt * KB, hi = lo + KB;
-  if (threadIdx.x == 0) {
-    int c = (int)((lo * P) / p.U);
-    while (c + 1 < P && sk_start(c + 1, p.U, P) <= lo) ++c;
-    while (c > 0 && sk_start(c, p.U, P) > lo) --c;
-    int n = 0;
-    for (int cc = c; cc < P && n < 512; ++cc) {
-      const int64_t u0 = sk_start(cc, p.U, P), u1 = sk_start(cc + 1, p.U, P);
-      if (u0 >= hi) break;
-      if (u1 <= lo || u1 == u0) continue;
-      s_src[n++] = cc * 2 + ((u0 / KB == tt) ? 0 : 1);
-    }
-    s_n = n;
+  // the contributors are consecutive CTAs starting near lo P / U (at most
+  // P / tail + 2 of them): thread i tests CTA c0 + i, then an ordered
+  // compaction by warp ballots lists them with their fragment slots
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int c0 = max(0, (int)((lo * P) / p.U) - 2);
+  const int cc = c0 + (int)threadIdx.x;
+  bool f = false;
+  int slot = 0;
+  if (cc < P) {
+    const int64_t u0 = sk_start(cc, p.U, P), u1 = sk_start(cc + 1, p.U, P);
+    f = u0 < hi && u1 > lo && u1 > u0;
+    slot = (u0 / KB == tt) ? 0 : 1;
   }
+  const unsigned b = __ballot_sync(0xffffffffu, f);
+  if (lane == 0) s_cnt[w] = __popc(b);
+  __syncthreads();
+  int pos = __popc(b & ((1u << lane) - 1u)), n = 0;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    if (k < w) pos += s_cnt[k];
+    n += s_cnt[k];
+  }
+  if (f) s_src[pos] = cc * 2 + slot;
   __syncthreads();
   // block (tt, y): rows 4 y .. 4 y + 3 of the tile, a thread per 4 columns
   const int tile = p.full_waves * P + tt;
   const int q4 = p.dp / 4;
   const int r = blockIdx.y * 4 + threadIdx.x / 64, c4 = threadIdx.x % 64;
-  const int n = s_n;
   const int64_t gr = (int64_t)tile * BM + r;
   if (gr >= p.Mout || c4 >= q4) return;
   const float4* frag = reinterpret_cast<const float4*>(p.frag);
@@ -560,26 +569,17 @@ k_gram_tc(const float* __restrict__ Y, int64_t ldy, int64_t M, int d, int dp, in
       const int row = e >> 6, c = (e & 63) * 4;
       float v[4] = {(c < d) ? xv[q].x : 0.f, (c + 1 < d) ? xv[q].y : 0.f,
                     (c + 2 < d) ? xv[q].z : 0.f, (c + 3 < d) ? xv[q].w : 0.f};
-      float hv[4], mv[4], lv[4];
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        hv[j] = __bfloat162float(__float2bfloat16_rn(v[j]));
-        const float r1 = v[j] - hv[j];
-        mv[j] = __bfloat162float(__float2bfloat16_rn(r1));
-        lv[j] = r1 - mv[j];
-      }
+      uint32_t hp[2], mp[2], lp[2];
+      split3_bf16x4(v, hp, mp, lp);
       const int box = c >> 6, cb = c & 63;
       const uint32_t off = (uint32_t)box * GT_BOX + (uint32_t)row * 128 +
                            ((uint32_t)((cb >> 3) ^ (row & 7)) << 4) + (uint32_t)((cb & 7) * 2);
       const uint32_t a = stage + off;
-      asm volatile("st.shared.v2.b32 [%0], {%1, %2};" ::"r"(a), "r"(pack_bf16x2(hv[0], hv[1])),
-                   "r"(pack_bf16x2(hv[2], hv[3]))
+      asm volatile("st.shared.v2.b32 [%0], {%1, %2};" ::"r"(a), "r"(hp[0]), "r"(hp[1]) : "memory");
+      asm volatile("st.shared.v2.b32 [%0], {%1, %2};" ::"r"(a + GT_SPLIT), "r"(mp[0]), "r"(mp[1])
                    : "memory");
-      asm volatile("st.shared.v2.b32 [%0], {%1, %2};" ::"r"(a + GT_SPLIT),
-                   "r"(pack_bf16x2(mv[0], mv[1])), "r"(pack_bf16x2(mv[2], mv[3]))
-                   : "memory");
-      asm volatile("st.shared.v2.b32 [%0], {%1, %2};" ::"r"(a + 2 * GT_SPLIT),
-                   "r"(pack_bf16x2(lv[0], lv[1])), "r"(pack_bf16x2(lv[2], lv[3]))
+      asm volatile("st.shared.v2.b32 [%0], {%1, %2};" ::"r"(a + 2 * GT_SPLIT), "r"(lp[0]),
+                   "r"(lp[1])
                    : "memory");
     }
 #pragma unroll

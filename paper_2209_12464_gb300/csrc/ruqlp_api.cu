@@ -120,7 +120,7 @@ constexpr int kMaxSplits = 64;
 
 // Workspace layout for one problem.
 struct Layout {
-  size_t X, Y, Z, P, partial, G, Gf, R, Rw, Bt, frag, colptr, rowidx, cvals, cscratch, T, Om,
+  size_t X, Y, Z, P, partial, G, Gf, R, Rw, St, Bt, frag, colptr, rowidx, cvals, cscratch, T, Om,
       lrT1, lrT2, lrTmp, lrPart, svdW, svdV, svdS, svdOrd, svdTmp, svdU, svdVs, total;
 };
 
@@ -155,6 +155,8 @@ Layout layout_of(int64_t m, int64_t n, int d, Ty ct, int64_t nnz = -1, size_t va
     if (chol_tiles_supported(d) && chol_tiles_bytes(d) > rw) rw = chol_tiles_bytes(d);
     L.Rw = take(rw);
   }
+  // S = R^{-1} as three BF16 parts for the tensor-core Q = Y S
+  if (work_ty(ct) == Ty::F32 && dp <= 256) L.St = take(qmul_st_bytes(d));
   if (ct == Ty::BF16 && nnz < 0) {
     L.Bt = take((size_t)dp * round8(m > n ? m : n) * 2);
     L.frag = take(tc_frag_bytes(dp <= 256 ? dp : 256));  // per column chunk
@@ -346,8 +348,12 @@ ruqlp_status orth(ruqlp_ctx* h, const Layout& Lo, const Job& J, const void* Yin,
         }
         ProfScope pt(h, PROF_TRSM);
         const bool bt = make_bt && pass == passes - 1;
-        CK(trsm_tiles_f32(src, dp, (const float*)Rw, (float*)Qout, dp, M, d, st,
-                          bt ? base + Lo.Bt : nullptr, round8(M)));
+        if (!h->orth_simt && Lo.St != 0 && qmul_supported(M, d, dp, src, dp, Qout))
+          CK(qmul_tc(src, dp, (const float*)Rw, M, d, base + Lo.St, (float*)Qout, dp,
+                     bt ? base + Lo.Bt : nullptr, round8(M), &h->status->timeout, st));
+        else
+          CK(trsm_tiles_f32(src, dp, (const float*)Rw, (float*)Qout, dp, M, d, st,
+                            bt ? base + Lo.Bt : nullptr, round8(M)));
         if (bt && bt_made) *bt_made = true;
       } else {
         CK(chol_upper(G, d, s1, R, Rw, Ty::F32, h->status, nullptr, st, Ty::F32, pass == 0));

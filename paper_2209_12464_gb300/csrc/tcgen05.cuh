@@ -124,11 +124,35 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-__device__ __forceinline__ uint32_t pack_bf16x2(float a, float b) {
-  const uint32_t lo = __bfloat16_as_ushort(__float2bfloat16_rn(a));
-  const uint32_t hi = __bfloat16_as_ushort(__float2bfloat16_rn(b));
-  return lo | (hi << 16);
+// x rounded to BF16 (round to nearest even) as FP32 bits (low 16 bits zero),
+// by integer arithmetic on the full-rate ALUs; equal to __float2bfloat16_rn
+// for every finite x.
+__device__ __forceinline__ uint32_t bf16_rne_bits(float x) {
+  const uint32_t u = __float_as_uint(x);
+  return (u + 0x7FFFu + ((u >> 16) & 1u)) & 0xFFFF0000u;
 }
+
+// Three-way BF16 split x = h + m + l (h = bf16(x), m = bf16(x - h),
+// l = bf16(x - h - m)) of four values, packed as BF16 pairs:
+// hp[0] = (h1, h0), hp[1] = (h3, h2), likewise mp, lp.
+__device__ __forceinline__ void split3_bf16x4(const float (&v)[4], uint32_t (&hp)[2],
+                                              uint32_t (&mp)[2], uint32_t (&lp)[2]) {
+  uint32_t hb[4], mb[4], lb[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    hb[j] = bf16_rne_bits(v[j]);
+    const float r1 = v[j] - __uint_as_float(hb[j]);
+    mb[j] = bf16_rne_bits(r1);
+    lb[j] = bf16_rne_bits(r1 - __uint_as_float(mb[j]));
+  }
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    hp[q] = __byte_perm(hb[2 * q], hb[2 * q + 1], 0x7632);
+    mp[q] = __byte_perm(mb[2 * q], mb[2 * q + 1], 0x7632);
+    lp[q] = __byte_perm(lb[2 * q], lb[2 * q + 1], 0x7632);
+  }
+}
+
 
 }  // namespace
 }  // namespace ruqlp

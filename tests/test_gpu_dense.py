@@ -206,8 +206,9 @@ def test_light_and_full_intermediate_orth_agree(handle, case):
                                    (8192, 8192, 230, 26, 1)],
                          ids=["Ytall", "YZtall-q2", "d256"])
 def test_tensor_core_orth_matches_cuda_core_orth(handle, shape):
-    """orth() of tall Y and Z with tensor-core Grams (three-way BF16 split)
-    against the CUDA-core FP32 Gram (option orth_simt).  Compared where the
+    """orth() of tall Y and Z on the tensor cores (three-way BF16 split Gram
+    and Q = Y R^{-1}) against the CUDA-core FP32 Gram and blocked triangular
+    solve (option orth_simt).  Compared where the
     results are well determined whatever the rounding: the singular values of L (those of Q^T A P depend
     on the spans of Q and P only), the leading-k subspaces of Q and P (largest
     principal-angle sine), orthonormality, and the relative residual.  Single
