@@ -177,6 +177,10 @@ cudaError_t btrsm(const BMat* T, const int* prefix, int total, int count, int sr
 bool gram_tc_supported(int64_t M, int d, int64_t ldy, const void* Y);
 int gram_tc_ctas(int64_t M);
 size_t gram_tc_part_bytes(int d);
+// The upper triangle of C = X^T Y (same shape and rules as gram_tc; the
+// strictly lower triangle of C is set to zero): R_B = P^T B^T.
+cudaError_t gram_tc_upper(const float* X, const float* Y, int64_t ld, int64_t M, int d,
+                          float* part, double* C, int* err, cudaStream_t st);
 // Q = Y R^{-1} on the tensor cores (tall FP32 Y, M >= 8192, d <= 256): the
 // blocked Cholesky's tiles are inverted into St (qmul_st_bytes(d) bytes,
 // S^T as three BF16 parts), then Q (may alias Y) = Y S; Bt (optional)

@@ -492,14 +492,26 @@ namespace {
 // stage.  Slab sums (FP32) go to part[c]; k_gram_tc_reduce adds them in CTA
 // order with compensated FP32 summation.
 constexpr int GT_THREADS = 512;
-constexpr int GT_ROWS = 64;                      // rows per chunk
-constexpr uint32_t GT_BOX = 64 * 128;            // [64 rows][64 BF16] box, 8 KB
-constexpr uint32_t GT_SPLIT = 4 * GT_BOX;        // 256 columns
-constexpr uint32_t GT_STAGE = 3 * GT_SPLIT;      // h, m, l: 96 KB
+constexpr uint32_t GT_STAGE = 96 * 1024;  // h, m, l of one (or two) operands
+// Rows per chunk: 64 for Y^T Y, 32 for X^T Y (two operands per stage).
+template <bool SYM>
+struct GtShape {
+  static constexpr int ROWS = SYM ? 64 : 32;
+  static constexpr uint32_t BOX = ROWS * 128;     // [ROWS][64 BF16] box
+  static constexpr uint32_t SPLIT = 4 * BOX;      // 256 columns
+  static constexpr uint32_t OPER = 3 * SPLIT;     // h, m, l
+};
 
+// SYM: C = Y^T Y; else C = Y^T Y2 (A operand from Y, B from Y2; only the
+// upper block triangle is formed).
+template <bool SYM>
 __global__ void __launch_bounds__(GT_THREADS, 1)
-k_gram_tc(const float* __restrict__ Y, int64_t ldy, int64_t M, int d, int dp, int64_t slab_rows,
-          float* __restrict__ part, int* err) {
+k_gram_tc(const float* __restrict__ Y, const float* __restrict__ Y2, int64_t ldy, int64_t M,
+          int d, int dp, int64_t slab_rows, float* __restrict__ part, int* err) {
+  using Sh = GtShape<SYM>;
+  constexpr int GT_ROWS = Sh::ROWS;
+  constexpr uint32_t GT_BOX = Sh::BOX, GT_SPLIT = Sh::SPLIT;
+  constexpr uint32_t B_OFF = SYM ? 0 : Sh::OPER;  // B operand parts
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
   const uint32_t base = (raw + 1023u) & ~1023u;
@@ -535,17 +547,20 @@ k_gram_tc(const float* __restrict__ Y, int64_t ldy, int64_t M, int d, int dp, in
   const int n1 = dp > 128 ? dp - 128 : 16;  // M tile 1: columns 128..dp-1
   const uint32_t idesc1 = (idesc & ~(0x3Fu << 17)) | ((uint32_t)(n1 >> 3) << 17);
   bool ok = true;
-  // 64 rows x 64 groups of 4 columns (256 columns, zero beyond d) per chunk;
-  // chunk i + 1's loads are in flight while chunk i is converted
-  constexpr int PER = GT_ROWS * 64 / GT_THREADS;
+  // per operand GT_ROWS rows x 64 groups of 4 columns (256 columns, zero
+  // beyond d) per chunk; chunk i + 1's loads are in flight while chunk i is
+  // converted.  Element e: operand e / (GT_ROWS * 64) (always 0 when SYM)
+  constexpr int PER = (SYM ? 1 : 2) * GT_ROWS * 64 / GT_THREADS;
+  constexpr int OPE = GT_ROWS * 64;  // float4 per operand and chunk
   auto load = [&](int i, float4 (&x)[PER]) {
     const int64_t r0 = r_begin + (int64_t)i * GT_ROWS;
 #pragma unroll
     for (int q = 0; q < PER; ++q) {
       const int e = t + q * GT_THREADS;
-      const int row = e >> 6, c = (e & 63) * 4;
+      const int row = (e % OPE) >> 6, c = (e & 63) * 4;
+      const float* src = (SYM || e < OPE) ? Y : Y2;
       x[q] = (r0 + row < r_end && c < dp)
-                 ? *reinterpret_cast<const float4*>(Y + (r0 + row) * ldy + c)
+                 ? *reinterpret_cast<const float4*>(src + (r0 + row) * ldy + c)
                  : make_float4(0.f, 0.f, 0.f, 0.f);
     }
   };
@@ -566,7 +581,8 @@ k_gram_tc(const float* __restrict__ Y, int64_t ldy, int64_t M, int d, int dp, in
 #pragma unroll
     for (int q = 0; q < PER; ++q) {
       const int e = t + q * GT_THREADS;
-      const int row = e >> 6, c = (e & 63) * 4;
+      const int row = (e % OPE) >> 6, c = (e & 63) * 4;
+      const uint32_t obase = (SYM || e < OPE) ? 0u : Sh::OPER;
       float v[4] = {(c < d) ? xv[q].x : 0.f, (c + 1 < d) ? xv[q].y : 0.f,
                     (c + 2 < d) ? xv[q].z : 0.f, (c + 3 < d) ? xv[q].w : 0.f};
       uint32_t hp[2], mp[2], lp[2];
@@ -574,7 +590,7 @@ k_gram_tc(const float* __restrict__ Y, int64_t ldy, int64_t M, int d, int dp, in
       const int box = c >> 6, cb = c & 63;
       const uint32_t off = (uint32_t)box * GT_BOX + (uint32_t)row * 128 +
                            ((uint32_t)((cb >> 3) ^ (row & 7)) << 4) + (uint32_t)((cb & 7) * 2);
-      const uint32_t a = stage + off;
+      const uint32_t a = stage + obase + off;
       asm volatile("st.shared.v2.b32 [%0], {%1, %2};" ::"r"(a), "r"(hp[0]), "r"(hp[1]) : "memory");
       asm volatile("st.shared.v2.b32 [%0], {%1, %2};" ::"r"(a + GT_SPLIT), "r"(mp[0]), "r"(mp[1])
                    : "memory");
@@ -602,8 +618,8 @@ k_gram_tc(const float* __restrict__ Y, int64_t ldy, int64_t M, int d, int dp, in
           for (int q = 0; q < 6; ++q) {
             const uint64_t ad = sdesc(stage + pa[q] * GT_SPLIT + 2 * mt * GT_BOX + kk * 2048,
                                       GT_BOX, 1024);
-            const uint64_t bd = sdesc(stage + pb[q] * GT_SPLIT + 2 * mt * GT_BOX + kk * 2048,
-                                      GT_BOX, 1024);
+            const uint64_t bd = sdesc(
+                stage + B_OFF + pb[q] * GT_SPLIT + 2 * mt * GT_BOX + kk * 2048, GT_BOX, 1024);
             mma_bf16(tmem_base + (uint32_t)(mt * 256), ad, bd, id,
                      (i > 0 || kk > 0 || q > 0) ? 1u : 0u);
           }
@@ -680,7 +696,8 @@ __device__ __forceinline__ void two_sum_acc(float& s, float& c, float x) {
 // z = w, w + 8, ... in order, then the 8 warp sums are added in warp order
 // (a fixed, deterministic order).
 __global__ void __launch_bounds__(256) k_gram_tc_reduce(const float* __restrict__ part, int P,
-                                                        int d, int dp, double* __restrict__ C,
+                                                        int d, int dp, bool sym,
+                                                        double* __restrict__ C,
                                                         float* __restrict__ Cf) {
   __shared__ float ws[8][33], wc[8][33];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -710,12 +727,12 @@ __global__ void __launch_bounds__(256) k_gram_tc_reduce(const float* __restrict_
       tc += wc[k][lane];
     }
     const double v = (double)t + (double)tc;
-    C[(int64_t)col * d + i] = v;
+    const float f = t + tc;
     C[(int64_t)i * d + col] = v;
+    if (i != col) C[(int64_t)col * d + i] = sym ? v : 0.0;
     if (Cf != nullptr) {
-      const float f = t + tc;
-      Cf[(int64_t)col * d + i] = f;
       Cf[(int64_t)i * d + col] = f;
+      if (i != col) Cf[(int64_t)col * d + i] = sym ? f : 0.f;
     }
   }
 }
@@ -732,10 +749,10 @@ size_t tc_frag_bytes(int dp) { return (size_t)sm_count() * 2 * BM * dp * sizeof(
 // Rows per CTA (a multiple of the 64-row chunk) and the number of CTAs, every
 // one of which gets rows; functions of M (and the SM count) only.
 static int64_t gram_tc_slab(int64_t M) {
-  const int64_t chunks = (M + GT_ROWS - 1) / GT_ROWS;
+  const int64_t chunks = (M + 63) / 64;
   const int64_t p0 = std::min<int64_t>(sm_count(), std::max<int64_t>(chunks, 1));
   const int64_t slab = (M + p0 - 1) / p0;
-  return (slab + GT_ROWS - 1) / GT_ROWS * GT_ROWS;
+  return (slab + 63) / 64 * 64;  // a multiple of both kernels' chunk
 }
 
 int gram_tc_ctas(int64_t M) {
@@ -754,23 +771,42 @@ bool gram_tc_supported(int64_t M, int d, int64_t ldy, const void* Y) {
          ldy >= dp;
 }
 
-cudaError_t gram_tc(const float* Y, int64_t ldy, int64_t M, int d, float* part, double* C,
-                    float* Cf, int* err, cudaStream_t st) {
-  if (!gram_tc_supported(M, d, ldy, Y)) return cudaErrorInvalidValue;
+static cudaError_t gram_tc_run(const float* Y, const float* Y2, int64_t ldy, int64_t M, int d,
+                               float* part, double* C, float* Cf, int* err, cudaStream_t st) {
+  if (!gram_tc_supported(M, d, ldy, Y) || (Y2 != nullptr && ((uintptr_t)Y2 & 15) != 0))
+    return cudaErrorInvalidValue;
   const int dp = (d + 15) / 16 * 16;
   const int P = gram_tc_ctas(M);
   const int64_t slab = gram_tc_slab(M);
   const size_t smem = 1024 + 2 * (size_t)GT_STAGE + 64;
-  cudaError_t e =
-      cudaFuncSetAttribute(k_gram_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  k_gram_tc<<<P, GT_THREADS, smem, st>>>(Y, ldy, M, d, dp, slab, part, err);
+  cudaError_t e;
+  if (Y2 == nullptr) {
+    e = cudaFuncSetAttribute(k_gram_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
+    if (e != cudaSuccess) return e;
+    k_gram_tc<true><<<P, GT_THREADS, smem, st>>>(Y, nullptr, ldy, M, d, dp, slab, part, err);
+  } else {
+    e = cudaFuncSetAttribute(k_gram_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
+    if (e != cudaSuccess) return e;
+    k_gram_tc<false><<<P, GT_THREADS, smem, st>>>(Y, Y2, ldy, M, d, dp, slab, part, err);
+  }
   count_launch();
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  k_gram_tc_reduce<<<dim3(d, (dp + 31) / 32), 256, 0, st>>>(part, P, d, dp, C, Cf);
+  k_gram_tc_reduce<<<dim3(d, (dp + 31) / 32), 256, 0, st>>>(part, P, d, dp, Y2 == nullptr, C, Cf);
   count_launch();
   return cudaGetLastError();
+}
+
+cudaError_t gram_tc(const float* Y, int64_t ldy, int64_t M, int d, float* part, double* C,
+                    float* Cf, int* err, cudaStream_t st) {
+  return gram_tc_run(Y, nullptr, ldy, M, d, part, C, Cf, err, st);
+}
+
+cudaError_t gram_tc_upper(const float* X, const float* Y, int64_t ld, int64_t M, int d,
+                          float* part, double* C, int* err, cudaStream_t st) {
+  return gram_tc_run(X, Y, ld, M, d, part, C, nullptr, err, st);
 }
 
 cudaError_t tc_gemm(bool trans, const void* A, int64_t lda, int64_t m, int64_t n, const void* Bt,

@@ -602,6 +602,10 @@ ruqlp_status run_dense(ruqlp_ctx* h, const Job& J0) {
   if (wt == Ty::F64)
     CK(simt_gemm_tn(wt, wt, Ty::F64, Mul::F64, Pb, dp, Z, dp, G, d, d, J.n, d,
                     tn_splits(d, J.n, d, kMaxSplits), partial, nullptr, st));
+  else if (!h->orth_simt && gram_tc_supported(J.n, d, dp, Pb) && gram_tc_supported(J.n, d, dp, Z))
+    // R_B is upper triangular: its upper triangle on the tensor cores
+    CK(gram_tc_upper((const float*)Pb, (const float*)Z, dp, J.n, d, (float*)partial, G,
+                     &h->status->timeout, st));
   else
     CK(gram_f32((const float*)Pb, dp, (const float*)Z, dp, J.n, d, d, G, partial, kMaxSplits,
                 nullptr, st));
