@@ -484,19 +484,22 @@ namespace {
 //   Y^T Y ~= h'h + h'm + m'h + m'm + h'l + l'h
 // (the dropped m'l, l'm, l'l terms are below 2^-26 of |y_i||y_j|).  Products
 // of BF16 parts are exact in FP32, so the result matches an FP32 Gram.
-// Each CTA (512 threads) owns a slab of rows; per 64-row chunk all threads
-// write the three parts into a 128B-swizzled shared-memory stage (both
-// operands MN-major: rows of Y are the contraction), and thread 0 issues
-// 2 (M tiles of 128 Gram rows) x 6 (part pairs) x 4 (K = 16 rows) MMAs with
-// N = dp into TMEM, while the threads convert the next chunk into the other
-// stage.  Slab sums (FP32) go to part[c]; k_gram_tc_reduce adds them in CTA
-// order with compensated FP32 summation.
-constexpr int GT_THREADS = 512;
-constexpr uint32_t GT_STAGE = 96 * 1024;  // h, m, l of one (or two) operands
-// Rows per chunk: 64 for Y^T Y, 32 for X^T Y (two operands per stage).
+// Each CTA owns a slab of rows.  Warps 0..7 write each chunk's three parts
+// into a 128B-swizzled stage of a four-deep ring (both operands MN-major:
+// rows of Y are the contraction); warp 8 issues, per chunk, 2 (M tiles of
+// 128 Gram rows) x 6 (part pairs) x K/16 MMAs with N = dp into TMEM (M tile
+// 1 only over the columns from 128 on: the upper triangle).  Slab sums (FP32)
+// go to part[c]; k_gram_tc_reduce adds them in CTA order with compensated
+// FP32 summation.
+constexpr int GT_CONV = 8;                      // converter / epilogue warps
+constexpr int GT_THREADS = 32 * (GT_CONV + 1);  // + the MMA warp
+constexpr int GT_NST = 4;                       // ring depth
+constexpr uint32_t GT_STAGE = 48 * 1024;        // h, m, l of one (or two) operands
+constexpr int GT_SLAB = 32;                     // slab rows: a multiple of this
+// Rows per chunk: 32 for Y^T Y, 16 for X^T Y (two operands per stage).
 template <bool SYM>
 struct GtShape {
-  static constexpr int ROWS = SYM ? 64 : 32;
+  static constexpr int ROWS = SYM ? 32 : 16;
   static constexpr uint32_t BOX = ROWS * 128;     // [ROWS][64 BF16] box
   static constexpr uint32_t SPLIT = 4 * BOX;      // 256 columns
   static constexpr uint32_t OPER = 3 * SPLIT;     // h, m, l
@@ -516,18 +519,25 @@ k_gram_tc(const float* __restrict__ Y, const float* __restrict__ Y2, int64_t ldy
   const uint32_t raw = smem_u32(smem_raw);
   const uint32_t base = (raw + 1023u) & ~1023u;
   uint8_t* base_ptr = smem_raw + (base - raw);
-  const uint32_t bar = base + 2 * GT_STAGE;  // done[0], done[1], drain
-  uint32_t* tmem_slot = (uint32_t*)(base_ptr + 2 * GT_STAGE + 32);
+  // barriers: full[NST] (8 arrivals), empty[NST] (MMA commit), done, drain
+  const uint32_t bar = base + GT_NST * GT_STAGE;
+  auto full = [&](int s) { return bar + 8u * s; };
+  auto empty = [&](int s) { return bar + 8u * (GT_NST + s); };
+  const uint32_t done = bar + 16u * GT_NST, drain = done + 8;
+  uint32_t* tmem_slot = (uint32_t*)(base_ptr + GT_NST * GT_STAGE + 16 * GT_NST + 32);
   __shared__ int s_abort;
   const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
   if (t == 0) {
-    mbar_init(bar, 1);
-    mbar_init(bar + 8, 1);
-    mbar_init(bar + 16, 1);
+    for (int s2 = 0; s2 < GT_NST; ++s2) {
+      mbar_init(full(s2), GT_CONV);
+      mbar_init(empty(s2), 1);
+    }
+    mbar_init(done, 1);
+    mbar_init(drain, 1);
     s_abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  if (warp == 0) {
+  if (warp == GT_CONV) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(
                      smem_u32(tmem_slot))
                  : "memory");
@@ -541,101 +551,116 @@ k_gram_tc(const float* __restrict__ Y, const float* __restrict__ Y2, int64_t ldy
   const int64_t r_begin = (int64_t)blockIdx.x * slab_rows;
   const int64_t r_end = min(M, r_begin + slab_rows);
   const int nchunks = r_end > r_begin ? (int)((r_end - r_begin + GT_ROWS - 1) / GT_ROWS) : 0;
-  // kind::f16, BF16 x BF16 -> FP32, A and B MN-major, M = 128, N = dp
-  const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | (1u << 15) | (1u << 16) |
-                         ((uint32_t)(dp >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
   const int n1 = dp > 128 ? dp - 128 : 16;  // M tile 1: columns 128..dp-1
-  const uint32_t idesc1 = (idesc & ~(0x3Fu << 17)) | ((uint32_t)(n1 >> 3) << 17);
   bool ok = true;
-  // per operand GT_ROWS rows x 64 groups of 4 columns (256 columns, zero
-  // beyond d) per chunk; chunk i + 1's loads are in flight while chunk i is
-  // converted.  Element e: operand e / (GT_ROWS * 64) (always 0 when SYM)
-  constexpr int PER = (SYM ? 1 : 2) * GT_ROWS * 64 / GT_THREADS;
-  constexpr int OPE = GT_ROWS * 64;  // float4 per operand and chunk
-  auto load = [&](int i, float4 (&x)[PER]) {
-    const int64_t r0 = r_begin + (int64_t)i * GT_ROWS;
-#pragma unroll
-    for (int q = 0; q < PER; ++q) {
-      const int e = t + q * GT_THREADS;
-      const int row = (e % OPE) >> 6, c = (e & 63) * 4;
-      const float* src = (SYM || e < OPE) ? Y : Y2;
-      x[q] = (r0 + row < r_end && c < dp)
-                 ? *reinterpret_cast<const float4*>(src + (r0 + row) * ldy + c)
-                 : make_float4(0.f, 0.f, 0.f, 0.f);
-    }
-  };
-  float4 xv[PER];
-  if (nchunks > 0) load(0, xv);
-  for (int i = 0; i < nchunks && ok; ++i) {
-    const int st = i & 1;
-    const uint32_t stage = base + st * GT_STAGE;
-    if (i >= 2) {  // chunk i - 2's MMAs have read this stage (all threads agree)
-      const bool w = mbar_wait(bar + 8 * st, (uint32_t)(((i >> 1) - 1) & 1), abort_flag);
-      if (__syncthreads_or(!w)) {
-        ok = false;
-        break;
-      }
-    }
-    float4 xn[PER];
-    if (i + 1 < nchunks) load(i + 1, xn);
-#pragma unroll
-    for (int q = 0; q < PER; ++q) {
-      const int e = t + q * GT_THREADS;
-      const int row = (e % OPE) >> 6, c = (e & 63) * 4;
-      const uint32_t obase = (SYM || e < OPE) ? 0u : Sh::OPER;
-      float v[4] = {(c < d) ? xv[q].x : 0.f, (c + 1 < d) ? xv[q].y : 0.f,
-                    (c + 2 < d) ? xv[q].z : 0.f, (c + 3 < d) ? xv[q].w : 0.f};
-      uint32_t hp[2], mp[2], lp[2];
-      split3_bf16x4(v, hp, mp, lp);
-      const int box = c >> 6, cb = c & 63;
-      const uint32_t off = (uint32_t)box * GT_BOX + (uint32_t)row * 128 +
-                           ((uint32_t)((cb >> 3) ^ (row & 7)) << 4) + (uint32_t)((cb & 7) * 2);
-      const uint32_t a = stage + obase + off;
-      asm volatile("st.shared.v2.b32 [%0], {%1, %2};" ::"r"(a), "r"(hp[0]), "r"(hp[1]) : "memory");
-      asm volatile("st.shared.v2.b32 [%0], {%1, %2};" ::"r"(a + GT_SPLIT), "r"(mp[0]), "r"(mp[1])
-                   : "memory");
-      asm volatile("st.shared.v2.b32 [%0], {%1, %2};" ::"r"(a + 2 * GT_SPLIT), "r"(lp[0]),
-                   "r"(lp[1])
-                   : "memory");
-    }
-#pragma unroll
-    for (int q = 0; q < PER; ++q) xv[q] = xn[q];
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    __syncthreads();
-    if (t == 0) {
-      tc_fence_after();
-      // part pairs (A part, B part): hh, hm, mh, mm, hl, lh.  M tile 0 is
-      // Gram rows 0..127 against all dp columns; M tile 1 (rows 128..) only
-      // needs the columns from 128 on (the upper triangle)
+
+  if (warp == GT_CONV) {
+    // ---------------- MMA issuer (one lane) ----------------
+    if (lane == 0) {
+      // kind::f16, BF16 x BF16 -> FP32, A and B MN-major, M = 128, N = dp
+      const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | (1u << 15) | (1u << 16) |
+                             ((uint32_t)(dp >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+      const uint32_t idesc1 = (idesc & ~(0x3Fu << 17)) | ((uint32_t)(n1 >> 3) << 17);
       const int pa[6] = {0, 0, 1, 1, 0, 2}, pb[6] = {0, 1, 0, 1, 2, 0};
+      for (int i = 0; i < nchunks; ++i) {
+        const int st = i % GT_NST;
+        const uint32_t stage = base + st * GT_STAGE;
+        if (!mbar_wait(full(st), (uint32_t)((i / GT_NST) & 1), abort_flag)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        // part pairs (A part, B part): hh, hm, mh, mm, hl, lh.  M tile 0 is
+        // Gram rows 0..127 against all dp columns; M tile 1 (rows 128..) only
+        // needs the columns from 128 on (the upper triangle)
 #pragma unroll
-      for (int kk = 0; kk < GT_ROWS / 16; ++kk) {
+        for (int kk = 0; kk < GT_ROWS / 16; ++kk) {
 #pragma unroll
-        for (int mt = 0; mt < 2; ++mt) {
-          if (mt == 1 && dp <= 128) break;
-          const uint32_t id = mt == 0 ? idesc : idesc1;
+          for (int mt = 0; mt < 2; ++mt) {
+            if (mt == 1 && dp <= 128) break;
+            const uint32_t id = mt == 0 ? idesc : idesc1;
+            const uint64_t a0 = sdesc(stage + 2 * mt * GT_BOX + kk * 2048, GT_BOX, 1024);
+            const uint64_t b0 = sdesc(stage + B_OFF + 2 * mt * GT_BOX + kk * 2048, GT_BOX, 1024);
 #pragma unroll
-          for (int q = 0; q < 6; ++q) {
-            const uint64_t ad = sdesc(stage + pa[q] * GT_SPLIT + 2 * mt * GT_BOX + kk * 2048,
-                                      GT_BOX, 1024);
-            const uint64_t bd = sdesc(
-                stage + B_OFF + pb[q] * GT_SPLIT + 2 * mt * GT_BOX + kk * 2048, GT_BOX, 1024);
-            mma_bf16(tmem_base + (uint32_t)(mt * 256), ad, bd, id,
-                     (i > 0 || kk > 0 || q > 0) ? 1u : 0u);
+            for (int q = 0; q < 6; ++q)
+              mma_bf16(tmem_base + (uint32_t)(mt * 256), a0 + (uint64_t)((pa[q] * GT_SPLIT) >> 4),
+                       b0 + (uint64_t)((pb[q] * GT_SPLIT) >> 4), id,
+                       (i > 0 || kk > 0 || q > 0) ? 1u : 0u);
           }
         }
+        mma_commit(empty(st));
       }
-      mma_commit(bar + 8 * st);
+      if (ok) mma_commit(done);
+      else s_abort = 1;
     }
+  } else {
+    // ---------------- converters (warps 0..7) ----------------
+    // per operand GT_ROWS rows x 64 groups of 4 columns (256 columns, zero
+    // beyond d) per chunk; chunk i + 1's loads are in flight while chunk i
+    // is converted.  Element e: operand e / (GT_ROWS * 64) (always 0 when SYM)
+    constexpr int PER = (SYM ? 1 : 2) * GT_ROWS * 64 / (GT_CONV * 32);
+    constexpr int OPE = GT_ROWS * 64;  // float4 per operand and chunk
+    auto load = [&](int i, float4 (&x)[PER]) {
+      const int64_t r0 = r_begin + (int64_t)i * GT_ROWS;
+#pragma unroll
+      for (int q = 0; q < PER; ++q) {
+        const int e = t + q * GT_CONV * 32;
+        const int row = (e % OPE) >> 6, c = (e & 63) * 4;
+        const float* src = (SYM || e < OPE) ? Y : Y2;
+        x[q] = (r0 + row < r_end && c < dp)
+                   ? *reinterpret_cast<const float4*>(src + (r0 + row) * ldy + c)
+                   : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+    };
+    auto step = [&](int i, float4 (&cur)[PER], float4 (&nxt)[PER]) {
+      const int st = i % GT_NST;
+      const uint32_t stage = base + st * GT_STAGE;
+      if (i >= GT_NST &&
+          !mbar_wait(empty(st), (uint32_t)(((i / GT_NST) - 1) & 1), abort_flag)) {
+        ok = false;
+        return;
+      }
+      if (i + 1 < nchunks) load(i + 1, nxt);
+      asm volatile("" ::: "memory");  // the loads are issued before the conversion
+#pragma unroll
+      for (int q = 0; q < PER; ++q) {
+        const int e = t + q * GT_CONV * 32;
+        const int row = (e % OPE) >> 6, c = (e & 63) * 4;
+        const uint32_t obase = (SYM || e < OPE) ? 0u : Sh::OPER;
+        float v[4] = {(c < d) ? cur[q].x : 0.f, (c + 1 < d) ? cur[q].y : 0.f,
+                      (c + 2 < d) ? cur[q].z : 0.f, (c + 3 < d) ? cur[q].w : 0.f};
+        uint32_t hp[2], mp[2], lp[2];
+        split3_bf16x4(v, hp, mp, lp);
+        const int box = c >> 6, cb = c & 63;
+        const uint32_t off = (uint32_t)box * GT_BOX + (uint32_t)row * 128 +
+                             ((uint32_t)((cb >> 3) ^ (row & 7)) << 4) + (uint32_t)((cb & 7) * 2);
+        const uint32_t a = stage + obase + off;
+        asm volatile("st.shared.v2.b32 [%0], {%1, %2};" ::"r"(a), "r"(hp[0]), "r"(hp[1])
+                     : "memory");
+        asm volatile("st.shared.v2.b32 [%0], {%1, %2};" ::"r"(a + GT_SPLIT), "r"(mp[0]),
+                     "r"(mp[1])
+                     : "memory");
+        asm volatile("st.shared.v2.b32 [%0], {%1, %2};" ::"r"(a + 2 * GT_SPLIT), "r"(lp[0]),
+                     "r"(lp[1])
+                     : "memory");
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) mbar_arrive(full(st));
+    };
+    float4 x0[PER], x1[PER];
+    if (nchunks > 0) load(0, x0);
+    for (int i = 0; i < nchunks && ok; ++i) {
+      if (i & 1) step(i, x1, x0);
+      else step(i, x0, x1);
+    }
+    // the accumulators are final once every MMA has completed
+    if (ok && nchunks > 0 && !mbar_wait(done, 0, abort_flag)) ok = false;
+    if (!ok) s_abort = 1;
   }
-  // wait for the last chunk's MMAs (they complete in issue order)
-  if (ok && nchunks > 0) {
-    const int last = nchunks - 1;
-    const bool w = mbar_wait(bar + 8 * (last & 1), (uint32_t)((last >> 1) & 1), abort_flag);
-    if (__syncthreads_or(!w)) ok = false;
-  }
-  if (!ok && t == 0) atomicExch(err, 1);
   __syncthreads();
+  if (*abort_flag) ok = false;
+  if (!ok && t == 0) atomicExch(err, 1);
   tc_fence_after();
   // epilogue: warp w reads TMEM lanes 32 (w % 4) .. +31 of M tile w / 4,
   // Gram rows 32 g .. 32 g + 31 with g = w (row block), and stores the
@@ -644,10 +669,10 @@ k_gram_tc(const float* __restrict__ Y, const float* __restrict__ Y2, int64_t ldy
   // 32 g + l, so each store is one contiguous 128-byte line.
   const int nbr = (dp + 31) / 32;
   float* P = part + (int64_t)blockIdx.x * nbr * dp * 32;
-  {
+  if (warp < GT_CONV) {
     const int mt = warp >> 2, g4 = warp & 3, g = warp;
     const int c0 = mt * 128, ncol = mt == 0 ? dp : n1;
-    if (warp < 8 && g < nbr && (mt == 0 || dp > 128)) {
+    if (g < nbr && (mt == 0 || dp > 128)) {
       for (int c = 32 * g4; c < ncol; c += 16) {
         float v[16];
         if (ok && nchunks > 0) {
@@ -665,14 +690,14 @@ k_gram_tc(const float* __restrict__ Y, const float* __restrict__ Y2, int64_t ldy
   }
   tc_fence_before();
   __syncthreads();
-  if (t == 0) {  // every MMA this CTA issued has completed before TMEM is freed
-    tc_fence_after();
-    mma_commit(bar + 16);
-    volatile int never = 0;
-    mbar_wait(bar + 16, 0, &never);
-  }
-  __syncthreads();
-  if (warp == 0) {
+  if (warp == GT_CONV) {
+    if (lane == 0) {  // every MMA this CTA issued has completed before TMEM is freed
+      volatile int never = 0;
+      tc_fence_after();
+      mma_commit(drain);
+      mbar_wait(drain, 0, &never);
+    }
+    __syncwarp();
     tc_fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem_base)
                  : "memory");
@@ -749,10 +774,10 @@ size_t tc_frag_bytes(int dp) { return (size_t)sm_count() * 2 * BM * dp * sizeof(
 // Rows per CTA (a multiple of the 64-row chunk) and the number of CTAs, every
 // one of which gets rows; functions of M (and the SM count) only.
 static int64_t gram_tc_slab(int64_t M) {
-  const int64_t chunks = (M + 63) / 64;
+  const int64_t chunks = (M + GT_SLAB - 1) / GT_SLAB;
   const int64_t p0 = std::min<int64_t>(sm_count(), std::max<int64_t>(chunks, 1));
   const int64_t slab = (M + p0 - 1) / p0;
-  return (slab + 63) / 64 * 64;  // a multiple of both kernels' chunk
+  return (slab + GT_SLAB - 1) / GT_SLAB * GT_SLAB;  // a multiple of both kernels' chunk
 }
 
 int gram_tc_ctas(int64_t M) {
@@ -778,7 +803,7 @@ static cudaError_t gram_tc_run(const float* Y, const float* Y2, int64_t ldy, int
   const int dp = (d + 15) / 16 * 16;
   const int P = gram_tc_ctas(M);
   const int64_t slab = gram_tc_slab(M);
-  const size_t smem = 1024 + 2 * (size_t)GT_STAGE + 64;
+  const size_t smem = 1024 + GT_NST * (size_t)GT_STAGE + 16 * GT_NST + 64;
   cudaError_t e;
   if (Y2 == nullptr) {
     e = cudaFuncSetAttribute(k_gram_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
