@@ -308,6 +308,8 @@ __global__ void __launch_bounds__(NTH)
 k_chol_tiles(const float* __restrict__ G, int d, double shift_rel, int force_shift,
              float* __restrict__ tiles, DevStatus* __restrict__ status,
              const int32_t* __restrict__ gate) {
+  pdl_launch();
+  pdl_wait();
   if (gate != nullptr && *gate == 0) return;
   chol_body<NTH>(G, d, shift_rel, force_shift, tiles, status);
 }
@@ -500,6 +502,8 @@ __device__ __forceinline__ void trsm_body(const float* __restrict__ Y, int64_t l
 __global__ void __launch_bounds__(2 * SR1)
 k_trsm_tiles(const float* __restrict__ Y, int64_t ldy, const float* __restrict__ tiles, float* X,
              int64_t ldx, int64_t M, int d, __nv_bfloat16* __restrict__ Bt, int64_t ldbt) {
+  pdl_launch();
+  pdl_wait();
   trsm_body<SR1>(Y, ldy, tiles, X, ldx, M, d, blockIdx.x, Bt, ldbt);
 }
 
@@ -577,9 +581,10 @@ cudaError_t chol_tiles_f32(const float* G, int d, double shift_rel, bool force_s
   cudaError_t e =
       cudaFuncSetAttribute(k_chol_tiles, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
-  k_chol_tiles<<<1, NTH, sm, st>>>(G, d, shift_rel, force_shift ? 1 : 0, tiles, status, gate);
+  e = launch_pdl(k_chol_tiles, dim3(1), dim3(NTH), sm, st, G, d, shift_rel, force_shift ? 1 : 0,
+                 tiles, status, gate);
   count_launch();
-  return cudaGetLastError();
+  return e == cudaSuccess ? cudaGetLastError() : e;
 }
 
 cudaError_t trsm_tiles_f32(const float* Y, int64_t ldy, const float* tiles, float* X, int64_t ldx,
@@ -590,10 +595,10 @@ cudaError_t trsm_tiles_f32(const float* Y, int64_t ldy, const float* tiles, floa
   cudaError_t e =
       cudaFuncSetAttribute(k_trsm_tiles, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
-  k_trsm_tiles<<<ceil_div(M, SR1), 2 * SR1, sm, st>>>(Y, ldy, tiles, X, ldx, M, d,
-                                                      (__nv_bfloat16*)Bt, ldbt);
+  e = launch_pdl(k_trsm_tiles, dim3(ceil_div(M, SR1)), dim3(2 * SR1), sm, st, Y, ldy, tiles, X,
+                 ldx, M, d, (__nv_bfloat16*)Bt, ldbt);
   count_launch();
-  return cudaGetLastError();
+  return e == cudaSuccess ? cudaGetLastError() : e;
 }
 
 }  // namespace ruqlp

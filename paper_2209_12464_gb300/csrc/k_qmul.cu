@@ -90,6 +90,8 @@ k_trinv(const float* __restrict__ tiles, int d, int dp, __nv_bfloat16* __restric
   const int J = blockIdx.x;
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5, nw = TI_THREADS / 32;
   const int rg = lane >> 2, cg = lane & 3;
+  pdl_launch();
+  pdl_wait();
   // shared: Scol[K] (K <= J), R_IK at Rs[K (K - 1) / 2 + I] (I < K <= J),
   // diagonal inverses Ds[K] (K < J)
   float* Scol = sm;
@@ -247,6 +249,8 @@ k_qmul_tc(const __grid_constant__ CUtensorMap tmS, const __grid_constant__ QmPar
   tc_fence_after();
   const uint32_t tmem_base = *tmem_slot;
   volatile int* abort_flag = &s_abort;
+  pdl_launch();
+  pdl_wait();
 
   const int dp = p.dp, d = p.d;
   const int nsteps = (dp + 63) / 64;  // K chunks per tile
@@ -473,9 +477,10 @@ cudaError_t qmul_tc(const float* Y, int64_t ldy, const float* tiles, int64_t M, 
   cudaError_t e =
       cudaFuncSetAttribute(k_trinv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ti_smem);
   if (e != cudaSuccess) return e;
-  k_trinv<<<nb, TI_THREADS, ti_smem, st>>>(tiles, d, dp, (__nv_bfloat16*)St);
+  e = launch_pdl(k_trinv, dim3(nb), dim3(TI_THREADS), ti_smem, st, tiles, d, dp,
+                 (__nv_bfloat16*)St);
   count_launch();
-  e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   CUtensorMap map;
   if (!make_map(&map, St, KP, (uint64_t)3 * dp, KP, 64, 256)) return cudaErrorInvalidValue;
@@ -494,9 +499,9 @@ cudaError_t qmul_tc(const float* Y, int64_t ldy, const float* tiles, int64_t M, 
   if (e != cudaSuccess) return e;
   const int64_t ntiles = (M + QM_BM - 1) / QM_BM;
   const int P = (int)std::min<int64_t>(ntiles, sm_count());
-  k_qmul_tc<<<P, QM_THREADS, QM_SMEM, st>>>(map, p);
+  e = launch_pdl(k_qmul_tc, dim3(P), dim3(QM_THREADS), QM_SMEM, st, map, p);
   count_launch();
-  return cudaGetLastError();
+  return e == cudaSuccess ? cudaGetLastError() : e;
 }
 
 }  // namespace ruqlp

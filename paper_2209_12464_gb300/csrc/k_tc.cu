@@ -201,6 +201,8 @@ __device__ __forceinline__ void tc_body(const W& w, int* err, int S, int dpmax) 
   tc_fence_after();
   const uint32_t tmem_base = *tmem_slot;
   volatile int* abort_flag = &s_abort;
+  pdl_launch();
+  pdl_wait();
 
   if (warp == 0) {
     // ---------------- TMA producer ----------------
@@ -360,6 +362,8 @@ k_btc_gemm(const BTcTile* __restrict__ list, int n, const BMat* __restrict__ T,
 __global__ void __launch_bounds__(256) k_tc_fixup(TcParams p, int P) {
   __shared__ int s_src[256];
   __shared__ int s_cnt[8];
+  pdl_launch();
+  pdl_wait();
   const int tt = blockIdx.x;  // tail tile index
   const int64_t KB = p.KB;
   const int64_t lo = tt * KB, hi = lo + KB;
@@ -548,6 +552,8 @@ k_gram_tc(const float* __restrict__ Y, const float* __restrict__ Y2, int64_t ldy
   tc_fence_after();
   const uint32_t tmem_base = *tmem_slot;
   volatile int* abort_flag = &s_abort;
+  pdl_launch();
+  pdl_wait();
   const int64_t r_begin = (int64_t)blockIdx.x * slab_rows;
   const int64_t r_end = min(M, r_begin + slab_rows);
   const int nchunks = r_end > r_begin ? (int)((r_end - r_begin + GT_ROWS - 1) / GT_ROWS) : 0;
@@ -725,6 +731,8 @@ __global__ void __launch_bounds__(256) k_gram_tc_reduce(const float* __restrict_
                                                         double* __restrict__ C,
                                                         float* __restrict__ Cf) {
   __shared__ float ws[8][33], wc[8][33];
+  pdl_launch();
+  pdl_wait();
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int col = blockIdx.x, g = blockIdx.y, nbr = gridDim.y;
   if (col >= d || col < 32 * g) return;  // block-uniform
@@ -809,19 +817,22 @@ static cudaError_t gram_tc_run(const float* Y, const float* Y2, int64_t ldy, int
     e = cudaFuncSetAttribute(k_gram_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem);
     if (e != cudaSuccess) return e;
-    k_gram_tc<true><<<P, GT_THREADS, smem, st>>>(Y, nullptr, ldy, M, d, dp, slab, part, err);
+    e = launch_pdl(k_gram_tc<true>, dim3(P), dim3(GT_THREADS), smem, st, Y,
+                   (const float*)nullptr, ldy, M, d, dp, slab, part, err);
   } else {
     e = cudaFuncSetAttribute(k_gram_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem);
     if (e != cudaSuccess) return e;
-    k_gram_tc<false><<<P, GT_THREADS, smem, st>>>(Y, Y2, ldy, M, d, dp, slab, part, err);
+    e = launch_pdl(k_gram_tc<false>, dim3(P), dim3(GT_THREADS), smem, st, Y, Y2, ldy, M, d, dp,
+                   slab, part, err);
   }
   count_launch();
-  e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  k_gram_tc_reduce<<<dim3(d, (dp + 31) / 32), 256, 0, st>>>(part, P, d, dp, Y2 == nullptr, C, Cf);
+  e = launch_pdl(k_gram_tc_reduce, dim3(d, (dp + 31) / 32), dim3(256), 0, st, (const float*)part,
+                 P, d, dp, Y2 == nullptr, C, Cf);
   count_launch();
-  return cudaGetLastError();
+  return e == cudaSuccess ? cudaGetLastError() : e;
 }
 
 cudaError_t gram_tc(const float* Y, int64_t ldy, int64_t M, int d, float* part, double* C,
@@ -876,15 +887,15 @@ cudaError_t tc_gemm(bool trans, const void* A, int64_t lda, int64_t m, int64_t n
                                                (int)smem);
   if (e != cudaSuccess) return e;
   if (mark) mark(true);
-  if (trans) k_tc_gemm<true><<<P, NTHREADS, smem, st>>>(mA, mB, p);
-  else k_tc_gemm<false><<<P, NTHREADS, smem, st>>>(mA, mB, p);
+  e = trans ? launch_pdl(k_tc_gemm<true>, dim3(P), dim3(NTHREADS), smem, st, mA, mB, p)
+            : launch_pdl(k_tc_gemm<false>, dim3(P), dim3(NTHREADS), smem, st, mA, mB, p);
   if (mark) mark(false);
   count_launch();
-  e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaGetLastError();
   if (e != cudaSuccess || p.tail == 0) return e;
-  k_tc_fixup<<<dim3(p.tail, BM / 4), 256, 0, st>>>(p, P);
+  e = launch_pdl(k_tc_fixup, dim3(p.tail, BM / 4), dim3(256), 0, st, p, P);
   count_launch();
-  return cudaGetLastError();
+  return e == cudaSuccess ? cudaGetLastError() : e;
 }
 
 bool btc_encode(void* maps3, const void* A, int64_t lda, int64_t m, int64_t n, const void* Bt,
