@@ -58,10 +58,11 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--size", type=int, default=0, help="override m = n (testing only)")
     ap.add_argument("--workload", default="dense",
-                    choices=["dense", "batch", "serve", "csr", "csrlr"],
+                    choices=["dense", "batch", "serve", "csr", "csrlr", "orth"],
                     help="dense: one 20000 x 20000 matrix (the metric's workload); batch: "
                          "512 matrices of uneven shapes in one batched call; serve: Poisson "
-                         "arrivals through ruqlp_submit / ruqlp_poll")
+                         "arrivals through ruqlp_submit / ruqlp_poll; orth: ruqlp_orth of a "
+                         "20000 x 220 FP32 matrix (the dense workload's sketch shape)")
     ap.add_argument("--duration", type=float, default=2.0,
                     help="seconds of arrivals (serve workload)")
     ap.add_argument("--rate", type=float, default=2000.0, help="arrivals per second (serve)")
@@ -744,6 +745,47 @@ print(json.dumps({"seconds": t, "nnz": int(A["values"].shape[0])}))
                       "20000 x 100000 CSR of the same form (k=100, p=10, q=1)"}
 
 
+def run_orth(args, torch, dev, local, world, rank, dist):
+    """ruqlp_orth (shifted CholeskyQR3) of a seeded 20000 x 220 FP32 matrix
+    with condition number about 1e3, the shape of the dense workload's
+    sketch."""
+    from paper_2209_12464_gb300 import ruqlp
+    rows, d = M, K_RANK + P_OVER
+    g = torch.Generator(device=dev)
+    g.manual_seed(20000 + d)
+    U = torch.randn(rows, d, generator=g, device=dev)
+    # W = I + 0.1 N(0, 1/d): well conditioned (no torch.linalg, which a
+    # profiler run cannot load)
+    W = torch.eye(d, device=dev) + 0.1 * torch.randn(d, d, generator=g, device=dev) / d ** 0.5
+    s = torch.logspace(0, -3, d, device=dev)
+    Y = ((U * s[None, :]) @ W).contiguous()
+    stream = torch.cuda.current_stream(dev)
+    h = ruqlp.Handle(local, stream.cuda_stream)
+    for _ in range(max(args.warmup, 3)):
+        Q = h.orth(Y)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        Q = h.orth(Y)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / max(args.steps, 1)
+    err = float(torch.max(torch.abs(Q.double().T @ Q.double() - torch.eye(d, device=dev,
+                                                                        dtype=torch.float64))))
+    if rank == 0:
+        print(json.dumps({"metric": "ruqlp_orth time per call", "value": ms, "unit": "ms",
+                          "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+                          "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
+                          "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                          "config": {"workload": f"orth of a {rows} x {d} FP32 matrix, kappa ~1e3 "
+                                                 "(three CholeskyQR passes)"},
+                          "accuracy": {"max_abs_QtQ_minus_I": err}}))
+    h.close()
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -758,9 +800,9 @@ def main():
     import __graft_entry__ as g
     g.build()
     from paper_2209_12464_gb300 import ruqlp
-    if args.workload in ("batch", "serve", "csr", "csrlr"):
+    if args.workload in ("batch", "serve", "csr", "csrlr", "orth"):
         fn = {"batch": run_batch, "serve": run_serve, "csr": run_csr,
-              "csrlr": run_csr}[args.workload]
+              "csrlr": run_csr, "orth": run_orth}[args.workload]
         rc = fn(args, torch, dev, local, world, rank, dist)
         if world > 1:
             dist.destroy_process_group()
