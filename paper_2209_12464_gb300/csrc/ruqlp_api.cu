@@ -327,7 +327,6 @@ ruqlp_status orth(ruqlp_ctx* h, const Layout& Lo, const Job& J, const void* Yin,
   const int d = J.d, dp = J.dp;
   const Ty wt = J.wt;
   cudaStream_t st = h->stream;
-  CK(status_clear_shift(h->status, st));
   if (wt == Ty::F32 && !h->orth_fp64) {
     const double s1 = 64.0 * 5.960464477539063e-08;
     const bool blocked = chol_tiles_supported(d);
@@ -367,6 +366,7 @@ ruqlp_status orth(ruqlp_ctx* h, const Layout& Lo, const Job& J, const void* Yin,
       11.0 * ((double)M * d + (double)d * (d + 1)) * 1.1102230246251565e-16;
   const int S = tn_splits(d, M, d, kMaxSplits);
   const int32_t* gate = &h->status->shifted;
+  CK(status_clear_shift(h->status, st));  // this orth's shift flag gates pass 3
   // pass 1
   CK(simt_gemm_tn(wt, wt, Ty::F64, g, Yin, dp, Yin, dp, G, d, d, M, d, S, partial, nullptr, st));
   CK(chol_upper(G, d, srel, R, Rw, wt, h->status, nullptr, st));
