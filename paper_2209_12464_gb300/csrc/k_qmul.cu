@@ -65,6 +65,30 @@ __device__ __forceinline__ void tile_nn44(const float* __restrict__ A, const flo
   }
 }
 
+// The same over k in [k0, k0 + 8) only (one quarter of the contraction).
+__device__ __forceinline__ void tile_nn44_q(const float* __restrict__ A, const float* __restrict__ B,
+                                            int rg, int c0, int k0, float (&acc)[4][4]) {
+#pragma unroll
+  for (int k = k0; k < k0 + 8; k += 4) {
+    float4 a[4], b[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) a[i] = *reinterpret_cast<const float4*>(A + (rg + 8 * i) * TP + k);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) b[q] = *reinterpret_cast<const float4*>(B + (k + q) * TP + c0);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const float av[4] = {a[i].x, a[i].y, a[i].z, a[i].w};
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        acc[i][0] = fmaf(av[q], b[q].x, acc[i][0]);
+        acc[i][1] = fmaf(av[q], b[q].y, acc[i][1]);
+        acc[i][2] = fmaf(av[q], b[q].z, acc[i][2]);
+        acc[i][3] = fmaf(av[q], b[q].w, acc[i][3]);
+      }
+    }
+  }
+}
+
 // 32 x 32 tile (pitch 32, global) -> shared (pitch TP) with cp.async
 __device__ __forceinline__ void fetch_tile(float* dst, const float* src, int t, int nt) {
   for (int e = t; e < TB * 8; e += nt) {
@@ -97,6 +121,7 @@ k_trinv(const float* __restrict__ tiles, int d, int dp, __nv_bfloat16* __restric
   float* Scol = sm;
   float* Rs = Scol + (size_t)nb * TILE_F;
   float* Ds = Rs + (size_t)nb * (nb - 1) / 2 * TILE_F;
+  float* Ps = Ds + (size_t)nb * TILE_F;  // 4 partial products (k quarters)
   auto rtile = [&](int I, int K) { return tiles + (size_t)bidx(I, K, nb) * TB * TB; };
   auto dtile = [&](int K) { return tiles + (size_t)(ntiles + K) * TB * TB; };
   fetch_tile(Scol + (size_t)J * TILE_F, dtile(J), t, TI_THREADS);
@@ -133,18 +158,31 @@ k_trinv(const float* __restrict__ tiles, int d, int dp, __nv_bfloat16* __restric
             make_float4(a4[i][0], a4[i][1], a4[i][2], a4[i][3]);
     }
     __syncthreads();
-    // S_{K-1,J} = -S_{K-1,K-1} acc_{K-1}, in place: a warp per column half
-    // reads its whole strip before writing it
-    if (warp < 2) {
-      const int c0 = warp * 16 + cg * 4;
+    // S_{K-1,J} = -S_{K-1,K-1} acc_{K-1}, in place: warps (column half,
+    // k quarter) form partial products, then every thread adds the four
+    // partials of two entries in quarter order
+    float* D = Scol + (size_t)(K - 1) * TILE_F;
+    if (warp < 8) {
+      const int c0 = (warp & 1) * 16 + cg * 4, kq = warp >> 1;
       float o[4][4] = {};
-      float* D = Scol + (size_t)(K - 1) * TILE_F;
-      tile_nn44(Ds + (size_t)(K - 1) * TILE_F, D, rg, c0, o);
-      __syncwarp();
+      tile_nn44_q(Ds + (size_t)(K - 1) * TILE_F, D, rg, c0, 8 * kq, o);
+      float* Pq = Ps + (size_t)kq * TILE_F;
 #pragma unroll
       for (int i = 0; i < 4; ++i)
-        *reinterpret_cast<float4*>(D + (rg + 8 * i) * TP + c0) =
-            make_float4(-o[i][0], -o[i][1], -o[i][2], -o[i][3]);
+        *reinterpret_cast<float4*>(Pq + (rg + 8 * i) * TP + c0) =
+            make_float4(o[i][0], o[i][1], o[i][2], o[i][3]);
+    }
+    __syncthreads();
+    for (int e = t; e < TB * TB / 2; e += TI_THREADS) {
+      const int r = e >> 4, c = (e & 15) * 2;
+      float2 v = *reinterpret_cast<const float2*>(Ps + r * TP + c);
+#pragma unroll
+      for (int q = 1; q < 4; ++q) {
+        const float2 w = *reinterpret_cast<const float2*>(Ps + (size_t)q * TILE_F + r * TP + c);
+        v.x += w.x;
+        v.y += w.y;
+      }
+      *reinterpret_cast<float2*>(D + r * TP + c) = make_float2(-v.x, -v.y);
     }
     __syncthreads();
   }
@@ -473,7 +511,7 @@ cudaError_t qmul_tc(const float* Y, int64_t ldy, const float* tiles, int64_t M, 
     return cudaErrorInvalidValue;
   const int dp = (d + 15) / 16 * 16;
   const int nb = (d + TB - 1) / TB;
-  const size_t ti_smem = (size_t)(nb + nb * (nb - 1) / 2 + nb) * TILE_F * sizeof(float);
+  const size_t ti_smem = (size_t)(nb + nb * (nb - 1) / 2 + nb + 4) * TILE_F * sizeof(float);
   cudaError_t e =
       cudaFuncSetAttribute(k_trinv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ti_smem);
   if (e != cudaSuccess) return e;
