@@ -52,6 +52,11 @@ struct ruqlp_ctx {
   size_t stage_bytes = 0;
   int batch_graphs = 1;  // option "batch_graph"
   cudaStream_t cap_stream = nullptr;  // capture stream (the legacy stream cannot capture)
+  // host-buffer entry: large copies split over these streams (more copy
+  // engines), joined back into `stream` by events
+  static constexpr int kCopyStreams = 4;
+  cudaStream_t copy_streams[kCopyStreams] = {};
+  cudaEvent_t copy_ev[kCopyStreams + 1] = {};
   int64_t prof_count[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
   double prof_ms[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
   // request loop of ruqlp_submit / ruqlp_poll (created on the first submit)

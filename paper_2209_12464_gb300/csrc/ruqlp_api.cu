@@ -1125,6 +1125,10 @@ ruqlp_status ruqlp_destroy(ruqlp_handle h) {
   for (auto& g : h->batches)
     if (g.exec) cudaGraphExecDestroy(g.exec);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+  for (int i = 0; i < ruqlp_ctx::kCopyStreams; ++i)
+    if (h->copy_streams[i]) cudaStreamDestroy(h->copy_streams[i]);
+  for (int i = 0; i <= ruqlp_ctx::kCopyStreams; ++i)
+    if (h->copy_ev[i]) cudaEventDestroy(h->copy_ev[i]);
   if (h->stage) cudaFreeHost(h->stage);
   if (h->arena) cudaFree(h->arena);
   if (h->status) cudaFree(h->status);
@@ -1199,6 +1203,36 @@ ruqlp_status ruqlp_decompose(ruqlp_handle h, const ruqlp_matrix* A, const ruqlp_
   return single_end(h, out);
 }
 
+// A 2-D copy (rows of `width` bytes) split by rows over the handle's copy
+// streams, so that several copy engines share it; it starts once `st` reaches
+// this point and `st` continues once every part has landed.  Contiguous
+// blocks (both pitches equal to the width) go as 1-D copies.
+static ruqlp_status copy_split(ruqlp_ctx* h, void* dst, size_t dpitch, const void* src,
+                               size_t spitch, size_t width, size_t rows, cudaMemcpyKind kind,
+                               cudaStream_t st) {
+  constexpr int NS = ruqlp_ctx::kCopyStreams;
+  if (!h->copy_streams[0]) {
+    for (int i = 0; i < NS; ++i)
+      CK(cudaStreamCreateWithFlags(&h->copy_streams[i], cudaStreamNonBlocking));
+    for (int i = 0; i <= NS; ++i) CK(cudaEventCreateWithFlags(&h->copy_ev[i], cudaEventDisableTiming));
+  }
+  const int parts = (int)std::min<size_t>(NS, std::max<size_t>(1, rows * width >> 24));  // >= 16 MB each
+  CK(cudaEventRecord(h->copy_ev[NS], st));
+  const bool flat = dpitch == width && spitch == width;
+  for (int i = 0; i < parts; ++i) {
+    const size_t r0 = rows * i / parts, r1 = rows * (i + 1) / parts;
+    cudaStream_t cs = h->copy_streams[i];
+    CK(cudaStreamWaitEvent(cs, h->copy_ev[NS], 0));
+    char* d = (char*)dst + r0 * dpitch;
+    const char* s = (const char*)src + r0 * spitch;
+    if (flat) CK(cudaMemcpyAsync(d, s, (r1 - r0) * width, kind, cs));
+    else CK(cudaMemcpy2DAsync(d, dpitch, s, spitch, width, r1 - r0, kind, cs));
+    CK(cudaEventRecord(h->copy_ev[i], cs));
+    CK(cudaStreamWaitEvent(st, h->copy_ev[i], 0));
+  }
+  return RUQLP_OK;
+}
+
 ruqlp_status ruqlp_decompose_host(ruqlp_handle h, const ruqlp_matrix* A,
                                   const ruqlp_params* prm, ruqlp_outputs* out) {
   if (!h) return RUQLP_ERR_INVALID;
@@ -1255,8 +1289,9 @@ ruqlp_status ruqlp_decompose_host(ruqlp_handle h, const ruqlp_matrix* A,
     J.vals = base + oV;
   } else {
     const size_t aes = ty_size(J.ct);
-    CK(cudaMemcpy2DAsync(base + oA, (size_t)lds * aes, A->dense.data, (size_t)A->dense.ld * aes,
-                         (size_t)n * aes, (size_t)m, cudaMemcpyHostToDevice, st));
+    s = copy_split(h, base + oA, (size_t)lds * aes, A->dense.data, (size_t)A->dense.ld * aes,
+                   (size_t)n * aes, (size_t)m, cudaMemcpyHostToDevice, st);
+    if (s != RUQLP_OK) return s;
     J.A = base + oA;
     J.lda = lds;
   }
@@ -1272,9 +1307,13 @@ ruqlp_status ruqlp_decompose_host(ruqlp_handle h, const ruqlp_matrix* A,
              tc_supported(J.A, J.lda, std::min(J.dp, 256));
   s = run_dense(h, J);
   if (s != RUQLP_OK) return s;
-  CK(cudaMemcpyAsync(out->Q, base + oQ, (size_t)m * d * oes, cudaMemcpyDeviceToHost, st));
+  s = copy_split(h, out->Q, (size_t)d * oes, base + oQ, (size_t)d * oes, (size_t)d * oes,
+                 (size_t)m, cudaMemcpyDeviceToHost, st);
+  if (s != RUQLP_OK) return s;
   CK(cudaMemcpyAsync(out->L, base + oL, (size_t)d * d * oes, cudaMemcpyDeviceToHost, st));
-  CK(cudaMemcpyAsync(out->P, base + oP, (size_t)n * d * oes, cudaMemcpyDeviceToHost, st));
+  s = copy_split(h, out->P, (size_t)d * oes, base + oP, (size_t)d * oes, (size_t)d * oes,
+                 (size_t)n, cudaMemcpyDeviceToHost, st);
+  if (s != RUQLP_OK) return s;
   return finish(h, out);
 }
 
