@@ -845,6 +845,21 @@ cudaError_t gram_tc_upper(const float* X, const float* Y, int64_t ld, int64_t M,
   return gram_tc_run(X, Y, ld, M, d, part, C, nullptr, err, st);
 }
 
+namespace {
+// Dynamic shared memory of the product kernels: 1 KB alignment slack, the
+// ring, the 2 S + 5 mbarriers and the TMEM address word.
+size_t tc_smem(int stages, size_t stage_bytes) {
+  return 1024 + stages * stage_bytes + 8 * (2 * stages + 5) + 16;
+}
+// The deepest ring (at most 8 stages) within 226 KB of the 227 KB a CTA may
+// opt into: 5 stages of 44 KB at dp = 224, 4 of 48 KB at dp = 256.
+int tc_stages(size_t stage_bytes) {
+  int s = 8;
+  while (s > 0 && tc_smem(s, stage_bytes) > 226 * 1024) --s;
+  return s;
+}
+}  // namespace
+
 cudaError_t tc_gemm(bool trans, const void* A, int64_t lda, int64_t m, int64_t n, const void* Bt,
                     int64_t ldb, int dp, float* out, int64_t ldo, float* frag, int* err,
                     cudaStream_t st, const std::function<void(bool)>& mark) {
@@ -874,11 +889,10 @@ cudaError_t tc_gemm(bool trans, const void* A, int64_t lda, int64_t m, int64_t n
   p.tail = p.T - p.full_waves * P;
   p.U = (int64_t)p.tail * p.KB;
   const size_t stage_bytes = A_TILE_BYTES + (size_t)dp * BK * 2;
-  int stages = (int)((200 * 1024) / stage_bytes);
-  if (stages > 8) stages = 8;
+  const int stages = tc_stages(stage_bytes);
   if (stages < 2) return cudaErrorInvalidValue;
   p.stages = stages;
-  const size_t smem = 1024 + stages * stage_bytes + 8 * (2 * stages + 5) + 16;
+  const size_t smem = tc_smem(stages, stage_bytes);
   cudaError_t e = trans ? cudaFuncSetAttribute(k_tc_gemm<true>,
                                                cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                (int)smem)
@@ -919,9 +933,9 @@ cudaError_t btc_gemm(bool trans, const BMat* T, int count, const BTcTile* list, 
   if (n <= 0) return cudaSuccess;
   if (dpmax < 16 || dpmax > 256 || dpmax % 16) return cudaErrorInvalidValue;
   const size_t stage_bytes = A_TILE_BYTES + (size_t)dpmax * BK * 2;
-  int stages = (int)((200 * 1024) / stage_bytes);
-  if (stages > 8) stages = 8;
-  const size_t smem = 1024 + stages * stage_bytes + 8 * (2 * stages + 5) + 16;
+  const int stages = tc_stages(stage_bytes);
+  if (stages < 2) return cudaErrorInvalidValue;
+  const size_t smem = tc_smem(stages, stage_bytes);
   cudaError_t e = trans ? cudaFuncSetAttribute(k_btc_gemm<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    (int)smem)
             : cudaFuncSetAttribute(k_btc_gemm<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
