@@ -214,6 +214,7 @@ constexpr int QM_BM = 128;
 constexpr uint32_t QM_APART = QM_BM * 128;       // A part: [128 rows][64 BF16], 16 KB
 constexpr uint32_t QM_ASTAGE = 3 * QM_APART;     // 48 KB
 constexpr uint32_t QM_BPART = 256 * 128;         // B part: [256 rows][64 BF16], 32 KB
+constexpr uint32_t QM_BBOX = 64 * 128;           // one TMA box of a part: 64 rows, 8 KB
 constexpr uint32_t QM_B = 3 * QM_BPART;          // 96 KB
 constexpr int QM_SP = 20;                        // epilogue staging pitch (floats)
 constexpr uint32_t QM_STG = QM_CONV * 32 * QM_SP * 4;  // 20 KB
@@ -228,17 +229,21 @@ struct QmParams {
   __nv_bfloat16* Bt;  // optional Q^T (dp x ldbt)
   int64_t ldbt;
   int64_t M;
+  int64_t R;  // rows per CTA
+  int gs;     // sub-tiles per group (1 or 2)
   int d, dp;
   int* err;
 };
 
-// Per 128-row tile, K chunk c (k in [64 c, 64 c + 64)) contributes to the
-// output columns n >= 64 c only: one MMA chain of width N = dp - 64 c.
-// Warps 0..7 convert Y chunks into two A stages and drain finished
-// accumulators (the epilogue of tile i - 1 runs after the first chunk of
-// tile i, while its MMAs proceed); warp 8 loads the S parts of each chunk
-// with TMA into one B buffer; warp 9 issues the MMAs.  Two TMEM
-// accumulators (2 x 256 columns).
+// Every CTA owns an equal range of ceil(M / CTAs) rows (so no CTA takes a
+// second tile while the others idle), handled as groups of two 128-row
+// sub-tiles that share each chunk's S load.  K chunk c (k in [64 c, 64 c +
+// 64)) contributes to the output columns n >= 64 c only: per sub-tile one MMA
+// chain of width N = dp - 64 c, whose S rows 64 c .. dp - 1 come in 64-row TMA
+// boxes.  Warps 0..7 convert Y chunks into the two A stages (one per
+// sub-tile) and drain the accumulators (the epilogue of group g - 1 runs
+// after chunk 0 of group g is converted); warp 8 loads the S parts; warp 9
+// issues the MMAs.  One TMEM accumulator per sub-tile (2 x 256 columns).
 __global__ void __launch_bounds__(QM_THREADS, 1)
 k_qmul_tc(const __grid_constant__ CUtensorMap tmS, const __grid_constant__ QmParams p) {
   extern __shared__ uint8_t smem_raw[];
@@ -291,30 +296,46 @@ k_qmul_tc(const __grid_constant__ CUtensorMap tmS, const __grid_constant__ QmPar
   pdl_wait();
 
   const int dp = p.dp, d = p.d;
-  const int nsteps = (dp + 63) / 64;  // K chunks per tile
-  const int64_t ntiles = (p.M + QM_BM - 1) / QM_BM;
-  const int my_tiles =
-      (int64_t)blockIdx.x < ntiles ? (int)((ntiles - 1 - blockIdx.x) / gridDim.x + 1) : 0;
-  const int total = my_tiles * nsteps;
+  const int nsteps = (dp + 63) / 64;  // K chunks
+  // this CTA's rows [r_begin, r_end), in groups of gs (1 or 2) 128-row
+  // sub-tiles.  gs = 2: sub-tile s uses A stage s and accumulator s.  gs = 1:
+  // the steps alternate between the A stages and the groups between the
+  // accumulators, so the epilogue of a group overlaps the next one's MMAs.
+  const int gs = p.gs;
+  const int64_t r_begin = (int64_t)blockIdx.x * p.R;
+  const int64_t r_end = min(p.M, r_begin + p.R);
+  const int ngroups =
+      r_end > r_begin ? (int)((r_end - r_begin + gs * QM_BM - 1) / (gs * QM_BM)) : 0;
+  auto sub_row0 = [&](int g, int s) { return r_begin + (int64_t)(gs * g + s) * QM_BM; };
+  auto nsub = [&](int g) { return gs == 2 && sub_row0(g, 1) < r_end ? 2 : 1; };
+  // A stage of sub-tile s at step j and its use count before step j
+  auto astage = [&](int j, int s) { return gs == 2 ? s : (j & 1); };
+  auto ause = [&](int j) { return gs == 2 ? j : (j >> 1); };
+  // accumulator of sub-tile s of group g and its use count before group g
+  auto aset = [&](int g, int s) { return gs == 2 ? s : (g & 1); };
+  auto acc_use = [&](int g) { return gs == 2 ? g : (g >> 1); };
+  const int total = ngroups * nsteps;
 
   if (warp == QM_PROD) {
-    // ---------------- TMA producer: S^T parts, rows 64 c .. ----------------
+    // ---------------- TMA producer: S^T parts, rows 64 c .. dp - 1 ----------------
     if (lane == 0) {
       const uint64_t pol = policy_evict_last();
       bool pending = false;
       uint32_t pend_par = 0;
-      for (int g = 0; g < total; ++g) {
-        const int c = g % nsteps;
-        if (g >= 1 && !mbar_wait(b_empty, (uint32_t)((g - 1) & 1), abort_flag)) {
+      for (int j = 0; j < total; ++j) {
+        const int c = j % nsteps;
+        const int nbox = (dp - 64 * c + 63) / 64;  // 64-row boxes per part
+        if (j >= 1 && !mbar_wait(b_empty, (uint32_t)((j - 1) & 1), abort_flag)) {
           s_abort = 1;
           break;
         }
-        mbar_expect_tx(b_full, 3 * QM_BPART);
-#pragma unroll
+        mbar_expect_tx(b_full, 3u * (uint32_t)nbox * QM_BBOX);
         for (int q = 0; q < 3; ++q)
-          tma_load_2d(sB + q * QM_BPART, &tmS, b_full, 64 * c, q * dp + 64 * c, pol);
+          for (int b = 0; b < nbox; ++b)
+            tma_load_2d(sB + q * QM_BPART + b * QM_BBOX, &tmS, b_full, 64 * c,
+                        q * dp + 64 * c + 64 * b, pol);
         pending = true;
-        pend_par = (uint32_t)(g & 1);
+        pend_par = (uint32_t)(j & 1);
       }
       volatile int never = 0;
       // the last copy must land before the CTA exits (the MMA warp waited for
@@ -326,39 +347,45 @@ k_qmul_tc(const __grid_constant__ CUtensorMap tmS, const __grid_constant__ QmPar
     if (lane == 0) {
       bool ok = true;
       const int pa[6] = {0, 0, 1, 1, 0, 2}, pb[6] = {0, 1, 0, 1, 2, 0};
-      int g = 0;
-      for (int i = 0; i < my_tiles && ok; ++i) {
-        const int set = i & 1;
-        if (i >= 2 && !mbar_wait(acc_empty(set), (uint32_t)(((i >> 1) - 1) & 1), abort_flag)) {
-          ok = false;
-          break;
-        }
+      const uint64_t bd0 = sdesc(sB, 16, 1024);
+      for (int g = 0; g < ngroups && ok; ++g) {
+        const int ns = nsub(g), v = acc_use(g);
+        // the accumulators were drained by the epilogue of their last group
+        for (int s = 0; s < ns && v >= 1 && ok; ++s)
+          ok = mbar_wait(acc_empty(aset(g, s)), (uint32_t)((v - 1) & 1), abort_flag);
+        if (!ok) break;
         tc_fence_after();
-        for (int c = 0; c < nsteps; ++c, ++g) {
-          const int st = g & 1;
-          const uint32_t stA = base + st * QM_ASTAGE;
-          if (!mbar_wait(a_full(st), (uint32_t)((g >> 1) & 1), abort_flag) ||
-              !mbar_wait(b_full, (uint32_t)(g & 1), abort_flag)) {
+        for (int c = 0; c < nsteps; ++c) {
+          const int j = g * nsteps + c;
+          if (!mbar_wait(b_full, (uint32_t)(j & 1), abort_flag)) {
             ok = false;
             break;
           }
-          tc_fence_after();
           const int n = dp - 64 * c;
           const uint32_t id = idesc_bf16(n, false);
-          const uint32_t dcol = tmem_base + (uint32_t)(256 * set + 64 * c);
-          const uint64_t ad0 = sdesc(stA, 16, 1024), bd0 = sdesc(sB, 16, 1024);
-#pragma unroll
-          for (int kk = 0; kk < 4; ++kk) {
-#pragma unroll
-            for (int q = 0; q < 6; ++q) {
-              const uint64_t ad = ad0 + (uint64_t)((pa[q] * QM_APART + kk * 32) >> 4);
-              const uint64_t bd = bd0 + (uint64_t)((pb[q] * QM_BPART + kk * 32) >> 4);
-              mma_bf16(dcol, ad, bd, id, (c > 0 || kk > 0 || q > 0) ? 1u : 0u);
+          for (int s = 0; s < ns; ++s) {
+            const int st = astage(j, s), set = aset(g, s);
+            if (!mbar_wait(a_full(st), (uint32_t)(ause(j) & 1), abort_flag)) {
+              ok = false;
+              break;
             }
+            tc_fence_after();
+            const uint32_t dcol = tmem_base + (uint32_t)(256 * set + 64 * c);
+            const uint64_t ad0 = sdesc(base + st * QM_ASTAGE, 16, 1024);
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk) {
+#pragma unroll
+              for (int q = 0; q < 6; ++q) {
+                const uint64_t ad = ad0 + (uint64_t)((pa[q] * QM_APART + kk * 32) >> 4);
+                const uint64_t bd = bd0 + (uint64_t)((pb[q] * QM_BPART + kk * 32) >> 4);
+                mma_bf16(dcol, ad, bd, id, (c > 0 || kk > 0 || q > 0) ? 1u : 0u);
+              }
+            }
+            mma_commit(a_empty(st));
+            if (c == nsteps - 1) mma_commit(acc_full(set));
           }
-          mma_commit(a_empty(st));
+          if (!ok) break;
           mma_commit(b_empty);
-          if (c == nsteps - 1) mma_commit(acc_full(set));
         }
       }
       if (!ok) s_abort = 1;
@@ -366,14 +393,14 @@ k_qmul_tc(const __grid_constant__ CUtensorMap tmS, const __grid_constant__ QmPar
   } else {
     // ---------------- converters + epilogue (warps 0..7) ----------------
     const int ct = t;  // 0..255
-    // the A chunk of (tile i, chunk c): 128 rows x 64 columns of Y
-    auto load_a = [&](int i, int c, float4 (&x)[QM_PER]) {
-      const int64_t r0 = ((int64_t)blockIdx.x + (int64_t)i * gridDim.x) * QM_BM;
+    // unit (g, c, s): sub-tile s of group g, columns 64 c .. 64 c + 63 of Y
+    auto load_a = [&](int g, int c, int s, float4 (&x)[QM_PER]) {
+      const int64_t r0 = sub_row0(g, s);
 #pragma unroll
       for (int q = 0; q < QM_PER; ++q) {
         const int e = ct + q * QM_CONV * 32;
         const int row = e >> 4, k = c * 64 + (e & 15) * 4;
-        x[q] = (r0 + row < p.M && k < d)
+        x[q] = (r0 + row < r_end && k < d)
                    ? *reinterpret_cast<const float4*>(p.Y + (r0 + row) * p.ldy + k)
                    : make_float4(0.f, 0.f, 0.f, 0.f);
         if (k + 3 >= d && k < d) {  // zero the columns past d
@@ -383,22 +410,33 @@ k_qmul_tc(const __grid_constant__ CUtensorMap tmS, const __grid_constant__ QmPar
         }
       }
     };
+    // the unit after (g, c, s) in issue order; false after the last
+    auto next_unit = [&](int& g, int& c, int& s) {
+      if (s == 0 && nsub(g) == 2) {
+        s = 1;
+        return true;
+      }
+      s = 0;
+      if (++c == nsteps) {
+        c = 0;
+        if (++g == ngroups) return false;
+      }
+      return true;
+    };
     bool ok = true;
-    // one chunk step: wait for the A stage, start the next chunk's loads into
-    // nxt, convert cur into the stage, signal the MMA warp
-    auto step = [&](int g, int i, int c, float4 (&cur)[QM_PER], float4 (&nxt)[QM_PER]) {
-      const int st = g & 1;
+    // one unit: wait for its A stage, start the next unit's loads into nxt,
+    // convert cur into the stage, signal the MMA warp
+    auto unit = [&](int g, int c, int s, float4 (&cur)[QM_PER], float4 (&nxt)[QM_PER]) {
+      const int j = g * nsteps + c, st = astage(j, s), u = ause(j);
       const uint32_t stA = base + st * QM_ASTAGE;
-      if (g >= 2 && !mbar_wait(a_empty(st), (uint32_t)(((g >> 1) - 1) & 1), abort_flag)) {
+      if (u >= 1 &&
+          !__all_sync(0xffffffffu, mbar_wait(a_empty(st), (uint32_t)((u - 1) & 1), abort_flag))) {
         ok = false;
-        return;
+        return false;
       }
-      int ni = i, nc = c + 1;
-      if (nc == nsteps) {
-        nc = 0;
-        ++ni;
-      }
-      if (ni < my_tiles) load_a(ni, nc, nxt);
+      int ng = g, nc = c, nsb = s;
+      const bool more = next_unit(ng, nc, nsb);
+      if (more) load_a(ng, nc, nsb, nxt);
       asm volatile("" ::: "memory");  // the loads are issued before the conversion
 #pragma unroll
       for (int q = 0; q < QM_PER; ++q) {
@@ -422,58 +460,66 @@ k_qmul_tc(const __grid_constant__ CUtensorMap tmS, const __grid_constant__ QmPar
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       __syncwarp();
       if (lane == 0) mbar_arrive(a_full(st));
+      return more;
     };
-    // drain accumulator set j & 1 (tile j): warp w reads TMEM lanes
-    // 32 (w % 4) + lane (tile rows) and columns 128 (w / 4) .. + 127, stages
-    // 16 columns at a time and stores 64-byte row segments
+    // drain the accumulators of group g: warp w reads TMEM lanes
+    // 32 (w % 4) + lane (sub-tile rows) and columns 128 (w / 4) .. + 127,
+    // stages 16 columns at a time and stores 64-byte row segments
     float* stg = stg_all + warp * 32 * QM_SP;
-    auto epilogue = [&](int j) {
-      const int set = j & 1;
-      if (!mbar_wait(acc_full(set), (uint32_t)((j >> 1) & 1), abort_flag)) {
-        ok = false;
-        return;
-      }
-      tc_fence_after();
+    auto epilogue = [&](int g) {
       const int h = warp >> 2, q4 = warp & 3;
-      const int64_t rbase = ((int64_t)blockIdx.x + (int64_t)j * gridDim.x) * QM_BM + q4 * 32;
       const int c1 = min(dp, 128 * h + 128);
-      for (int col = 128 * h; col < c1; col += 16) {
-        float v[16];
-        tmem_ld16(tmem_base + (uint32_t)(256 * set + col) + ((uint32_t)(q4 * 32) << 16), v);
-#pragma unroll
-        for (int u = 0; u < 4; ++u)
-          *reinterpret_cast<float4*>(stg + lane * QM_SP + 4 * u) =
-              make_float4(v[4 * u], v[4 * u + 1], v[4 * u + 2], v[4 * u + 3]);
-        if (p.Bt != nullptr && rbase + lane < p.M) {
-#pragma unroll
-          for (int u = 0; u < 16; ++u)
-            p.Bt[(int64_t)(col + u) * p.ldbt + rbase + lane] = __float2bfloat16_rn(v[u]);
+      for (int s = 0; s < nsub(g); ++s) {
+        const int set = aset(g, s);
+        if (!__all_sync(0xffffffffu,
+                        mbar_wait(acc_full(set), (uint32_t)(acc_use(g) & 1), abort_flag))) {
+          ok = false;
+          return;
         }
-        __syncwarp();
+        tc_fence_after();
+        const int64_t rbase = sub_row0(g, s) + q4 * 32;
+        for (int col = 128 * h; col < c1; col += 16) {
+          float v[16];
+          tmem_ld16(tmem_base + (uint32_t)(256 * set + col) + ((uint32_t)(q4 * 32) << 16), v);
 #pragma unroll
-        for (int rr = 0; rr < 4; ++rr) {
-          const int row = rr * 8 + (lane >> 2), c4 = lane & 3;
-          if (rbase + row < p.M)
-            *reinterpret_cast<float4*>(p.Q + (rbase + row) * p.ldq + col + 4 * c4) =
-                *reinterpret_cast<const float4*>(stg + row * QM_SP + 4 * c4);
+          for (int u = 0; u < 4; ++u)
+            *reinterpret_cast<float4*>(stg + lane * QM_SP + 4 * u) =
+                make_float4(v[4 * u], v[4 * u + 1], v[4 * u + 2], v[4 * u + 3]);
+          if (p.Bt != nullptr && rbase + lane < r_end) {
+#pragma unroll
+            for (int u = 0; u < 16; ++u)
+              p.Bt[(int64_t)(col + u) * p.ldbt + rbase + lane] = __float2bfloat16_rn(v[u]);
+          }
+          __syncwarp();
+#pragma unroll
+          for (int rr = 0; rr < 4; ++rr) {
+            const int row = rr * 8 + (lane >> 2), c4 = lane & 3;
+            if (rbase + row < r_end)
+              *reinterpret_cast<float4*>(p.Q + (rbase + row) * p.ldq + col + 4 * c4) =
+                  *reinterpret_cast<const float4*>(stg + row * QM_SP + 4 * c4);
+          }
+          __syncwarp();
         }
+        tc_fence_before();
         __syncwarp();
+        if (lane == 0) mbar_arrive(acc_empty(set));
       }
-      tc_fence_before();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(acc_empty(set));
     };
-    float4 x0[QM_PER], x1[QM_PER];
-    if (my_tiles > 0) load_a(0, 0, x0);
-    int g = 0;
-    for (int i = 0; i < my_tiles && ok; ++i) {
-      for (int c = 0; c < nsteps && ok; ++c, ++g) {
-        if (g & 1) step(g, i, c, x1, x0);
-        else step(g, i, c, x0, x1);
-        if (c == 0 && i > 0 && ok) epilogue(i - 1);
+    if (ngroups > 0) {
+      float4 x0[QM_PER], x1[QM_PER];
+      load_a(0, 0, 0, x0);
+      int g = 0, c = 0, s = 0;
+      bool more = true;
+      for (int u = 0; more && ok; ++u) {
+        const int pg = g, pc = c, ps = s;
+        more = (u & 1) ? unit(g, c, s, x1, x0) : unit(g, c, s, x0, x1);
+        if (!ok) break;
+        if (more) next_unit(g, c, s);
+        // group pg - 1 is drained once chunk 0 of group pg is converted
+        if (pc == 0 && pg > 0 && ps == nsub(pg) - 1) epilogue(pg - 1);
       }
+      if (ok) epilogue(ngroups - 1);
     }
-    if (ok && my_tiles > 0) epilogue(my_tiles - 1);
     if (!ok) s_abort = 1;
   }
   __syncthreads();
@@ -521,7 +567,7 @@ cudaError_t qmul_tc(const float* Y, int64_t ldy, const float* tiles, int64_t M, 
   if (e == cudaSuccess) e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   CUtensorMap map;
-  if (!make_map(&map, St, KP, (uint64_t)3 * dp, KP, 64, 256)) return cudaErrorInvalidValue;
+  if (!make_map(&map, St, KP, (uint64_t)3 * dp, KP, 64, 64)) return cudaErrorInvalidValue;
   QmParams p;
   p.Y = Y;
   p.ldy = ldy;
@@ -535,8 +581,12 @@ cudaError_t qmul_tc(const float* Y, int64_t ldy, const float* tiles, int64_t M, 
   p.err = err;
   e = cudaFuncSetAttribute(k_qmul_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)QM_SMEM);
   if (e != cudaSuccess) return e;
-  const int64_t ntiles = (M + QM_BM - 1) / QM_BM;
-  const int P = (int)std::min<int64_t>(ntiles, sm_count());
+  // equal row ranges, one per CTA (at most one per SM); up to 256 rows a
+  // CTA's two sub-tiles share each S load, beyond that its 128-row sub-tiles
+  // pipeline one after another
+  p.R = (M + sm_count() - 1) / sm_count();
+  p.gs = p.R <= 2 * QM_BM ? 2 : 1;
+  const int P = (int)((M + p.R - 1) / p.R);
   e = launch_pdl(k_qmul_tc, dim3(P), dim3(QM_THREADS), QM_SMEM, st, map, p);
   count_launch();
   return e == cudaSuccess ? cudaGetLastError() : e;
