@@ -237,10 +237,11 @@ __device__ __forceinline__ void chol_body(const float* __restrict__ G, int d, do
     __syncthreads();
     const float fill = attempt == 0 ? 1.f : add;
     // Step K = -1 only factors the first diagonal tile; step K >= 0 does the
-    // panel of tile row K, the trailing update, then the next diagonal tile.
-    // (Overlapping that factorisation with the trailing update measured no
-    // faster: the one-warp chain slows down as much as the overlap saves.)
-    // The factorisation has one call site (its unrolled code is large).
+    // panel of tile row K, updates tile (K+1, K+1), then factors it on warp 0
+    // while the warps of the other three schedulers (warp % 4 != 0) do the
+    // rest of the trailing update, so that the one-warp chain keeps its issue
+    // slots.  The factorisation has one call site (its unrolled code is
+    // large).
     for (int K = -1; K < nb; ++K) {
       if (K >= 0) {
         if (s_bad) break;
@@ -268,11 +269,12 @@ __device__ __forceinline__ void chol_body(const float* __restrict__ G, int d, do
         }
         __syncthreads();
       }
-      // (c) trailing update B_IJ -= B_KI^T B_KJ, then the next diagonal tile
+      // (c) trailing update B_IJ -= B_KI^T B_KJ (items 0 and 1 are the two
+      // halves of tile (K+1, K+1)) and the next diagonal tile
       const int rem = nb - K - 1;
       if (rem > 0) {
         if (K >= 0) {
-          for (int u = warp; u < rem * (rem + 1); u += nw) update(K, rem, u);
+          if (warp < 2) update(K, rem, warp);
           __syncthreads();
         }
         if (warp == 0) {
@@ -281,6 +283,9 @@ __device__ __forceinline__ void chol_body(const float* __restrict__ G, int d, do
             if (attempt == 0) s_bad = 1;  // retry on G + shift I
             else s_rankdef = 1;           // pivots replaced by the shift
           }
+        } else if (K >= 0 && (warp & 3) != 0) {
+          const int nw3 = nw - nw / 4, w3 = warp - warp / 4 - 1;  // 0 .. nw3 - 1
+          for (int u = 2 + w3; u < rem * (rem + 1); u += nw3) update(K, rem, u);
         }
       }
       __syncthreads();
