@@ -156,6 +156,9 @@ def test_gram_entry_matches_fp64_products(handle, shape, dtype):
 ORTH_CASES = [  # M, d, log10 kappa
     (1000, 30, 1), (1000, 30, 5), (20011, 220, 3), (5003, 64, 6), (300, 300, 2), (129, 1, 0),
     (777, 37, 4), (4096, 272, 3), (9000, 100, 5), (16384, 256, 2), (8192, 17, 3),
+    # tall FP32 Y on the tensor cores: 152 equal row ranges of 256 rows (two
+    # full sub-tiles), of 257 (three sub-tiles, the last one row) and of 395
+    (38912, 64, 2), (38913, 64, 2), (60013, 96, 3),
 ]
 
 
