@@ -13,15 +13,14 @@
 //  * k_qmul_tc: Q = Y S with tcgen05.mma (BF16 x BF16 -> FP32 in TMEM).  Y is
 //    split the same way on the fly; of the nine part products the six above
 //    2^-24 are kept (hh, hm, mh, mm, hl, lh), so Q matches an FP32 product.
-//    One CTA per SM takes 128-row tiles; a tile is accumulated over 64-wide
-//    K chunks, chunk c only into the columns n >= 64 c (S is upper
-//    triangular).  Converter warps write the Y chunk's parts into one of two
-//    128B-swizzled stages while a producer warp loads the S parts with TMA
-//    and an MMA warp issues 6 x 4 MMAs per chunk; the epilogue of a tile
-//    drains TMEM (two accumulators) while the next tile's MMAs run, and
-//    stores Q (and optionally Q^T in BF16, the next product's operand).  A
-//    tile's rows are read in full before they are written, so Q may
-//    overwrite Y.
+//    One CTA per SM owns an equal range of rows, taken as 128-row sub-tiles;
+//    a sub-tile is accumulated over 64-wide K chunks, chunk c only into the
+//    columns n >= 64 c (S is upper triangular).  Converter warps write the Y
+//    chunk's parts into 128B-swizzled stages while a producer warp loads the
+//    S parts with TMA and an MMA warp issues 6 x 4 MMAs per chunk and
+//    sub-tile; the epilogue drains TMEM (two accumulators) and stores Q (and
+//    optionally Q^T in BF16, the next product's operand).  A sub-tile's rows
+//    are read in full before they are written, so Q may overwrite Y.
 // Every mbarrier wait is bounded; on timeout the CTA sets the error word,
 // waits for its own copies and MMAs, frees TMEM and returns.
 #include <cuda.h>
