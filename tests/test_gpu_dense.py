@@ -186,10 +186,10 @@ def test_orth_matches_householder_q(handle, case, dtype):
 
 @pytest.mark.parametrize("case", CASES[:4], ids=[c[0] for c in CASES[:4]])
 def test_light_and_full_intermediate_orth_agree(handle, case):
-    """Intermediate orth() results with one shifted CholeskyQR pass (default)
-    and with full orthonormalisation give the same Q, L, P within the FP32
-    tolerance (exact arithmetic: identical, the bases differ by upper-
-    triangular factors)."""
+    """Intermediate orth() results with two CholeskyQR passes (default) and
+    with the three passes of a final basis (option orth_full) give the same
+    Q, L, P within the FP32 tolerance (exact arithmetic: identical, the
+    bases differ by upper-triangular factors)."""
     name, m, n, k, p, q, tail = case
     A, Om = _case(*case, seed=wl.MASTER_SEED + 11 * m + n)
     Ag = torch.from_numpy(A).float().cuda()
