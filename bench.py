@@ -78,6 +78,22 @@ def dist_env():
             int(os.environ.get("WORLD_SIZE", 1)))
 
 
+def max_over_ranks(torch, dist, world, x, device):
+    """The largest x over the ranks (the slowest rank sets the job's time);
+    x itself on one rank."""
+    if world <= 1:
+        return x
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(world, units_per_rank, seconds):
+    """Whole-job throughput: the units every rank processed (the same on each
+    rank: weak scaling) over the slowest rank's time."""
+    return world * units_per_rank / seconds
+
+
 # ---------------------------------------------------------------------------
 # clocks sampled during the timed region
 # ---------------------------------------------------------------------------
@@ -326,15 +342,12 @@ def run_batch(args, torch, dev, local, world, rank, dist):
         dist.barrier()
     ck = clocks.stop()
     ms = e0.elapsed_time(e1) / max(args.steps, 1)
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(torch, dist, world, ms, dev)
     passes = 2 * B_Q + 2
     elements = sum(m * n for m, n, k, p in shapes)
     bytes_a = elements * DT_BYTES[args.dtype]
-    value = world * passes * bytes_a / (ms * 1e-3) / 1e9
-    dps = world * len(shapes) / (ms * 1e-3)
+    value = job_rate(world, passes * bytes_a / 1e9, ms * 1e-3)
+    dps = job_rate(world, len(shapes), ms * 1e-3)
 
     # accuracy on a sample: relative residual against the unrounded matrix
     # (FP64 on the device), and the same for the plain single-matrix FP32 path
@@ -436,13 +449,10 @@ def run_batch(args, torch, dev, local, world, rank, dist):
                     ht.copy_(t, non_blocking=True)
             torch.cuda.synchronize()
         te = (time.perf_counter() - t0) / ke
-        if world > 1:
-            t = torch.tensor([te], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            te = float(t.item())
-        e2e = {"value": world * passes * bytes_a / te / 1e9, "unit": "GB/s",
+        te = max_over_ranks(torch, dist, world, te, dev)
+        e2e = {"value": job_rate(world, passes * bytes_a / 1e9, te), "unit": "GB/s",
                "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo, "ms_per_step": te * 1e3,
-               "decompositions_per_s": world * len(shapes) / te}
+               "decompositions_per_s": job_rate(world, len(shapes), te)}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -644,14 +654,11 @@ def run_csr(args, torch, dev, local, world, rank, dist):
         dist.barrier()
     ck = clocks.stop()
     ms = e0.elapsed_time(e1) / max(args.steps, 1)
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(torch, dist, world, ms, dev)
     passes = 2 * q + 2
     vbytes = va.element_size()
     bytes_a = nnz * (4 + vbytes) + (m + 1) * 4  # CSR of A (the CSC copy of A^T is the same size)
-    value = world * passes * bytes_a / (ms * 1e-3) / 1e9
+    value = job_rate(world, passes * bytes_a / 1e9, ms * 1e-3)
     h.set_option("profile", 1)
     for _ in range(2):
         step()
@@ -845,13 +852,10 @@ def main():
         dist.barrier()
     ck = clocks.stop()
     ms = e0.elapsed_time(e1) / max(args.steps, 1)
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(torch, dist, world, ms, dev)
     bytes_a = m * n * DT_BYTES[args.dtype]
     passes = 2 * q + 2
-    value = world * passes * bytes_a / (ms * 1e-3) / 1e9
+    value = job_rate(world, passes * bytes_a / 1e9, ms * 1e-3)
 
     # accuracy at this speed (FP64 measurement on the device, against the
     # unrounded A)
@@ -925,13 +929,10 @@ def main():
         for _ in range(ke):
             h.decompose_host(Ah, Omh, k, p, q, ho)
         te = (time.perf_counter() - t0) / ke
-        if world > 1:
-            t = torch.tensor([te], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            te = float(t.item())
+        te = max_over_ranks(torch, dist, world, te, dev)
         bi = Ah.numel() * Ah.element_size() + Omh.numel() * 8
         bo = sum(x.numel() * x.element_size() for x in ho)
-        e2e = {"value": world * passes * bytes_a / te / 1e9, "unit": "GB/s",
+        e2e = {"value": job_rate(world, passes * bytes_a / 1e9, te), "unit": "GB/s",
                "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo, "ms_per_step": te * 1e3}
 
     cpu = None
