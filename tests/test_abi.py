@@ -65,3 +65,26 @@ def test_workspace_bytes_host_logic(lib):
 
 def test_version(lib):
     assert "sm_103a" in lib.ruqlp_version()
+
+
+def test_missing_library_raises_with_no_fallback(tmp_path):
+    """Without the built library every entry point raises (there is no CPU
+    or PyTorch path to fall back on)."""
+    code = "\n".join([
+        "import sys",
+        f"sys.path.insert(0, {ROOT!r})",
+        "from paper_2209_12464_gb300 import ruqlp",
+        f"ruqlp.LIB_PATH = {str(tmp_path / 'absent.so')!r}",
+        "for call in (lambda: ruqlp.lib(), lambda: ruqlp.Handle(0, 0),",
+        "             lambda: ruqlp.ruqlp_version()):",
+        "    try:",
+        "        call()",
+        "    except RuntimeError as e:",
+        "        print('raised', 'not built' in str(e))",
+        "    else:",
+        "        print('returned')",
+    ])
+    r = subprocess.run([__import__("sys").executable, "-c", code], capture_output=True, text=True,
+                       timeout=300)
+    assert r.returncode == 0, r.stderr
+    assert r.stdout.split() == ["raised", "True"] * 3, r.stdout
