@@ -54,10 +54,11 @@ size_t chol_tiles_bytes(int d);
 cudaError_t chol_tiles_f32(const float* G, int d, double shift_rel, bool force_shift,
                            float* tiles, DevStatus* status, const int32_t* gate, cudaStream_t st);
 // Bt (optional): also X^T in BF16 (dp x ldbt, zero rows d..dp), the next
-// tensor-core product's B operand.
+// tensor-core product's B operand; Btl (optional) its low part
+// bf16(x - bf16(x)) for the two-part product.
 cudaError_t trsm_tiles_f32(const float* Y, int64_t ldy, const float* tiles, float* X, int64_t ldx,
                            int64_t M, int d, cudaStream_t st, void* Bt = nullptr,
-                           int64_t ldbt = 0);
+                           int64_t ldbt = 0, void* Btl = nullptr);
 
 // C (d1 x d2, FP64, ld d2) = X^T W for FP32 X (M x d1, ld ldx) and W (M x d2,
 // ld ldw): FP32 products summed in FP32 within a row slab, slabs summed in
@@ -79,6 +80,12 @@ cudaError_t trsm_right_upper(Ty ty, const void* Y, int64_t ldy, const void* R, v
 cudaError_t copy_cast_2d(Ty ts, const void* src, int64_t lds, Ty td, void* dst, int64_t ldd,
                          int64_t rows, int64_t cols, cudaStream_t st);
 
+// dst[rows x cols] (FP32, ld ldd) <- src (F32 or F64) rounded to the sum of
+// its two BF16 parts, h + bf16(v - h) with h = bf16(v) (the skinny operand of
+// the two-part BF16 product on the CUDA cores).
+cudaError_t round2_bf16_2d(Ty ts, const void* src, int64_t lds, float* dst, int64_t ldd,
+                          int64_t rows, int64_t cols, cudaStream_t st);
+
 // L (d x d, type tl, ld ldl (0: d)) <- transpose of the upper triangle of R
 // (FP64, ld d), zeros above the diagonal.  With `upper` the upper triangle is
 // copied as is instead (finish_paper output).
@@ -91,17 +98,20 @@ cudaError_t write_L(const double* R, int d, Ty tl, void* L, bool upper, cudaStre
 // for the stream-K fragments; err: device word set on a wait timeout.
 // mark(true) / mark(false) are called right before / after the main kernel
 // launch (used to bracket it with profiling events); may be empty.
+// Btl (optional, same layout as Bt): the low BF16 part of the skinny operand;
+// then out = A (Bt + Btl)^T (or A^T ...), two MMAs per A tile.
 cudaError_t tc_gemm(bool trans, const void* A, int64_t lda, int64_t m, int64_t n, const void* Bt,
                     int64_t ldb, int dp, float* out, int64_t ldo, float* frag, int* err,
-                    cudaStream_t st, const std::function<void(bool)>& mark = {});
+                    cudaStream_t st, const std::function<void(bool)>& mark = {},
+                    const void* Btl = nullptr);
 size_t tc_frag_bytes(int dp);
 // Whether tc_gemm accepts these operands (alignment / size rules).
 bool tc_supported(const void* A, int64_t lda, int dp);
 
 // dst[dp x rows] (BF16, ld ldd) = transpose of src[rows x cols] (ld lds), rows
-// cols..dp-1 of dst zero.
+// cols..dp-1 of dst zero; lo (optional, same layout) the low BF16 parts.
 cudaError_t transpose_to_bf16(Ty ts, const void* src, int64_t lds, int64_t rows, int cols, int dp,
-                              void* dst, int64_t ldd, cudaStream_t st);
+                              void* dst, int64_t ldd, cudaStream_t st, void* lo = nullptr);
 
 // CSR products (k_csr.cu), values FP32 or BF16, dense operands FP32.
 // csr_validate ORs into *flag: 1 bad rowptr, 2 bad / unsorted / duplicate
@@ -136,6 +146,7 @@ struct BMat {
   const double* omega;  // NULL: generated from seed (philox.cuh)
   uint64_t seed;
   void* Bt;        // dp x ldbt BF16 (tensor-core items): the transposed skinny operand
+  void* Btl;       // its low BF16 part (same layout), for the two-part B^T = A^T Q
   int64_t ldbt;
   int use_tc, pad2;
   void* Qout;
@@ -158,18 +169,20 @@ __host__ __device__ inline int64_t gram_slabs(int64_t M, int max_slabs, int64_t*
   return (M + slab - 1) / slab;
 }
 int bgemm_tiles(int64_t rows, int d);
+// split2 (BF16 A): the skinny operand is rounded to the sum of its two BF16
+// parts (the two-part B^T = A^T Q), else to BF16.
 cudaError_t bgemm(bool trans, Ty ta, Ty tb, const BMat* T, const int* prefix, int total, int count,
-                  int src, int dst, cudaStream_t st);
+                  int src, int dst, cudaStream_t st, bool split2 = false);
 int bgram_tiles(int64_t M, int d, bool sym, int max_slabs);
 cudaError_t bgram(const BMat* T, const int* prefix, int total, int count, int src, int src2,
                   int max_slabs, int dmax, cudaStream_t st);
 int btrsm_blocks(int64_t M);
 cudaError_t bchol(const BMat* T, int count, double shift_rel, bool force_shift, int dmax,
                   cudaStream_t st);
-// make_bt: also write the result transposed in BF16 to each tensor-core
-// item's Bt (the next product's B operand).
+// make_bt: 1 = also write the result transposed in BF16 to each tensor-core
+// item's Bt (the next product's B operand); 2 = and its low part to Btl.
 cudaError_t btrsm(const BMat* T, const int* prefix, int total, int count, int src, int dst,
-                  int dmax, cudaStream_t st, bool make_bt = false);
+                  int dmax, cudaStream_t st, int make_bt = 0);
 // Tensor-core Gram C = Y^T Y of a tall FP32 Y (M >= 8192, d <= 256, ld a
 // multiple of 4, 16-byte aligned) via a three-way BF16 split; part holds
 // the FP32 slab sums (gram_tc_part_bytes(d) bytes at most); C (FP64) and Cf
@@ -184,11 +197,13 @@ cudaError_t gram_tc_upper(const float* X, const float* Y, int64_t ld, int64_t M,
 // Q = Y R^{-1} on the tensor cores (tall FP32 Y, M >= 8192, d <= 256): the
 // blocked Cholesky's tiles are inverted into St (qmul_st_bytes(d) bytes,
 // S^T as three BF16 parts), then Q (may alias Y) = Y S; Bt (optional)
-// receives Q^T in BF16 with leading dimension ldbt.  err: timeout word.
+// receives Q^T in BF16 with leading dimension ldbt, Btl (optional) its low
+// BF16 part.  err: timeout word.
 size_t qmul_st_bytes(int d);
 bool qmul_supported(int64_t M, int d, int64_t ldy, const void* Y, int64_t ldq, const void* Q);
 cudaError_t qmul_tc(const float* Y, int64_t ldy, const float* tiles, int64_t M, int d, void* St,
-                    float* Q, int64_t ldq, void* Bt, int64_t ldbt, int* err, cudaStream_t st);
+                    float* Q, int64_t ldq, void* Bt, int64_t ldbt, int* err, cudaStream_t st,
+                    void* Btl = nullptr);
 // 2-D BF16 tensor map (128-byte swizzle) over a row-major [outer][inner]
 // array with leading dimension ld_elems; box box_inner x box_outer.
 bool make_map(CUtensorMap* m, const void* ptr, uint64_t inner, uint64_t outer, uint64_t ld_elems,
@@ -218,14 +233,18 @@ cudaError_t omega_philox(uint64_t seed, int64_t n, int d, double* out, int64_t l
 struct BTcTile {
   int mat, tile;
 };
-// Encode the three tensor maps of one matrix (A, Bt over n, Bt over m) into
-// maps3 (3 x CUtensorMap, 64-byte aligned); a_only re-encodes A alone.
-bool btc_encode(void* maps3, const void* A, int64_t lda, int64_t m, int64_t n, const void* Bt,
-                int64_t ldbt, int dp, bool a_only);
+// Encode the four tensor maps of one matrix (A, Bt over n, Bt over m, Btl
+// over m) into maps4 (btc_map_bytes() bytes, 64-byte aligned); a_only
+// re-encodes A alone.
+bool btc_encode(void* maps4, const void* A, int64_t lda, int64_t m, int64_t n, const void* Bt,
+                const void* Btl, int64_t ldbt, int dp, bool a_only);
+// Bytes of one matrix's tensor maps.
 size_t btc_map_bytes();
-// buf[dst] = A Bt^T (trans: A^T Bt^T) for the tile list's matrices.
+// buf[dst] = A Bt^T (trans: A^T Bt^T) for the tile list's matrices; b2
+// (trans only): A^T (Bt + Btl)^T, the two-part product.
 cudaError_t btc_gemm(bool trans, const BMat* T, int count, const BTcTile* list, int n,
-                     const void* maps, int src, int dst, int dpmax, int* err, cudaStream_t st);
+                     const void* maps, int src, int dst, int dpmax, int* err, cudaStream_t st,
+                     bool b2 = false);
 cudaError_t bcast_omega(const BMat* T, int count, int64_t max_elems, cudaStream_t st);
 cudaError_t boutputs(const BMat* T, int count, int64_t max_elems, cudaStream_t st);
 

@@ -342,13 +342,15 @@ k_bchol(const BMat* __restrict__ T, double shift_rel, int force_shift) {
 constexpr int SR1 = 32, SRB = 128;
 constexpr int NPF = 3;        // tile buffers (prefetch distance NPF - 1)
 // Bt (optional): also write X^T in BF16 (dp x ldbt, K-major: the next
-// tensor-core product's B operand), zero in the padding rows d..dp.
+// tensor-core product's B operand), zero in the padding rows d..dp; Btl
+// (optional) the low parts bf16(x - bf16(x)) in the same layout.
 template <int SR>
 __device__ __forceinline__ void trsm_body(const float* __restrict__ Y, int64_t ldy,
                                           const float* __restrict__ tiles, float* X, int64_t ldx,
                                           int64_t M, int d, int rb,
                                           __nv_bfloat16* __restrict__ Bt = nullptr,
-                                          int64_t ldbt = 0) {
+                                          int64_t ldbt = 0,
+                                          __nv_bfloat16* __restrict__ Btl = nullptr) {
   constexpr int TT = 2 * SR, YP = SR + 4, RG = SR / 4;
   extern __shared__ __align__(16) float ys[];  // (nb * 32) x YP, ys[c * YP + r]
   __shared__ __align__(16) float Rt[NPF][TB][TB];
@@ -499,17 +501,24 @@ __device__ __forceinline__ void trsm_body(const float* __restrict__ Y, int64_t l
     const int dp = (d + 15) / 16 * 16;
     for (int e = t; e < SR * dp; e += TT) {
       const int r = e % SR, c = e / SR;
-      if (r < nr) Bt[(int64_t)c * ldbt + r0 + r] = __float2bfloat16_rn(c < d ? ys[c * YP + r] : 0.f);
+      if (r < nr) {
+        const float v = c < d ? ys[c * YP + r] : 0.f;
+        const __nv_bfloat16 hv = __float2bfloat16_rn(v);
+        Bt[(int64_t)c * ldbt + r0 + r] = hv;
+        if (Btl != nullptr)
+          Btl[(int64_t)c * ldbt + r0 + r] = __float2bfloat16_rn(v - __bfloat162float(hv));
+      }
     }
   }
 }
 
 __global__ void __launch_bounds__(2 * SR1)
 k_trsm_tiles(const float* __restrict__ Y, int64_t ldy, const float* __restrict__ tiles, float* X,
-             int64_t ldx, int64_t M, int d, __nv_bfloat16* __restrict__ Bt, int64_t ldbt) {
+             int64_t ldx, int64_t M, int d, __nv_bfloat16* __restrict__ Bt, int64_t ldbt,
+             __nv_bfloat16* __restrict__ Btl) {
   pdl_launch();
   pdl_wait();
-  trsm_body<SR1>(Y, ldy, tiles, X, ldx, M, d, blockIdx.x, Bt, ldbt);
+  trsm_body<SR1>(Y, ldy, tiles, X, ldx, M, d, blockIdx.x, Bt, ldbt, Btl);
 }
 
 // Batched: block t -> (matrix, 128-row block); M = rows of buf[src].
@@ -525,7 +534,8 @@ k_btrsm(const BMat* __restrict__ T, const int* __restrict__ prefix, int count, i
   const BMat& b = T[lo];
   const int64_t M = (src == B_Y) ? b.m : b.n;
   trsm_body<SRB>(bbuf(b, src), b.dp, b.tiles, bbuf(b, dst), b.dp, M, b.d, t - prefix[lo],
-            (make_bt && b.use_tc) ? (__nv_bfloat16*)b.Bt : nullptr, b.ldbt);
+            (make_bt && b.use_tc) ? (__nv_bfloat16*)b.Bt : nullptr, b.ldbt,
+            (make_bt == 2 && b.use_tc) ? (__nv_bfloat16*)b.Btl : nullptr);
 }
 
 }  // namespace
@@ -553,14 +563,14 @@ cudaError_t bchol(const BMat* T, int count, double shift_rel, bool force_shift, 
 }
 
 cudaError_t btrsm(const BMat* T, const int* prefix, int total, int count, int src, int dst,
-                  int dmax, cudaStream_t st, bool make_bt) {
+                  int dmax, cudaStream_t st, int make_bt) {
   if (total <= 0) return cudaSuccess;
   const int nb = (dmax + TB - 1) / TB;
   const size_t sm = (size_t)nb * TB * (SRB + 4) * sizeof(float);
   cudaError_t e =
       cudaFuncSetAttribute(k_btrsm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
-  k_btrsm<<<total, 2 * SRB, sm, st>>>(T, prefix, count, src, dst, make_bt ? 1 : 0);
+  k_btrsm<<<total, 2 * SRB, sm, st>>>(T, prefix, count, src, dst, make_bt);
   count_launch();
   return cudaGetLastError();
 }
@@ -593,7 +603,7 @@ cudaError_t chol_tiles_f32(const float* G, int d, double shift_rel, bool force_s
 }
 
 cudaError_t trsm_tiles_f32(const float* Y, int64_t ldy, const float* tiles, float* X, int64_t ldx,
-                           int64_t M, int d, cudaStream_t st, void* Bt, int64_t ldbt) {
+                           int64_t M, int d, cudaStream_t st, void* Bt, int64_t ldbt, void* Btl) {
   if (M <= 0) return cudaSuccess;
   const int nb = (d + TB - 1) / TB;
   const size_t sm = (size_t)nb * TB * (SR1 + 4) * sizeof(float);
@@ -601,7 +611,8 @@ cudaError_t trsm_tiles_f32(const float* Y, int64_t ldy, const float* tiles, floa
       cudaFuncSetAttribute(k_trsm_tiles, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
   e = launch_pdl(k_trsm_tiles, dim3(ceil_div(M, SR1)), dim3(2 * SR1), sm, st, Y, ldy, tiles, X,
-                 ldx, M, d, (__nv_bfloat16*)Bt, ldbt);
+                 ldx, M, d, (__nv_bfloat16*)Bt, ldbt,
+                 Bt != nullptr ? (__nv_bfloat16*)Btl : nullptr);
   count_launch();
   return e == cudaSuccess ? cudaGetLastError() : e;
 }

@@ -164,6 +164,19 @@ __global__ void k_copy_cast(const TS* __restrict__ src, int64_t lds, TD* __restr
   dst[i * ldd + j] = Cvt<TD>::from(src[i * lds + j]);
 }
 
+// dst = h + bf16(v - h), h = bf16(v): v rounded to the sum of its two BF16
+// parts (exact in FP32), the skinny operand of a two-part BF16 product.
+template <typename TS>
+__global__ void k_round2_bf16(const TS* __restrict__ src, int64_t lds, float* __restrict__ dst,
+                              int64_t ldd, int64_t rows, int64_t cols) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= rows * cols) return;
+  const int64_t i = idx / cols, j = idx % cols;
+  const float v = (float)src[i * lds + j];
+  const float h = __bfloat162float(__float2bfloat16_rn(v));
+  dst[i * ldd + j] = h + __bfloat162float(__float2bfloat16_rn(v - h));
+}
+
 template <typename TL>
 __global__ void k_write_L(const double* __restrict__ R, int d, TL* __restrict__ L, bool upper,
                           int ldl) {
@@ -245,6 +258,21 @@ cudaError_t trsm_right_upper(Ty ty, const void* Y, int64_t ldy, const void* R, v
     return cudaGetLastError();
   }
   return cudaErrorInvalidValue;
+}
+
+cudaError_t round2_bf16_2d(Ty ts, const void* src, int64_t lds, float* dst, int64_t ldd,
+                          int64_t rows, int64_t cols, cudaStream_t st) {
+  const int64_t tot = rows * cols;
+  if (tot <= 0) return cudaSuccess;
+  const int grid = ceil_div(tot, 256);
+  if (ts == Ty::F32)
+    k_round2_bf16<float><<<grid, 256, 0, st>>>((const float*)src, lds, dst, ldd, rows, cols);
+  else if (ts == Ty::F64)
+    k_round2_bf16<double><<<grid, 256, 0, st>>>((const double*)src, lds, dst, ldd, rows, cols);
+  else
+    return cudaErrorInvalidValue;
+  count_launch();
+  return cudaGetLastError();
 }
 
 cudaError_t copy_cast_2d(Ty ts, const void* src, int64_t lds, Ty td, void* dst, int64_t ldd,

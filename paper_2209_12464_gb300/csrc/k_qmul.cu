@@ -225,7 +225,8 @@ struct QmParams {
   int64_t ldy;
   float* Q;
   int64_t ldq;
-  __nv_bfloat16* Bt;  // optional Q^T (dp x ldbt)
+  __nv_bfloat16* Bt;   // optional Q^T (dp x ldbt)
+  __nv_bfloat16* Btl;  // optional low part of Q^T (two-part products)
   int64_t ldbt;
   int64_t M;
   int64_t R;  // rows per CTA
@@ -486,8 +487,13 @@ k_qmul_tc(const __grid_constant__ CUtensorMap tmS, const __grid_constant__ QmPar
                 make_float4(v[4 * u], v[4 * u + 1], v[4 * u + 2], v[4 * u + 3]);
           if (p.Bt != nullptr && rbase + lane < r_end) {
 #pragma unroll
-            for (int u = 0; u < 16; ++u)
-              p.Bt[(int64_t)(col + u) * p.ldbt + rbase + lane] = __float2bfloat16_rn(v[u]);
+            for (int u = 0; u < 16; ++u) {
+              const __nv_bfloat16 hv = __float2bfloat16_rn(v[u]);
+              p.Bt[(int64_t)(col + u) * p.ldbt + rbase + lane] = hv;
+              if (p.Btl != nullptr)
+                p.Btl[(int64_t)(col + u) * p.ldbt + rbase + lane] =
+                    __float2bfloat16_rn(v[u] - __bfloat162float(hv));
+            }
           }
           __syncwarp();
 #pragma unroll
@@ -551,7 +557,8 @@ bool qmul_supported(int64_t M, int d, int64_t ldy, const void* Y, int64_t ldq, c
 }
 
 cudaError_t qmul_tc(const float* Y, int64_t ldy, const float* tiles, int64_t M, int d, void* St,
-                    float* Q, int64_t ldq, void* Bt, int64_t ldbt, int* err, cudaStream_t st) {
+                    float* Q, int64_t ldq, void* Bt, int64_t ldbt, int* err, cudaStream_t st,
+                    void* Btl) {
   if (!qmul_supported(M, d, ldy, Y, ldq, Q) || ((uintptr_t)St & 15) != 0)
     return cudaErrorInvalidValue;
   const int dp = (d + 15) / 16 * 16;
@@ -573,6 +580,7 @@ cudaError_t qmul_tc(const float* Y, int64_t ldy, const float* tiles, int64_t M, 
   p.Q = Q;
   p.ldq = ldq;
   p.Bt = (__nv_bfloat16*)Bt;
+  p.Btl = Bt != nullptr ? (__nv_bfloat16*)Btl : nullptr;
   p.ldbt = ldbt;
   p.M = M;
   p.d = d;

@@ -26,8 +26,10 @@ template <typename T> __device__ __forceinline__ T zero() { return T(0); }
 // TRANS_A = true:  A is K x M (row-major, lda): C = A^T B.
 // blockIdx.z selects a K slab [kz0, kz1); with PARTIAL the FP64 tile sums go to
 // C + z*M*ldc (a [splits][M][ldc] FP64 buffer).
+// ROUND_B: 1 = the B operand is rounded to BF16 as it is staged; 2 = to the
+// sum of its two BF16 parts, h + bf16(b - h) (exact in FP32).
 template <bool TRANS_A, typename TA, typename TB, typename TC, Mul MODE, bool PARTIAL,
-          bool ROUND_B = false>
+          int ROUND_B = 0>
 __device__ __forceinline__ void gemm_tile(const TA* __restrict__ A, int64_t lda,
                                           const TB* __restrict__ B, int64_t ldb,
                                           TC* __restrict__ C, int64_t ldc, int64_t M, int64_t K,
@@ -71,7 +73,11 @@ __device__ __forceinline__ void gemm_tile(const TA* __restrict__ A, int64_t lda,
       TM v = zero<TM>();
       if (gk < kz1 && gn < N) {
         v = Cvt<TM>::from(B[gk * ldb + gn]);
-        if constexpr (ROUND_B) v = __bfloat162float(__float2bfloat16_rn(v));
+        if constexpr (ROUND_B == 1) v = __bfloat162float(__float2bfloat16_rn(v));
+        if constexpr (ROUND_B == 2) {
+          const float h = __bfloat162float(__float2bfloat16_rn(v));
+          v = h + __bfloat162float(__float2bfloat16_rn(v - h));
+        }
       }
       Bs[r][c] = v;
     }
@@ -127,7 +133,7 @@ k_gemm(const TA* __restrict__ A, int64_t lda, const TB* __restrict__ B, int64_t 
 // matrix i = (prefix[i] <= t < prefix[i+1]) and a 64 x 64 output tile of it.
 //   TRANS_A = false: buf[dst] (m x d) = A buf[src] (n x d)
 //   TRANS_A = true:  buf[dst] (n x d) = A^T buf[src] (m x d)
-template <bool TRANS_A, typename TA, typename TB>
+template <bool TRANS_A, typename TA, typename TB, int SPLIT2 = 0>
 __global__ void __launch_bounds__(NT)
 k_bgemm(const BMat* __restrict__ T, const int* __restrict__ prefix, int count, int src, int dst) {
   const int t = blockIdx.x;
@@ -140,9 +146,10 @@ k_bgemm(const BMat* __restrict__ T, const int* __restrict__ prefix, int count, i
   const int local = t - prefix[lo];
   const int ntn = (b.d + BN - 1) / BN;
   const int64_t Mout = TRANS_A ? b.n : b.m, K = TRANS_A ? b.m : b.n;
-  // with BF16 A the skinny operand is rounded to BF16 as it is staged, the
-  // product the single-matrix BF16 path computes
-  gemm_tile<TRANS_A, TA, TB, float, Mul::F32, false, std::is_same<TA, __nv_bfloat16>::value>(
+  // with BF16 A the skinny operand is rounded to BF16 (or to its two-part
+  // BF16 sum) as it is staged, the product the single-matrix BF16 path computes
+  constexpr int RB = std::is_same<TA, __nv_bfloat16>::value ? (SPLIT2 ? 2 : 1) : 0;
+  gemm_tile<TRANS_A, TA, TB, float, Mul::F32, false, RB>(
       (const TA*)b.A, b.lda, (const TB*)bbuf(b, src), b.dp, bbuf(b, dst), b.dp, Mout, K, b.d,
       ((K + BK - 1) / BK) * BK, local / ntn, local % ntn, 0);
 }
@@ -231,14 +238,18 @@ cudaError_t simt_gemm_nn(Ty ta, Ty tb, Ty tc, Mul mul, const void* A, int64_t ld
 int bgemm_tiles(int64_t rows, int d) { return ceil_div(rows, BM) * ceil_div(d, BN); }
 
 cudaError_t bgemm(bool trans, Ty ta, Ty tb, const BMat* T, const int* prefix, int total, int count,
-                  int src, int dst, cudaStream_t st) {
+                  int src, int dst, cudaStream_t st, bool split2) {
   if (total <= 0) return cudaSuccess;
   if (tb == Ty::F32) {
     if (ta == Ty::F32) {
       if (trans) k_bgemm<true, float, float><<<total, NT, 0, st>>>(T, prefix, count, src, dst);
       else k_bgemm<false, float, float><<<total, NT, 0, st>>>(T, prefix, count, src, dst);
     } else if (ta == Ty::BF16) {
-      if (trans) k_bgemm<true, __nv_bfloat16, float><<<total, NT, 0, st>>>(T, prefix, count, src, dst);
+      if (trans && split2)
+        k_bgemm<true, __nv_bfloat16, float, 1><<<total, NT, 0, st>>>(T, prefix, count, src, dst);
+      else if (trans) k_bgemm<true, __nv_bfloat16, float><<<total, NT, 0, st>>>(T, prefix, count, src, dst);
+      else if (split2)
+        k_bgemm<false, __nv_bfloat16, float, 1><<<total, NT, 0, st>>>(T, prefix, count, src, dst);
       else k_bgemm<false, __nv_bfloat16, float><<<total, NT, 0, st>>>(T, prefix, count, src, dst);
     } else {
       return cudaErrorInvalidValue;

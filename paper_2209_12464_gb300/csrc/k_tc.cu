@@ -35,6 +35,7 @@ constexpr int BM = 128;       // rows of an output tile (MMA M)
 constexpr int BK = 64;        // K per stage (one 128-byte swizzle row of BF16)
 constexpr int NTHREADS = 192;
 constexpr int A_TILE_BYTES = BM * BK * 2;  // 16 KB
+constexpr int kBatchMaps = 4;              // tensor maps per batched matrix
 
 struct TcParams {
   int64_t Mout;   // output rows
@@ -83,6 +84,7 @@ __device__ __forceinline__ Item get_item(const TcParams& p, int i) {
 struct TcItem {
   const CUtensorMap* mA;
   const CUtensorMap* mB;
+  const CUtensorMap* mB2;  // low BF16 part of the skinny operand (two-part products)
   int tile, kb0, kb1, dp;
   float* out;
   int64_t ldo, rows;
@@ -93,12 +95,13 @@ struct TcItem {
 struct WorkSingle {
   const CUtensorMap* mA;
   const CUtensorMap* mB;
+  const CUtensorMap* mB2;
   const TcParams* p;
   static constexpr bool kGlobalMaps = false;
   __device__ int count() const { return item_count(*p); }
   __device__ TcItem get(int i) const {
     const Item it = get_item(*p, i);
-    TcItem r{mA, mB, it.tile, it.kb0, it.kb1, p->dp, nullptr, 0, 0, false};
+    TcItem r{mA, mB, mB2, it.tile, it.kb0, it.kb1, p->dp, nullptr, 0, 0, false};
     if (it.slot < 0) {
       r.out = p->out + (int64_t)it.tile * BM * p->ldo;
       r.ldo = p->ldo;
@@ -114,8 +117,9 @@ struct WorkSingle {
 
 // Batched work: CTA c takes tiles c, c + P, c + 2P, ... of a host-built list
 // (whole tiles only, so every tile is one K-ordered accumulation whichever CTA
-// runs it).  Tensor maps live in global memory, three per matrix: A (64 x 64
-// boxes), Bt over n (for A X) and Bt over m (for A^T Y).
+// runs it).  Tensor maps live in global memory, kBatchMaps per matrix: A
+// (64 x 64 boxes), Bt over n (for A X), Bt over m (for A^T Y) and the low
+// part Btl over m (the two-part B^T = A^T Q).
 struct WorkBatch {
   const BTcTile* list;
   int n;
@@ -132,8 +136,9 @@ struct WorkBatch {
     const BMat& b = T[w.mat];
     const int64_t K = trans ? b.m : b.n, Mout = trans ? b.n : b.m;
     TcItem r;
-    r.mA = maps + 3 * (int64_t)w.mat;
-    r.mB = maps + 3 * (int64_t)w.mat + (trans ? 2 : 1);
+    r.mA = maps + kBatchMaps * (int64_t)w.mat;
+    r.mB = maps + kBatchMaps * (int64_t)w.mat + (trans ? 2 : 1);
+    r.mB2 = maps + kBatchMaps * (int64_t)w.mat + 3;
     r.tile = w.tile;
     r.kb0 = 0;
     r.kb1 = (int)((K + BK - 1) / BK);
@@ -153,13 +158,18 @@ __device__ __forceinline__ void tmap_acquire(const CUtensorMap* m) {
 
 // The warp-specialised pipeline shared by both kernels.  dpmax sizes the
 // shared-memory stages; each item's own dp sets its B bytes and MMA N.
-template <bool TRANS, class W>
+// B2: the skinny operand comes in two BF16 parts, b = h + l (l = bf16(b - h),
+// so h + l carries about 16 significant bits of the FP32 value); each stage
+// holds both parts' tiles and every A tile is multiplied by both into the same
+// accumulator, D += A h + A l.
+template <bool TRANS, bool B2, class W>
 __device__ __forceinline__ void tc_body(const W& w, int* err, int S, int dpmax) {
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
   const uint32_t base = (raw + 1023u) & ~1023u;
   uint8_t* base_ptr = smem_raw + (base - raw);
-  const uint32_t stage_bytes = A_TILE_BYTES + (uint32_t)dpmax * BK * 2;
+  const uint32_t b_tile = (uint32_t)dpmax * BK * 2;  // a multiple of 1024 bytes
+  const uint32_t stage_bytes = A_TILE_BYTES + (B2 ? 2u : 1u) * b_tile;
   const uint32_t bar_base = base + S * stage_bytes;
   // barriers: full[S], empty[S], tfull[2], tempty[2], drain; then the TMEM address
   auto full_bar = [&](int s) { return bar_base + 8u * s; };
@@ -188,6 +198,7 @@ __device__ __forceinline__ void tc_body(const W& w, int* err, int S, int dpmax) 
       const TcItem it = w.get(0);
       asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)it.mA) : "memory");
       asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)it.mB) : "memory");
+      if (B2) asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)it.mB2) : "memory");
     }
   }
   if (warp == 1) {
@@ -218,9 +229,10 @@ __device__ __forceinline__ void tc_body(const W& w, int* err, int S, int dpmax) 
         if (W::kGlobalMaps && it.mA != last_a) {  // maps written before the launch
           tmap_acquire(it.mA);
           tmap_acquire(it.mB);
+          if (B2) tmap_acquire(it.mB2);
           last_a = it.mA;
         }
-        const uint32_t bytes = A_TILE_BYTES + (uint32_t)it.dp * BK * 2;
+        const uint32_t bytes = A_TILE_BYTES + (B2 ? 2u : 1u) * (uint32_t)it.dp * BK * 2;
         for (int kb = it.kb0; kb < it.kb1; ++kb) {
           if (!mbar_wait(empty_bar(stage), phase ^ 1u, abort_flag)) { ok = false; break; }
           ++issued;
@@ -240,6 +252,7 @@ __device__ __forceinline__ void tc_body(const W& w, int* err, int S, int dpmax) 
                         kb * BK, pol_a);
           }
           tma_load_2d(sb, it.mB, full_bar(stage), kb * BK, 0, pol_b);
+          if (B2) tma_load_2d(sb + b_tile, it.mB2, full_bar(stage), kb * BK, 0, pol_b);
           if (++stage == S) { stage = 0; phase ^= 1u; }
         }
       }
@@ -284,6 +297,7 @@ __device__ __forceinline__ void tc_body(const W& w, int* err, int S, int dpmax) 
             else        ad = sdesc(sa + kk * 2048, A_TILE_BYTES / 2, 1024);
             bd = sdesc(sb + kk * 32, 16, 1024);
             mma_bf16(tmem_d, ad, bd, idesc, (kb > it.kb0 || kk > 0) ? 1u : 0u);
+            if (B2) mma_bf16(tmem_d, ad, sdesc(sb + b_tile + kk * 32, 16, 1024), idesc, 1u);
           }
           mma_commit(empty_bar(stage));
           if (++stage == S) { stage = 0; phase ^= 1u; }
@@ -339,20 +353,20 @@ __device__ __forceinline__ void tc_body(const W& w, int* err, int S, int dpmax) 
   }
 }
 
-template <bool TRANS>
+template <bool TRANS, bool B2>
 __global__ void __launch_bounds__(NTHREADS, 1)
 k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-          const __grid_constant__ TcParams p) {
-  const WorkSingle w{&tmA, &tmB, &p};
-  tc_body<TRANS>(w, p.err, p.stages, p.dp);
+          const __grid_constant__ CUtensorMap tmB2, const __grid_constant__ TcParams p) {
+  const WorkSingle w{&tmA, &tmB, &tmB2, &p};
+  tc_body<TRANS, B2>(w, p.err, p.stages, p.dp);
 }
 
-template <bool TRANS>
+template <bool TRANS, bool B2>
 __global__ void __launch_bounds__(NTHREADS, 1)
 k_btc_gemm(const BTcTile* __restrict__ list, int n, const BMat* __restrict__ T,
            const CUtensorMap* __restrict__ maps, int dst, int stages, int dpmax, int* err) {
   const WorkBatch w{list, n, T, maps, dst, TRANS};
-  tc_body<TRANS>(w, err, stages, dpmax);
+  tc_body<TRANS, B2>(w, err, stages, dpmax);
 }
 
 // Sum the stream-K fragments of each tail tile in CTA order into the output.
@@ -417,10 +431,12 @@ __global__ void __launch_bounds__(256) k_tc_fixup(TcParams p, int P) {
   *reinterpret_cast<float4*>(p.out + gr * p.ldo + 4 * c4) = s;
 }
 
-// dst[c][r] = bf16(src[r][c]) for c < cols, 0 for cols <= c < dp (r < rows).
+// dst[c][r] = bf16(src[r][c]) for c < cols, 0 for cols <= c < dp (r < rows);
+// lo (optional): the low part, bf16(src[r][c] - dst[c][r]).
 template <typename TS>
 __global__ void k_transpose_bf16(const TS* __restrict__ src, int64_t lds, int64_t rows, int cols,
-                                 int dp, __nv_bfloat16* __restrict__ dst, int64_t ldd) {
+                                 int dp, __nv_bfloat16* __restrict__ dst, int64_t ldd,
+                                 __nv_bfloat16* __restrict__ lo) {
   __shared__ float t[32][33];
   const int64_t r0 = (int64_t)blockIdx.x * 32;
   const int c0 = blockIdx.y * 32;
@@ -435,7 +451,12 @@ __global__ void k_transpose_bf16(const TS* __restrict__ src, int64_t lds, int64_
   for (int i = threadIdx.y; i < 32; i += blockDim.y) {
     const int c = c0 + i;
     const int64_t r = r0 + threadIdx.x;
-    if (c < dp && r < rows) dst[(int64_t)c * ldd + r] = __float2bfloat16_rn(t[threadIdx.x][i]);
+    if (c < dp && r < rows) {
+      const float v = t[threadIdx.x][i];
+      const __nv_bfloat16 h = __float2bfloat16_rn(v);
+      dst[(int64_t)c * ldd + r] = h;
+      if (lo != nullptr) lo[(int64_t)c * ldd + r] = __float2bfloat16_rn(v - __bfloat162float(h));
+    }
   }
 }
 
@@ -862,17 +883,24 @@ int tc_stages(size_t stage_bytes) {
 
 cudaError_t tc_gemm(bool trans, const void* A, int64_t lda, int64_t m, int64_t n, const void* Bt,
                     int64_t ldb, int dp, float* out, int64_t ldo, float* frag, int* err,
-                    cudaStream_t st, const std::function<void(bool)>& mark) {
+                    cudaStream_t st, const std::function<void(bool)>& mark, const void* Btl) {
   if (dp < 16 || dp > 256 || dp % 16 != 0) return cudaErrorInvalidValue;
   if (lda % 8 != 0 || ldb % 8 != 0 || ((uintptr_t)A & 15) || ((uintptr_t)Bt & 15) || ldo % 4 != 0 ||
-      ((uintptr_t)out & 15))
+      ((uintptr_t)out & 15) || ((uintptr_t)Btl & 15))
     return cudaErrorInvalidValue;
+  const bool b2 = Btl != nullptr;
   const int64_t Mout = trans ? n : m, K = trans ? m : n;
-  CUtensorMap mA, mB;
+  CUtensorMap mA, mB, mB2;
   if (!make_map(&mA, A, (uint64_t)n, (uint64_t)m, (uint64_t)lda, 64, trans ? 64 : BM))
     return cudaErrorInvalidValue;
   if (!make_map(&mB, Bt, (uint64_t)K, (uint64_t)dp, (uint64_t)ldb, 64, (uint32_t)dp))
     return cudaErrorInvalidValue;
+  if (b2) {
+    if (!make_map(&mB2, Btl, (uint64_t)K, (uint64_t)dp, (uint64_t)ldb, 64, (uint32_t)dp))
+      return cudaErrorInvalidValue;
+  } else {
+    mB2 = mB;  // unused
+  }
   TcParams p{};
   p.Mout = Mout;
   p.K = K;
@@ -888,21 +916,17 @@ cudaError_t tc_gemm(bool trans, const void* A, int64_t lda, int64_t m, int64_t n
   p.full_waves = p.T / P;
   p.tail = p.T - p.full_waves * P;
   p.U = (int64_t)p.tail * p.KB;
-  const size_t stage_bytes = A_TILE_BYTES + (size_t)dp * BK * 2;
+  const size_t stage_bytes = A_TILE_BYTES + (b2 ? 2 : 1) * (size_t)dp * BK * 2;
   const int stages = tc_stages(stage_bytes);
   if (stages < 2) return cudaErrorInvalidValue;
   p.stages = stages;
   const size_t smem = tc_smem(stages, stage_bytes);
-  cudaError_t e = trans ? cudaFuncSetAttribute(k_tc_gemm<true>,
-                                               cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                               (int)smem)
-                        : cudaFuncSetAttribute(k_tc_gemm<false>,
-                                               cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                               (int)smem);
+  auto kern = trans ? (b2 ? k_tc_gemm<true, true> : k_tc_gemm<true, false>)
+                    : (b2 ? k_tc_gemm<false, true> : k_tc_gemm<false, false>);
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   if (mark) mark(true);
-  e = trans ? launch_pdl(k_tc_gemm<true>, dim3(P), dim3(NTHREADS), smem, st, mA, mB, p)
-            : launch_pdl(k_tc_gemm<false>, dim3(P), dim3(NTHREADS), smem, st, mA, mB, p);
+  e = launch_pdl(kern, dim3(P), dim3(NTHREADS), smem, st, mA, mB, mB2, p);
   if (mark) mark(false);
   count_launch();
   if (e == cudaSuccess) e = cudaGetLastError();
@@ -912,10 +936,10 @@ cudaError_t tc_gemm(bool trans, const void* A, int64_t lda, int64_t m, int64_t n
   return e == cudaSuccess ? cudaGetLastError() : e;
 }
 
-bool btc_encode(void* maps3, const void* A, int64_t lda, int64_t m, int64_t n, const void* Bt,
-                int64_t ldbt, int dp, bool a_only) {
+bool btc_encode(void* maps4, const void* A, int64_t lda, int64_t m, int64_t n, const void* Bt,
+                const void* Btl, int64_t ldbt, int dp, bool a_only) {
   CUtensorMap t;  // encoded in an aligned temporary, then copied into place
-  uint8_t* dst = (uint8_t*)maps3;
+  uint8_t* dst = (uint8_t*)maps4;
   if (!make_map(&t, A, (uint64_t)n, (uint64_t)m, (uint64_t)lda, 64, 64)) return false;
   memcpy(dst, &t, sizeof(t));
   if (a_only) return true;
@@ -923,42 +947,45 @@ bool btc_encode(void* maps3, const void* A, int64_t lda, int64_t m, int64_t n, c
   memcpy(dst + sizeof(t), &t, sizeof(t));
   if (!make_map(&t, Bt, (uint64_t)m, (uint64_t)dp, (uint64_t)ldbt, 64, (uint32_t)dp)) return false;
   memcpy(dst + 2 * sizeof(t), &t, sizeof(t));
+  if (!make_map(&t, Btl, (uint64_t)m, (uint64_t)dp, (uint64_t)ldbt, 64, (uint32_t)dp)) return false;
+  memcpy(dst + 3 * sizeof(t), &t, sizeof(t));
   return true;
 }
 
-size_t btc_map_bytes() { return sizeof(CUtensorMap); }
+size_t btc_map_bytes() { return kBatchMaps * sizeof(CUtensorMap); }
 
 cudaError_t btc_gemm(bool trans, const BMat* T, int count, const BTcTile* list, int n,
-                     const void* maps, int src, int dst, int dpmax, int* err, cudaStream_t st) {
+                     const void* maps, int src, int dst, int dpmax, int* err, cudaStream_t st,
+                     bool b2) {
   if (n <= 0) return cudaSuccess;
   if (dpmax < 16 || dpmax > 256 || dpmax % 16) return cudaErrorInvalidValue;
-  const size_t stage_bytes = A_TILE_BYTES + (size_t)dpmax * BK * 2;
+  if (b2 && !trans) return cudaErrorInvalidValue;  // the low part is mapped over m only
+  const size_t stage_bytes = A_TILE_BYTES + (b2 ? 2 : 1) * (size_t)dpmax * BK * 2;
   const int stages = tc_stages(stage_bytes);
   if (stages < 2) return cudaErrorInvalidValue;
   const size_t smem = tc_smem(stages, stage_bytes);
-  cudaError_t e = trans ? cudaFuncSetAttribute(k_btc_gemm<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   (int)smem)
-            : cudaFuncSetAttribute(k_btc_gemm<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   (int)smem);
+  auto kern = trans ? (b2 ? k_btc_gemm<true, true> : k_btc_gemm<true, false>)
+                    : k_btc_gemm<false, false>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int P = sm_count();
   if (n < P) P = n;
   const CUtensorMap* mp = (const CUtensorMap*)maps;
-  if (trans) k_btc_gemm<true><<<P, NTHREADS, smem, st>>>(list, n, T, mp, dst, stages, dpmax, err);
-  else k_btc_gemm<false><<<P, NTHREADS, smem, st>>>(list, n, T, mp, dst, stages, dpmax, err);
+  kern<<<P, NTHREADS, smem, st>>>(list, n, T, mp, dst, stages, dpmax, err);
   count_launch();
   return cudaGetLastError();
 }
 
 cudaError_t transpose_to_bf16(Ty ts, const void* src, int64_t lds, int64_t rows, int cols, int dp,
-                              void* dst, int64_t ldd, cudaStream_t st) {
+                              void* dst, int64_t ldd, cudaStream_t st, void* lo) {
   dim3 grid(ceil_div(rows, 32), ceil_div(dp, 32)), block(32, 8);
   if (ts == Ty::F64)
     k_transpose_bf16<double><<<grid, block, 0, st>>>((const double*)src, lds, rows, cols, dp,
-                                                     (__nv_bfloat16*)dst, ldd);
+                                                     (__nv_bfloat16*)dst, ldd,
+                                                     (__nv_bfloat16*)lo);
   else if (ts == Ty::F32)
     k_transpose_bf16<float><<<grid, block, 0, st>>>((const float*)src, lds, rows, cols, dp,
-                                                    (__nv_bfloat16*)dst, ldd);
+                                                    (__nv_bfloat16*)dst, ldd, (__nv_bfloat16*)lo);
   else
     return cudaErrorInvalidValue;
   count_launch();

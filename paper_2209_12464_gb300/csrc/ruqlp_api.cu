@@ -120,7 +120,7 @@ constexpr int kMaxSplits = 64;
 
 // Workspace layout for one problem.
 struct Layout {
-  size_t X, Y, Z, P, partial, G, Gf, R, Rw, St, Bt, frag, colptr, rowidx, cvals, cscratch, T, Om,
+  size_t X, Y, Z, P, partial, G, Gf, R, Rw, St, Bt, Btl, frag, colptr, rowidx, cvals, cscratch, T, Om,
       lrT1, lrT2, lrTmp, lrPart, svdW, svdV, svdS, svdOrd, svdTmp, svdU, svdVs, total;
 };
 
@@ -158,7 +158,12 @@ Layout layout_of(int64_t m, int64_t n, int d, Ty ct, int64_t nnz = -1, size_t va
   // S = R^{-1} as three BF16 parts for the tensor-core Q = Y S
   if (work_ty(ct) == Ty::F32 && dp <= 256) L.St = take(qmul_st_bytes(d));
   if (ct == Ty::BF16 && nnz < 0) {
-    L.Bt = take((size_t)dp * round8(m > n ? m : n) * 2);
+    // the transposed BF16 skinny operand, then its low BF16 part (the
+    // two-part B^T = A^T Q); the CUDA-core kernel's rounded FP32 operand
+    // (K x d) fits the two together
+    const size_t one = (size_t)dp * round8(m > n ? m : n) * 2;
+    L.Bt = take(2 * one);
+    L.Btl = L.Bt + one;
     L.frag = take(tc_frag_bytes(dp <= 256 ? dp : 256));  // per column chunk
   }
   if (finish) L.T = take((size_t)m * dp * wes);
@@ -312,10 +317,11 @@ struct Job {
 //    Gram).  (A single-SM FP64 Cholesky of a 220 x 220 Gram costs ~0.45 ms on
 //    GB300, whose FP64 rate is 1/58 of FP32.)
 // make_bt: the last solve also writes Q^T in BF16 to the arena's Bt (the
-// next tensor-core product's operand); returns whether it did.
+// next tensor-core product's operand), and with split2 its low BF16 part to
+// Btl (the two-part B^T = A^T Q); returns whether it did.
 ruqlp_status orth(ruqlp_ctx* h, const Layout& Lo, const Job& J, const void* Yin, void* Qout,
                   int64_t M, bool final_basis = true, bool make_bt = false,
-                  bool* bt_made = nullptr) {
+                  bool* bt_made = nullptr, bool split2 = false) {
   if (bt_made) *bt_made = false;
   ProfScope ps(h, PROF_ORTH);
   char* base = (char*)h->arena;
@@ -347,12 +353,13 @@ ruqlp_status orth(ruqlp_ctx* h, const Layout& Lo, const Job& J, const void* Yin,
         }
         ProfScope pt(h, PROF_TRSM);
         const bool bt = make_bt && pass == passes - 1;
+        void* btl = (bt && split2) ? base + Lo.Btl : nullptr;
         if (!h->orth_simt && Lo.St != 0 && qmul_supported(M, d, dp, src, dp, Qout))
           CK(qmul_tc(src, dp, (const float*)Rw, M, d, base + Lo.St, (float*)Qout, dp,
-                     bt ? base + Lo.Bt : nullptr, round8(M), &h->status->timeout, st));
+                     bt ? base + Lo.Bt : nullptr, round8(M), &h->status->timeout, st, btl));
         else
           CK(trsm_tiles_f32(src, dp, (const float*)Rw, (float*)Qout, dp, M, d, st,
-                            bt ? base + Lo.Bt : nullptr, round8(M)));
+                            bt ? base + Lo.Bt : nullptr, round8(M), btl));
         if (bt && bt_made) *bt_made = true;
       } else {
         CK(chol_upper(G, d, s1, R, Rw, Ty::F32, h->status, nullptr, st, Ty::F32, pass == 0));
@@ -386,8 +393,14 @@ ruqlp_status orth(ruqlp_ctx* h, const Layout& Lo, const Job& J, const void* Yin,
 //   trans = false: out[m x dp] = A Xin, Xin n x d;
 //   trans = true:  out[n x dp] = A^T Xin, Xin m x d;
 // Xin has type xt and leading dimension ldx; out is the work type, ld dp.
+// split2 (BF16 A): the skinny operand is taken as the sum of its two BF16
+// parts, h + bf16(x - h), instead of bf16(x) -- the last product B^T = A^T Q,
+// whose rounding of Q would otherwise enter L directly (Q dQ^T A with
+// ||dQ^T A|| about 2^-9 sqrt(d / m) ||A||); the sketch products only need
+// the span of their operand.
 ruqlp_status product(ruqlp_ctx* h, const Layout& Lo, const Job& J, bool trans, Ty xt,
-                     const void* Xin, int64_t ldx, void* out, bool bt_ready = false) {
+                     const void* Xin, int64_t ldx, void* out, bool bt_ready = false,
+                     bool split2 = false) {
   ProfScope p(h, trans ? PROF_ATX : PROF_AX);
   cudaStream_t st = h->stream;
   char* base = (char*)h->arena;
@@ -429,6 +442,7 @@ ruqlp_status product(ruqlp_ctx* h, const Layout& Lo, const Job& J, bool trans, T
     // the MMA's N is at most 256: wider sketches run as column chunks of
     // equal width (multiples of 16), each one pass over A
     void* Bt = base + Lo.Bt;
+    void* Btl = split2 ? base + Lo.Btl : nullptr;
     const int64_t ldb = round8(K);
     const int nch = (J.dp + 255) / 256;
     const int w = round16((J.dp + nch - 1) / nch);
@@ -438,7 +452,7 @@ ruqlp_status product(ruqlp_ctx* h, const Layout& Lo, const Job& J, bool trans, T
       const int cols = std::max(0, std::min(J.d - c0, wc));
       if (!(bt_ready && nch == 1))  // else the last solve of orth() wrote it
         CK(transpose_to_bf16(xt, (const char*)Xin + (size_t)c0 * xes, ldx, K, cols, wc, Bt, ldb,
-                             st));
+                             st, Btl));
       CK(tc_gemm(trans, J.A, J.lda, J.m, J.n, Bt, ldb, wc, (float*)out + c0, J.dp,
                  (float*)(base + Lo.frag), &h->status->timeout, st,
                  h->profile ? [&](bool begin) {
@@ -449,12 +463,20 @@ ruqlp_status product(ruqlp_ctx* h, const Layout& Lo, const Job& J, bool trans, T
                      cudaEventRecord(b, st);
                      h->spans.push_back({trans ? PROF_TC_ATX : PROF_TC_AX, a, b});
                    }
-                 } : std::function<void(bool)>()));
+                 } : std::function<void(bool)>(), Btl));
     }
     return RUQLP_OK;
   }
   const Mul mul = (J.ct == Ty::F64) ? Mul::F64 : Mul::F32;
-  if (J.ct == Ty::BF16) {
+  if (J.ct == Ty::BF16 && split2) {
+    // the two-part operand, rounded as the tensor cores use it (h + l is exact
+    // in FP32)
+    float* Xr = (float*)(base + Lo.Bt);
+    CK(round2_bf16_2d(xt, Xin, ldx, Xr, J.d, K, J.d, st));
+    Xin = Xr;
+    xt = Ty::F32;
+    ldx = J.d;
+  } else if (J.ct == Ty::BF16) {
     // BF16 compute rounds the skinny operand to BF16 on either kernel, so the
     // CUDA-core kernel computes the same product as the tensor cores
     void* Xb = base + Lo.Bt;
@@ -580,7 +602,7 @@ ruqlp_status run_dense(ruqlp_ctx* h, const Job& J0) {
   // the orth() before a tensor-core product hands it the transposed BF16 Q
   const bool fuse_bt = J.use_tc && J.dp <= 256;
   bool btY = false, btZ = false;
-  s = orth(h, Lo, J, Y, Y, J.m, J.q == 0, fuse_bt, &btY);
+  s = orth(h, Lo, J, Y, Y, J.m, J.q == 0, fuse_bt, &btY, J.q == 0);
   if (s != RUQLP_OK) return s;
   // a4: power iteration with orthonormalisation (Algorithm 2)
   for (int it = 0; it < J.q; ++it) {
@@ -590,11 +612,11 @@ ruqlp_status run_dense(ruqlp_ctx* h, const Job& J0) {
     if (s != RUQLP_OK) return s;
     s = product(h, Lo, J, false, wt, Z, dp, Y, btZ);
     if (s != RUQLP_OK) return s;
-    s = orth(h, Lo, J, Y, Y, J.m, it == J.q - 1, fuse_bt, &btY);
+    s = orth(h, Lo, J, Y, Y, J.m, it == J.q - 1, fuse_bt, &btY, it == J.q - 1);
     if (s != RUQLP_OK) return s;
   }
-  // a5: B^T = A^T Q
-  s = product(h, Lo, J, true, wt, Y, dp, Z, btY);
+  // a5: B^T = A^T Q (BF16 A: Q as two BF16 parts)
+  s = product(h, Lo, J, true, wt, Y, dp, Z, btY, true);
   if (s != RUQLP_OK) return s;
   // a6: [P, R_B] = qr(B^T): P = orth(B^T), R_B = P^T B^T
   s = orth(h, Lo, J, Z, Pb, J.n);
@@ -725,7 +747,7 @@ size_t batch_item_bytes(const ruqlp_matrix* A, const ruqlp_params* prm) {
   int64_t slab;
   const int64_t sl = std::max(gram_slabs(m, kMaxSplits, &slab), gram_slabs(n, kMaxSplits, &slab));
   const size_t per = (size_t)(3 * n + m) * dp * 4 + (size_t)sl * d * d * 8 + (size_t)d * d * 12 +
-                     chol_tiles_bytes(d) + (size_t)dp * std::max(m, n) * 2 + 8 * 256;
+                     chol_tiles_bytes(d) + (size_t)2 * dp * std::max(m, n) * 2 + 8 * 256;
   // plus its share of the metadata (table entry, prefixes, tile lists, maps)
   return per + 4096 + (size_t)(ceil_div(m, 128) + ceil_div(n, 128)) * 8;
 }
@@ -792,7 +814,7 @@ ruqlp_status batch_launches(ruqlp_ctx* h, const BatchPlan& bp, int count, int q,
   CK(cudaMemsetAsync(base + bp.off_status, 0, bp.total - bp.off_status, st));
   // make_bt: the last solve also writes the BF16 transposed operand of the
   // next tensor-core product (so that product needs no transpose launch)
-  auto orth_b = [&](int src, int dst, int passes, bool make_bt) -> ruqlp_status {
+  auto orth_b = [&](int src, int dst, int passes, int make_bt) -> ruqlp_status {
     ProfScope sp(ph, PROF_ORTH);
     const int gp = (src == B_Y) ? PF_GY : PF_GN;
     const int tp = (src == B_Y) ? PF_TY : PF_TN2;
@@ -800,34 +822,36 @@ ruqlp_status batch_launches(ruqlp_ctx* h, const BatchPlan& bp, int count, int q,
       const int from = pass == 0 ? src : dst;
       CK(bgram(T, pre(gp), tot(gp), count, from, from, kMaxSplits, bp.dmax, st));
       CK(bchol(T, count, s1, pass == 0, bp.dmax, st));
-      CK(btrsm(T, pre(tp), tot(tp), count, from, dst, bp.dmax, st, make_bt && pass == passes - 1));
+      CK(btrsm(T, pre(tp), tot(tp), count, from, dst, bp.dmax, st,
+               pass == passes - 1 ? make_bt : 0));
     }
     return RUQLP_OK;
   };
-  auto prod = [&](bool trans, int src, int dst) -> ruqlp_status {
+  // split2: the two-part skinny operand of B^T = A^T Q (as product() above)
+  auto prod = [&](bool trans, int src, int dst, bool split2) -> ruqlp_status {
     ProfScope sp(ph, trans ? PROF_ATX : PROF_AX);
     const int pf = trans ? PF_TN : PF_NN;
-    CK(bgemm(trans, ct, Ty::F32, T, pre(pf), tot(pf), count, src, dst, st));
+    CK(bgemm(trans, ct, Ty::F32, T, pre(pf), tot(pf), count, src, dst, st, split2));
     const auto& list = trans ? bp.tc_tn : bp.tc_nn;
-    if (!list.empty()) {  // Bt was written by the step that produced buf[src]
+    if (!list.empty()) {  // Bt (and Btl) were written by the step that produced buf[src]
       ProfScope tc(ph, trans ? PROF_TC_ATX : PROF_TC_AX);
       CK(btc_gemm(trans, T, count, (const BTcTile*)(base + (trans ? bp.off_tc_tn : bp.off_tc_nn)),
-                  (int)list.size(), base + bp.off_maps, src, dst, bp.dpmax_tc, err, st));
+                  (int)list.size(), base + bp.off_maps, src, dst, bp.dpmax_tc, err, st, split2));
     }
     return RUQLP_OK;
   };
   ruqlp_status s;
   CK(bcast_omega(T, count, bp.max_omega, st));
-  if ((s = prod(false, B_X, B_Y)) != RUQLP_OK) return s;
-  if ((s = orth_b(B_Y, B_Y, q == 0 ? 3 : 2, true)) != RUQLP_OK) return s;
+  if ((s = prod(false, B_X, B_Y, false)) != RUQLP_OK) return s;
+  if ((s = orth_b(B_Y, B_Y, q == 0 ? 3 : 2, q == 0 ? 2 : 1)) != RUQLP_OK) return s;
   for (int it = 0; it < q; ++it) {
-    if ((s = prod(true, B_Y, B_Z)) != RUQLP_OK) return s;
-    if ((s = orth_b(B_Z, B_Z, 2, true)) != RUQLP_OK) return s;
-    if ((s = prod(false, B_Z, B_Y)) != RUQLP_OK) return s;
-    if ((s = orth_b(B_Y, B_Y, it == q - 1 ? 3 : 2, true)) != RUQLP_OK) return s;
+    if ((s = prod(true, B_Y, B_Z, false)) != RUQLP_OK) return s;
+    if ((s = orth_b(B_Z, B_Z, 2, 1)) != RUQLP_OK) return s;
+    if ((s = prod(false, B_Z, B_Y, false)) != RUQLP_OK) return s;
+    if ((s = orth_b(B_Y, B_Y, it == q - 1 ? 3 : 2, it == q - 1 ? 2 : 1)) != RUQLP_OK) return s;
   }
-  if ((s = prod(true, B_Y, B_Z)) != RUQLP_OK) return s;
-  if ((s = orth_b(B_Z, B_P, 3, false)) != RUQLP_OK) return s;
+  if ((s = prod(true, B_Y, B_Z, true)) != RUQLP_OK) return s;
+  if ((s = orth_b(B_Z, B_P, 3, 0)) != RUQLP_OK) return s;
   CK(bgram(T, pre(PF_GPZ), tot(PF_GPZ), count, B_P, B_Z, kMaxSplits, bp.dmax, st));
   CK(boutputs(T, count, bp.max_out, st));
   return RUQLP_OK;
@@ -911,7 +935,7 @@ ruqlp_status batch_begin(ruqlp_ctx* h, int count, const ruqlp_matrix* A, const r
     oG[i] = take((size_t)d * d * 8);
     oGf[i] = take((size_t)d * d * 4);
     oT[i] = take(chol_tiles_bytes(d));
-    oB[i] = b.use_tc ? take((size_t)dp * b.ldbt * 2) : 0;
+    oB[i] = b.use_tc ? take((size_t)2 * dp * b.ldbt * 2) : 0;  // Bt, then Btl
     bp.dmax = std::max(bp.dmax, d);
     if (b.use_tc) bp.dpmax_tc = std::max(bp.dpmax_tc, dp);
     bp.max_omega = std::max<int64_t>(bp.max_omega, n * dp);
@@ -930,7 +954,7 @@ ruqlp_status batch_begin(ruqlp_ctx* h, int count, const ruqlp_matrix* A, const r
     }
   bp.off_tc_nn = take(sizeof(BTcTile) * std::max<size_t>(n_nn, 1));
   bp.off_tc_tn = take(sizeof(BTcTile) * std::max<size_t>(n_tn, 1));
-  const size_t map3 = 3 * btc_map_bytes();
+  const size_t map3 = btc_map_bytes();  // all tensor maps of one matrix
   bp.off_maps = take(map3 * count);
   bp.meta_end = off;
   bp.off_status = take(sizeof(DevStatus) * count);
@@ -960,6 +984,7 @@ ruqlp_status batch_begin(ruqlp_ctx* h, int count, const ruqlp_matrix* A, const r
     b.Gf = (float*)(base + oGf[i]);
     b.tiles = (float*)(base + oT[i]);
     b.Bt = b.use_tc ? (void*)(base + oB[i]) : nullptr;
+    b.Btl = b.use_tc ? (void*)(base + oB[i] + (size_t)b.dp * b.ldbt * 2) : nullptr;
     b.omega = prm[i].omega;
     b.seed = prm[i].omega_seed;
     b.Qout = out[i].Q;
@@ -1004,7 +1029,7 @@ ruqlp_status batch_begin(ruqlp_ctx* h, int count, const ruqlp_matrix* A, const r
   for (int i = 0; i < count; ++i) {
     const BMat& b = bp.table[i];
     if (!b.use_tc || (g->aptr[i] == b.A && g->alda[i] == b.lda)) continue;
-    if (!btc_encode(g->maps.data() + map3 * i, b.A, b.lda, b.m, b.n, b.Bt, b.ldbt, b.dp,
+    if (!btc_encode(g->maps.data() + map3 * i, b.A, b.lda, b.m, b.n, b.Bt, b.Btl, b.ldbt, b.dp,
                     g->aptr[i] != nullptr))
       return fail(h, RUQLP_ERR_INVALID, "batch item %d: tensor map encoding failed", i);
     g->aptr[i] = b.A;

@@ -60,12 +60,11 @@ def _pad8(A):
     return wl.aligned_rows(A)
 
 
-def _bf16_bound(r0, d, m):
-    """BF16 products round the skinny operand to BF16 (relative 2^-9 per
-    entry); the last one, B^T = A^T bf16(Q), adds Q dQ^T A with
-    ||dQ^T A||_F about 2^-9 sqrt(d / m) ||A||_F.  Relative residual bound
-    against the unrounded matrix: 1.05 x the FP64 oracle's plus 2^-8 sqrt(d/m)."""
-    return 1.05 * r0 + 2.0 ** -8 * np.sqrt(d / m)
+def _bf16_bound(r0):
+    """The reduced-precision bar: the relative residual is at most 1.05x the
+    FP64 oracle's on the same (BF16) values.  The last product B^T = A^T Q
+    takes Q as two BF16 parts, so the rounding of Q does not enter L."""
+    return 1.05 * r0
 
 
 def _single(handle, A, om, k, p, q):
@@ -169,12 +168,13 @@ def test_batch_tensor_core_items(handle):
         for run in runs:
             for x, y in zip(run[i][:3], one[:3]):
                 assert torch.equal(x, y), (i, MIX[i])
-    for i, ((m, n, k, p), A64, om) in enumerate(zip(MIX, As, Oms)):
+    for i, ((m, n, k, p), om) in enumerate(zip(MIX, Oms)):
         Q, L, P = (t.double().cpu().numpy() for t in runs[0][i][:3])
+        A64 = Ag[i].double().cpu().numpy()  # the BF16 values the GPU saw
         ref = oracle.ruqlp(A64, om, Q_ITERS)
         r = oracle.residual_fro_small(A64, Q, L, P)
         r0 = oracle.residual_fro_small(A64, ref["Q"], ref["L"], ref["P"])
-        assert r <= _bf16_bound(r0, k + p, m), (i, MIX[i], r, r0)
+        assert r <= _bf16_bound(r0), (i, MIX[i], r, r0)
         l11 = abs(ref["L"][0, 0])
         assert np.max(np.abs(np.abs(np.diag(L))[:k] - np.abs(np.diag(ref["L"]))[:k])) <= 2e-2 * l11
         d = k + p
@@ -254,8 +254,8 @@ def test_batched_workload_512(handle, dtype):
             r0 = oracle.residual_fro_small(Aseen, ref["Q"], ref["L"], ref["P"])
             assert abs(r - r0) <= 1e-5
         else:
-            A64 = A32[i].double().cpu().numpy()
+            A64 = Ag[i].double().cpu().numpy()  # the BF16 values the GPU saw
             ref = oracle.ruqlp(A64, om, 1)
             r = oracle.residual_fro_small(A64, Q, L, P)
             r0 = oracle.residual_fro_small(A64, ref["Q"], ref["L"], ref["P"])
-            assert r <= _bf16_bound(r0, k + p, m), (i, shapes[i], r, r0)
+            assert r <= _bf16_bound(r0), (i, shapes[i], r, r0)

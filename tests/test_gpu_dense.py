@@ -37,6 +37,10 @@ CASES = [
     ("tall-3000x200-d64", 3000, 200, 48, 16, 1, 1e-2),
     ("d280-1500x1200", 1500, 1200, 256, 24, 1, 1e-2),
     ("tall-9000x700-tcgram", 9000, 700, 100, 20, 1, 1e-2),
+    # the widest sketch the ABI accepts (d = 512) and a ragged d past the
+    # 288-column blocked Cholesky (one-CTA Cholesky and row solve there)
+    ("d512-1500x1200", 1500, 1200, 480, 32, 1, 1e-2),
+    ("d417-1300x900", 1300, 900, 400, 17, 1, 1e-2),
 ]
 
 
@@ -159,6 +163,8 @@ ORTH_CASES = [  # M, d, log10 kappa
     # tall FP32 Y on the tensor cores: 152 equal row ranges of 256 rows (two
     # full sub-tiles), of 257 (three sub-tiles, the last one row) and of 395
     (38912, 64, 2), (38913, 64, 2), (60013, 96, 3),
+    # d past the blocked Cholesky's 288 columns, up to the ABI's 512
+    (2000, 512, 3), (3001, 417, 2), (12000, 300, 3),
 ]
 
 
