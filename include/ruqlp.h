@@ -47,7 +47,8 @@ typedef enum {
   RUQLP_ERR_INVALID = 2,    /* bad argument (sizes, pointers, dtype) */
   RUQLP_ERR_BUDGET = 3,     /* workspace would exceed the HBM budget */
   RUQLP_ERR_CUDA = 4,       /* a CUDA runtime / launch error */
-  RUQLP_ERR_BREAKDOWN = 5,  /* orth() failed even after its fallbacks */
+  RUQLP_ERR_BREAKDOWN = 5,  /* orth() failed even after its fallbacks (not
+                               returned since the TSQR fallback exists) */
   RUQLP_ERR_TIMEOUT = 6     /* a bounded device wait ran out */
 } ruqlp_status;
 
@@ -60,8 +61,20 @@ typedef enum {
 /* Output flags (ruqlp_outputs.flags), OR-ed over all orth() calls. */
 #define RUQLP_FLAG_SHIFTED 0x1u    /* a Cholesky broke down; the shifted
                                       CholeskyQR3 path was taken */
-#define RUQLP_FLAG_RANKDEF 0x2u    /* even the shifted Cholesky broke down:
-                                      the input is numerically rank deficient */
+#define RUQLP_FLAG_RANKDEF 0x2u    /* CholeskyQR could not orthonormalise a
+                                      sketch: a pivot failed even after the
+                                      shift, or the last pass of a final basis
+                                      met a Gram far from I (a pivot outside
+                                      [1/2, 2]) -- the sketch is numerically
+                                      rank deficient at the working precision
+                                      (e.g. an exactly rank-k A with d > k).
+                                      The decomposition was then redone with
+                                      Householder TSQR (RUQLP_FLAG_TSQR). */
+#define RUQLP_FLAG_TSQR 0x4u       /* every orth() of the returned result was
+                                      a Householder TSQR (Section II-A's
+                                      unpivoted QR; Demmel et al. 2012): after
+                                      RUQLP_FLAG_RANKDEF, or with the
+                                      "orth_tsqr" option */
 
 typedef struct {
   int device;               /* CUDA device ordinal */
@@ -188,6 +201,12 @@ ruqlp_status ruqlp_set_stream(ruqlp_handle h, void* cuda_stream);
  *   it (to 0 or 1) also zeroes the accumulators.
  * Errors: INVALID (unknown name). */
 ruqlp_status ruqlp_set_option(ruqlp_handle h, const char* name, int64_t value);
+/* (continued) "orth_tsqr": 1 = every orth() is a Householder TSQR (leaf QRs
+ *   of row blocks, a binary tree of stacked-R QRs, explicit Q; Demmel,
+ *   Grigori, Hoemmen, Langou 2012) -- the unpivoted QR of Section II-A taken
+ *   literally, stable whatever the sketch's conditioning or rank, slower
+ *   than CholeskyQR; 0 (default) = CholeskyQR, with TSQR as the automatic
+ *   fallback for sketches flagged RUQLP_FLAG_RANKDEF. */
 
 /* Grow the workspace arena now for problems up to m x n with d columns in
  * the given compute dtype (nnz < 0: dense A; nnz >= 0: CSR A with that many

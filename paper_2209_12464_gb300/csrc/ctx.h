@@ -30,6 +30,12 @@ struct ruqlp_ctx {
                         // intermediate ones take two)
   int bf16_simt = 0;    // 1: BF16 products on CUDA cores instead of tensor cores
   int orth_simt = 0;    // 1: orth() Grams and Q = Y R^{-1} on CUDA cores
+  int orth_tsqr = 0;    // 1: every orth() is a Householder TSQR
+  bool tsqr_now = false;  // this run takes the TSQR orth() (fallback rerun)
+  // the last single decomposition's arguments, for its TSQR rerun
+  ruqlp_matrix last_A{};
+  ruqlp_params last_prm{};
+  ruqlp_outputs last_out{};
   // phase timing with CUDA events on the handle's stream (option "profile")
   bool profile = false;
   struct Span { int cat; cudaEvent_t a, b; };
@@ -43,7 +49,7 @@ struct ruqlp_ctx {
     cudaGraphExec_t exec = nullptr;
     int seen = 0;
     int64_t launches = 0;           // kernels in the captured graph
-    std::vector<uint8_t> maps;      // 3 tensor maps per matrix
+    std::vector<uint8_t> maps;      // the tensor maps of every matrix
     std::vector<const void*> aptr;  // A each A map was encoded for
     std::vector<int64_t> alda;
   };
@@ -72,6 +78,9 @@ namespace ruqlp {
 struct BatchRun {
   int count = 0;
   size_t off_status = 0, off_err = 0;
+  // the items, for the TSQR rerun of any that CholeskyQR could not handle
+  std::vector<ruqlp_matrix> A;
+  std::vector<ruqlp_params> prm;
 };
 
 // Validate and launch one decomposition on h's stream and arena (returns

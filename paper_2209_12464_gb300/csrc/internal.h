@@ -40,9 +40,12 @@ int tn_splits(int64_t M, int64_t K, int64_t N, int max_splits);
 // Writes R (upper, FP64, ld d, zero lower part) and Rw = R in type tw.
 // A non-null `gate` makes it a no-op unless *gate != 0.  tf: arithmetic of
 // the factorisation (F64 or F32); force_shift: factor G + shift I directly.
+// check: 1 = the last pass of a CholeskyQR (its Gram should be close to I:
+// a pivot outside [1/2, 2] raises RUQLP_FLAG_RANKDEF); 2 = the same while
+// status->shifted is 0 (no third pass will follow); 0 = no check.
 cudaError_t chol_upper(const double* G, int d, double shift_rel, double* R, void* Rw,
                        Ty tw, DevStatus* status, const int32_t* gate, cudaStream_t st,
-                       Ty tf = Ty::F64, bool force_shift = false);
+                       Ty tf = Ty::F64, bool force_shift = false, int check = 0);
 
 // FP32 blocked Cholesky of a d x d FP64 Gram in one CTA (d <= 256):
 // G + shift I = R^T R (shift = shift_rel * trace(G) when force_shift or after
@@ -51,8 +54,10 @@ cudaError_t chol_upper(const double* G, int d, double shift_rel, double* R, void
 // trsm_tiles_f32 uses to form X = Y R^{-1} (X may alias Y).
 bool chol_tiles_supported(int d);
 size_t chol_tiles_bytes(int d);
+// check: as chol_upper's check = 1.
 cudaError_t chol_tiles_f32(const float* G, int d, double shift_rel, bool force_shift,
-                           float* tiles, DevStatus* status, const int32_t* gate, cudaStream_t st);
+                           float* tiles, DevStatus* status, const int32_t* gate, cudaStream_t st,
+                           bool check = false);
 // Bt (optional): also X^T in BF16 (dp x ldbt, zero rows d..dp), the next
 // tensor-core product's B operand; Btl (optional) its low part
 // bf16(x - bf16(x)) for the two-part product.
@@ -178,7 +183,7 @@ cudaError_t bgram(const BMat* T, const int* prefix, int total, int count, int sr
                   int max_slabs, int dmax, cudaStream_t st);
 int btrsm_blocks(int64_t M);
 cudaError_t bchol(const BMat* T, int count, double shift_rel, bool force_shift, int dmax,
-                  cudaStream_t st);
+                  cudaStream_t st, bool check = false);
 // make_bt: 1 = also write the result transposed in BF16 to each tensor-core
 // item's Bt (the next product's B operand); 2 = and its low part to Btl.
 cudaError_t btrsm(const BMat* T, const int* prefix, int total, int count, int src, int dst,
@@ -223,6 +228,14 @@ cudaError_t write_diag(Ty t, const void* s, int d, Ty to, void* L, cudaStream_t 
 // out += t for a rows x d FP32 block (the low-rank term of a CSR input).
 cudaError_t add_rows_f32(float* out, int64_t ldo, const float* t, int64_t ldt, int64_t rows, int d,
                          cudaStream_t st);
+
+// Householder TSQR (k_tsqr.cu): Q (M x d, ld ldq, may alias Y) = the
+// orthonormal factor of Y (M x d, ld ldy) with diag(R) >= 0, F32 or F64,
+// M >= d; work: tsqr_work_bytes(t, M, d) bytes of device memory.
+size_t tsqr_work_bytes(Ty t, int64_t M, int d);
+bool tsqr_supported(Ty t, int64_t M, int d);
+cudaError_t tsqr(Ty t, const void* Y, int64_t ldy, int64_t M, int d, void* Q, int64_t ldq,
+                 void* work, cudaStream_t st);
 
 // Omega (n x d, FP64, row-major with ld ldo) from the counter-based generator
 // of philox.cuh.

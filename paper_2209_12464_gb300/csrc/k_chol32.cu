@@ -67,8 +67,9 @@ __device__ __forceinline__ void load_col(const float* __restrict__ T, int lane, 
 // inverse of the unit lower factor; lane c's copy of column c, scaled by
 // 1 / r_jj as pivot j is formed, is row c of S.  Reciprocal square roots
 // replace IEEE sqrt/divide (the factor only has to be consistent with the
-// solve that uses it).  A non-positive pivot is replaced by bad_fill; the
-// return value (same in every lane) reports whether that happened.
+// solve that uses it).  A non-positive pivot is replaced by bad_fill.  The
+// return value (same in every lane) has bit 0 set if that happened and bit 1
+// if any pivot fell outside [1/2, 2] (a Gram that is not close to I).
 __device__ __forceinline__ void load_row(const float* __restrict__ p, float (&r)[TB]) {
 #pragma unroll
   for (int q = 0; q < TB / 4; ++q) {
@@ -80,13 +81,13 @@ __device__ __forceinline__ void load_row(const float* __restrict__ p, float (&r)
   }
 }
 
-__device__ __noinline__ bool factor_tile(float* __restrict__ B, float* __restrict__ Sout,
-                                         float* __restrict__ rb, int lane, float bad_fill) {
+__device__ __noinline__ int factor_tile(float* __restrict__ B, float* __restrict__ Sout,
+                                        float* __restrict__ rb, int lane, float bad_fill) {
   float col[TB], ecol[TB];
   load_col(B, lane, col);
 #pragma unroll
   for (int i = 0; i < TB; ++i) ecol[i] = (i == lane) ? 1.f : 0.f;
-  bool bad = false;
+  bool bad = false, far = false;
 #pragma unroll
   for (int k = 0; k < TB; ++k) {
     __syncwarp();
@@ -97,6 +98,7 @@ __device__ __noinline__ bool factor_tile(float* __restrict__ B, float* __restric
     load_row(rb, row);
     const bool nonpos = !(piv > 0.f) || !(piv < 3.0e38f);
     bad = bad || nonpos;
+    far = far || !(piv >= 0.5f && piv <= 2.0f);
     piv = nonpos ? bad_fill : piv;
     const float rinv = rsqrtf(piv);
     const float rkc = ((lane == k) ? piv : col[k]) * rinv;  // r_kc for c >= k
@@ -121,7 +123,7 @@ __device__ __noinline__ bool factor_tile(float* __restrict__ B, float* __restric
     Sout[lane * TP + r] = (r >= lane) ? ecol[r] : 0.f;
   }
   __syncwarp();
-  return !bad;
+  return (bad ? 1 : 0) | (far ? 2 : 0);
 }
 
 // Blocked Cholesky G (+ shift I) = R^T R, d <= 288, one CTA of NT threads
@@ -129,13 +131,18 @@ __device__ __noinline__ bool factor_tile(float* __restrict__ B, float* __restric
 // depend on NT).  Writes the upper tiles R_IJ (I <= J) and the diagonal-tile
 // inverses R_KK^{-1}, FP32, 32 x 32 row-major each, to `tiles`: first the
 // nb (nb+1)/2 R tiles in row-of-tiles order, then the nb inverse tiles.
+// check: this is the last pass of a CholeskyQR whose input should already be
+// orthonormal to working accuracy, so every pivot must lie in [1/2, 2]; if
+// one does not, the sketch is numerically rank deficient for CholeskyQR at
+// this precision and RUQLP_FLAG_RANKDEF is raised (the host then redoes the
+// decomposition with Householder TSQR).
 template <int NT>
 __device__ __forceinline__ void chol_body(const float* __restrict__ G, int d, double shift_rel,
                                           int force_shift, float* __restrict__ tiles,
-                                          DevStatus* __restrict__ status) {
+                                          DevStatus* __restrict__ status, int check) {
   extern __shared__ __align__(16) float sm[];
   __shared__ float s_shift;
-  __shared__ int s_bad, s_rankdef;
+  __shared__ int s_bad, s_rankdef, s_far;
   __shared__ __align__(16) float s_row[TB];
   __shared__ unsigned char s_tI[MAXNB * (MAXNB + 1) / 2], s_tJ[MAXNB * (MAXNB + 1) / 2];
   const int nb = (d + TB - 1) / TB;
@@ -147,7 +154,10 @@ __device__ __forceinline__ void chol_body(const float* __restrict__ G, int d, do
   // a lane's 4 x 4 block within a 32 x 16 half tile: rows 4 rg.., columns 4 cg..
   const int rg = lane >> 2, cg = lane & 3;
 
-  if (tid == 0) s_rankdef = 0;
+  if (tid == 0) {
+    s_rankdef = 0;
+    s_far = 0;
+  }
   if (tid < ntiles) {  // packed tile index -> (I, J)
     int I = 0, tt = tid;
     while (tt >= nb - I) { tt -= nb - I; ++I; }
@@ -278,11 +288,12 @@ __device__ __forceinline__ void chol_body(const float* __restrict__ G, int d, do
           __syncthreads();
         }
         if (warp == 0) {
-          const bool ok = factor_tile(tile(K + 1, K + 1), dinv_sm, s_row, lane, fill);
-          if (lane == 0 && !ok) {
+          const int fr = factor_tile(tile(K + 1, K + 1), dinv_sm, s_row, lane, fill);
+          if (lane == 0 && (fr & 1)) {
             if (attempt == 0) s_bad = 1;  // retry on G + shift I
             else s_rankdef = 1;           // pivots replaced by the shift
           }
+          if (lane == 0 && (fr & 2) && check && attempt == 0) s_far = 1;
         } else if (K >= 0 && (warp & 3) != 0) {
           const int nw3 = nw - nw / 4, w3 = warp - warp / 4 - 1;  // 0 .. nw3 - 1
           for (int u = 2 + w3; u < rem * (rem + 1); u += nw3) update(K, rem, u);
@@ -305,27 +316,27 @@ __device__ __forceinline__ void chol_body(const float* __restrict__ G, int d, do
       status->shifted = 1;
       if (!force_shift) status->flags |= RUQLP_FLAG_SHIFTED;
     }
-    if (s_rankdef) status->flags |= RUQLP_FLAG_RANKDEF;
+    if (s_rankdef || s_far) status->flags |= RUQLP_FLAG_RANKDEF;
   }
 }
 
 __global__ void __launch_bounds__(NTH)
 k_chol_tiles(const float* __restrict__ G, int d, double shift_rel, int force_shift,
              float* __restrict__ tiles, DevStatus* __restrict__ status,
-             const int32_t* __restrict__ gate) {
+             const int32_t* __restrict__ gate, int check) {
   pdl_launch();
   pdl_wait();
   if (gate != nullptr && *gate == 0) return;
-  chol_body<NTH>(G, d, shift_rel, force_shift, tiles, status);
+  chol_body<NTH>(G, d, shift_rel, force_shift, tiles, status, check);
 }
 
 // One CTA per matrix of the problem table; small batches of small d take
 // 128-thread CTAs, four per SM.
 template <int NT>
 __global__ void __launch_bounds__(NT, NT == 128 ? 4 : 1)
-k_bchol(const BMat* __restrict__ T, double shift_rel, int force_shift) {
+k_bchol(const BMat* __restrict__ T, double shift_rel, int force_shift, int check) {
   const BMat& b = T[blockIdx.x];
-  chol_body<NT>(b.Gf, b.d, shift_rel, force_shift, b.tiles, b.status);
+  chol_body<NT>(b.Gf, b.d, shift_rel, force_shift, b.tiles, b.status, check);
 }
 
 // X = Y R^{-1} by blocked forward substitution over 32-column tiles:
@@ -543,7 +554,7 @@ k_btrsm(const BMat* __restrict__ T, const int* __restrict__ prefix, int count, i
 int btrsm_blocks(int64_t M) { return ceil_div(M, SRB); }
 
 cudaError_t bchol(const BMat* T, int count, double shift_rel, bool force_shift, int dmax,
-                  cudaStream_t st) {
+                  cudaStream_t st, bool check) {
   if (count <= 0) return cudaSuccess;
   if (!chol_tiles_supported(dmax)) return cudaErrorInvalidValue;
   const size_t sm = chol_tiles_smem(dmax);
@@ -551,12 +562,12 @@ cudaError_t bchol(const BMat* T, int count, double shift_rel, bool force_shift, 
     cudaError_t e =
         cudaFuncSetAttribute(k_bchol<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
-    k_bchol<128><<<count, 128, sm, st>>>(T, shift_rel, force_shift ? 1 : 0);
+    k_bchol<128><<<count, 128, sm, st>>>(T, shift_rel, force_shift ? 1 : 0, check ? 1 : 0);
   } else {
     cudaError_t e =
         cudaFuncSetAttribute(k_bchol<NTH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
-    k_bchol<NTH><<<count, NTH, sm, st>>>(T, shift_rel, force_shift ? 1 : 0);
+    k_bchol<NTH><<<count, NTH, sm, st>>>(T, shift_rel, force_shift ? 1 : 0, check ? 1 : 0);
   }
   count_launch();
   return cudaGetLastError();
@@ -590,14 +601,15 @@ size_t chol_tiles_bytes(int d) {
 }
 
 cudaError_t chol_tiles_f32(const float* G, int d, double shift_rel, bool force_shift,
-                           float* tiles, DevStatus* status, const int32_t* gate, cudaStream_t st) {
+                           float* tiles, DevStatus* status, const int32_t* gate, cudaStream_t st,
+                           bool check) {
   if (!chol_tiles_supported(d)) return cudaErrorInvalidValue;
   const size_t sm = chol_tiles_smem(d);
   cudaError_t e =
       cudaFuncSetAttribute(k_chol_tiles, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
   e = launch_pdl(k_chol_tiles, dim3(1), dim3(NTH), sm, st, G, d, shift_rel, force_shift ? 1 : 0,
-                 tiles, status, gate);
+                 tiles, status, gate, check ? 1 : 0);
   count_launch();
   return e == cudaSuccess ? cudaGetLastError() : e;
 }

@@ -28,17 +28,22 @@ template <> __device__ __forceinline__ float from_f64<float>(double v) { return 
 // Right-looking Cholesky G = R^T R (upper R), one CTA, arithmetic in TF.
 // Attempt 0 factors G (skipped with force_shift); if a pivot is not positive
 // it restarts on G + shift I (attempt 1), where a pivot that is still not
-// positive is replaced by `shift` (rank deficiency, flagged).
+// positive is replaced by `shift` (rank deficiency, flagged).  check = 1 (or
+// 2 while status->shifted is still 0, i.e. no later pass will run): the last
+// pass of a CholeskyQR, whose Gram should be close to I -- a pivot outside
+// [1/2, 2] flags RUQLP_FLAG_RANKDEF.
 template <bool PACKED, typename TF, typename TW>
 __global__ void __launch_bounds__(CHOL_THREADS)
 k_chol(const double* __restrict__ G, int d, double shift_rel, int force_shift,
        double* __restrict__ R, TW* __restrict__ Rw, DevStatus* __restrict__ status,
-       const int32_t* __restrict__ gate) {
+       const int32_t* __restrict__ gate, int check) {
   if (gate != nullptr && *gate == 0) return;
   extern __shared__ double smem_d[];
   __shared__ int s_bad;
   __shared__ int s_rankdef;
+  __shared__ int s_far;
   __shared__ double s_shift;
+  const bool check_on = check == 1 || (check == 2 && status->shifted == 0);
   TF* W = PACKED ? reinterpret_cast<TF*>(smem_d) : reinterpret_cast<TF*>(R);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int nwarps = blockDim.x >> 5;
@@ -50,6 +55,7 @@ k_chol(const double* __restrict__ G, int d, double shift_rel, int force_shift,
     if (!(sh > 0.0)) sh = 1e-300;
     s_shift = sh;
     s_rankdef = 0;
+    s_far = 0;
   }
   int attempt = force_shift ? 1 : 0;
   for (; attempt < 2; ++attempt) {
@@ -63,6 +69,7 @@ k_chol(const double* __restrict__ G, int d, double shift_rel, int force_shift,
     for (int k = 0; k < d; ++k) {
       if (tid == 0) {
         TF piv = W[uidx<PACKED>(k, k, d)];
+        if (check_on && attempt == 0 && !(piv >= TF(0.5) && piv <= TF(2))) s_far = 1;
         if (!(piv > TF(0)) || !isfinite((double)piv)) {
           if (attempt == 0) {
             s_bad = 1;
@@ -116,7 +123,7 @@ k_chol(const double* __restrict__ G, int d, double shift_rel, int force_shift,
       status->shifted = 1;
       if (!force_shift) status->flags |= RUQLP_FLAG_SHIFTED;
     }
-    if (s_rankdef) status->flags |= RUQLP_FLAG_RANKDEF;
+    if (s_rankdef || s_far) status->flags |= RUQLP_FLAG_RANKDEF;
   }
 }
 
@@ -198,7 +205,7 @@ __global__ void k_status(DevStatus* s, int full) {
 
 cudaError_t chol_upper(const double* G, int d, double shift_rel, double* R, void* Rw, Ty tw,
                        DevStatus* status, const int32_t* gate, cudaStream_t st, Ty tf,
-                       bool force_shift) {
+                       bool force_shift, int check) {
   const size_t esz = (tf == Ty::F64) ? sizeof(double) : sizeof(float);
   const size_t packed = (size_t)d * (d + 1) / 2 * esz;
   const bool use_smem = packed <= CHOL_SMEM_MAX;
@@ -212,7 +219,7 @@ cudaError_t chol_upper(const double* G, int d, double shift_rel, double* R, void
                                      (int)CHOL_SMEM_MAX);                                   \
     if (e != cudaSuccess) return e;                                                         \
     k_chol<PK, TF, TW><<<1, CHOL_THREADS, sm, st>>>(G, d, shift_rel, fs, R, (TW*)Rw, status, \
-                                                    gate);                                  \
+                                                    gate, check);                           \
     count_launch();                                                                         \
     return cudaGetLastError();                                                              \
   }

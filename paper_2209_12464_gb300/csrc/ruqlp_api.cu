@@ -121,15 +121,16 @@ constexpr int kMaxSplits = 64;
 // Workspace layout for one problem.
 struct Layout {
   size_t X, Y, Z, P, partial, G, Gf, R, Rw, St, Bt, Btl, frag, colptr, rowidx, cvals, cscratch, T, Om,
-      lrT1, lrT2, lrTmp, lrPart, svdW, svdV, svdS, svdOrd, svdTmp, svdU, svdVs, total;
+      lrT1, lrT2, lrTmp, lrPart, svdW, svdV, svdS, svdOrd, svdTmp, svdU, svdVs, Ts, total;
 };
 
 inline int64_t round8(int64_t x) { return (x + 7) / 8 * 8; }
 
 // nnz >= 0: A is CSR with nnz nonzeros of val_bytes each (CSC copy kept too).
 // finish: room for Algorithm 1 step 5 (an m x dp buffer for Q P~).
+// tsqr: room for the Householder TSQR orth() (the rank-deficiency fallback).
 Layout layout_of(int64_t m, int64_t n, int d, Ty ct, int64_t nnz = -1, size_t val_bytes = 0,
-                 int finish = 0, bool gen_omega = false, int64_t lr_r = 0) {
+                 int finish = 0, bool gen_omega = false, int64_t lr_r = 0, bool tsqr = false) {
   Layout L{};
   const int dp = round16(d);
   const size_t wes = ty_size(work_ty(ct));
@@ -189,6 +190,7 @@ Layout layout_of(int64_t m, int64_t n, int d, Ty ct, int64_t nnz = -1, size_t va
     L.cvals = take((size_t)(nnz > 0 ? nnz : 1) * val_bytes);
     L.cscratch = take((size_t)2 * n * sizeof(int32_t));
   }
+  if (tsqr) L.Ts = take(tsqr_work_bytes(work_ty(ct), std::max<int64_t>(std::max(m, n), d), d));
   L.total = off;
   return L;
 }
@@ -333,6 +335,16 @@ ruqlp_status orth(ruqlp_ctx* h, const Layout& Lo, const Job& J, const void* Yin,
   const int d = J.d, dp = J.dp;
   const Ty wt = J.wt;
   cudaStream_t st = h->stream;
+  if (h->tsqr_now || h->orth_tsqr) {
+    // Householder TSQR: the unpivoted QR itself, stable whatever the rank
+    // (the fallback when a CholeskyQR pass flagged the sketch as numerically
+    // rank deficient); the next tensor-core product transposes Q itself
+    if (Lo.Ts == 0 || !tsqr_supported(wt, M, d))
+      return fail(h, RUQLP_ERR_INVALID, "internal: no TSQR workspace for %lld x %d",
+                  (long long)M, d);
+    CK(tsqr(wt, Yin, dp, M, d, Qout, dp, base + Lo.Ts, st));
+    return RUQLP_OK;
+  }
   if (wt == Ty::F32 && !h->orth_fp64) {
     const double s1 = 64.0 * 5.960464477539063e-08;
     const bool blocked = chol_tiles_supported(d);
@@ -349,7 +361,10 @@ ruqlp_status orth(ruqlp_ctx* h, const Layout& Lo, const Job& J, const void* Yin,
       if (blocked) {
         {
           ProfScope pc(h, PROF_CHOL);
-          CK(chol_tiles_f32(Gf, d, s1, pass == 0, (float*)Rw, h->status, nullptr, st));
+          // the last pass of a final basis sees a Gram close to I, or flags
+          // the sketch as numerically rank deficient
+          CK(chol_tiles_f32(Gf, d, s1, pass == 0, (float*)Rw, h->status, nullptr, st,
+                            pass == 2));
         }
         ProfScope pt(h, PROF_TRSM);
         const bool bt = make_bt && pass == passes - 1;
@@ -362,7 +377,8 @@ ruqlp_status orth(ruqlp_ctx* h, const Layout& Lo, const Job& J, const void* Yin,
                             bt ? base + Lo.Bt : nullptr, round8(M), btl));
         if (bt && bt_made) *bt_made = true;
       } else {
-        CK(chol_upper(G, d, s1, R, Rw, Ty::F32, h->status, nullptr, st, Ty::F32, pass == 0));
+        CK(chol_upper(G, d, s1, R, Rw, Ty::F32, h->status, nullptr, st, Ty::F32, pass == 0,
+                      pass == 2 ? 1 : 0));
         CK(trsm_right_upper(Ty::F32, src, dp, Rw, Qout, dp, M, d, nullptr, st));
       }
     }
@@ -378,13 +394,14 @@ ruqlp_status orth(ruqlp_ctx* h, const Layout& Lo, const Job& J, const void* Yin,
   CK(simt_gemm_tn(wt, wt, Ty::F64, g, Yin, dp, Yin, dp, G, d, d, M, d, S, partial, nullptr, st));
   CK(chol_upper(G, d, srel, R, Rw, wt, h->status, nullptr, st));
   CK(trsm_right_upper(wt, Yin, dp, Rw, Qout, dp, M, d, nullptr, st));
-  // pass 2
+  // pass 2 (the last one unless pass 1 shifted: then its Gram must be close
+  // to I, else the sketch is numerically rank deficient)
   CK(simt_gemm_tn(wt, wt, Ty::F64, g, Qout, dp, Qout, dp, G, d, d, M, d, S, partial, nullptr, st));
-  CK(chol_upper(G, d, srel, R, Rw, wt, h->status, nullptr, st));
+  CK(chol_upper(G, d, srel, R, Rw, wt, h->status, nullptr, st, Ty::F64, false, 2));
   CK(trsm_right_upper(wt, Qout, dp, Rw, Qout, dp, M, d, nullptr, st));
-  // pass 3 (only after a shift)
+  // pass 3 (only after a shift; the last pass)
   CK(simt_gemm_tn(wt, wt, Ty::F64, g, Qout, dp, Qout, dp, G, d, d, M, d, S, partial, gate, st));
-  CK(chol_upper(G, d, srel, R, Rw, wt, h->status, gate, st));
+  CK(chol_upper(G, d, srel, R, Rw, wt, h->status, gate, st, Ty::F64, false, 1));
   CK(trsm_right_upper(wt, Qout, dp, Rw, Qout, dp, M, d, gate, st));
   return RUQLP_OK;
 }
@@ -555,9 +572,10 @@ ruqlp_status prepare_csr(ruqlp_ctx* h, const Layout& Lo, Job& J) {
 ruqlp_status run_dense(ruqlp_ctx* h, const Job& J0) {
   Job J = J0;
   const bool gen = J.omega == nullptr;
+  const bool ts = h->tsqr_now || h->orth_tsqr;
   const Layout Lo = J.csr ? layout_of(J.m, J.n, J.d, J.ct, J.nnz, ty_size(J.tv), J.finish_paper,
-                                      gen, J.lr_r)
-                          : layout_of(J.m, J.n, J.d, J.ct, -1, 0, J.finish_paper, gen);
+                                      gen, J.lr_r, ts)
+                          : layout_of(J.m, J.n, J.d, J.ct, -1, 0, J.finish_paper, gen, 0, ts);
   ruqlp_status s = ensure_arena(h, Lo.total);
   if (s != RUQLP_OK) return s;
   CK(status_reset(h->status, h->stream));
@@ -686,6 +704,7 @@ ruqlp_status finish(ruqlp_ctx* h, ruqlp_outputs* out) {
   CK(cudaStreamSynchronize(h->stream));
   if (h->profile) prof_collect(h);
   out->flags = (uint32_t)h->status_host->flags;
+  if (h->tsqr_now || h->orth_tsqr) out->flags |= RUQLP_FLAG_TSQR;
   if (h->status_host->timeout)
     return fail(h, RUQLP_ERR_TIMEOUT, "a bounded device wait ran out in a tensor-core product");
   if (h->status_host->invalid & 4)
@@ -706,6 +725,9 @@ ruqlp_status single_begin(ruqlp_ctx* h, const ruqlp_matrix* A, const ruqlp_param
   int d;
   ruqlp_status s = validate(h, A, prm, out, &m, &n, &d);
   if (s != RUQLP_OK) return s;
+  h->last_A = *A;
+  h->last_prm = *prm;
+  h->last_out = *out;
   CK(cudaSetDevice(h->device));
   Job J{};
   fill_job(A, prm, out, m, n, d, J);
@@ -717,7 +739,21 @@ ruqlp_status single_begin(ruqlp_ctx* h, const ruqlp_matrix* A, const ruqlp_param
   return run_dense(h, J);
 }
 
-ruqlp_status single_end(ruqlp_ctx* h, ruqlp_outputs* out) { return finish(h, out); }
+// A decomposition whose CholeskyQR flagged a numerically rank-deficient
+// sketch (RUQLP_FLAG_RANKDEF) is run again with every orth() a Householder
+// TSQR, the paper's unpivoted QR taken literally; its flags then carry both
+// RUQLP_FLAG_RANKDEF and RUQLP_FLAG_TSQR.
+ruqlp_status single_end(ruqlp_ctx* h, ruqlp_outputs* out) {
+  ruqlp_status s = finish(h, out);
+  if (s != RUQLP_OK || !(out->flags & RUQLP_FLAG_RANKDEF) || h->tsqr_now || h->orth_tsqr)
+    return s;
+  h->tsqr_now = true;
+  s = single_begin(h, &h->last_A, &h->last_prm, &h->last_out);
+  if (s == RUQLP_OK) s = finish(h, out);
+  h->tsqr_now = false;
+  out->flags |= RUQLP_FLAG_RANKDEF;
+  return s;
+}
 
 ruqlp_status check_request(ruqlp_ctx* h, const ruqlp_matrix* A, const ruqlp_params* prm,
                            const ruqlp_outputs* out, int* d) {
@@ -765,6 +801,7 @@ void copy_options(const ruqlp_ctx* from, ruqlp_ctx* to) {
   to->orth_full = from->orth_full;
   to->bf16_simt = from->bf16_simt;
   to->orth_simt = from->orth_simt;
+  to->orth_tsqr = from->orth_tsqr;
 }
 
 ruqlp_status set_error(ruqlp_ctx* h, ruqlp_status s, const char* msg) {
@@ -821,7 +858,7 @@ ruqlp_status batch_launches(ruqlp_ctx* h, const BatchPlan& bp, int count, int q,
     for (int pass = 0; pass < passes; ++pass) {
       const int from = pass == 0 ? src : dst;
       CK(bgram(T, pre(gp), tot(gp), count, from, from, kMaxSplits, bp.dmax, st));
-      CK(bchol(T, count, s1, pass == 0, bp.dmax, st));
+      CK(bchol(T, count, s1, pass == 0, bp.dmax, st, pass == 2));
       CK(btrsm(T, pre(tp), tot(tp), count, from, dst, bp.dmax, st,
                pass == passes - 1 ? make_bt : 0));
     }
@@ -1086,6 +1123,8 @@ ruqlp_status batch_begin(ruqlp_ctx* h, int count, const ruqlp_matrix* A, const r
   run->count = count;
   run->off_status = bp.off_status;
   run->off_err = bp.off_err;
+  run->A.assign(A, A + count);
+  run->prm.assign(prm, prm + count);
   return RUQLP_OK;
 }
 
@@ -1101,6 +1140,17 @@ ruqlp_status batch_end(ruqlp_ctx* h, const BatchRun& run, ruqlp_outputs* out) {
   if (h->profile) prof_collect(h);
   for (int i = 0; i < run.count; ++i) out[i].flags = (uint32_t)stat[i].flags;
   if (derr) return fail(h, RUQLP_ERR_TIMEOUT, "a bounded device wait ran out in a batched product");
+  // items whose sketch CholeskyQR could not orthonormalise: alone on the
+  // single-matrix path, which reruns them with Householder TSQR (as it would
+  // had they come alone)
+  for (int i = 0; i < run.count; ++i) {
+    if (!(out[i].flags & RUQLP_FLAG_RANKDEF) || i >= (int)run.A.size()) continue;
+    ruqlp_outputs o = out[i];
+    ruqlp_status s = single_begin(h, &run.A[i], &run.prm[i], &o);
+    if (s == RUQLP_OK) s = single_end(h, &o);
+    if (s != RUQLP_OK) return fail(h, s, "batch item %d (TSQR rerun): %s", i, h->err.c_str());
+    out[i].flags = o.flags;
+  }
   return RUQLP_OK;
 }
 
@@ -1190,6 +1240,10 @@ ruqlp_status ruqlp_set_option(ruqlp_handle h, const char* name, int64_t value) {
     h->orth_simt = value ? 1 : 0;
     return RUQLP_OK;
   }
+  if (strcmp(name, "orth_tsqr") == 0) {
+    h->orth_tsqr = value ? 1 : 0;
+    return RUQLP_OK;
+  }
   if (strcmp(name, "profile") == 0) {
     h->profile = value != 0;
     for (int i = 0; i < kProfN; ++i) {
@@ -1258,10 +1312,25 @@ static ruqlp_status copy_split(ruqlp_ctx* h, void* dst, size_t dpitch, const voi
   return RUQLP_OK;
 }
 
+static ruqlp_status decompose_host_once(ruqlp_handle h, const ruqlp_matrix* A,
+                                       const ruqlp_params* prm, ruqlp_outputs* out);
+
 ruqlp_status ruqlp_decompose_host(ruqlp_handle h, const ruqlp_matrix* A,
                                   const ruqlp_params* prm, ruqlp_outputs* out) {
   if (!h) return RUQLP_ERR_INVALID;
   h->err.clear();
+  ruqlp_status s = decompose_host_once(h, A, prm, out);
+  if (s != RUQLP_OK || !(out->flags & RUQLP_FLAG_RANKDEF) || h->orth_tsqr) return s;
+  // numerically rank-deficient sketch: again, with Householder TSQR orth()s
+  h->tsqr_now = true;
+  s = decompose_host_once(h, A, prm, out);
+  h->tsqr_now = false;
+  out->flags |= RUQLP_FLAG_RANKDEF;
+  return s;
+}
+
+static ruqlp_status decompose_host_once(ruqlp_handle h, const ruqlp_matrix* A,
+                                       const ruqlp_params* prm, ruqlp_outputs* out) {
   int64_t m, n;
   int d;
   ruqlp_status s = validate(h, A, prm, out, &m, &n, &d);
@@ -1274,8 +1343,10 @@ ruqlp_status ruqlp_decompose_host(ruqlp_handle h, const ruqlp_matrix* A,
   const size_t oes = ty_size(J.ot);
   // the workspace first, then staging for A, Omega and the outputs
   const bool gen = prm->omega == nullptr;  // run_dense's layout, which comes first
-  const Layout Lo = J.csr ? layout_of(m, n, d, J.ct, J.nnz, ty_size(J.tv), J.finish_paper, gen)
-                          : layout_of(m, n, d, J.ct, -1, 0, J.finish_paper, gen);
+  const bool ts = h->tsqr_now || h->orth_tsqr;
+  const Layout Lo = J.csr ? layout_of(m, n, d, J.ct, J.nnz, ty_size(J.tv), J.finish_paper, gen,
+                                      0, ts)
+                          : layout_of(m, n, d, J.ct, -1, 0, J.finish_paper, gen, 0, ts);
   size_t off = align_up(Lo.total, 256);
   auto take = [&](size_t bytes) {
     const size_t o = off;
@@ -1428,17 +1499,27 @@ ruqlp_status ruqlp_orth(ruqlp_handle h, const void* Y, int64_t M, int d, int64_t
   J.dp = round16(d);
   J.ct = dtype == RUQLP_F64 ? Ty::F64 : Ty::F32;
   J.wt = J.ct;
-  const Layout Lo = layout_of(M, d, d, J.ct);
-  ruqlp_status s = ensure_arena(h, Lo.total);
-  if (s != RUQLP_OK) return s;
-  void* W = (char*)h->arena + Lo.Y;
-  CK(status_reset(h->status, h->stream));
-  CK(copy_cast_2d(J.wt, Y, ldy, J.wt, W, J.dp, M, d, h->stream));
-  s = orth(h, Lo, J, W, W, M);
-  if (s != RUQLP_OK) return s;
-  CK(copy_cast_2d(J.wt, W, J.dp, J.wt, Q, ldq, M, d, h->stream));
+  // CholeskyQR first; a numerically rank-deficient Y goes again through the
+  // Householder TSQR
   ruqlp_outputs dummy{};
-  return finish(h, &dummy);
+  for (int attempt = 0; attempt < 2; ++attempt) {
+    h->tsqr_now = attempt == 1;
+    const Layout Lo = layout_of(M, d, d, J.ct, -1, 0, 0, false, 0, h->tsqr_now || h->orth_tsqr);
+    ruqlp_status s = ensure_arena(h, Lo.total);
+    if (s == RUQLP_OK) {
+      void* W = (char*)h->arena + Lo.Y;
+      CK(status_reset(h->status, h->stream));
+      CK(copy_cast_2d(J.wt, Y, ldy, J.wt, W, J.dp, M, d, h->stream));
+      s = orth(h, Lo, J, W, W, M);
+      if (s == RUQLP_OK) {
+        CK(copy_cast_2d(J.wt, W, J.dp, J.wt, Q, ldq, M, d, h->stream));
+        s = finish(h, &dummy);
+      }
+    }
+    h->tsqr_now = false;
+    if (s != RUQLP_OK || !(dummy.flags & RUQLP_FLAG_RANKDEF) || h->orth_tsqr) return s;
+  }
+  return RUQLP_OK;
 }
 
 ruqlp_status ruqlp_gram(ruqlp_handle h, const void* Y, int64_t M, int d, int64_t ldy,

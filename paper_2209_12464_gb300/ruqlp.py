@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(_PKG, "libruqlp.so")
 
 OK, NOT_READY, ERR_INVALID, ERR_BUDGET, ERR_CUDA, ERR_BREAKDOWN, ERR_TIMEOUT = range(7)
 F64, F32, BF16 = 0, 1, 2
-FLAG_SHIFTED, FLAG_RANKDEF = 0x1, 0x2
+FLAG_SHIFTED, FLAG_RANKDEF, FLAG_TSQR = 0x1, 0x2, 0x4
 STATUS_NAMES = {0: "OK", 1: "NOT_READY", 2: "ERR_INVALID", 3: "ERR_BUDGET", 4: "ERR_CUDA",
                 5: "ERR_BREAKDOWN", 6: "ERR_TIMEOUT"}
 
