@@ -216,6 +216,56 @@ print(json.dumps({"seconds": t}))
                       f"({dtype}) so the ratio is the time per decomposition"}
 
 
+def oracle_full(A32, Om, q, L_gpu, resid_gpu):
+    """The FP64 oracle, as it stands, on the whole workload matrix the GPU
+    decomposed (the unrounded FP32 A, widened to FP64) and the same Omega, in a
+    spawned process using every host core: its wall time (the CPU baseline on
+    the full configuration) and the error of the GPU result against it --
+    the residual ratio and max_i | |L_ii| - |L_ii^oracle| | / |L_11^oracle|."""
+    import numpy as np
+    tmp = tempfile.mkdtemp(prefix="ruqlp_oracle_")
+    fa, fo, fr = (os.path.join(tmp, x) for x in ("A.npy", "Om.npy", "res.npz"))
+    try:
+        np.save(fa, A32.cpu().numpy())
+        np.save(fo, Om.cpu().numpy())
+        code = r"""
+import sys, time, json
+sys.path.insert(0, %r)
+import numpy as np
+import oracle
+A = np.load(%r).astype(np.float64)
+Om = np.load(%r)
+t0 = time.perf_counter()
+ref = oracle.ruqlp(A, Om, %d)
+t = time.perf_counter() - t0
+r0 = oracle.residual_fro(A, ref["Q"], ref["L"], ref["P"])
+np.savez(%r, diag=np.diag(ref["L"]), r0=r0, seconds=t)
+print(json.dumps({"seconds": t}))
+""" % (ROOT, fa, fo, q, fr)
+        env = dict(os.environ)
+        cores = os.cpu_count() or 1
+        for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+            env[v] = str(cores)
+        env["CUDA_VISIBLE_DEVICES"] = ""
+        r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env,
+                           timeout=1800)
+        if r.returncode != 0:
+            return None, {"error": r.stderr[-400:]}
+        z = np.load(fr)
+        dg = np.abs(np.diag(L_gpu.double().cpu().numpy()))
+        do = np.abs(z["diag"])
+        r0 = float(z["r0"])
+        acc = {"oracle_residual_fro": r0, "residual_ratio_to_oracle": resid_gpu / r0,
+               "max_abs_diagL_dev_rel_L11": float(np.max(np.abs(dg - do)) / do[0]),
+               "oracle": "oracle.ruqlp, FP64, same A (unrounded FP32 values) and Omega"}
+        return float(z["seconds"]), acc
+    finally:
+        for x in (fa, fo, fr):
+            if os.path.exists(x):
+                os.remove(x)
+        os.rmdir(tmp)
+
+
 def run_reference(args):
     rank, _, world = dist_env()
     if rank != 0:
@@ -861,7 +911,6 @@ def main():
     # unrounded A)
     Qo, Lo, Po = outs
     resid = residual_gpu(torch, A32, Qo, Lo, Po)
-    del A32
     # approximate Eckart-Young floor: spectrum tail plus the noise energy
     # outside a rank-d subspace ((m-d)(n-d) of its m n entries)
     floor = math.sqrt(float((sig[d:] ** 2).sum()) + (NOISE ** 2) * (m - d) * (n - d)) / math.sqrt(
@@ -897,6 +946,11 @@ def main():
         achieved = alg / (avg * 1e-3) / 1e9
         roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                     "frac": achieved / hbm_peak, "traffic": tc_traffic(m, n, d),
+                    "traffic_source": "dram__bytes_read.sum + dram__bytes_write.sum of one "
+                                      "k_tc_gemm launch captured at 10240 x 10240 and scaled by "
+                                      "the units processed to the 20000 x 20000 launch "
+                                      "(profiles/k_tc_gemm_dense10240_bf16.md); not measured "
+                                      "in this run",
                     "kernel": "k_tc_gemm (tcgen05 A X / A^T Y, one pass over A per launch)",
                     "alg_bytes_per_launch": alg, "avg_launch_ms": avg, "launches": cnt,
                     "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)",
@@ -936,8 +990,22 @@ def main():
                "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo, "ms_per_step": te * 1e3}
 
     cpu = None
+    acc_oracle = {}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(args.dtype, rows=2000)
+        # the FP64 oracle on the full workload: CPU baseline and per-result
+        # error of this run's output against it
+        secs, acc_oracle = oracle_full(A32, Om, q, outs[1], resid)
+        if secs is not None:
+            cores = os.cpu_count() or 1
+            cpu = {"value": passes * bytes_a / 1e9 / secs, "unit": "GB/s", "cores": cores,
+                   "kind": "oracle", "seconds": secs,
+                   "sample": f"the full workload: oracle.ruqlp (FP64 numpy, own Householder "
+                             f"QR) on the same {m} x {n} matrix and Omega; bytes counted as "
+                             f"(2q+2) x bytes(A in {args.dtype}) so the ratio is the time per "
+                             f"decomposition"}
+        else:
+            cpu = cpu_baseline(args.dtype, rows=2000)
+    del A32
 
     if rank == 0:
         out = {"metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world,
@@ -951,7 +1019,7 @@ def main():
                           "l2": "inputs larger than L2 (A is %.0f MB vs 129 MB L2)" % (bytes_a / 1e6),
                           "parallelism": f"replicas x{world}"},
                "accuracy": {"residual_fro": resid, "approx_floor_fro": floor,
-                            "flags": flags},
+                            "flags": flags, **acc_oracle},
                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                "gpu_launches": launches, "clocks": ck,
                "hbm_frac_of_measured": value / world / hbm_peak}

@@ -201,7 +201,18 @@ ruqlp_status ruqlp_set_stream(ruqlp_handle h, void* cuda_stream);
  *   it (to 0 or 1) also zeroes the accumulators.
  * Errors: INVALID (unknown name). */
 ruqlp_status ruqlp_set_option(ruqlp_handle h, const char* name, int64_t value);
-/* (continued) "orth_tsqr": 1 = every orth() is a Householder TSQR (leaf QRs
+/* (continued) "test_withhold_stage": test hook, off by default.  1 = in each
+ *   tensor-core product that follows, the first CTA never loads its first
+ *   shared-memory stage, so the MMA warp's bounded wait (2 s) runs out and the
+ *   call returns RUQLP_ERR_TIMEOUT after the CTA has drained its copies and
+ *   freed its tensor memory; the handle stays usable.  Exercises the timeout
+ *   path without faulting or hanging the GPU.
+ * (continued) "tc_nsplit": column split of the tensor-core products: 0
+ *   (default) = chosen per product shape by the library's tuner (below);
+ *   1, 2, 4 = that split (each 128-row tile of the output taken as that many
+ *   items of dp / split columns by consecutive CTAs; needs dp / split to be a
+ *   multiple of 16, else the product returns RUQLP_ERR_CUDA).
+ * (continued) "orth_tsqr": 1 = every orth() is a Householder TSQR (leaf QRs
  *   of row blocks, a binary tree of stacked-R QRs, explicit Q; Demmel,
  *   Grigori, Hoemmen, Langou 2012) -- the unpivoted QR of Section II-A taken
  *   literally, stable whatever the sketch's conditioning or rank, slower
@@ -357,6 +368,19 @@ ruqlp_status ruqlp_omega(ruqlp_handle h, int64_t n, int d, uint64_t seed, double
 
 /* Kernels launched by this library in this process so far (all handles). */
 int64_t ruqlp_launch_count(void);
+
+/* Tile tuner of the tensor-core products (the sketch / power / B^T passes
+ * of Section III-D, the bulk of the O(mnd) work): the first product of each
+ * shape (orientation, two-part operand, output rows, K, dp) outside stream
+ * capture times every valid column split (1, 2, 4; each with the deepest
+ * shared-memory ring that fits) twice with CUDA events and keeps the fastest
+ * for the process; that configuration computes the result, so results are
+ * deterministic from then on.  ruqlp_tune_file(path) loads earlier choices
+ * from a text file (one "tc_gemm trans two_part rows K dp split stages us"
+ * line each) and appends every new choice to it; NULL or "" stops the
+ * mirroring.  Returns the number of entries loaded.  Process-wide (all
+ * handles); thread-safe. */
+int ruqlp_tune_file(const char* path);
 
 /* With the "profile" option on: number of spans and their summed device time
  * (milliseconds, CUDA events on the handle's stream) of a phase:

@@ -31,6 +31,8 @@ struct ruqlp_ctx {
   int bf16_simt = 0;    // 1: BF16 products on CUDA cores instead of tensor cores
   int orth_simt = 0;    // 1: orth() Grams and Q = Y R^{-1} on CUDA cores
   int orth_tsqr = 0;    // 1: every orth() is a Householder TSQR
+  int tc_nsplit = 0;    // tensor-core products: column split (0 = tuned per shape)
+  int test_withhold = 0;  // test hook: the next tensor-core products run out a wait
   bool tsqr_now = false;  // this run takes the TSQR orth() (fallback rerun)
   // the last single decomposition's arguments, for its TSQR rerun
   ruqlp_matrix last_A{};

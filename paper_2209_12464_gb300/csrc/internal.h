@@ -105,10 +105,17 @@ cudaError_t write_L(const double* R, int d, Ty tl, void* L, bool upper, cudaStre
 // launch (used to bracket it with profiling events); may be empty.
 // Btl (optional, same layout as Bt): the low BF16 part of the skinny operand;
 // then out = A (Bt + Btl)^T (or A^T ...), two MMAs per A tile.
+// force_ns > 0: that column split (dp / force_ns a multiple of 16); 0: the
+// configuration the tuner measured fastest for this shape.  withhold (test
+// hook): CTA 0 never loads its first ring stage, so its bounded waits run
+// out and the launch ends on the timeout path (err set, TMEM freed).
 cudaError_t tc_gemm(bool trans, const void* A, int64_t lda, int64_t m, int64_t n, const void* Bt,
                     int64_t ldb, int dp, float* out, int64_t ldo, float* frag, int* err,
                     cudaStream_t st, const std::function<void(bool)>& mark = {},
-                    const void* Btl = nullptr);
+                    const void* Btl = nullptr, int force_ns = 0, int withhold = 0);
+// Mirror the product tuner's choices in a text file (loaded now, appended
+// to as shapes are tuned); returns the entries loaded.
+int tune_file(const char* path);
 size_t tc_frag_bytes(int dp);
 // Whether tc_gemm accepts these operands (alignment / size rules).
 bool tc_supported(const void* A, int64_t lda, int dp);

@@ -17,13 +17,24 @@
 // Work split: output tiles of 128 rows are dealt to the CTAs in whole waves
 // (data parallel); the tiles of the last partial wave are split over all
 // CTAs along K (stream-K) into FP32 fragments, summed afterwards in CTA
-// order by a fix-up kernel (deterministic; no atomics).
+// order by a fix-up kernel (deterministic; no atomics).  With a column split
+// ns > 1 every 128-row tile is ns items of dp / ns output columns, dealt to
+// consecutive CTAs: they stream the same A tile at the same time (the
+// second read comes from L2), and each stage holds only a dp / ns slice of
+// the skinny operand, so the ring is deeper and more of A is in flight per
+// SM (the product is HBM-latency bound: bytes in flight / latency).  ns and
+// the ring depth per shape come from a measured tuner (tc_gemm below).
 // Every mbarrier wait is bounded (~2 s of %globaltimer); on timeout the CTA
 // sets an error word, stops issuing work, and frees its TMEM before exiting.
 #include <algorithm>
+#include <array>
 #include <cuda.h>
 #include <cudaTypedefs.h>
+#include <map>
+#include <mutex>
+#include <stdio.h>
 #include <string.h>
+#include <string>
 
 #include "internal.h"
 #include "tcgen05.cuh"
@@ -40,14 +51,16 @@ constexpr int kBatchMaps = 4;              // tensor maps per batched matrix
 struct TcParams {
   int64_t Mout;   // output rows
   int64_t K;      // contraction length
-  int dp;         // N (multiple of 16, <= 256)
+  int dp;         // output columns (multiple of 16, <= 256)
+  int ns, dpi;    // column split: items of dpi = dp / ns columns (MMA N)
   int stages;
   float* out;
   int64_t ldo;
-  float* frag;    // [P][2][BM][dp]
+  float* frag;    // [P][2][BM][dpi]
   int T, KB, full_waves, tail;
   int64_t U;      // stream-K units = tail * KB
   int* err;
+  int withhold;   // test hook: CTA 0 never loads its first stage (its waits run out)
 };
 
 // A CTA's work, generated on the fly: items 0..full_waves-1 are whole tiles
@@ -85,7 +98,8 @@ struct TcItem {
   const CUtensorMap* mA;
   const CUtensorMap* mB;
   const CUtensorMap* mB2;  // low BF16 part of the skinny operand (two-part products)
-  int tile, kb0, kb1, dp;
+  int tile, kb0, kb1, dp;  // 128-row tile, K blocks, output columns (MMA N)
+  int bcol;                // first output column (row of the skinny operand Bt)
   float* out;
   int64_t ldo, rows;
   bool a_split;  // K-major A loaded as two 64-row boxes (batched maps)
@@ -101,14 +115,15 @@ struct WorkSingle {
   __device__ int count() const { return item_count(*p); }
   __device__ TcItem get(int i) const {
     const Item it = get_item(*p, i);
-    TcItem r{mA, mB, mB2, it.tile, it.kb0, it.kb1, p->dp, nullptr, 0, 0, false};
+    const int mt = it.tile / p->ns, h = it.tile - mt * p->ns;
+    TcItem r{mA, mB, mB2, mt, it.kb0, it.kb1, p->dpi, h * p->dpi, nullptr, 0, 0, false};
     if (it.slot < 0) {
-      r.out = p->out + (int64_t)it.tile * BM * p->ldo;
+      r.out = p->out + (int64_t)mt * BM * p->ldo + r.bcol;
       r.ldo = p->ldo;
-      r.rows = p->Mout - (int64_t)it.tile * BM;
+      r.rows = p->Mout - (int64_t)mt * BM;
     } else {
-      r.out = p->frag + ((int64_t)blockIdx.x * 2 + it.slot) * BM * p->dp;
-      r.ldo = p->dp;
+      r.out = p->frag + ((int64_t)blockIdx.x * 2 + it.slot) * BM * p->dpi;
+      r.ldo = p->dpi;
       r.rows = BM;
     }
     return r;
@@ -143,6 +158,7 @@ struct WorkBatch {
     r.kb0 = 0;
     r.kb1 = (int)((K + BK - 1) / BK);
     r.dp = b.dp;
+    r.bcol = 0;
     r.out = bbuf(b, dst) + (int64_t)w.tile * BM * b.dp;
     r.ldo = b.dp;
     r.rows = Mout - (int64_t)w.tile * BM;
@@ -163,7 +179,8 @@ __device__ __forceinline__ void tmap_acquire(const CUtensorMap* m) {
 // holds both parts' tiles and every A tile is multiplied by both into the same
 // accumulator, D += A h + A l.
 template <bool TRANS, bool B2, class W>
-__device__ __forceinline__ void tc_body(const W& w, int* err, int S, int dpmax) {
+__device__ __forceinline__ void tc_body(const W& w, int* err, int S, int dpmax,
+                                        int withhold = 0) {
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
   const uint32_t base = (raw + 1023u) & ~1023u;
@@ -235,6 +252,12 @@ __device__ __forceinline__ void tc_body(const W& w, int* err, int S, int dpmax) 
         const uint32_t bytes = A_TILE_BYTES + (B2 ? 2u : 1u) * (uint32_t)it.dp * BK * 2;
         for (int kb = it.kb0; kb < it.kb1; ++kb) {
           if (!mbar_wait(empty_bar(stage), phase ^ 1u, abort_flag)) { ok = false; break; }
+          if (withhold && blockIdx.x == 0 && i == 0 && kb == it.kb0) {
+            // test hook: this stage is never loaded, so the MMA warp's bounded
+            // wait on it runs out and the CTA takes its timeout path
+            if (++stage == S) { stage = 0; phase ^= 1u; }
+            continue;
+          }
           ++issued;
           const uint32_t sa = base + stage * stage_bytes, sb = sa + A_TILE_BYTES;
           mbar_expect_tx(full_bar(stage), bytes);
@@ -251,8 +274,8 @@ __device__ __forceinline__ void tc_body(const W& w, int* err, int S, int dpmax) 
             tma_load_2d(sa + A_TILE_BYTES / 2, it.mA, full_bar(stage), it.tile * BM + 64,
                         kb * BK, pol_a);
           }
-          tma_load_2d(sb, it.mB, full_bar(stage), kb * BK, 0, pol_b);
-          if (B2) tma_load_2d(sb + b_tile, it.mB2, full_bar(stage), kb * BK, 0, pol_b);
+          tma_load_2d(sb, it.mB, full_bar(stage), kb * BK, it.bcol, pol_b);
+          if (B2) tma_load_2d(sb + b_tile, it.mB2, full_bar(stage), kb * BK, it.bcol, pol_b);
           if (++stage == S) { stage = 0; phase ^= 1u; }
         }
       }
@@ -358,7 +381,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
           const __grid_constant__ CUtensorMap tmB2, const __grid_constant__ TcParams p) {
   const WorkSingle w{&tmA, &tmB, &tmB2, &p};
-  tc_body<TRANS, B2>(w, p.err, p.stages, p.dp);
+  tc_body<TRANS, B2>(w, p.err, p.stages, p.dpi, p.withhold);
 }
 
 template <bool TRANS, bool B2>
@@ -407,9 +430,10 @@ __global__ void __launch_bounds__(256) k_tc_fixup(TcParams p, int P) {
   __syncthreads();
   // block (tt, y): rows 4 y .. 4 y + 3 of the tile, a thread per 4 columns
   const int tile = p.full_waves * P + tt;
-  const int q4 = p.dp / 4;
+  const int mt = tile / p.ns, col0 = (tile - mt * p.ns) * p.dpi;
+  const int q4 = p.dpi / 4;
   const int r = blockIdx.y * 4 + threadIdx.x / 64, c4 = threadIdx.x % 64;
-  const int64_t gr = (int64_t)tile * BM + r;
+  const int64_t gr = (int64_t)mt * BM + r;
   if (gr >= p.Mout || c4 >= q4) return;
   const float4* frag = reinterpret_cast<const float4*>(p.frag);
   // sixteen 16-byte loads in flight, summed in contributor order
@@ -428,7 +452,7 @@ __global__ void __launch_bounds__(256) k_tc_fixup(TcParams p, int P) {
         s.w += v[u].w;
       }
   }
-  *reinterpret_cast<float4*>(p.out + gr * p.ldo + 4 * c4) = s;
+  *reinterpret_cast<float4*>(p.out + gr * p.ldo + col0 + 4 * c4) = s;
 }
 
 // dst[c][r] = bf16(src[r][c]) for c < cols, 0 for cols <= c < dp (r < rows);
@@ -761,15 +785,15 @@ __global__ void __launch_bounds__(256) k_gram_tc_reduce(const float* __restrict_
   const int64_t slab = (int64_t)nbr * dp * 32, src = ((int64_t)g * dp + col) * 32 + lane;
   float s = 0.f, c = 0.f;
   int z = w;
-  for (; z + 8 * 3 < P; z += 8 * 4) {
-    const float a = part[z * slab + src], b = part[(z + 8) * slab + src];
-    const float x = part[(z + 16) * slab + src], e = part[(z + 24) * slab + src];
-    two_sum_acc(s, c, a);
-    two_sum_acc(s, c, b);
-    two_sum_acc(s, c, x);
-    two_sum_acc(s, c, e);
+  // sixteen slab loads in flight per lane, then added in slab order
+  for (; z < P; z += 8 * 16) {
+    float v[16];
+#pragma unroll
+    for (int u = 0; u < 16; ++u) v[u] = (z + 8 * u < P) ? part[(z + 8 * u) * slab + src] : 0.f;
+#pragma unroll
+    for (int u = 0; u < 16; ++u)
+      if (z + 8 * u < P) two_sum_acc(s, c, v[u]);
   }
-  for (; z < P; z += 8) two_sum_acc(s, c, part[z * slab + src]);
   ws[w][lane] = s;
   wc[w][lane] = c;
   __syncthreads();
@@ -881,22 +905,55 @@ int tc_stages(size_t stage_bytes) {
 }
 }  // namespace
 
-cudaError_t tc_gemm(bool trans, const void* A, int64_t lda, int64_t m, int64_t n, const void* Bt,
-                    int64_t ldb, int dp, float* out, int64_t ldo, float* frag, int* err,
-                    cudaStream_t st, const std::function<void(bool)>& mark, const void* Btl) {
-  if (dp < 16 || dp > 256 || dp % 16 != 0) return cudaErrorInvalidValue;
-  if (lda % 8 != 0 || ldb % 8 != 0 || ((uintptr_t)A & 15) || ((uintptr_t)Bt & 15) || ldo % 4 != 0 ||
-      ((uintptr_t)out & 15) || ((uintptr_t)Btl & 15))
-    return cudaErrorInvalidValue;
-  const bool b2 = Btl != nullptr;
-  const int64_t Mout = trans ? n : m, K = trans ? m : n;
+namespace {
+
+// Launch configuration of one product: column split and ring depth.
+struct TcCfg {
+  int ns = 1, stages = 0;
+};
+
+size_t tc_stage_bytes(int dp, int ns, bool b2) {
+  return A_TILE_BYTES + (b2 ? 2 : 1) * (size_t)(dp / ns) * BK * 2;
+}
+
+bool tc_ns_valid(int dp, int ns) { return dp % ns == 0 && (dp / ns) % 16 == 0 && dp / ns >= 16; }
+
+// The measured choice per product shape (trans, two-part, output rows, K,
+// dp), process-wide, optionally mirrored in a text file (ruqlp_tune_file).
+std::mutex g_tune_mu;
+std::map<std::array<int64_t, 5>, TcCfg> g_tune;
+std::string g_tune_path;
+
+void tune_save_line(const std::array<int64_t, 5>& key, const TcCfg& c, double us) {
+  if (g_tune_path.empty()) return;
+  FILE* f = fopen(g_tune_path.c_str(), "a");
+  if (!f) return;
+  fprintf(f, "tc_gemm %lld %lld %lld %lld %lld %d %d %.3f\n", (long long)key[0], (long long)key[1],
+          (long long)key[2], (long long)key[3], (long long)key[4], c.ns, c.stages, us);
+  fclose(f);
+}
+
+struct TcOperands {
+  bool trans, b2;
+  const void *A, *Bt, *Btl;
+  int64_t lda, m, n, ldb, ldo;
+  int dp;
+  float *out, *frag;
+  int* err;
+};
+
+// One product launch (and its stream-K fix-up) with configuration c.
+cudaError_t tc_launch(const TcOperands& o, const TcCfg& c, cudaStream_t st,
+                      const std::function<void(bool)>& mark, int withhold = 0) {
+  const int64_t Mout = o.trans ? o.n : o.m, K = o.trans ? o.m : o.n;
+  const int dpi = o.dp / c.ns;
   CUtensorMap mA, mB, mB2;
-  if (!make_map(&mA, A, (uint64_t)n, (uint64_t)m, (uint64_t)lda, 64, trans ? 64 : BM))
+  if (!make_map(&mA, o.A, (uint64_t)o.n, (uint64_t)o.m, (uint64_t)o.lda, 64, o.trans ? 64 : BM))
     return cudaErrorInvalidValue;
-  if (!make_map(&mB, Bt, (uint64_t)K, (uint64_t)dp, (uint64_t)ldb, 64, (uint32_t)dp))
+  if (!make_map(&mB, o.Bt, (uint64_t)K, (uint64_t)o.dp, (uint64_t)o.ldb, 64, (uint32_t)dpi))
     return cudaErrorInvalidValue;
-  if (b2) {
-    if (!make_map(&mB2, Btl, (uint64_t)K, (uint64_t)dp, (uint64_t)ldb, 64, (uint32_t)dp))
+  if (o.b2) {
+    if (!make_map(&mB2, o.Btl, (uint64_t)K, (uint64_t)o.dp, (uint64_t)o.ldb, 64, (uint32_t)dpi))
       return cudaErrorInvalidValue;
   } else {
     mB2 = mB;  // unused
@@ -904,25 +961,25 @@ cudaError_t tc_gemm(bool trans, const void* A, int64_t lda, int64_t m, int64_t n
   TcParams p{};
   p.Mout = Mout;
   p.K = K;
-  p.dp = dp;
-  p.out = out;
-  p.ldo = ldo;
-  p.frag = frag;
-  p.err = err;
-  p.T = ceil_div(Mout, BM);
+  p.dp = o.dp;
+  p.ns = c.ns;
+  p.dpi = dpi;
+  p.out = o.out;
+  p.ldo = o.ldo;
+  p.frag = o.frag;
+  p.err = o.err;
+  p.T = ceil_div(Mout, BM) * c.ns;
   p.KB = ceil_div(K, BK);
   int P = sm_count();  // never more CTAs than the fragment buffer has slots for
   if ((int64_t)p.T * p.KB < P) P = p.T * p.KB;
   p.full_waves = p.T / P;
   p.tail = p.T - p.full_waves * P;
   p.U = (int64_t)p.tail * p.KB;
-  const size_t stage_bytes = A_TILE_BYTES + (b2 ? 2 : 1) * (size_t)dp * BK * 2;
-  const int stages = tc_stages(stage_bytes);
-  if (stages < 2) return cudaErrorInvalidValue;
-  p.stages = stages;
-  const size_t smem = tc_smem(stages, stage_bytes);
-  auto kern = trans ? (b2 ? k_tc_gemm<true, true> : k_tc_gemm<true, false>)
-                    : (b2 ? k_tc_gemm<false, true> : k_tc_gemm<false, false>);
+  p.stages = c.stages;
+  p.withhold = withhold;
+  const size_t smem = tc_smem(c.stages, tc_stage_bytes(o.dp, c.ns, o.b2));
+  auto kern = o.trans ? (o.b2 ? k_tc_gemm<true, true> : k_tc_gemm<true, false>)
+                      : (o.b2 ? k_tc_gemm<false, true> : k_tc_gemm<false, false>);
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   if (mark) mark(true);
@@ -934,6 +991,111 @@ cudaError_t tc_gemm(bool trans, const void* A, int64_t lda, int64_t m, int64_t n
   e = launch_pdl(k_tc_fixup, dim3(p.tail, BM / 4), dim3(256), 0, st, p, P);
   count_launch();
   return e == cudaSuccess ? cudaGetLastError() : e;
+}
+
+}  // namespace
+
+int tune_file(const char* path) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune_path = path ? path : "";
+  if (g_tune_path.empty()) return 0;
+  FILE* f = fopen(g_tune_path.c_str(), "r");
+  if (!f) return 0;
+  int n = 0;
+  char tag[32];
+  long long k0, k1, k2, k3, k4;
+  int ns, stages;
+  double us;
+  while (fscanf(f, "%31s %lld %lld %lld %lld %lld %d %d %lf", tag, &k0, &k1, &k2, &k3, &k4, &ns,
+                &stages, &us) == 9) {
+    if (strcmp(tag, "tc_gemm") != 0 || !tc_ns_valid((int)k4, ns) || stages < 2 ||
+        tc_smem(stages, tc_stage_bytes((int)k4, ns, k1 != 0)) > 226 * 1024)
+      continue;
+    TcCfg c;
+    c.ns = ns;
+    c.stages = stages;
+    g_tune[{k0, k1, k2, k3, k4}] = c;
+    ++n;
+  }
+  fclose(f);
+  return n;
+}
+
+// Products of one shape run with the configuration measured fastest the
+// first time that shape is seen (outside stream capture): every valid
+// column split ns in {1, 2, 4} with the deepest ring that fits, each timed
+// twice with CUDA events on the stream (the better time counts); the chosen
+// configuration then computes the result, so repeated calls are bitwise
+// equal.  force_ns > 0 skips the tuner.
+cudaError_t tc_gemm(bool trans, const void* A, int64_t lda, int64_t m, int64_t n, const void* Bt,
+                    int64_t ldb, int dp, float* out, int64_t ldo, float* frag, int* err,
+                    cudaStream_t st, const std::function<void(bool)>& mark, const void* Btl,
+                    int force_ns, int withhold) {
+  if (dp < 16 || dp > 256 || dp % 16 != 0) return cudaErrorInvalidValue;
+  if (lda % 8 != 0 || ldb % 8 != 0 || ((uintptr_t)A & 15) || ((uintptr_t)Bt & 15) || ldo % 4 != 0 ||
+      ((uintptr_t)out & 15) || ((uintptr_t)Btl & 15))
+    return cudaErrorInvalidValue;
+  TcOperands o{trans, Btl != nullptr, A, Bt, Btl, lda, m, n, ldb, ldo, dp, out, frag, err};
+  auto cfg_of = [&](int ns) {
+    TcCfg c;
+    c.ns = ns;
+    c.stages = tc_stages(tc_stage_bytes(dp, ns, o.b2));
+    return c;
+  };
+  if (force_ns > 0) {
+    if (!tc_ns_valid(dp, force_ns)) return cudaErrorInvalidValue;
+    const TcCfg c = cfg_of(force_ns);
+    if (c.stages < 2) return cudaErrorInvalidValue;
+    return tc_launch(o, c, st, mark, withhold);
+  }
+  const int64_t Mout = trans ? n : m, K = trans ? m : n;
+  const std::array<int64_t, 5> key = {trans ? 1 : 0, o.b2 ? 1 : 0, Mout, K, dp};
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune.find(key);
+    if (it != g_tune.end()) return tc_launch(o, it->second, st, mark, withhold);
+  }
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone)
+    return tc_launch(o, cfg_of(1), st, mark);  // no timing inside a capture
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    if (e0) cudaEventDestroy(e0);
+    return tc_launch(o, cfg_of(1), st, mark);
+  }
+  TcCfg best = cfg_of(1);
+  float best_ms = 1e30f;
+  for (int ns : {1, 2, 4}) {
+    if (!tc_ns_valid(dp, ns)) continue;
+    const TcCfg c = cfg_of(ns);
+    if (c.stages < 2) continue;
+    float t = 1e30f;
+    for (int rep = 0; rep < 2; ++rep) {
+      cudaEventRecord(e0, st);
+      cudaError_t e = tc_launch(o, c, st, {});
+      cudaEventRecord(e1, st);
+      if (e != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        return e != cudaSuccess ? e : cudaErrorUnknown;
+      }
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      t = std::min(t, ms);
+    }
+    if (t < best_ms * 0.99f) {  // a larger split must win clearly
+      best_ms = t;
+      best = c;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune[key] = best;
+    tune_save_line(key, best, 1e3 * best_ms);
+  }
+  return tc_launch(o, best, st, mark, withhold);
 }
 
 bool btc_encode(void* maps4, const void* A, int64_t lda, int64_t m, int64_t n, const void* Bt,

@@ -480,7 +480,7 @@ ruqlp_status product(ruqlp_ctx* h, const Layout& Lo, const Job& J, bool trans, T
                      cudaEventRecord(b, st);
                      h->spans.push_back({trans ? PROF_TC_ATX : PROF_TC_AX, a, b});
                    }
-                 } : std::function<void(bool)>(), Btl));
+                 } : std::function<void(bool)>(), Btl, h->tc_nsplit, h->test_withhold));
     }
     return RUQLP_OK;
   }
@@ -802,6 +802,7 @@ void copy_options(const ruqlp_ctx* from, ruqlp_ctx* to) {
   to->bf16_simt = from->bf16_simt;
   to->orth_simt = from->orth_simt;
   to->orth_tsqr = from->orth_tsqr;
+  to->tc_nsplit = from->tc_nsplit;
 }
 
 ruqlp_status set_error(ruqlp_ctx* h, ruqlp_status s, const char* msg) {
@@ -1244,6 +1245,16 @@ ruqlp_status ruqlp_set_option(ruqlp_handle h, const char* name, int64_t value) {
     h->orth_tsqr = value ? 1 : 0;
     return RUQLP_OK;
   }
+  if (strcmp(name, "test_withhold_stage") == 0) {
+    h->test_withhold = value ? 1 : 0;
+    return RUQLP_OK;
+  }
+  if (strcmp(name, "tc_nsplit") == 0) {
+    if (value != 0 && value != 1 && value != 2 && value != 4)
+      return fail(h, RUQLP_ERR_INVALID, "tc_nsplit must be 0 (tuned), 1, 2 or 4");
+    h->tc_nsplit = (int)value;
+    return RUQLP_OK;
+  }
   if (strcmp(name, "profile") == 0) {
     h->profile = value != 0;
     for (int i = 0; i < kProfN; ++i) {
@@ -1426,6 +1437,8 @@ ruqlp_status ruqlp_omega(ruqlp_handle h, int64_t n, int d, uint64_t seed, double
 const char* ruqlp_last_error(ruqlp_handle h) { return h ? h->err.c_str() : "NULL handle"; }
 
 int64_t ruqlp_launch_count(void) { return launch_count(); }
+
+int ruqlp_tune_file(const char* path) { return tune_file(path); }
 
 ruqlp_status ruqlp_sketch(ruqlp_handle h, const ruqlp_matrix* A, int trans, const void* X,
                           int64_t ldx, int d, void* Y, int64_t ldy) {

@@ -86,6 +86,7 @@ _SIGS = {
     "ruqlp_omega": (c_int, [c_void_p, c_int64, c_int, ctypes.c_uint64, c_void_p]),
     "ruqlp_last_error": (c_char_p, [c_void_p]),
     "ruqlp_launch_count": (c_int64, []),
+    "ruqlp_tune_file": (c_int, [c_char_p]),
     "ruqlp_sketch": (c_int, [c_void_p, ctypes.POINTER(Matrix), c_int, c_void_p, c_int64, c_int,
                              c_void_p, c_int64]),
     "ruqlp_orth": (c_int, [c_void_p, c_void_p, c_int64, c_int, c_int64, c_int, c_void_p,
@@ -208,6 +209,10 @@ def ruqlp_gram_noalloc(Y, M, d, ldy, dtype, G, stream):
 
 def ruqlp_launch_count():
     return lib().ruqlp_launch_count()
+
+
+def ruqlp_tune_file(path):
+    return lib().ruqlp_tune_file(path.encode() if path else None)
 
 
 def ruqlp_profile(h, phase):

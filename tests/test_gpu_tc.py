@@ -196,3 +196,65 @@ def test_bf16_decompose_full_size_residual_vs_fp64_oracle(handle):
     ref = oracle.ruqlp(Ah, Om.cpu().numpy(), q)
     r0 = oracle.residual_fro(Ah, ref["Q"], ref["L"], ref["P"])
     assert r_gpu <= 1.05 * r0, (r_gpu, r0)
+
+
+# column split of the tensor-core products: each 128-row output tile as ns
+# items of dp / ns columns (dp / ns a multiple of 16); ragged m and K,
+# stream-K tails and the 20000-row workload shape included
+SPLIT_SHAPES = [(1000, 800, 32), (19459, 136, 224), (152 * 128 + 5, 96, 128), (300, 7000, 64),
+                (4096, 2048, 256), (20000, 2000, 224)]
+
+
+@pytest.mark.parametrize("ns", [1, 2, 4])
+@pytest.mark.parametrize("trans", [False, True], ids=["AX", "AtX"])
+@pytest.mark.parametrize("shape", SPLIT_SHAPES, ids=[f"{a}x{b}d{c}" for a, b, c in SPLIT_SHAPES])
+def test_tc_product_column_split_parity(handle, shape, trans, ns):
+    m, n, d = shape
+    if d % (16 * ns):
+        pytest.skip("dp / ns must be a multiple of 16")
+    rng = np.random.default_rng(m * 3 + n + d + ns)
+    A = _bf16(rng.standard_normal((m, n)))
+    K = m if trans else n
+    X = torch.from_numpy(rng.standard_normal((K, d))).float()
+    handle.set_option("tc_nsplit", ns)
+    try:
+        Y = handle.sketch(A.cuda(), X.cuda(), trans=trans).double().cpu().numpy()
+    finally:
+        handle.set_option("tc_nsplit", 0)
+    Ah = A.double().numpy()
+    Xh = X.to(torch.bfloat16).double().numpy()
+    ref = oracle.apply_At(Ah, Xh) if trans else oracle.apply_A(Ah, Xh)
+    mag = (np.abs(Ah).T if trans else np.abs(Ah)) @ np.abs(Xh)
+    err = np.abs(Y - ref)
+    assert np.all(err <= 4.0 * math.sqrt(K) * U32 * mag + 1e-30), float((err / (mag + 1e-300)).max())
+
+
+def test_tuner_file_and_determinism(handle, tmp_path):
+    """The product tuner: the first product of a new shape writes its choice
+    to the tune file (a valid split and ring depth); a BF16 decomposition of a
+    fresh shape is bitwise the same on its first (tuning) and second call;
+    reloading the file restores the entries."""
+    path = str(tmp_path / "tune.txt")
+    assert ruqlp.ruqlp_tune_file(path) == 0
+    try:
+        m, n, k, p, q = 6000, 4096, 56, 8, 1  # d = 64: splits 1, 2, 4 are all valid
+        A, _, _, _ = wl.dense_spectral(123, m, n, wl.spectrum_gap(n, k, 1e-2), noise_std=1e-6)
+        Om = torch.from_numpy(wl.omega(124, n, k + p)).cuda()
+        Ag = torch.from_numpy(A).to(torch.bfloat16).cuda()
+        a = handle.decompose(Ag, Om, k, p, q)
+        b = handle.decompose(Ag, Om, k, p, q)
+        for x, y in zip(a[:3], b[:3]):
+            assert torch.equal(x, y)
+        lines = [ln.split() for ln in open(path).read().splitlines() if ln.strip()]
+        assert lines, "no tuning entry written"
+        shapes = set()
+        for ln in lines:
+            assert ln[0] == "tc_gemm" and len(ln) == 9
+            trans, two, rows, K, dp, ns, stages = (int(v) for v in ln[1:8])
+            assert dp == 64 and ns in (1, 2, 4) and (dp // ns) % 16 == 0 and stages >= 2
+            shapes.add((trans, two, rows, K))
+        # A X (rows m, K n), A^T Y (rows n, K m) and the two-part B^T = A^T Q
+        assert {(0, 0, m, n), (1, 0, n, m), (1, 1, n, m)} <= shapes, shapes
+        assert ruqlp.ruqlp_tune_file(path) == len(lines)
+    finally:
+        ruqlp.ruqlp_tune_file(None)
