@@ -67,9 +67,8 @@ __device__ __forceinline__ void load_col(const float* __restrict__ T, int lane, 
 // inverse of the unit lower factor; lane c's copy of column c, scaled by
 // 1 / r_jj as pivot j is formed, is row c of S.  Reciprocal square roots
 // replace IEEE sqrt/divide (the factor only has to be consistent with the
-// solve that uses it).  A non-positive pivot is replaced by bad_fill.  The
-// return value (same in every lane) has bit 0 set if that happened and bit 1
-// if any pivot fell outside [1/2, 2] (a Gram that is not close to I).
+// solve that uses it).  A non-positive pivot is replaced by bad_fill; the
+// return value (same in every lane) reports whether that happened.
 __device__ __forceinline__ void load_row(const float* __restrict__ p, float (&r)[TB]) {
 #pragma unroll
   for (int q = 0; q < TB / 4; ++q) {
@@ -81,13 +80,13 @@ __device__ __forceinline__ void load_row(const float* __restrict__ p, float (&r)
   }
 }
 
-__device__ __noinline__ int factor_tile(float* __restrict__ B, float* __restrict__ Sout,
-                                        float* __restrict__ rb, int lane, float bad_fill) {
+__device__ __noinline__ bool factor_tile(float* __restrict__ B, float* __restrict__ Sout,
+                                         float* __restrict__ rb, int lane, float bad_fill) {
   float col[TB], ecol[TB];
   load_col(B, lane, col);
 #pragma unroll
   for (int i = 0; i < TB; ++i) ecol[i] = (i == lane) ? 1.f : 0.f;
-  bool bad = false, far = false;
+  bool bad = false;
 #pragma unroll
   for (int k = 0; k < TB; ++k) {
     __syncwarp();
@@ -98,7 +97,6 @@ __device__ __noinline__ int factor_tile(float* __restrict__ B, float* __restrict
     load_row(rb, row);
     const bool nonpos = !(piv > 0.f) || !(piv < 3.0e38f);
     bad = bad || nonpos;
-    far = far || !(piv >= 0.5f && piv <= 2.0f);
     piv = nonpos ? bad_fill : piv;
     const float rinv = rsqrtf(piv);
     const float rkc = ((lane == k) ? piv : col[k]) * rinv;  // r_kc for c >= k
@@ -123,7 +121,7 @@ __device__ __noinline__ int factor_tile(float* __restrict__ B, float* __restrict
     Sout[lane * TP + r] = (r >= lane) ? ecol[r] : 0.f;
   }
   __syncwarp();
-  return (bad ? 1 : 0) | (far ? 2 : 0);
+  return !bad;
 }
 
 // Blocked Cholesky G (+ shift I) = R^T R, d <= 288, one CTA of NT threads
@@ -288,12 +286,11 @@ __device__ __forceinline__ void chol_body(const float* __restrict__ G, int d, do
           __syncthreads();
         }
         if (warp == 0) {
-          const int fr = factor_tile(tile(K + 1, K + 1), dinv_sm, s_row, lane, fill);
-          if (lane == 0 && (fr & 1)) {
+          const bool ok = factor_tile(tile(K + 1, K + 1), dinv_sm, s_row, lane, fill);
+          if (lane == 0 && !ok) {
             if (attempt == 0) s_bad = 1;  // retry on G + shift I
             else s_rankdef = 1;           // pivots replaced by the shift
           }
-          if (lane == 0 && (fr & 2) && check && attempt == 0) s_far = 1;
         } else if (K >= 0 && (warp & 3) != 0) {
           const int nw3 = nw - nw / 4, w3 = warp - warp / 4 - 1;  // 0 .. nw3 - 1
           for (int u = 2 + w3; u < rem * (rem + 1); u += nw3) update(K, rem, u);
@@ -302,6 +299,17 @@ __device__ __forceinline__ void chol_body(const float* __restrict__ G, int d, do
       __syncthreads();
     }
     if (!s_bad) break;
+  }
+  __syncthreads();
+  if (check && warp == 0) {
+    // the last pass of a CholeskyQR: its Gram should be close to I, so every
+    // pivot r_ii^2 lies in [1/2, 2] and no retry with the shift was needed
+    bool far = attempt > 0 && !force_shift;
+    for (int i = lane; i < d; i += 32) {
+      const float r = tile(i / TB, i / TB)[(i % TB) * (TP + 1)];
+      far = far || !(r * r >= 0.5f && r * r <= 2.0f);
+    }
+    if (__any_sync(0xffffffffu, far) && lane == 0) s_far = 1;
   }
   __syncthreads();
   // write the R tiles (32 x 32 row-major each; the inverses are out already)
