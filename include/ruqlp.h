@@ -345,8 +345,9 @@ ruqlp_status ruqlp_gram(ruqlp_handle h, const void* Y, int64_t M, int d, int64_t
  * allocates nothing: the FP64 partial sums live in one fixed 4 MiB device
  * array that every GPU loading the library keeps until the process exits, so
  * d is limited to 256 (larger d returns RUQLP_ERR_BUDGET).  The first call
- * on each device looks up that array's device address (cudaGetSymbolAddress);
- * make that first call before any stream capture.  All calls share the one
+ * on each device looks up that array's device address (cudaGetSymbolAddress),
+ * and so does the first call after that device's context has changed (a
+ * cudaDeviceReset); make those first calls before any stream capture.  All calls share the one
  * array: calls whose work overlaps on the GPU (other streams, other host
  * threads) race and give wrong results -- order them on one stream.  Each
  * call overwrites what it uses, so no clearing is needed between calls.

@@ -8,6 +8,9 @@
 // ruqlp_gram_noalloc computes the same G = Y^T Y as ruqlp_gram with the same
 // split-K kernel, but its FP64 partial sums live in a fixed device array
 // compiled into the library instead of a handle's workspace arena.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include <mutex>
 
 #include "../../include/ruqlp.h"
@@ -25,19 +28,45 @@ static __device__ __align__(256) double g_gram_scratch[kScratchDoubles];
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
 double* g_scratch_addr[kMaxDevices] = {};
+CUcontext g_scratch_ctx[kMaxDevices] = {};
+
+// The calling thread's current CUDA context (driver entry point, looked up
+// once); nullptr when it cannot be read.
+CUcontext current_context() {
+  static PFN_cuCtxGetCurrent_v4000 fn = nullptr;
+  static bool looked = false;
+  if (!looked) {
+    void* ptr = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &ptr, 4000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (PFN_cuCtxGetCurrent_v4000)ptr;
+    looked = true;
+  }
+  CUcontext c = nullptr;
+  if (fn == nullptr || fn(&c) != CUDA_SUCCESS) return nullptr;
+  return c;
+}
 
 // Device address of the scratch array on the calling thread's current device,
-// looked up once per device (with that device current) and cached.  In host
-// code the name g_gram_scratch is only a host-side stand-in, so kernels must be
-// given this address instead.
+// looked up with that device current the first time it is used there, and
+// again whenever the device's context has changed since (a cudaDeviceReset
+// tears the context down and reloads the module, which can move the array).
+// In host code the name g_gram_scratch is only a host-side stand-in, so
+// kernels must be given this address instead.
 ruqlp_status scratch_address(double** out) {
   int dev = -1;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return RUQLP_ERR_CUDA;
+  // (before the runtime has made a context current there is none: then the
+  // lookup below creates it and the next call records it)
+  const CUcontext ctx = current_context();
   std::lock_guard<std::mutex> lock(g_mu);
-  if (!g_scratch_addr[dev]) {
+  if (!g_scratch_addr[dev] || ctx == nullptr || ctx != g_scratch_ctx[dev]) {
     void* p = nullptr;
     if (cudaGetSymbolAddress(&p, g_gram_scratch) != cudaSuccess || !p) return RUQLP_ERR_CUDA;
     g_scratch_addr[dev] = static_cast<double*>(p);
+    g_scratch_ctx[dev] = ctx;
   }
   *out = g_scratch_addr[dev];
   return RUQLP_OK;

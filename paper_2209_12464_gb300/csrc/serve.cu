@@ -12,6 +12,10 @@
 //      up to `max_batch` items); any other request runs alone; a launch is
 //      admitted only while the arenas of all slots fit the budget;
 //   3. sleeps until a submit arrives or ~20 us pass while work is in flight.
+// The handle's mutex guards only the queue and the request table: the loop
+// takes it to pick and pop requests and to publish results, and does its
+// CUDA work (launches, completion handling, freeing idle arenas) without it,
+// so ruqlp_submit / ruqlp_poll never wait behind a launch or a cudaFree.
 // Requests that arrive while others run are admitted into the next idle
 // slot, so their work overlaps on the device.  Because each item of a batch
 // gets bitwise the result it gets alone, a request's result does not depend
@@ -44,12 +48,16 @@ struct Request {
   double t_submit = 0, t_start = 0, t_done = 0;
 };
 
+// Owned by the scheduler thread; the request data a launch needs is copied
+// in (the request table may rehash while the slot runs).
 struct Slot {
   ruqlp_ctx* ctx = nullptr;
   cudaStream_t stream = nullptr;
   cudaEvent_t ev = nullptr;
   bool busy = false, batch = false;
   std::vector<uint64_t> ids;
+  std::vector<ruqlp_matrix> A;
+  std::vector<ruqlp_params> prm;
   std::vector<ruqlp_outputs> outs;
   BatchRun run;
 };
@@ -131,92 +139,117 @@ void finish_req(Server& S, uint64_t id, ruqlp_status st, uint32_t flags, const s
   r.state = 2;
 }
 
-// 1. completions
+// A finished request's result, published under the mutex.
+struct Done {
+  uint64_t id;
+  ruqlp_status st;
+  uint32_t flags;
+  std::string err;
+  double t;
+};
+
+void publish(Server& S, std::vector<Done>& done) {
+  if (done.empty()) return;
+  std::lock_guard<std::mutex> g(S.mu);
+  for (const Done& d : done) finish_req(S, d.id, d.st, d.flags, d.err, d.t);
+  done.clear();
+}
+
+// 1. completions (no lock held: batch_end / single_end synchronise and may
+// rerun a flagged item)
 bool retire(Server& S) {
-  bool any = false;
+  std::vector<Done> done;
   for (auto& s : S.slots) {
     if (!s.busy) continue;
     const cudaError_t q = cudaEventQuery(s.ev);
     if (q == cudaErrorNotReady) continue;
-    any = true;
-    const double t = S.now();
     s.ctx->err.clear();
     if (s.batch) {
       const ruqlp_status st = batch_end(s.ctx, s.run, s.outs.data());
+      const double t = S.now();
       for (size_t i = 0; i < s.ids.size(); ++i)
-        finish_req(S, s.ids[i], st, s.outs[i].flags, s.ctx->err, t);
+        done.push_back({s.ids[i], st, s.outs[i].flags, s.ctx->err, t});
     } else {
-      Request& r = S.reqs[s.ids[0]];
-      const ruqlp_status st = single_end(s.ctx, &r.oc);
-      finish_req(S, s.ids[0], st, r.oc.flags, s.ctx->err, t);
+      const ruqlp_status st = single_end(s.ctx, &s.outs[0]);
+      done.push_back({s.ids[0], st, s.outs[0].flags, s.ctx->err, S.now()});
     }
     s.busy = false;
     s.ids.clear();
   }
+  const bool any = !done.empty();
+  publish(S, done);
   return any;
 }
 
-// 2. admissions
+// 2. admissions: pick under the mutex, launch without it
 bool admit(Server& S) {
   bool any = false;
-  while (!S.queue.empty()) {
+  for (;;) {
     int k = -1;
     for (int i = 0; i < (int)S.slots.size(); ++i)
       if (!S.slots[i].busy) { k = i; break; }
     if (k < 0) break;
     Slot& s = S.slots[k];
-    const uint64_t head = S.queue.front();
-    Request& r0 = S.reqs[head];
     std::vector<uint64_t> take;
     size_t need = 0;
-    if (r0.batch) {
-      for (size_t j = 0; j < S.queue.size() && (int)take.size() < S.max_batch; ++j) {
-        Request& r = S.reqs[S.queue[j]];
-        if (!r.batch || r.prm.compute != r0.prm.compute || r.prm.q != r0.prm.q) break;
-        if (!take.empty() && !fits(S, k, need + r.bytes)) break;
-        take.push_back(S.queue[j]);
-        need += r.bytes;
+    bool batch = false;
+    {
+      std::lock_guard<std::mutex> g(S.mu);
+      if (S.queue.empty()) break;
+      const Request& r0 = S.reqs[S.queue.front()];
+      batch = r0.batch;
+      if (batch) {
+        for (size_t j = 0; j < S.queue.size() && (int)take.size() < S.max_batch; ++j) {
+          const Request& r = S.reqs[S.queue[j]];
+          if (!r.batch || r.prm.compute != r0.prm.compute || r.prm.q != r0.prm.q) break;
+          if (!take.empty() && !fits(S, k, need + r.bytes)) break;
+          take.push_back(S.queue[j]);
+          need += r.bytes;
+        }
+        need += 65536;
+      } else {
+        take.push_back(S.queue.front());
+        need = r0.bytes;
       }
-      need += 65536;
-    } else {
-      take.push_back(head);
-      need = r0.bytes;
     }
     if (!fits(S, k, need)) {
-      trim_idle(S, k);
+      trim_idle(S, k);  // cudaFree outside the mutex
       if (!fits(S, k, need)) break;  // wait for running work to free memory
     }
-    for (size_t j = 0; j < take.size(); ++j) S.queue.pop_front();
+    // only this thread pops, so the picked requests are still at the front
     const double t = S.now();
-    copy_options(S.h, s.ctx);
-    s.ctx->err.clear();
-    s.ids = take;
-    s.batch = r0.batch;
-    ruqlp_status st;
-    if (s.batch) {
-      std::vector<ruqlp_matrix> A(take.size());
-      std::vector<ruqlp_params> P(take.size());
-      s.outs.resize(take.size());
+    s.A.resize(take.size());
+    s.prm.resize(take.size());
+    s.outs.resize(take.size());
+    {
+      std::lock_guard<std::mutex> g(S.mu);
       for (size_t j = 0; j < take.size(); ++j) {
+        S.queue.pop_front();
         Request& r = S.reqs[take[j]];
-        A[j] = r.A;
-        P[j] = r.prm;
+        s.A[j] = r.A;
+        s.prm[j] = r.prm;
         s.outs[j] = r.oc;
         r.state = 1;
         r.t_start = t;
       }
-      st = batch_begin(s.ctx, (int)take.size(), A.data(), P.data(), s.outs.data(), false, &s.run);
-    } else {
-      Request& r = S.reqs[head];
-      r.state = 1;
-      r.t_start = t;
-      st = single_begin(s.ctx, &r.A, &r.prm, &r.oc);
     }
+    copy_options(S.h, s.ctx);
+    s.ctx->err.clear();
+    s.ids = take;
+    s.batch = batch;
+    ruqlp_status st;
+    if (batch)
+      st = batch_begin(s.ctx, (int)take.size(), s.A.data(), s.prm.data(), s.outs.data(), false,
+                       &s.run);
+    else
+      st = single_begin(s.ctx, &s.A[0], &s.prm[0], &s.outs[0]);
     if (st == RUQLP_OK && cudaEventRecord(s.ev, s.stream) != cudaSuccess) st = RUQLP_ERR_CUDA;
     if (st != RUQLP_OK) {
       // the launch failed as a whole: wait for whatever was queued, report
       cudaStreamSynchronize(s.stream);
-      for (uint64_t id : take) finish_req(S, id, st, 0, s.ctx->err, S.now());
+      std::vector<Done> done;
+      for (uint64_t id : take) done.push_back({id, st, 0u, s.ctx->err, S.now()});
+      publish(S, done);
       s.ids.clear();
     } else {
       s.busy = true;
@@ -228,12 +261,12 @@ bool admit(Server& S) {
 
 void loop(Server* S) {
   cudaSetDevice(S->h->device);
-  std::unique_lock<std::mutex> lk(S->mu);
   for (;;) {
     const bool r = retire(*S);
     const bool a = admit(*S);
     bool busy = false;
     for (auto& s : S->slots) busy = busy || s.busy;
+    std::unique_lock<std::mutex> lk(S->mu);
     if (S->stop && !busy && S->queue.empty()) break;
     if (r || a) continue;
     if (busy) S->cv.wait_for(lk, std::chrono::microseconds(20));

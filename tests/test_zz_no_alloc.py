@@ -29,9 +29,12 @@ def test_gram_noalloc_matches_gram_entry_two_calls(ruqlp):
     h = ruqlp.Handle(0, stream)
     try:
         rng = np.random.default_rng(2026)
-        # two calls in a row through the shared scratch: a large one that fills
-        # many partial slabs, then a smaller one that reuses stale contents
-        for M, d, dt in [(20011, 220, torch.float32), (5003, 64, torch.float64)]:
+        # calls in a row through the shared scratch: a large one that fills
+        # many partial slabs, a smaller one that reuses stale contents, and
+        # d = 256 with enough rows that the slab count is clamped to the 8
+        # that fill the 4 MiB scratch exactly (8 x 256^2 doubles)
+        for M, d, dt in [(20011, 220, torch.float32), (5003, 64, torch.float64),
+                         (40000, 256, torch.float32)]:
             Y = torch.from_numpy(rng.standard_normal((M, d))).to(dt).cuda()
             G_ref = h.gram(Y)
             G = torch.full((d, d), float("nan"), dtype=torch.float64, device="cuda")
