@@ -785,15 +785,15 @@ __global__ void __launch_bounds__(256) k_gram_tc_reduce(const float* __restrict_
   const int64_t slab = (int64_t)nbr * dp * 32, src = ((int64_t)g * dp + col) * 32 + lane;
   float s = 0.f, c = 0.f;
   int z = w;
-  // sixteen slab loads in flight per lane, then added in slab order
-  for (; z < P; z += 8 * 16) {
-    float v[16];
-#pragma unroll
-    for (int u = 0; u < 16; ++u) v[u] = (z + 8 * u < P) ? part[(z + 8 * u) * slab + src] : 0.f;
-#pragma unroll
-    for (int u = 0; u < 16; ++u)
-      if (z + 8 * u < P) two_sum_acc(s, c, v[u]);
+  for (; z + 8 * 3 < P; z += 8 * 4) {
+    const float a = part[z * slab + src], b = part[(z + 8) * slab + src];
+    const float x = part[(z + 16) * slab + src], e = part[(z + 24) * slab + src];
+    two_sum_acc(s, c, a);
+    two_sum_acc(s, c, b);
+    two_sum_acc(s, c, x);
+    two_sum_acc(s, c, e);
   }
+  for (; z < P; z += 8) two_sum_acc(s, c, part[z * slab + src]);
   ws[w][lane] = s;
   wc[w][lane] = c;
   __syncthreads();
