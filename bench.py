@@ -67,6 +67,9 @@ def parse():
                     help="seconds of arrivals (serve workload)")
     ap.add_argument("--rate", type=float, default=2000.0, help="arrivals per second (serve)")
     ap.add_argument("--count", type=int, default=512, help="batch size (batch workload)")
+    ap.add_argument("--tune-file", default="",
+                    help="product tuner cache (ruqlp_tune_file): read at start, measured "
+                         "choices appended; pins the tuner's choices for a profiled rerun")
     ap.add_argument("--gen", default="haar", choices=["haar", "fast"],
                     help="haar: the workload's Haar U, V (torch.linalg.qr); fast: Gaussian "
                          "low-rank stand-in for profiling tools that cannot load torch.linalg")
@@ -887,6 +890,8 @@ def main():
     import __graft_entry__ as g
     g.build()
     from paper_2209_12464_gb300 import ruqlp
+    if args.tune_file:
+        ruqlp.ruqlp_tune_file(args.tune_file)
     if args.workload in ("batch", "serve", "csr", "csrlr", "orth"):
         fn = {"batch": run_batch, "serve": run_serve, "csr": run_csr,
               "csrlr": run_csr, "orth": run_orth}[args.workload]
