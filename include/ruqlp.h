@@ -196,6 +196,10 @@ ruqlp_status ruqlp_set_stream(ruqlp_handle h, void* cuda_stream);
  *   and Q = Y R^{-1} on the CUDA cores (FP32 Gram tiles, blocked triangular
  *   solve); 0 (default) = on the tensor cores (three-way BF16 split of the
  *   FP32 operands, FP32 accumulation: FP32-level results).
+ *   "batch_orth_tc": 1 = in ruqlp_decompose_batch, BF16 items with
+ *   k + p <= 80 run their CholeskyQR passes (Grams, Q = Y R^{-1}) on the
+ *   tensor cores, as tall single matrices do (ignored with "orth_simt" or
+ *   "bf16_simt" = 1); 0 (default) = on the CUDA cores.
  *   "profile": 1 = bracket every phase with CUDA events on the handle's
  *   stream and accumulate their durations (read with ruqlp_profile); setting
  *   it (to 0 or 1) also zeroes the accumulators.
@@ -249,9 +253,13 @@ ruqlp_status ruqlp_decompose(ruqlp_handle h, const ruqlp_matrix* A,
  * triangular solves) is one launch over all items; the launch sequence is
  * captured in a CUDA graph the second time a batch signature (shapes, q,
  * dtype) is seen and replayed afterwards (option "batch_graph" = 0 turns
- * this off).  BF16 products run on the CUDA cores here.  An FP32 item gives
- * bitwise the result of ruqlp_decompose on it (for BF16: with option
- * "bf16_simt" = 1).  Returns after completion; out[i].flags per item.
+ * this off).  BF16 items whose rows start on 16-byte boundaries take their
+ * products on the tensor cores (option "bf16_simt" = 1: the CUDA cores);
+ * option "batch_orth_tc" moves the CholeskyQR passes of narrow BF16 items
+ * there too.  Every item gives bitwise
+ * its result in a batch of one; an FP32 item also bitwise the result of
+ * ruqlp_decompose on it (for BF16: with option "bf16_simt" = 1).  Returns
+ * after completion; out[i].flags per item.
  * Errors: INVALID (with the failing item's index in ruqlp_last_error),
  * BUDGET, CUDA. */
 ruqlp_status ruqlp_decompose_batch(ruqlp_handle h, int count, const ruqlp_matrix* A,

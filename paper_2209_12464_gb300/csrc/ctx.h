@@ -30,6 +30,7 @@ struct ruqlp_ctx {
                         // intermediate ones take two)
   int bf16_simt = 0;    // 1: BF16 products on CUDA cores instead of tensor cores
   int orth_simt = 0;    // 1: orth() Grams and Q = Y R^{-1} on CUDA cores
+  int batch_orth_tc = 0;  // 1: batched BF16 items with dp <= 80 take the tensor-core passes
   int orth_tsqr = 0;    // 1: every orth() is a Householder TSQR
   int tc_nsplit = 0;    // tensor-core products: column split (0 = tuned per shape)
   int test_withhold = 0;  // test hook: the next tensor-core products run out a wait

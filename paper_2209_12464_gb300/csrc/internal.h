@@ -160,7 +160,11 @@ struct BMat {
   void* Bt;        // dp x ldbt BF16 (tensor-core items): the transposed skinny operand
   void* Btl;       // its low BF16 part (same layout), for the two-part B^T = A^T Q
   int64_t ldbt;
-  int use_tc, pad2;
+  // orth_tc: this item's CholeskyQR runs on the tensor cores (bgram_tc,
+  // btrinv, bqmul_tc); St then holds the three BF16 parts of (R^{-1})^T,
+  // 3 x dp x 128
+  void* St;
+  int use_tc, orth_tc;
   void* Qout;
   void* Lout;
   void* Pout;
@@ -186,8 +190,36 @@ int bgemm_tiles(int64_t rows, int d);
 cudaError_t bgemm(bool trans, Ty ta, Ty tb, const BMat* T, const int* prefix, int total, int count,
                   int src, int dst, cudaStream_t st, bool split2 = false);
 int bgram_tiles(int64_t M, int d, bool sym, int max_slabs);
+// Batched CholeskyQR passes on the tensor cores (k_borth.cu, k_qmul.cu) for
+// items with orth_tc (dp <= BO_DPMAX).  Work comes as units (a row range of
+// one item); CTA c of a launch takes units uoff[c] .. uoff[c + 1] - 1, the
+// host having balanced their rows over the CTAs.
+//  * bgram_tc: one unit = one row slab of gram_slabs(); its FP32 sum of the
+//    three-way BF16 split products (tcgen05) goes to the item's partial[slab]
+//    as FP64, lower triangle (row j >= column i); bgram_reduce then adds the
+//    slabs in order into G and Gf;
+//  * btrinv: St = parts of (R^{-1})^T from the Cholesky's tiles (d <= 128);
+//  * bqmul_tc: buf[dst] = buf[src] R^{-1} over the units' rows (the same
+//    six-part-product rule as qmul_tc); make_bt as btrsm's.
+constexpr int BO_DPMAX = 80;
+struct BoUnit {
+  int item, rows;  // table index; rows of the unit
+  int64_t row0;    // first row
+};
+constexpr int BO_KP = 128;  // K padding of the St parts
+constexpr int BO_MAXU = 64;  // units a CTA of bgram_tc / bqmul_tc takes at most
+size_t bo_st_bytes(int d);
+cudaError_t bgram_tc(const BMat* T, const BoUnit* units, const int* uoff, int grid, int src,
+                     int max_slabs, int* err, cudaStream_t st);
+cudaError_t btrinv(const BMat* T, const int* list, int n, int dmax, cudaStream_t st);
+cudaError_t bqmul_tc(const BMat* T, const BoUnit* units, const int* uoff, int grid, int src,
+                     int dst, int make_bt, int* err, cudaStream_t st);
+// reduce = false: only the CUDA-core tiles (bgram_reduce adds the slabs
+// later, e.g. together with bgram_tc's)
 cudaError_t bgram(const BMat* T, const int* prefix, int total, int count, int src, int src2,
-                  int max_slabs, int dmax, cudaStream_t st);
+                  int max_slabs, int dmax, cudaStream_t st, bool reduce = true);
+cudaError_t bgram_reduce(const BMat* T, int count, int src, int src2, int max_slabs, int dmax,
+                         cudaStream_t st);
 int btrsm_blocks(int64_t M);
 cudaError_t bchol(const BMat* T, int count, double shift_rel, bool force_shift, int dmax,
                   cudaStream_t st, bool check = false);

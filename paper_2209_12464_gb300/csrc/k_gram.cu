@@ -294,7 +294,10 @@ __global__ void k_bgram_reduce(const BMat* __restrict__ Tb, int src, int src2, i
   int64_t slab;
   const int slabs = (int)gram_slabs(M, max_slabs, &slab);
   const int i = (int)(idx / d), j = (int)(idx % d);
-  const int64_t so = (sym && j < i) ? ((int64_t)j * d + i) : idx;
+  // symmetric partials hold one triangle: the upper one from the CUDA-core
+  // tiles, the lower one from the tensor-core kernel (orth_tc items)
+  const bool mirror = sym && (b.orth_tc ? j > i : j < i);
+  const int64_t so = mirror ? ((int64_t)j * d + i) : idx;
   const double s = slab_sum(b.partial, slabs, (int64_t)d * d, so);
   b.G[idx] = s;
   b.Gf[idx] = (float)s;
@@ -310,17 +313,22 @@ int bgram_tiles(int64_t M, int d, bool sym, int max_slabs) {
   return (sym ? nb * (nb + 1) / 2 : nb * nb) * slabs;
 }
 
-cudaError_t bgram(const BMat* T, const int* prefix, int total, int count, int src, int src2,
-                  int max_slabs, int dmax, cudaStream_t st) {
-  if (total <= 0) return cudaSuccess;
-  k_bgram<<<total, NT, 0, st>>>(T, prefix, count, src, src2, max_slabs);
-  count_launch();
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
+cudaError_t bgram_reduce(const BMat* T, int count, int src, int src2, int max_slabs, int dmax,
+                         cudaStream_t st) {
   k_bgram_reduce<<<dim3(ceil_div((int64_t)dmax * dmax, 256), count), 256, 0, st>>>(T, src, src2,
                                                                                  max_slabs);
   count_launch();
   return cudaGetLastError();
+}
+
+cudaError_t bgram(const BMat* T, const int* prefix, int total, int count, int src, int src2,
+                  int max_slabs, int dmax, cudaStream_t st, bool reduce) {
+  if (total <= 0) return cudaSuccess;
+  k_bgram<<<total, NT, 0, st>>>(T, prefix, count, src, src2, max_slabs);
+  count_launch();
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess || !reduce) return e;
+  return bgram_reduce(T, count, src, src2, max_slabs, dmax, st);
 }
 
 cudaError_t gram_f32(const float* X, int64_t ldx, const float* W, int64_t ldw, int64_t M, int d1,

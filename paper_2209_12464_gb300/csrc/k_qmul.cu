@@ -34,6 +34,7 @@ namespace {
 constexpr int TB = 32;   // tile edge of the Cholesky's blocking
 constexpr int TP = 36;   // shared-memory row pitch (16-byte aligned rows)
 constexpr int KP = 256;  // padded K of the S^T parts
+constexpr int KPB = BO_KP;  // the same for batched items (d <= 128)
 constexpr size_t TILE_F = (size_t)TB * TP;
 
 __device__ __forceinline__ int bidx(int I, int J, int nb) { return I * nb - (I * (I - 1)) / 2 + (J - I); }
@@ -100,17 +101,16 @@ __device__ __forceinline__ void fetch_tile(float* dst, const float* src, int t, 
 
 constexpr int TI_THREADS = 512;
 
-// grid = nb CTAs (block column J = blockIdx.x).  tiles: the Cholesky's R
-// tiles (packed upper block triangle, 32 x 32 row-major each) followed by
-// the nb diagonal-tile inverses.  Writes rows n = 32 J .. of St[3][dp][KP].
-// Every tile the column needs (R_IK for I < K <= J, S_KK for K <= J) is
-// loaded at once; acc_I is accumulated in the slot of S_IJ and turned into
+// Block column J of S = R^{-1}.  tiles: the Cholesky's R tiles (packed
+// upper block triangle, 32 x 32 row-major each) followed by the nb
+// diagonal-tile inverses.  Writes rows n = 32 J .. of St[3][dp][KPX] (K padded
+// to KPX).  Every tile the column needs (R_IK for I < K <= J, S_KK for K <= J)
+// is loaded at once; acc_I is accumulated in the slot of S_IJ and turned into
 // S_IJ in place.
-__global__ void __launch_bounds__(TI_THREADS)
-k_trinv(const float* __restrict__ tiles, int d, int dp, __nv_bfloat16* __restrict__ St) {
-  extern __shared__ __align__(16) float sm[];
+template <int KPX>
+__device__ __forceinline__ void trinv_body(const float* __restrict__ tiles, int d, int dp, int J,
+                                           __nv_bfloat16* __restrict__ St, float* sm) {
   const int nb = (d + TB - 1) / TB, ntiles = nb * (nb + 1) / 2;
-  const int J = blockIdx.x;
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5, nw = TI_THREADS / 32;
   const int rg = lane >> 2, cg = lane & 3;
   pdl_launch();
@@ -187,8 +187,8 @@ k_trinv(const float* __restrict__ tiles, int d, int dp, __nv_bfloat16* __restric
   }
   // St[p][n][k] = part p of S[k][n], n = 32 J + c: lane = k within a
   // 32-row block, so a warp writes 64 contiguous bytes per row n
-  for (int e = warp; e < TB * (KP / TB); e += nw) {
-    const int c = e / (KP / TB), kb = e % (KP / TB);
+  for (int e = warp; e < TB * (KPX / TB); e += nw) {
+    const int c = e / (KPX / TB), kb = e % (KPX / TB);
     const int n = J * TB + c, k = kb * TB + lane;
     if (n >= dp) continue;
     float v = 0.f;
@@ -197,11 +197,28 @@ k_trinv(const float* __restrict__ tiles, int d, int dp, __nv_bfloat16* __restric
     const float r1 = v - __bfloat162float(h);
     const __nv_bfloat16 m = __float2bfloat16_rn(r1);
     const __nv_bfloat16 l = __float2bfloat16_rn(r1 - __bfloat162float(m));
-    const size_t o = (size_t)n * KP + k;
+    const size_t o = (size_t)n * KPX + k;
     St[o] = h;
-    St[(size_t)dp * KP + o] = m;
-    St[2 * (size_t)dp * KP + o] = l;
+    St[(size_t)dp * KPX + o] = m;
+    St[2 * (size_t)dp * KPX + o] = l;
   }
+}
+
+// grid = nb CTAs (block column J = blockIdx.x), S^T parts K-padded to 256.
+__global__ void __launch_bounds__(TI_THREADS)
+k_trinv(const float* __restrict__ tiles, int d, int dp, __nv_bfloat16* __restrict__ St) {
+  extern __shared__ __align__(16) float sm[];
+  trinv_body<KP>(tiles, d, dp, blockIdx.x, St, sm);
+}
+
+// Batched: grid (block columns, items); item list[blockIdx.y] of the table,
+// S^T parts K-padded to 128 in its St buffer.
+__global__ void __launch_bounds__(TI_THREADS)
+k_btrinv(const BMat* __restrict__ T, const int* __restrict__ list) {
+  extern __shared__ __align__(16) float sm[];
+  const BMat& b = T[list[blockIdx.y]];
+  if ((int)blockIdx.x >= (b.d + TB - 1) / TB) return;  // block-uniform
+  trinv_body<KPB>(b.tiles, b.d, b.dp, blockIdx.x, (__nv_bfloat16*)b.St, sm);
 }
 
 constexpr int QM_CONV = 8;                      // converter / epilogue warps
@@ -597,6 +614,24 @@ cudaError_t qmul_tc(const float* Y, int64_t ldy, const float* tiles, int64_t M, 
   e = launch_pdl(k_qmul_tc, dim3(P), dim3(QM_THREADS), QM_SMEM, st, map, p);
   count_launch();
   return e == cudaSuccess ? cudaGetLastError() : e;
+}
+
+size_t bo_st_bytes(int d) {
+  const int dp = (d + 15) / 16 * 16;
+  return (size_t)3 * dp * KPB * sizeof(__nv_bfloat16);
+}
+
+cudaError_t btrinv(const BMat* T, const int* list, int n, int dmax, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  if (dmax > KPB) return cudaErrorInvalidValue;
+  const int nb = (dmax + TB - 1) / TB;
+  const size_t smem = (size_t)(nb + nb * (nb - 1) / 2 + nb + 4) * TILE_F * sizeof(float);
+  cudaError_t e =
+      cudaFuncSetAttribute(k_btrinv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k_btrinv<<<dim3(nb, n), TI_THREADS, smem, st>>>(T, list);
+  count_launch();
+  return cudaGetLastError();
 }
 
 }  // namespace ruqlp

@@ -801,6 +801,7 @@ void copy_options(const ruqlp_ctx* from, ruqlp_ctx* to) {
   to->orth_full = from->orth_full;
   to->bf16_simt = from->bf16_simt;
   to->orth_simt = from->orth_simt;
+  to->batch_orth_tc = from->batch_orth_tc;
   to->orth_tsqr = from->orth_tsqr;
   to->tc_nsplit = from->tc_nsplit;
 }
@@ -830,9 +831,19 @@ struct BatchPlan {
   std::vector<BMat> table;
   std::vector<int> prefix[7];  // NN, TN, gramY, gramN, gramPZ, trsmY, trsmN (CUDA-core tiles)
   std::vector<BTcTile> tc_nn, tc_tn;  // tensor-core tile lists
+  // tensor-core CholeskyQR items (orth_tc): their list (for k_btrinv) and,
+  // over Y (m rows) and over Z (n rows), the Gram units (one row slab each)
+  // and the Q = Y R^{-1} units with their per-CTA ranges
+  struct BoPlan {
+    std::vector<BoUnit> gu, qu;
+    std::vector<int> goff, qoff;
+    size_t o_gu, o_goff, o_qu, o_qoff;
+  } bo[2];
+  std::vector<int> bo_items;
+  size_t off_bo_items;
   size_t off_meta, off_table, off_prefix[7], off_tc_nn, off_tc_tn, off_maps, meta_end;
   size_t off_status, off_err, total;
-  int dmax, dpmax_tc;
+  int dmax, dpmax_tc, dmax_otc;
   int64_t max_omega, max_out;
 };
 
@@ -852,16 +863,28 @@ ruqlp_status batch_launches(ruqlp_ctx* h, const BatchPlan& bp, int count, int q,
   CK(cudaMemsetAsync(base + bp.off_status, 0, bp.total - bp.off_status, st));
   // make_bt: the last solve also writes the BF16 transposed operand of the
   // next tensor-core product (so that product needs no transpose launch)
+  // (items with orth_tc take the tensor-core Gram and Q = Y R^{-1}, the
+  // others the CUDA-core kernels; both share the Cholesky launch)
   auto orth_b = [&](int src, int dst, int passes, int make_bt) -> ruqlp_status {
     ProfScope sp(ph, PROF_ORTH);
-    const int gp = (src == B_Y) ? PF_GY : PF_GN;
-    const int tp = (src == B_Y) ? PF_TY : PF_TN2;
+    const bool y = src == B_Y;
+    const int gp = y ? PF_GY : PF_GN;
+    const int tp = y ? PF_TY : PF_TN2;
+    const auto& bo = bp.bo[y ? 0 : 1];
+    const int ng = (int)bo.goff.size() - 1, nq = (int)bo.qoff.size() - 1;
+    auto dev = [&](size_t o) { return base + o; };
     for (int pass = 0; pass < passes; ++pass) {
       const int from = pass == 0 ? src : dst;
-      CK(bgram(T, pre(gp), tot(gp), count, from, from, kMaxSplits, bp.dmax, st));
+      const int mb = pass == passes - 1 ? make_bt : 0;
+      CK(bgram(T, pre(gp), tot(gp), count, from, from, kMaxSplits, bp.dmax, st, false));
+      CK(bgram_tc(T, (const BoUnit*)dev(bo.o_gu), (const int*)dev(bo.o_goff), ng, from,
+                  kMaxSplits, err, st));
+      if (tot(gp) > 0 || ng > 0) CK(bgram_reduce(T, count, from, from, kMaxSplits, bp.dmax, st));
       CK(bchol(T, count, s1, pass == 0, bp.dmax, st, pass == 2));
-      CK(btrsm(T, pre(tp), tot(tp), count, from, dst, bp.dmax, st,
-               pass == passes - 1 ? make_bt : 0));
+      CK(btrsm(T, pre(tp), tot(tp), count, from, dst, bp.dmax, st, mb));
+      CK(btrinv(T, (const int*)dev(bp.off_bo_items), (int)bp.bo_items.size(), bp.dmax_otc, st));
+      CK(bqmul_tc(T, (const BoUnit*)dev(bo.o_qu), (const int*)dev(bo.o_qoff), nq, from, dst, mb,
+                  err, st));
     }
     return RUQLP_OK;
   };
@@ -946,6 +969,7 @@ ruqlp_status batch_begin(ruqlp_ctx* h, int count, const ruqlp_matrix* A, const r
   bp.table.resize(count);
   bp.dmax = 0;
   bp.dpmax_tc = 0;
+  bp.dmax_otc = 0;
   bp.max_omega = 0;
   bp.max_out = 0;
   size_t off = 0;
@@ -955,13 +979,23 @@ ruqlp_status batch_begin(ruqlp_ctx* h, int count, const ruqlp_matrix* A, const r
     return o;
   };
   std::vector<size_t> oX(count), oY(count), oZ(count), oP(count), oPa(count), oG(count),
-      oT(count), oB(count), oGf(count);
+      oT(count), oB(count), oGf(count), oS(count);
   for (int i = 0; i < count; ++i) {
     const ruqlp_dense& D = A[i].dense;
     const int64_t m = D.m, n = D.n;
     const int d = dd[i], dp = round16(d);
     BMat& b = bp.table[i];
     b.use_tc = (ct0 == Ty::BF16 && !h->bf16_simt && tc_supported(D.data, D.ld, dp)) ? 1 : 0;
+    // option batch_orth_tc: BF16 items of width dp <= 80 run their
+    // CholeskyQR passes on the tensor cores (a rule on the dtype, the
+    // options and d only, so an item decides the same alone and in any
+    // batch).  Off by default: at these widths the three-way BF16 split
+    // costs the converter warps more per value than the CUDA-core Gram's d
+    // multiply-adds (measured slower on the batched workload)
+    b.orth_tc = (ct0 == Ty::BF16 && h->batch_orth_tc && !h->bf16_simt && !h->orth_simt &&
+                 dp <= BO_DPMAX)
+                    ? 1
+                    : 0;
     b.ldbt = align_up((size_t)std::max(m, n), 8);
     int64_t slab;
     const int64_t sl = std::max(gram_slabs(m, kMaxSplits, &slab), gram_slabs(n, kMaxSplits, &slab));
@@ -974,6 +1008,8 @@ ruqlp_status batch_begin(ruqlp_ctx* h, int count, const ruqlp_matrix* A, const r
     oGf[i] = take((size_t)d * d * 4);
     oT[i] = take(chol_tiles_bytes(d));
     oB[i] = b.use_tc ? take((size_t)2 * dp * b.ldbt * 2) : 0;  // Bt, then Btl
+    oS[i] = b.orth_tc ? take(bo_st_bytes(d)) : 0;
+    if (b.orth_tc) bp.dmax_otc = std::max(bp.dmax_otc, d);
     bp.dmax = std::max(bp.dmax, d);
     if (b.use_tc) bp.dpmax_tc = std::max(bp.dpmax_tc, dp);
     bp.max_omega = std::max<int64_t>(bp.max_omega, n * dp);
@@ -992,6 +1028,60 @@ ruqlp_status batch_begin(ruqlp_ctx* h, int count, const ruqlp_matrix* A, const r
     }
   bp.off_tc_nn = take(sizeof(BTcTile) * std::max<size_t>(n_nn, 1));
   bp.off_tc_tn = take(sizeof(BTcTile) * std::max<size_t>(n_tn, 1));
+  {
+    // tensor-core CholeskyQR work: Gram units are the row slabs of
+    // gram_slabs() (the summation order, a function of the shape), dealt to
+    // at most one CTA per SM in contiguous runs of about equal rows; Q = Y
+    // R^{-1} cuts the items' rows into one run per CTA, multiples of the
+    // 128-row sub-tile (any cut gives the same rows of Q)
+    const int G = sm_count();
+    for (int i = 0; i < count; ++i)
+      if (bp.table[i].orth_tc) bp.bo_items.push_back(i);
+    for (int kind = 0; kind < 2; ++kind) {
+      auto& bo = bp.bo[kind];
+      auto rows = [&](int i) { return kind == 0 ? A[i].dense.m : A[i].dense.n; };
+      int64_t R = 0;
+      for (int i : bp.bo_items) {
+        int64_t slab;
+        gram_slabs(rows(i), kMaxSplits, &slab);
+        for (int64_t r0 = 0; r0 < rows(i); r0 += slab)
+          bo.gu.push_back({i, (int)std::min<int64_t>(slab, rows(i) - r0), r0});
+        R += rows(i);
+      }
+      // (a run also ends at BO_MAXU units, the CTA's descriptor table)
+      bo.goff.assign(1, 0);
+      const int gg = std::min<int>(G, (int)bo.gu.size());
+      int64_t acc = 0;
+      for (int u = 0; u < (int)bo.gu.size(); ++u) {
+        acc += bo.gu[u].rows;
+        const int c = (int)bo.goff.size();
+        if ((c < gg && acc * gg >= (int64_t)c * R) || u + 1 - bo.goff.back() == BO_MAXU)
+          bo.goff.push_back(u + 1);
+      }
+      if (bo.goff.back() != (int)bo.gu.size()) bo.goff.push_back((int)bo.gu.size());
+      bo.qoff.assign(1, 0);
+      const int64_t quota = std::max<int64_t>(128, ceil_div(ceil_div(R, G), 128) * 128);
+      int64_t fill = 0;
+      for (int i : bp.bo_items) {
+        for (int64_t r0 = 0; r0 < rows(i);) {
+          const int64_t take_rows = std::min(rows(i) - r0, quota - fill);
+          bo.qu.push_back({i, (int)take_rows, r0});
+          r0 += take_rows;
+          fill += take_rows;
+          if (fill == quota || (int)bo.qu.size() - bo.qoff.back() == BO_MAXU) {
+            bo.qoff.push_back((int)bo.qu.size());
+            fill = 0;
+          }
+        }
+      }
+      if (bo.qoff.back() != (int)bo.qu.size()) bo.qoff.push_back((int)bo.qu.size());
+      bo.o_gu = take(sizeof(BoUnit) * std::max<size_t>(bo.gu.size(), 1));
+      bo.o_goff = take(sizeof(int) * bo.goff.size());
+      bo.o_qu = take(sizeof(BoUnit) * std::max<size_t>(bo.qu.size(), 1));
+      bo.o_qoff = take(sizeof(int) * bo.qoff.size());
+    }
+    bp.off_bo_items = take(sizeof(int) * std::max<size_t>(bp.bo_items.size(), 1));
+  }
   const size_t map3 = btc_map_bytes();  // all tensor maps of one matrix
   bp.off_maps = take(map3 * count);
   bp.meta_end = off;
@@ -1023,17 +1113,19 @@ ruqlp_status batch_begin(ruqlp_ctx* h, int count, const ruqlp_matrix* A, const r
     b.tiles = (float*)(base + oT[i]);
     b.Bt = b.use_tc ? (void*)(base + oB[i]) : nullptr;
     b.Btl = b.use_tc ? (void*)(base + oB[i] + (size_t)b.dp * b.ldbt * 2) : nullptr;
+    b.St = b.orth_tc ? (void*)(base + oS[i]) : nullptr;
     b.omega = prm[i].omega;
     b.seed = prm[i].omega_seed;
     b.Qout = out[i].Q;
     b.Lout = out[i].L;
     b.Pout = out[i].P;
     b.status = (DevStatus*)(base + bp.off_status) + i;
+    const bool cc = !b.orth_tc;  // CholeskyQR on the CUDA cores
     const int cnt[7] = {b.use_tc ? 0 : bgemm_tiles(b.m, b.d), b.use_tc ? 0 : bgemm_tiles(b.n, b.d),
-                        bgram_tiles(b.m, b.d, true, kMaxSplits),
-                        bgram_tiles(b.n, b.d, true, kMaxSplits),
-                        bgram_tiles(b.n, b.d, false, kMaxSplits), btrsm_blocks(b.m),
-                        btrsm_blocks(b.n)};
+                        cc ? bgram_tiles(b.m, b.d, true, kMaxSplits) : 0,
+                        cc ? bgram_tiles(b.n, b.d, true, kMaxSplits) : 0,
+                        bgram_tiles(b.n, b.d, false, kMaxSplits), cc ? btrsm_blocks(b.m) : 0,
+                        cc ? btrsm_blocks(b.n) : 0};
     for (int k = 0; k < 7; ++k) bp.prefix[k][i + 1] = bp.prefix[k][i] + cnt[k];
   }
   tc_list(bp.table, false, bp.tc_nn);
@@ -1046,6 +1138,7 @@ ruqlp_status batch_begin(ruqlp_ctx* h, int count, const ruqlp_matrix* A, const r
     key.push_back(bp.table[i].n);
     key.push_back(bp.table[i].d);
     key.push_back(bp.table[i].use_tc);
+    key.push_back(bp.table[i].orth_tc);
   }
   ruqlp_ctx::BatchEntry* g = nullptr;
   for (auto& c : h->batches)
@@ -1091,6 +1184,13 @@ ruqlp_status batch_begin(ruqlp_ctx* h, int count, const ruqlp_matrix* A, const r
   put(bp.off_tc_nn, bp.tc_nn.data(), sizeof(BTcTile) * bp.tc_nn.size());
   put(bp.off_tc_tn, bp.tc_tn.data(), sizeof(BTcTile) * bp.tc_tn.size());
   put(bp.off_maps, g->maps.data(), g->maps.size());
+  for (const auto& bo : bp.bo) {
+    put(bo.o_gu, bo.gu.data(), sizeof(BoUnit) * bo.gu.size());
+    put(bo.o_goff, bo.goff.data(), sizeof(int) * bo.goff.size());
+    put(bo.o_qu, bo.qu.data(), sizeof(BoUnit) * bo.qu.size());
+    put(bo.o_qoff, bo.qoff.data(), sizeof(int) * bo.qoff.size());
+  }
+  put(bp.off_bo_items, bp.bo_items.data(), sizeof(int) * bp.bo_items.size());
   cudaStream_t st = h->stream;
   CK(cudaMemcpyAsync(base + bp.off_meta, img, meta, cudaMemcpyHostToDevice, st));
   const bool graphs = graphs_ok && h->batch_graphs && !h->profile;  // profiling runs eagerly
@@ -1140,7 +1240,7 @@ ruqlp_status batch_end(ruqlp_ctx* h, const BatchRun& run, ruqlp_outputs* out) {
   CK(cudaStreamSynchronize(st));
   if (h->profile) prof_collect(h);
   for (int i = 0; i < run.count; ++i) out[i].flags = (uint32_t)stat[i].flags;
-  if (derr) return fail(h, RUQLP_ERR_TIMEOUT, "a bounded device wait ran out in a batched product");
+  if (derr) return fail(h, RUQLP_ERR_TIMEOUT, "a bounded device wait ran out in a batched kernel");
   // items whose sketch CholeskyQR could not orthonormalise: alone on the
   // single-matrix path, which reruns them with Householder TSQR (as it would
   // had they come alone)
@@ -1239,6 +1339,10 @@ ruqlp_status ruqlp_set_option(ruqlp_handle h, const char* name, int64_t value) {
   }
   if (strcmp(name, "orth_simt") == 0) {
     h->orth_simt = value ? 1 : 0;
+    return RUQLP_OK;
+  }
+  if (strcmp(name, "batch_orth_tc") == 0) {
+    h->batch_orth_tc = value ? 1 : 0;
     return RUQLP_OK;
   }
   if (strcmp(name, "orth_tsqr") == 0) {

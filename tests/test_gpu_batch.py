@@ -182,6 +182,51 @@ def test_batch_tensor_core_items(handle):
         assert np.max(np.abs(P.T @ P - np.eye(d))) <= 2e-5
 
 
+# BF16 items for the tensor-core CholeskyQR passes (dp <= 80): one and two
+# 32-row chunks, several 512-row Gram slabs and 1024-row units, d = 80 (the
+# widest such item) beside d = 81 (CUDA-core passes in the same batch), a
+# partial 128-row sub-tile, and a 4-row last unit
+TCO = [(40, 300, 10, 6), (3000, 200, 60, 12), (1500, 2500, 70, 10), (700, 900, 73, 8),
+       (5000, 120, 20, 8), (129, 4100, 30, 8), (33, 64, 8, 8)]
+
+
+def test_batch_tc_orth_items(handle):
+    """BF16 batch whose CholeskyQR passes run on the tensor cores (option
+    batch_orth_tc: the six-part BF16 split of Y^T Y and Q = Y R^{-1},
+    Section II-A): every item bitwise equals its batch of one; accuracy
+    against the oracle by the BF16 rule; |diag(L)| within 1e-4 |L_11| of the
+    same batch with the default CUDA-core passes."""
+    As, Oms = _mix(wl.MASTER_SEED + 44, TCO)
+    Ag = [_pad8(torch.from_numpy(A).bfloat16().cuda()) for A in As]
+    Og = [torch.from_numpy(o).cuda() for o in Oms]
+    ks, ps = [s[2] for s in TCO], [s[3] for s in TCO]
+    cc = handle.decompose_batch(Ag, Og, ks, None, Q_ITERS, ps=ps)
+    handle.set_option("batch_orth_tc", 1)
+    try:
+        res = handle.decompose_batch(Ag, Og, ks, None, Q_ITERS, ps=ps)
+        for i in range(len(TCO)):
+            one = handle.decompose_batch([Ag[i]], [Og[i]], [ks[i]], ps[i], Q_ITERS)[0]
+            for x, y in zip(res[i][:3], one[:3]):
+                assert torch.equal(x, y), (i, TCO[i])
+    finally:
+        handle.set_option("batch_orth_tc", 0)
+    for i, ((m, n, k, p), om) in enumerate(zip(TCO, Oms)):
+        assert res[i][3] & ruqlp.FLAG_RANKDEF == 0
+        Q, L, P = (t.double().cpu().numpy() for t in res[i][:3])
+        Lc = cc[i][1].double().cpu().numpy()
+        A64 = Ag[i].double().cpu().numpy()
+        ref = oracle.ruqlp(A64, om, Q_ITERS)
+        r = oracle.residual_fro_small(A64, Q, L, P)
+        r0 = oracle.residual_fro_small(A64, ref["Q"], ref["L"], ref["P"])
+        assert r <= _bf16_bound(r0), (i, TCO[i], r, r0)
+        l11 = abs(ref["L"][0, 0])
+        assert np.max(np.abs(np.abs(np.diag(L))[:k] - np.abs(np.diag(ref["L"]))[:k])) <= 2e-2 * l11
+        assert np.max(np.abs(np.abs(np.diag(L))[:k] - np.abs(np.diag(Lc))[:k])) <= 1e-4 * l11, i
+        d = k + p
+        assert np.max(np.abs(Q.T @ Q - np.eye(d))) <= 2e-5, i
+        assert np.max(np.abs(P.T @ P - np.eye(d))) <= 2e-5, i
+
+
 @pytest.mark.parametrize("bad", ["mixed_dtype", "mixed_q", "d289", "empty", "f64"])
 def test_batch_invalid_rejected(handle, bad):
     A1 = torch.randn(300, 280, device="cuda")
