@@ -465,7 +465,15 @@ __device__ __forceinline__ void trsm_body(const float* __restrict__ Y, int64_t l
       asm volatile("cp.async.wait_group %0;" ::"n"(NPF - 1) : "memory");  // step's tile landed
       __syncthreads();
       const float* R = &Rt[sidx % NPF][0][0];
+      // block column J holds vJ = min(32, d - 32 J) columns: a thread whose
+      // four columns lie past them skips the tile product (its outputs are
+      // never written), and the diagonal step sums k < vJ only (the inverse
+      // of R_JJ is upper triangular: S[k][j] = 0 for k > j, so the terms
+      // dropped for j < vJ are exact zeros)
+      const int vJ = min(TB, d - J * TB);
+      const bool live = cg * 4 < vJ;
       if (K < J) {
+        if (live)
 #pragma unroll 8
         for (int k = 0; k < TB; ++k) {
           const float4 y = *col4(K * TB + k);
@@ -482,8 +490,9 @@ __device__ __forceinline__ void trsm_body(const float* __restrict__ Y, int64_t l
         for (int i = 0; i < 4; ++i)
 #pragma unroll
           for (int j = 0; j < 4; ++j) out[i][j] = 0.f;
-#pragma unroll 8
-        for (int k = 0; k < TB; ++k) {
+        const int kend = live ? vJ : 0;
+#pragma unroll 4
+        for (int k = 0; k < kend; ++k) {
           const float4 y = *col4(J * TB + k);
           const float4 r = *reinterpret_cast<const float4*>(R + k * TB + cg * 4);
           const float yv[4] = {y.x, y.y, y.z, y.w}, rv[4] = {r.x, r.y, r.z, r.w};
