@@ -101,15 +101,17 @@ __device__ __forceinline__ void fetch_tile(float* dst, const float* src, int t, 
 
 constexpr int TI_THREADS = 512;
 
-// Block column J of S = R^{-1}.  tiles: the Cholesky's R tiles (packed
-// upper block triangle, 32 x 32 row-major each) followed by the nb
-// diagonal-tile inverses.  Writes rows n = 32 J .. of St[3][dp][KPX] (K padded
-// to KPX).  Every tile the column needs (R_IK for I < K <= J, S_KK for K <= J)
-// is loaded at once; acc_I is accumulated in the slot of S_IJ and turned into
-// S_IJ in place.
+// Columns 32 J + 16 h .. + 15 of S = R^{-1} (block column J, half h: the two
+// halves are independent right-hand sides of the back substitution, so each
+// has its own CTA and the chain's tile products are spread over twice the
+// SMs).  tiles: the Cholesky's R tiles (packed upper block triangle, 32 x 32
+// row-major each) followed by the nb diagonal-tile inverses.  Writes rows
+// n = 32 J + 16 h .. of St[3][dp][KPX] (K padded to KPX).  Every tile the
+// column needs (R_IK for I < K <= J, S_KK for K <= J) is loaded at once;
+// acc_I is accumulated in the slot of S_IJ and turned into S_IJ in place.
 template <int KPX>
 __device__ __forceinline__ void trinv_body(const float* __restrict__ tiles, int d, int dp, int J,
-                                           __nv_bfloat16* __restrict__ St, float* sm) {
+                                           int h, __nv_bfloat16* __restrict__ St, float* sm) {
   const int nb = (d + TB - 1) / TB, ntiles = nb * (nb + 1) / 2;
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5, nw = TI_THREADS / 32;
   const int rg = lane >> 2, cg = lane & 3;
@@ -137,9 +139,9 @@ __device__ __forceinline__ void trinv_body(const float* __restrict__ tiles, int 
   __syncthreads();
   for (int K = J; K >= 1; --K) {
     const float* SKJ = Scol + (size_t)K * TILE_F;
-    // acc_I += R_IK S_KJ, items (I, column half)
-    for (int u = warp; u < 2 * K; u += nw) {
-      const int I = u >> 1, c0 = (u & 1) * 16 + cg * 4;
+    // acc_I += R_IK S_KJ, one item per I (this CTA's column half)
+    for (int u = warp; u < K; u += nw) {
+      const int I = u, c0 = h * 16 + cg * 4;
       float* C = Scol + (size_t)I * TILE_F;
       float a4[4][4];
 #pragma unroll
@@ -157,12 +159,12 @@ __device__ __forceinline__ void trinv_body(const float* __restrict__ tiles, int 
             make_float4(a4[i][0], a4[i][1], a4[i][2], a4[i][3]);
     }
     __syncthreads();
-    // S_{K-1,J} = -S_{K-1,K-1} acc_{K-1}, in place: warps (column half,
-    // k quarter) form partial products, then every thread adds the four
+    // S_{K-1,J} = -S_{K-1,K-1} acc_{K-1}, in place: warps (k quarter) form
+    // partial products of this half, then every thread adds the four
     // partials of two entries in quarter order
     float* D = Scol + (size_t)(K - 1) * TILE_F;
-    if (warp < 8) {
-      const int c0 = (warp & 1) * 16 + cg * 4, kq = warp >> 1;
+    if (warp < 4) {
+      const int c0 = h * 16 + cg * 4, kq = warp;
       float o[4][4] = {};
       tile_nn44_q(Ds + (size_t)(K - 1) * TILE_F, D, rg, c0, 8 * kq, o);
       float* Pq = Ps + (size_t)kq * TILE_F;
@@ -172,8 +174,8 @@ __device__ __forceinline__ void trinv_body(const float* __restrict__ tiles, int 
             make_float4(o[i][0], o[i][1], o[i][2], o[i][3]);
     }
     __syncthreads();
-    for (int e = t; e < TB * TB / 2; e += TI_THREADS) {
-      const int r = e >> 4, c = (e & 15) * 2;
+    for (int e = t; e < TB * 8; e += TI_THREADS) {
+      const int r = e >> 3, c = h * 16 + (e & 7) * 2;
       float2 v = *reinterpret_cast<const float2*>(Ps + r * TP + c);
 #pragma unroll
       for (int q = 1; q < 4; ++q) {
@@ -187,8 +189,8 @@ __device__ __forceinline__ void trinv_body(const float* __restrict__ tiles, int 
   }
   // St[p][n][k] = part p of S[k][n], n = 32 J + c: lane = k within a
   // 32-row block, so a warp writes 64 contiguous bytes per row n
-  for (int e = warp; e < TB * (KPX / TB); e += nw) {
-    const int c = e / (KPX / TB), kb = e % (KPX / TB);
+  for (int e = warp; e < 16 * (KPX / TB); e += nw) {
+    const int c = h * 16 + e / (KPX / TB), kb = e % (KPX / TB);
     const int n = J * TB + c, k = kb * TB + lane;
     if (n >= dp) continue;
     float v = 0.f;
@@ -204,21 +206,22 @@ __device__ __forceinline__ void trinv_body(const float* __restrict__ tiles, int 
   }
 }
 
-// grid = nb CTAs (block column J = blockIdx.x), S^T parts K-padded to 256.
+// grid = 2 nb CTAs (block column J = blockIdx.x / 2, half blockIdx.x % 2),
+// S^T parts K-padded to 256.
 __global__ void __launch_bounds__(TI_THREADS)
 k_trinv(const float* __restrict__ tiles, int d, int dp, __nv_bfloat16* __restrict__ St) {
   extern __shared__ __align__(16) float sm[];
-  trinv_body<KP>(tiles, d, dp, blockIdx.x, St, sm);
+  trinv_body<KP>(tiles, d, dp, blockIdx.x >> 1, blockIdx.x & 1, St, sm);
 }
 
-// Batched: grid (block columns, items); item list[blockIdx.y] of the table,
+// Batched: grid (2 x block columns, items); item list[blockIdx.y] of the table,
 // S^T parts K-padded to 128 in its St buffer.
 __global__ void __launch_bounds__(TI_THREADS)
 k_btrinv(const BMat* __restrict__ T, const int* __restrict__ list) {
   extern __shared__ __align__(16) float sm[];
   const BMat& b = T[list[blockIdx.y]];
-  if ((int)blockIdx.x >= (b.d + TB - 1) / TB) return;  // block-uniform
-  trinv_body<KPB>(b.tiles, b.d, b.dp, blockIdx.x, (__nv_bfloat16*)b.St, sm);
+  if ((int)(blockIdx.x >> 1) >= (b.d + TB - 1) / TB) return;  // block-uniform
+  trinv_body<KPB>(b.tiles, b.d, b.dp, blockIdx.x >> 1, blockIdx.x & 1, (__nv_bfloat16*)b.St, sm);
 }
 
 constexpr int QM_CONV = 8;                      // converter / epilogue warps
@@ -584,7 +587,7 @@ cudaError_t qmul_tc(const float* Y, int64_t ldy, const float* tiles, int64_t M, 
   cudaError_t e =
       cudaFuncSetAttribute(k_trinv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ti_smem);
   if (e != cudaSuccess) return e;
-  e = launch_pdl(k_trinv, dim3(nb), dim3(TI_THREADS), ti_smem, st, tiles, d, dp,
+  e = launch_pdl(k_trinv, dim3(2 * nb), dim3(TI_THREADS), ti_smem, st, tiles, d, dp,
                  (__nv_bfloat16*)St);
   count_launch();
   if (e == cudaSuccess) e = cudaGetLastError();
@@ -629,7 +632,7 @@ cudaError_t btrinv(const BMat* T, const int* list, int n, int dmax, cudaStream_t
   cudaError_t e =
       cudaFuncSetAttribute(k_btrinv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  k_btrinv<<<dim3(nb, n), TI_THREADS, smem, st>>>(T, list);
+  k_btrinv<<<dim3(2 * nb, n), TI_THREADS, smem, st>>>(T, list);
   count_launch();
   return cudaGetLastError();
 }
