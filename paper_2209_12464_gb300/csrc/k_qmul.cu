@@ -39,44 +39,23 @@ constexpr size_t TILE_F = (size_t)TB * TP;
 
 __device__ __forceinline__ int bidx(int I, int J, int nb) { return I * nb - (I * (I - 1)) / 2 + (J - I); }
 
-// acc[i][j] += sum_k A[rg + 8 i][k] B[k][c0 + j] for a lane's 4 x 4 block
-// of a 32 x 32 tile product A B (row-major tiles, pitch TP).  Rows rg + 8 i
-// keep the four 128-bit loads of A conflict-free.
-__device__ __forceinline__ void tile_nn44(const float* __restrict__ A, const float* __restrict__ B,
-                                          int rg, int c0, float (&acc)[4][4]) {
+// acc[i][j] += sum_{k0 <= k < k1} A[rg + (128 / W) i][k] B[k][c0 + j] for a
+// lane's (W / 4) x 4 block of a 32-row x W-column strip of A B (lanes:
+// rg = lane / (W / 4), c0 = strip + 4 (lane % (W / 4))); k in order.
+template <int W>
+__device__ __forceinline__ void tile_strip(const float* __restrict__ A, const float* __restrict__ B,
+                                           int rg, int c0, int k0, int k1,
+                                           float (&acc)[W / 4][4]) {
+  constexpr int RI = W / 4, RS = 128 / W;
 #pragma unroll 2
-  for (int k = 0; k < TB; k += 4) {
-    float4 a[4], b[4];
+  for (int k = k0; k < k1; k += 4) {
+    float4 a[RI], b[4];
 #pragma unroll
-    for (int i = 0; i < 4; ++i) a[i] = *reinterpret_cast<const float4*>(A + (rg + 8 * i) * TP + k);
-#pragma unroll
-    for (int q = 0; q < 4; ++q) b[q] = *reinterpret_cast<const float4*>(B + (k + q) * TP + c0);
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const float av[4] = {a[i].x, a[i].y, a[i].z, a[i].w};
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        acc[i][0] = fmaf(av[q], b[q].x, acc[i][0]);
-        acc[i][1] = fmaf(av[q], b[q].y, acc[i][1]);
-        acc[i][2] = fmaf(av[q], b[q].z, acc[i][2]);
-        acc[i][3] = fmaf(av[q], b[q].w, acc[i][3]);
-      }
-    }
-  }
-}
-
-// The same over k in [k0, k0 + 8) only (one quarter of the contraction).
-__device__ __forceinline__ void tile_nn44_q(const float* __restrict__ A, const float* __restrict__ B,
-                                            int rg, int c0, int k0, float (&acc)[4][4]) {
-#pragma unroll
-  for (int k = k0; k < k0 + 8; k += 4) {
-    float4 a[4], b[4];
-#pragma unroll
-    for (int i = 0; i < 4; ++i) a[i] = *reinterpret_cast<const float4*>(A + (rg + 8 * i) * TP + k);
+    for (int i = 0; i < RI; ++i) a[i] = *reinterpret_cast<const float4*>(A + (rg + RS * i) * TP + k);
 #pragma unroll
     for (int q = 0; q < 4; ++q) b[q] = *reinterpret_cast<const float4*>(B + (k + q) * TP + c0);
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
+    for (int i = 0; i < RI; ++i) {
       const float av[4] = {a[i].x, a[i].y, a[i].z, a[i].w};
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
@@ -100,21 +79,25 @@ __device__ __forceinline__ void fetch_tile(float* dst, const float* src, int t, 
 }
 
 constexpr int TI_THREADS = 512;
+constexpr int TI_W = 4;                 // columns of S per CTA (a strip)
+constexpr int TI_STRIPS = TB / TI_W;    // strips per 32-column block
 
-// Columns 32 J + 16 h .. + 15 of S = R^{-1} (block column J, half h: the two
-// halves are independent right-hand sides of the back substitution, so each
-// has its own CTA and the chain's tile products are spread over twice the
-// SMs).  tiles: the Cholesky's R tiles (packed upper block triangle, 32 x 32
+// Columns 32 J + W h .. + W - 1 of S = R^{-1} (block column J, strip h of
+// 32 / W: the strips are independent right-hand sides of the back
+// substitution, so each has its own CTA, the chain's tile products shrink to
+// 32 x W strips and every element is formed exactly as with whole tiles).
+// tiles: the Cholesky's R tiles (packed upper block triangle, 32 x 32
 // row-major each) followed by the nb diagonal-tile inverses.  Writes rows
-// n = 32 J + 16 h .. of St[3][dp][KPX] (K padded to KPX).  Every tile the
+// n = 32 J + W h .. of St[3][dp][KPX] (K padded to KPX).  Every tile the
 // column needs (R_IK for I < K <= J, S_KK for K <= J) is loaded at once;
 // acc_I is accumulated in the slot of S_IJ and turned into S_IJ in place.
 template <int KPX>
 __device__ __forceinline__ void trinv_body(const float* __restrict__ tiles, int d, int dp, int J,
                                            int h, __nv_bfloat16* __restrict__ St, float* sm) {
+  constexpr int W = TI_W, RI = W / 4, RS = 128 / W;
   const int nb = (d + TB - 1) / TB, ntiles = nb * (nb + 1) / 2;
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5, nw = TI_THREADS / 32;
-  const int rg = lane >> 2, cg = lane & 3;
+  const int rg = lane / RI, c0 = h * W + (lane % RI) * 4;
   pdl_launch();
   pdl_wait();
   // shared: Scol[K] (K <= J), R_IK at Rs[K (K - 1) / 2 + I] (I < K <= J),
@@ -139,43 +122,43 @@ __device__ __forceinline__ void trinv_body(const float* __restrict__ tiles, int 
   __syncthreads();
   for (int K = J; K >= 1; --K) {
     const float* SKJ = Scol + (size_t)K * TILE_F;
-    // acc_I += R_IK S_KJ, one item per I (this CTA's column half)
+    // acc_I += R_IK S_KJ, one item per I (this CTA's strip)
     for (int u = warp; u < K; u += nw) {
-      const int I = u, c0 = h * 16 + cg * 4;
+      const int I = u;
       float* C = Scol + (size_t)I * TILE_F;
-      float a4[4][4];
+      float a4[RI][4];
 #pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        const float4 v = *reinterpret_cast<const float4*>(C + (rg + 8 * i) * TP + c0);
+      for (int i = 0; i < RI; ++i) {
+        const float4 v = *reinterpret_cast<const float4*>(C + (rg + RS * i) * TP + c0);
         a4[i][0] = v.x;
         a4[i][1] = v.y;
         a4[i][2] = v.z;
         a4[i][3] = v.w;
       }
-      tile_nn44(Rs + ((size_t)K * (K - 1) / 2 + I) * TILE_F, SKJ, rg, c0, a4);
+      tile_strip<W>(Rs + ((size_t)K * (K - 1) / 2 + I) * TILE_F, SKJ, rg, c0, 0, TB, a4);
 #pragma unroll
-      for (int i = 0; i < 4; ++i)
-        *reinterpret_cast<float4*>(C + (rg + 8 * i) * TP + c0) =
+      for (int i = 0; i < RI; ++i)
+        *reinterpret_cast<float4*>(C + (rg + RS * i) * TP + c0) =
             make_float4(a4[i][0], a4[i][1], a4[i][2], a4[i][3]);
     }
     __syncthreads();
     // S_{K-1,J} = -S_{K-1,K-1} acc_{K-1}, in place: warps (k quarter) form
-    // partial products of this half, then every thread adds the four
+    // partial products of this strip, then every thread adds the four
     // partials of two entries in quarter order
     float* D = Scol + (size_t)(K - 1) * TILE_F;
     if (warp < 4) {
-      const int c0 = h * 16 + cg * 4, kq = warp;
-      float o[4][4] = {};
-      tile_nn44_q(Ds + (size_t)(K - 1) * TILE_F, D, rg, c0, 8 * kq, o);
+      const int kq = warp;
+      float o[RI][4] = {};
+      tile_strip<W>(Ds + (size_t)(K - 1) * TILE_F, D, rg, c0, 8 * kq, 8 * kq + 8, o);
       float* Pq = Ps + (size_t)kq * TILE_F;
 #pragma unroll
-      for (int i = 0; i < 4; ++i)
-        *reinterpret_cast<float4*>(Pq + (rg + 8 * i) * TP + c0) =
+      for (int i = 0; i < RI; ++i)
+        *reinterpret_cast<float4*>(Pq + (rg + RS * i) * TP + c0) =
             make_float4(o[i][0], o[i][1], o[i][2], o[i][3]);
     }
     __syncthreads();
-    for (int e = t; e < TB * 8; e += TI_THREADS) {
-      const int r = e >> 3, c = h * 16 + (e & 7) * 2;
+    for (int e = t; e < TB * (W / 2); e += TI_THREADS) {
+      const int r = e / (W / 2), c = h * W + (e % (W / 2)) * 2;
       float2 v = *reinterpret_cast<const float2*>(Ps + r * TP + c);
 #pragma unroll
       for (int q = 1; q < 4; ++q) {
@@ -189,8 +172,8 @@ __device__ __forceinline__ void trinv_body(const float* __restrict__ tiles, int 
   }
   // St[p][n][k] = part p of S[k][n], n = 32 J + c: lane = k within a
   // 32-row block, so a warp writes 64 contiguous bytes per row n
-  for (int e = warp; e < 16 * (KPX / TB); e += nw) {
-    const int c = h * 16 + e / (KPX / TB), kb = e % (KPX / TB);
+  for (int e = warp; e < W * (KPX / TB); e += nw) {
+    const int c = h * W + e / (KPX / TB), kb = e % (KPX / TB);
     const int n = J * TB + c, k = kb * TB + lane;
     if (n >= dp) continue;
     float v = 0.f;
@@ -206,22 +189,23 @@ __device__ __forceinline__ void trinv_body(const float* __restrict__ tiles, int 
   }
 }
 
-// grid = 2 nb CTAs (block column J = blockIdx.x / 2, half blockIdx.x % 2),
-// S^T parts K-padded to 256.
+// grid = TI_STRIPS nb CTAs (block column J = blockIdx.x / TI_STRIPS, strip
+// blockIdx.x % TI_STRIPS), S^T parts K-padded to 256.
 __global__ void __launch_bounds__(TI_THREADS)
 k_trinv(const float* __restrict__ tiles, int d, int dp, __nv_bfloat16* __restrict__ St) {
   extern __shared__ __align__(16) float sm[];
-  trinv_body<KP>(tiles, d, dp, blockIdx.x >> 1, blockIdx.x & 1, St, sm);
+  trinv_body<KP>(tiles, d, dp, blockIdx.x / TI_STRIPS, blockIdx.x % TI_STRIPS, St, sm);
 }
 
-// Batched: grid (2 x block columns, items); item list[blockIdx.y] of the table,
+// Batched: grid (TI_STRIPS x block columns, items); item list[blockIdx.y] of the table,
 // S^T parts K-padded to 128 in its St buffer.
 __global__ void __launch_bounds__(TI_THREADS)
 k_btrinv(const BMat* __restrict__ T, const int* __restrict__ list) {
   extern __shared__ __align__(16) float sm[];
   const BMat& b = T[list[blockIdx.y]];
-  if ((int)(blockIdx.x >> 1) >= (b.d + TB - 1) / TB) return;  // block-uniform
-  trinv_body<KPB>(b.tiles, b.d, b.dp, blockIdx.x >> 1, blockIdx.x & 1, (__nv_bfloat16*)b.St, sm);
+  if ((int)(blockIdx.x / TI_STRIPS) >= (b.d + TB - 1) / TB) return;  // block-uniform
+  trinv_body<KPB>(b.tiles, b.d, b.dp, blockIdx.x / TI_STRIPS, blockIdx.x % TI_STRIPS,
+                  (__nv_bfloat16*)b.St, sm);
 }
 
 constexpr int QM_CONV = 8;                      // converter / epilogue warps
@@ -587,7 +571,7 @@ cudaError_t qmul_tc(const float* Y, int64_t ldy, const float* tiles, int64_t M, 
   cudaError_t e =
       cudaFuncSetAttribute(k_trinv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ti_smem);
   if (e != cudaSuccess) return e;
-  e = launch_pdl(k_trinv, dim3(2 * nb), dim3(TI_THREADS), ti_smem, st, tiles, d, dp,
+  e = launch_pdl(k_trinv, dim3(TI_STRIPS * nb), dim3(TI_THREADS), ti_smem, st, tiles, d, dp,
                  (__nv_bfloat16*)St);
   count_launch();
   if (e == cudaSuccess) e = cudaGetLastError();
@@ -632,7 +616,7 @@ cudaError_t btrinv(const BMat* T, const int* list, int n, int dmax, cudaStream_t
   cudaError_t e =
       cudaFuncSetAttribute(k_btrinv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  k_btrinv<<<dim3(2 * nb, n), TI_THREADS, smem, st>>>(T, list);
+  k_btrinv<<<dim3(TI_STRIPS * nb, n), TI_THREADS, smem, st>>>(T, list);
   count_launch();
   return cudaGetLastError();
 }
