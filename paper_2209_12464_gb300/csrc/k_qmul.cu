@@ -442,10 +442,15 @@ k_qmul_tc(const __grid_constant__ CUtensorMap tmS, const __grid_constant__ QmPar
       const bool more = next_unit(ng, nc, nsb);
       if (more) load_a(ng, nc, nsb, nxt);
       asm volatile("" ::: "memory");  // the loads are issued before the conversion
+      // rows past the CTA's range are not converted: a row of the MMA's
+      // output depends on the same row of A only, and those output rows are
+      // never stored (a range of 132 rows leaves a 4-row second sub-tile)
+      const int64_t r0s = sub_row0(g, s);
 #pragma unroll
       for (int q = 0; q < QM_PER; ++q) {
         const int e = ct + q * QM_CONV * 32;
         const int row = e >> 4, kc = (e & 15) * 4;
+        if (r0s + row >= r_end) continue;
         const float v[4] = {cur[q].x, cur[q].y, cur[q].z, cur[q].w};
         uint32_t hp[2], mp[2], lp[2];
         split3_bf16x4(v, hp, mp, lp);
@@ -482,7 +487,8 @@ k_qmul_tc(const __grid_constant__ CUtensorMap tmS, const __grid_constant__ QmPar
         }
         tc_fence_after();
         const int64_t rbase = sub_row0(g, s) + q4 * 32;
-        for (int col = 128 * h; col < c1; col += 16) {
+        // (a warp whose 32 rows all lie past the range has nothing to store)
+        for (int col = 128 * h; col < c1 && rbase < r_end; col += 16) {
           float v[16];
           tmem_ld16(tmem_base + (uint32_t)(256 * set + col) + ((uint32_t)(q4 * 32) << 16), v);
 #pragma unroll
