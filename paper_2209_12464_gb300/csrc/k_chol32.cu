@@ -559,7 +559,7 @@ k_btrsm(const BMat* __restrict__ T, const int* __restrict__ prefix, int count, i
     const int mid = (lo + hi) >> 1;
     if (prefix[mid] <= t) lo = mid; else hi = mid;
   }
-  const BMat& b = T[lo];
+  const BMat& b = T[prefix[count + 1 + lo]];  // the launch order's item lo
   const int64_t M = (src == B_Y) ? b.m : b.n;
   trsm_body<SRB>(bbuf(b, src), b.dp, b.tiles, bbuf(b, dst), b.dp, M, b.d, t - prefix[lo],
             (make_bt && b.use_tc) ? (__nv_bfloat16*)b.Bt : nullptr, b.ldbt,

@@ -259,7 +259,7 @@ k_bgram(const BMat* __restrict__ Tb, const int* __restrict__ prefix, int count, 
     const int mid = (lo + hi) >> 1;
     if (prefix[mid] <= t) lo = mid; else hi = mid;
   }
-  const BMat& b = Tb[lo];
+  const BMat& b = Tb[prefix[count + 1 + lo]];  // the launch order's item lo
   const int local = t - prefix[lo];
   const bool sym = src == src2;
   const int64_t M = (src == B_Y) ? b.m : b.n;

@@ -142,7 +142,7 @@ k_bgemm(const BMat* __restrict__ T, const int* __restrict__ prefix, int count, i
     const int mid = (lo + hi) >> 1;
     if (prefix[mid] <= t) lo = mid; else hi = mid;
   }
-  const BMat& b = T[lo];
+  const BMat& b = T[prefix[count + 1 + lo]];  // the launch order's item lo
   const int local = t - prefix[lo];
   const int ntn = (b.d + BN - 1) / BN;
   const int64_t Mout = TRANS_A ? b.n : b.m, K = TRANS_A ? b.m : b.n;

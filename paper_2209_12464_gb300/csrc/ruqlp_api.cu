@@ -1015,10 +1015,12 @@ ruqlp_status batch_begin(ruqlp_ctx* h, int count, const ruqlp_matrix* A, const r
     bp.max_omega = std::max<int64_t>(bp.max_omega, n * dp);
     bp.max_out = std::max<int64_t>(bp.max_out, (m + n) * d + (int64_t)d * d);
   }
-  for (int k = 0; k < 7; ++k) bp.prefix[k].assign(count + 1, 0);
+  // each prefix array: count + 1 tile offsets over the launch order, then
+  // the order itself (count item indices)
+  for (int k = 0; k < 7; ++k) bp.prefix[k].assign(2 * count + 1, 0);
   bp.off_meta = off;
   bp.off_table = take(sizeof(BMat) * count);
-  for (int k = 0; k < 7; ++k) bp.off_prefix[k] = take(sizeof(int) * (count + 1));
+  for (int k = 0; k < 7; ++k) bp.off_prefix[k] = take(sizeof(int) * (2 * count + 1));
   // tile lists are sized below, after the table is filled
   size_t n_nn = 0, n_tn = 0;
   for (int i = 0; i < count; ++i)
@@ -1091,6 +1093,8 @@ ruqlp_status batch_begin(ruqlp_ctx* h, int count, const ruqlp_matrix* A, const r
   ruqlp_status s = ensure_arena(h, bp.total);
   if (s != RUQLP_OK) return s;
   char* base = (char*)h->arena;
+  std::vector<int> cnts[7];
+  for (int k = 0; k < 7; ++k) cnts[k].assign(count, 0);
   for (int i = 0; i < count; ++i) {
     BMat& b = bp.table[i];
     const ruqlp_dense& D = A[i].dense;
@@ -1126,7 +1130,25 @@ ruqlp_status batch_begin(ruqlp_ctx* h, int count, const ruqlp_matrix* A, const r
                         cc ? bgram_tiles(b.n, b.d, true, kMaxSplits) : 0,
                         bgram_tiles(b.n, b.d, false, kMaxSplits), cc ? btrsm_blocks(b.m) : 0,
                         cc ? btrsm_blocks(b.n) : 0};
-    for (int k = 0; k < 7; ++k) bp.prefix[k][i + 1] = bp.prefix[k][i] + cnt[k];
+    for (int k = 0; k < 7; ++k) cnts[k][i] = cnt[k];
+  }
+  // the CUDA-core launches take their tiles widest item first (a tile's cost
+  // grows with d^2), so the last wave holds the cheapest tiles; a tile's
+  // result does not depend on when it runs
+  {
+    std::vector<int> order(count);
+    for (int i = 0; i < count; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+      const BMat &a = bp.table[x], &b = bp.table[y];
+      if (a.dp != b.dp) return a.dp > b.dp;
+      return a.m + a.n > b.m + b.n;
+    });
+    for (int k = 0; k < 7; ++k) {
+      for (int pos = 0; pos < count; ++pos) {
+        bp.prefix[k][pos + 1] = bp.prefix[k][pos] + cnts[k][order[pos]];
+        bp.prefix[k][count + 1 + pos] = order[pos];
+      }
+    }
   }
   tc_list(bp.table, false, bp.tc_nn);
   tc_list(bp.table, true, bp.tc_tn);
@@ -1180,7 +1202,8 @@ ruqlp_status batch_begin(ruqlp_ctx* h, int count, const ruqlp_matrix* A, const r
     if (bytes) memcpy(img + (o - bp.off_meta), src, bytes);
   };
   put(bp.off_table, bp.table.data(), sizeof(BMat) * count);
-  for (int k = 0; k < 7; ++k) put(bp.off_prefix[k], bp.prefix[k].data(), sizeof(int) * (count + 1));
+  for (int k = 0; k < 7; ++k)
+    put(bp.off_prefix[k], bp.prefix[k].data(), sizeof(int) * (2 * count + 1));
   put(bp.off_tc_nn, bp.tc_nn.data(), sizeof(BTcTile) * bp.tc_nn.size());
   put(bp.off_tc_tn, bp.tc_tn.data(), sizeof(BTcTile) * bp.tc_tn.size());
   put(bp.off_maps, g->maps.data(), g->maps.size());
