@@ -190,6 +190,12 @@ int bgemm_tiles(int64_t rows, int d);
 cudaError_t bgemm(bool trans, Ty ta, Ty tb, const BMat* T, const int* prefix, int total, int count,
                   int src, int dst, cudaStream_t st, bool split2 = false);
 int bgram_tiles(int64_t M, int d, bool sym, int max_slabs);
+// Symmetric batched Grams of the items with round16(d) <= 80 (k_bgram_sym:
+// one CTA per row slab, upper-triangle blocks only); bgram_sym_ctas is an
+// item's CTA count (0 for wider items, whose tiles go to bgram).
+int bgram_sym_ctas(int64_t M, int d, int max_slabs);
+cudaError_t bgram_sym(const BMat* T, const int* prefix, int total, int count, int src,
+                      int max_slabs, cudaStream_t st);
 // Batched CholeskyQR passes on the tensor cores (k_borth.cu, k_qmul.cu) for
 // items with orth_tc (dp <= BO_DPMAX).  Work comes as units (a row range of
 // one item); CTA c of a launch takes units uoff[c] .. uoff[c + 1] - 1, the

@@ -371,14 +371,18 @@ __device__ __forceinline__ void trsm_body(const float* __restrict__ Y, int64_t l
                                           int64_t ldbt = 0,
                                           __nv_bfloat16* __restrict__ Btl = nullptr) {
   constexpr int TT = 2 * SR, YP = SR + 4, RG = SR / 4;
-  extern __shared__ __align__(16) float ys[];  // (nb * 32) x YP, ys[c * YP + r]
+  extern __shared__ __align__(16) float ys[];  // round4(d) x YP, ys[c * YP + r]
   __shared__ __align__(16) float Rt[NPF][TB][TB];
   const int nb = (d + TB - 1) / TB;
   const int ntiles = nb * (nb + 1) / 2;
   const int64_t r0 = (int64_t)rb * SR;
   const int nr = (int)min((int64_t)SR, M - r0);
   const int t = threadIdx.x;
-  const int nv = nb * TB / 4;  // 4-column groups per padded row
+  // 4-column groups holding columns below d: the padding columns of the
+  // last block column are never read as inputs (the diagonal step sums
+  // k < vJ only and no block column K < J reaches past d), so they are not
+  // staged
+  const int nv = (d + 3) / 4;
   const bool vec = (ldy % 4 == 0) && (((uintptr_t)Y & 15) == 0);
   // stage: item e -> row e % SR, column group e / SR (a warp takes one group
   // of 32 rows, so the transposed stores hit 32 banks); 8 loads in flight
@@ -442,11 +446,17 @@ __device__ __forceinline__ void trsm_body(const float* __restrict__ Y, int64_t l
   auto col4 = [&](int c) { return reinterpret_cast<float4*>(ys + c * YP + rg * 4); };
   int sidx = 0;
   for (int J = 0; J < nb; ++J) {
+    // block column J holds vJ = min(32, d - 32 J) columns: a thread whose
+    // four columns lie past them (not live) neither reads nor writes the
+    // staged block in this block column, so the staging holds only the
+    // columns below d rounded up to 4
+    const int vJ = min(TB, d - J * TB);
+    const bool live = cg * 4 < vJ;
     float acc[4][4];
     __syncthreads();
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-      const float4 v = *col4(J * TB + cg * 4 + j);
+      const float4 v = live ? *col4(J * TB + cg * 4 + j) : make_float4(0.f, 0.f, 0.f, 0.f);
       acc[0][j] = v.x;
       acc[1][j] = v.y;
       acc[2][j] = v.z;
@@ -456,7 +466,7 @@ __device__ __forceinline__ void trsm_body(const float* __restrict__ Y, int64_t l
       __syncthreads();  // everyone is done with the buffer about to be refilled
       if (sidx + NPF - 1 < nsteps) fetch((sidx + NPF - 1) % NPF, step_tile(sidx + NPF - 1));
       asm volatile("cp.async.commit_group;" ::: "memory");
-      if (K == J) {
+      if (K == J && live) {
         // stage the updated tile of this row block, then multiply by R_JJ^{-1}
 #pragma unroll
         for (int j = 0; j < 4; ++j)
@@ -465,13 +475,10 @@ __device__ __forceinline__ void trsm_body(const float* __restrict__ Y, int64_t l
       asm volatile("cp.async.wait_group %0;" ::"n"(NPF - 1) : "memory");  // step's tile landed
       __syncthreads();
       const float* R = &Rt[sidx % NPF][0][0];
-      // block column J holds vJ = min(32, d - 32 J) columns: a thread whose
-      // four columns lie past them skips the tile product (its outputs are
-      // never written), and the diagonal step sums k < vJ only (the inverse
-      // of R_JJ is upper triangular: S[k][j] = 0 for k > j, so the terms
-      // dropped for j < vJ are exact zeros)
-      const int vJ = min(TB, d - J * TB);
-      const bool live = cg * 4 < vJ;
+      // a thread that is not live skips the tile products; the diagonal
+      // step sums k < min(vJ, 4 cg + 4) only (the inverse of R_JJ is upper
+      // triangular: S[k][j] = 0 for k > j, so the terms dropped for the
+      // thread's columns j <= 4 cg + 3 are exact zeros)
       if (K < J) {
         if (live)
 #pragma unroll 8
@@ -490,7 +497,7 @@ __device__ __forceinline__ void trsm_body(const float* __restrict__ Y, int64_t l
         for (int i = 0; i < 4; ++i)
 #pragma unroll
           for (int j = 0; j < 4; ++j) out[i][j] = 0.f;
-        const int kend = live ? vJ : 0;
+        const int kend = live ? min(vJ, cg * 4 + 4) : 0;
 #pragma unroll 4
         for (int k = 0; k < kend; ++k) {
           const float4 y = *col4(J * TB + k);
@@ -502,9 +509,10 @@ __device__ __forceinline__ void trsm_body(const float* __restrict__ Y, int64_t l
             for (int j = 0; j < 4; ++j) out[i][j] = fmaf(yv[i], rv[j], out[i][j]);
         }
         __syncthreads();
+        if (live)
 #pragma unroll
-        for (int j = 0; j < 4; ++j)
-          *col4(J * TB + cg * 4 + j) = make_float4(out[0][j], out[1][j], out[2][j], out[3][j]);
+          for (int j = 0; j < 4; ++j)
+            *col4(J * TB + cg * 4 + j) = make_float4(out[0][j], out[1][j], out[2][j], out[3][j]);
       }
     }
   }
@@ -527,14 +535,47 @@ __device__ __forceinline__ void trsm_body(const float* __restrict__ Y, int64_t l
   }
   if (Bt != nullptr) {  // rows of X^T are columns of the staged block: contiguous in r
     const int dp = (d + 15) / 16 * 16;
-    for (int e = t; e < SR * dp; e += TT) {
-      const int r = e % SR, c = e / SR;
-      if (r < nr) {
-        const float v = c < d ? ys[c * YP + r] : 0.f;
-        const __nv_bfloat16 hv = __float2bfloat16_rn(v);
-        Bt[(int64_t)c * ldbt + r0 + r] = hv;
-        if (Btl != nullptr)
-          Btl[(int64_t)c * ldbt + r0 + r] = __float2bfloat16_rn(v - __bfloat162float(hv));
+    // eight consecutive rows of one column per item: two 128-bit shared
+    // loads and one 128-bit store per part
+    const bool vb = ((((uintptr_t)Bt | (uintptr_t)(Btl != nullptr ? Btl : Bt)) & 15) == 0) &&
+                    (ldbt % 8 == 0) && (r0 % 8 == 0);
+    constexpr int G8 = SR / 8;
+    for (int e = t; e < G8 * dp; e += TT) {
+      const int r = (e % G8) * 8, c = e / G8;
+      if (r >= nr) continue;
+      float v[8];
+      if (c < d) {
+        const float4 a = *reinterpret_cast<const float4*>(ys + c * YP + r);
+        const float4 b = *reinterpret_cast<const float4*>(ys + c * YP + r + 4);
+        v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+        v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+      } else {
+#pragma unroll
+        for (int u = 0; u < 8; ++u) v[u] = 0.f;
+      }
+      __nv_bfloat16 h[8], l[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        h[u] = __float2bfloat16_rn(v[u]);
+        l[u] = __float2bfloat16_rn(v[u] - __bfloat162float(h[u]));
+      }
+      const int64_t o = (int64_t)c * ldbt + r0 + r;
+      if (vb && r + 8 <= nr) {
+        auto pack = [](const __nv_bfloat16 (&x)[8]) {
+          uint32_t w[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u)
+            w[u] = (uint32_t)__bfloat16_as_ushort(x[2 * u]) |
+                   ((uint32_t)__bfloat16_as_ushort(x[2 * u + 1]) << 16);
+          return make_uint4(w[0], w[1], w[2], w[3]);
+        };
+        *reinterpret_cast<uint4*>(Bt + o) = pack(h);
+        if (Btl != nullptr) *reinterpret_cast<uint4*>(Btl + o) = pack(l);
+      } else {
+        for (int u = 0; u < 8 && r + u < nr; ++u) {
+          Bt[o + u] = h[u];
+          if (Btl != nullptr) Btl[o + u] = l[u];
+        }
       }
     }
   }
@@ -593,8 +634,7 @@ cudaError_t bchol(const BMat* T, int count, double shift_rel, bool force_shift, 
 cudaError_t btrsm(const BMat* T, const int* prefix, int total, int count, int src, int dst,
                   int dmax, cudaStream_t st, int make_bt) {
   if (total <= 0) return cudaSuccess;
-  const int nb = (dmax + TB - 1) / TB;
-  const size_t sm = (size_t)nb * TB * (SRB + 4) * sizeof(float);
+  const size_t sm = (size_t)((dmax + 3) / 4 * 4) * (SRB + 4) * sizeof(float);
   cudaError_t e =
       cudaFuncSetAttribute(k_btrsm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
@@ -634,8 +674,7 @@ cudaError_t chol_tiles_f32(const float* G, int d, double shift_rel, bool force_s
 cudaError_t trsm_tiles_f32(const float* Y, int64_t ldy, const float* tiles, float* X, int64_t ldx,
                            int64_t M, int d, cudaStream_t st, void* Bt, int64_t ldbt, void* Btl) {
   if (M <= 0) return cudaSuccess;
-  const int nb = (d + TB - 1) / TB;
-  const size_t sm = (size_t)nb * TB * (SR1 + 4) * sizeof(float);
+  const size_t sm = (size_t)((d + 3) / 4 * 4) * (SR1 + 4) * sizeof(float);
   cudaError_t e =
       cudaFuncSetAttribute(k_trsm_tiles, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;

@@ -284,6 +284,125 @@ k_bgram(const BMat* __restrict__ Tb, const int* __restrict__ prefix, int count, 
             local % tiles, local / tiles);
 }
 
+// Batched symmetric Grams of narrow items (dp <= 80), one CTA of NTS threads
+// per row slab.  The upper triangle is covered by 4 x 8 blocks (rows 4 bi..,
+// columns 8 bj.., the blocks with bj >= bi / 2: those holding an entry on or
+// above the diagonal), one block per thread, listed row by row (110 blocks at
+// dp = 80, 72 at 64, 42 at 48), so only about half of the square's
+// multiply-adds are issued.  Every entry (i <= j) is the same sequential FP32
+// sum over the slab's rows as in gram_tile (zero-padded rows of the last
+// chunk included), so results match it bitwise; entries below the diagonal
+// that a straddling block also forms are never read (the reduction mirrors
+// the upper triangle).
+constexpr int NTS = 128;
+constexpr int packed_blocks(int dp) {
+  int n = 0;
+  for (int bi = 0; bi < dp / 4; ++bi) n += dp / 8 - bi / 2;
+  return n;
+}
+template <int DP>
+__device__ __forceinline__ void gram_sym_packed(const float* __restrict__ X, int64_t ld,
+                                                int64_t M, int d, int64_t slab,
+                                                double* __restrict__ partial, int slab_id,
+                                                float* __restrict__ sbuf) {
+  constexpr int NBR = DP / 4, NBC = DP / 8;
+  constexpr int NV = TK * DP / 4 / NTS;  // float4s per thread per 32-row chunk
+  static_assert(NV * 4 * NTS == TK * DP, "chunk split");
+  static_assert(packed_blocks(DP) <= NTS, "one block per thread");
+  float(*Xs)[DP] = reinterpret_cast<float(*)[DP]>(sbuf);
+  const int64_t r_begin = (int64_t)slab_id * slab;
+  const int64_t r_end = min(M, r_begin + slab);
+  const int t = threadIdx.x;
+  int bi = 0, u = t;
+  while (bi < NBR && u >= NBC - bi / 2) {
+    u -= NBC - bi / 2;
+    ++bi;
+  }
+  const bool active = bi < NBR;
+  const int ra = 4 * (active ? bi : 0), cb = 8 * (active ? bi / 2 + u : 0);
+  float acc[4][8];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
+  auto load = [&](int64_t r0, float4 (&v)[NV]) {
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+      const int e = (q * NTS + t) * 4;
+      const int rr = e / DP, cc = e % DP;
+      const int64_t r = r0 + rr;
+      v[q] = (r < r_end) ? *reinterpret_cast<const float4*>(X + r * ld + cc)
+                         : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+  };
+  float4 vx[NV];
+  int64_t r0 = r_begin;
+  if (r0 < r_end) load(r0, vx);
+  for (; r0 < r_end; r0 += TK) {
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+      const int e = (q * NTS + t) * 4;
+      *reinterpret_cast<float4*>(&Xs[e / DP][e % DP]) = vx[q];
+    }
+    __syncthreads();
+    if (r0 + TK < r_end) load(r0 + TK, vx);  // next chunk while computing this one
+    if (active) {
+#pragma unroll 4
+      for (int k = 0; k < TK; ++k) {
+        const float4 a4 = *reinterpret_cast<const float4*>(&Xs[k][ra]);
+        const float4 b0 = *reinterpret_cast<const float4*>(&Xs[k][cb]);
+        const float4 b1 = *reinterpret_cast<const float4*>(&Xs[k][cb + 4]);
+        const float a[4] = {a4.x, a4.y, a4.z, a4.w};
+        const float b[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+      }
+    }
+    __syncthreads();
+  }
+  if (!active) return;
+  double* P = partial + (int64_t)slab_id * d * d;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int r = ra + i;
+    if (r >= d) continue;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int c = cb + j;
+      if (c < d) P[(int64_t)r * d + c] = (double)acc[i][j];
+    }
+  }
+}
+
+// Batched symmetric Grams of the items with dp <= 80: CTA t of the launch ->
+// (item, slab) through prefix (launch order appended, as k_bgram).
+__global__ void __launch_bounds__(NTS)
+k_bgram_sym(const BMat* __restrict__ Tb, const int* __restrict__ prefix, int count, int src,
+            int max_slabs) {
+  __shared__ __align__(16) float sbuf[TK * SMALL_MAX];
+  const int t = blockIdx.x;
+  int lo = 0, hi = count;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (prefix[mid] <= t) lo = mid; else hi = mid;
+  }
+  const BMat& b = Tb[prefix[count + 1 + lo]];
+  const int local = t - prefix[lo];
+  const int64_t M = (src == B_Y) ? b.m : b.n;
+  int64_t slab;
+  gram_slabs(M, max_slabs, &slab);
+  const float* X = bbuf(b, src);
+  switch (b.dp / 16) {
+    case 1: gram_sym_packed<16>(X, b.dp, M, b.d, slab, b.partial, local, sbuf); break;
+    case 2: gram_sym_packed<32>(X, b.dp, M, b.d, slab, b.partial, local, sbuf); break;
+    case 3: gram_sym_packed<48>(X, b.dp, M, b.d, slab, b.partial, local, sbuf); break;
+    case 4: gram_sym_packed<64>(X, b.dp, M, b.d, slab, b.partial, local, sbuf); break;
+    default: gram_sym_packed<80>(X, b.dp, M, b.d, slab, b.partial, local, sbuf); break;
+  }
+}
+
 __global__ void k_bgram_reduce(const BMat* __restrict__ Tb, int src, int src2, int max_slabs) {
   const BMat& b = Tb[blockIdx.y];
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -311,6 +430,19 @@ int bgram_tiles(int64_t M, int d, bool sym, int max_slabs) {
   const int slabs = (int)gram_slabs(M, max_slabs, &slab);
   if (gram_is_small((d + 15) / 16 * 16)) return slabs;
   return (sym ? nb * (nb + 1) / 2 : nb * nb) * slabs;
+}
+
+int bgram_sym_ctas(int64_t M, int d, int max_slabs) {
+  int64_t slab;
+  return gram_is_small((d + 15) / 16 * 16) ? (int)gram_slabs(M, max_slabs, &slab) : 0;
+}
+
+cudaError_t bgram_sym(const BMat* T, const int* prefix, int total, int count, int src,
+                      int max_slabs, cudaStream_t st) {
+  if (total <= 0) return cudaSuccess;
+  k_bgram_sym<<<total, NTS, 0, st>>>(T, prefix, count, src, max_slabs);
+  count_launch();
+  return cudaGetLastError();
 }
 
 cudaError_t bgram_reduce(const BMat* T, int count, int src, int src2, int max_slabs, int dmax,

@@ -827,9 +827,13 @@ ruqlp_status set_error(ruqlp_ctx* h, ruqlp_status s, const char* msg) {
 // equal ruqlp_decompose bitwise.
 namespace {
 
+enum { PF_NN = 0, PF_TN, PF_GY, PF_GN, PF_GPZ, PF_TY, PF_TN2, PF_GYW, PF_GNW, NPF };
+
 struct BatchPlan {
   std::vector<BMat> table;
-  std::vector<int> prefix[7];  // NN, TN, gramY, gramN, gramPZ, trsmY, trsmN (CUDA-core tiles)
+  // CUDA-core work per launch: NN, TN, gramY, gramN (narrow items), gramPZ,
+  // trsmY, trsmN, gramY, gramN (wide items)
+  std::vector<int> prefix[NPF];
   std::vector<BTcTile> tc_nn, tc_tn;  // tensor-core tile lists
   // tensor-core CholeskyQR items (orth_tc): their list (for k_btrinv) and,
   // over Y (m rows) and over Z (n rows), the Gram units (one row slab each)
@@ -841,13 +845,12 @@ struct BatchPlan {
   } bo[2];
   std::vector<int> bo_items;
   size_t off_bo_items;
-  size_t off_meta, off_table, off_prefix[7], off_tc_nn, off_tc_tn, off_maps, meta_end;
+  size_t off_meta, off_table, off_prefix[NPF], off_tc_nn, off_tc_tn, off_maps, meta_end;
   size_t off_status, off_err, total;
   int dmax, dpmax_tc, dmax_otc;
   int64_t max_omega, max_out;
 };
 
-enum { PF_NN = 0, PF_TN, PF_GY, PF_GN, PF_GPZ, PF_TY, PF_TN2 };
 
 ruqlp_status batch_launches(ruqlp_ctx* h, const BatchPlan& bp, int count, int q, Ty ct,
                             cudaStream_t st) {
@@ -868,7 +871,7 @@ ruqlp_status batch_launches(ruqlp_ctx* h, const BatchPlan& bp, int count, int q,
   auto orth_b = [&](int src, int dst, int passes, int make_bt) -> ruqlp_status {
     ProfScope sp(ph, PROF_ORTH);
     const bool y = src == B_Y;
-    const int gp = y ? PF_GY : PF_GN;
+    const int gp = y ? PF_GY : PF_GN, gw = y ? PF_GYW : PF_GNW;
     const int tp = y ? PF_TY : PF_TN2;
     const auto& bo = bp.bo[y ? 0 : 1];
     const int ng = (int)bo.goff.size() - 1, nq = (int)bo.qoff.size() - 1;
@@ -876,10 +879,11 @@ ruqlp_status batch_launches(ruqlp_ctx* h, const BatchPlan& bp, int count, int q,
     for (int pass = 0; pass < passes; ++pass) {
       const int from = pass == 0 ? src : dst;
       const int mb = pass == passes - 1 ? make_bt : 0;
-      CK(bgram(T, pre(gp), tot(gp), count, from, from, kMaxSplits, bp.dmax, st, false));
+      CK(bgram_sym(T, pre(gp), tot(gp), count, from, kMaxSplits, st));
+      CK(bgram(T, pre(gw), tot(gw), count, from, from, kMaxSplits, bp.dmax, st, false));
       CK(bgram_tc(T, (const BoUnit*)dev(bo.o_gu), (const int*)dev(bo.o_goff), ng, from,
                   kMaxSplits, err, st));
-      if (tot(gp) > 0 || ng > 0) CK(bgram_reduce(T, count, from, from, kMaxSplits, bp.dmax, st));
+      if (tot(gp) > 0 || tot(gw) > 0 || ng > 0) CK(bgram_reduce(T, count, from, from, kMaxSplits, bp.dmax, st));
       CK(bchol(T, count, s1, pass == 0, bp.dmax, st, pass == 2));
       CK(btrsm(T, pre(tp), tot(tp), count, from, dst, bp.dmax, st, mb));
       CK(btrinv(T, (const int*)dev(bp.off_bo_items), (int)bp.bo_items.size(), bp.dmax_otc, st));
@@ -1017,10 +1021,10 @@ ruqlp_status batch_begin(ruqlp_ctx* h, int count, const ruqlp_matrix* A, const r
   }
   // each prefix array: count + 1 tile offsets over the launch order, then
   // the order itself (count item indices)
-  for (int k = 0; k < 7; ++k) bp.prefix[k].assign(2 * count + 1, 0);
+  for (int k = 0; k < NPF; ++k) bp.prefix[k].assign(2 * count + 1, 0);
   bp.off_meta = off;
   bp.off_table = take(sizeof(BMat) * count);
-  for (int k = 0; k < 7; ++k) bp.off_prefix[k] = take(sizeof(int) * (2 * count + 1));
+  for (int k = 0; k < NPF; ++k) bp.off_prefix[k] = take(sizeof(int) * (2 * count + 1));
   // tile lists are sized below, after the table is filled
   size_t n_nn = 0, n_tn = 0;
   for (int i = 0; i < count; ++i)
@@ -1093,8 +1097,8 @@ ruqlp_status batch_begin(ruqlp_ctx* h, int count, const ruqlp_matrix* A, const r
   ruqlp_status s = ensure_arena(h, bp.total);
   if (s != RUQLP_OK) return s;
   char* base = (char*)h->arena;
-  std::vector<int> cnts[7];
-  for (int k = 0; k < 7; ++k) cnts[k].assign(count, 0);
+  std::vector<int> cnts[NPF];
+  for (int k = 0; k < NPF; ++k) cnts[k].assign(count, 0);
   for (int i = 0; i < count; ++i) {
     BMat& b = bp.table[i];
     const ruqlp_dense& D = A[i].dense;
@@ -1125,12 +1129,17 @@ ruqlp_status batch_begin(ruqlp_ctx* h, int count, const ruqlp_matrix* A, const r
     b.Pout = out[i].P;
     b.status = (DevStatus*)(base + bp.off_status) + i;
     const bool cc = !b.orth_tc;  // CholeskyQR on the CUDA cores
-    const int cnt[7] = {b.use_tc ? 0 : bgemm_tiles(b.m, b.d), b.use_tc ? 0 : bgemm_tiles(b.n, b.d),
-                        cc ? bgram_tiles(b.m, b.d, true, kMaxSplits) : 0,
-                        cc ? bgram_tiles(b.n, b.d, true, kMaxSplits) : 0,
-                        bgram_tiles(b.n, b.d, false, kMaxSplits), cc ? btrsm_blocks(b.m) : 0,
-                        cc ? btrsm_blocks(b.n) : 0};
-    for (int k = 0; k < 7; ++k) cnts[k][i] = cnt[k];
+    const bool narrow = bgram_sym_ctas(b.m, b.d, kMaxSplits) > 0;
+    const int cnt[NPF] = {b.use_tc ? 0 : bgemm_tiles(b.m, b.d),
+                          b.use_tc ? 0 : bgemm_tiles(b.n, b.d),
+                          cc ? bgram_sym_ctas(b.m, b.d, kMaxSplits) : 0,
+                          cc ? bgram_sym_ctas(b.n, b.d, kMaxSplits) : 0,
+                          bgram_tiles(b.n, b.d, false, kMaxSplits),
+                          cc ? btrsm_blocks(b.m) : 0,
+                          cc ? btrsm_blocks(b.n) : 0,
+                          cc && !narrow ? bgram_tiles(b.m, b.d, true, kMaxSplits) : 0,
+                          cc && !narrow ? bgram_tiles(b.n, b.d, true, kMaxSplits) : 0};
+    for (int k = 0; k < NPF; ++k) cnts[k][i] = cnt[k];
   }
   // the CUDA-core launches take their tiles widest item first (a tile's cost
   // grows with d^2), so the last wave holds the cheapest tiles; a tile's
@@ -1143,7 +1152,7 @@ ruqlp_status batch_begin(ruqlp_ctx* h, int count, const ruqlp_matrix* A, const r
       if (a.dp != b.dp) return a.dp > b.dp;
       return a.m + a.n > b.m + b.n;
     });
-    for (int k = 0; k < 7; ++k) {
+    for (int k = 0; k < NPF; ++k) {
       for (int pos = 0; pos < count; ++pos) {
         bp.prefix[k][pos + 1] = bp.prefix[k][pos] + cnts[k][order[pos]];
         bp.prefix[k][count + 1 + pos] = order[pos];
@@ -1202,7 +1211,7 @@ ruqlp_status batch_begin(ruqlp_ctx* h, int count, const ruqlp_matrix* A, const r
     if (bytes) memcpy(img + (o - bp.off_meta), src, bytes);
   };
   put(bp.off_table, bp.table.data(), sizeof(BMat) * count);
-  for (int k = 0; k < 7; ++k)
+  for (int k = 0; k < NPF; ++k)
     put(bp.off_prefix[k], bp.prefix[k].data(), sizeof(int) * (2 * count + 1));
   put(bp.off_tc_nn, bp.tc_nn.data(), sizeof(BTcTile) * bp.tc_nn.size());
   put(bp.off_tc_tn, bp.tc_tn.data(), sizeof(BTcTile) * bp.tc_tn.size());
