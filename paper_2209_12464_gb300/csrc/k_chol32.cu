@@ -133,14 +133,18 @@ __device__ __noinline__ bool factor_tile(float* __restrict__ B, float* __restric
 // orthonormal to working accuracy, so every pivot must lie in [1/2, 2]; if
 // one does not, the sketch is numerically rank deficient for CholeskyQR at
 // this precision and RUQLP_FLAG_RANKDEF is raised (the host then redoes the
-// decomposition with Householder TSQR).
+// decomposition with Householder TSQR).  When such a Gram is within
+// sqrt(2^-25 / d) of I entry by entry, the factor is formed to first order
+// in G - I instead of by elimination (the same factor to working precision;
+// no chain of pivots).
 template <int NT>
 __device__ __forceinline__ void chol_body(const float* __restrict__ G, int d, double shift_rel,
                                           int force_shift, float* __restrict__ tiles,
                                           DevStatus* __restrict__ status, int check) {
   extern __shared__ __align__(16) float sm[];
   __shared__ float s_shift;
-  __shared__ int s_bad, s_rankdef, s_far;
+  __shared__ int s_bad, s_rankdef, s_far, s_near;
+  __shared__ float s_red[NT / 32];
   __shared__ __align__(16) float s_row[TB];
   __shared__ unsigned char s_tI[MAXNB * (MAXNB + 1) / 2], s_tJ[MAXNB * (MAXNB + 1) / 2];
   const int nb = (d + TB - 1) / TB;
@@ -155,6 +159,7 @@ __device__ __forceinline__ void chol_body(const float* __restrict__ G, int d, do
   if (tid == 0) {
     s_rankdef = 0;
     s_far = 0;
+    s_near = 0;
   }
   if (tid < ntiles) {  // packed tile index -> (I, J)
     int I = 0, tt = tid;
@@ -243,6 +248,54 @@ __device__ __forceinline__ void chol_body(const float* __restrict__ G, int d, do
       *p = (i < d) ? *p + add : 1.f;
     }
     __syncthreads();
+    if (check && attempt == 0) {
+      // The last pass of a CholeskyQR: G = I + E with E at the level of the
+      // previous pass's loss of orthogonality.  R = I + X with X upper
+      // triangular solves X + X^T = E - X^T X, so X = Phi(E) (the strict
+      // upper triangle of E and half its diagonal) up to |X^T X| <= d e^2,
+      // e = max |E_ij|; when d e^2 <= 2^-25 that is below FP32 rounding and
+      // R = I + Phi(E) is the Cholesky factor to working precision, its
+      // diagonal tiles' inverses I - (R_KK - I) likewise (the dropped
+      // (R_KK - I)^2 is at most 32 e^2).  NaN entries fail the test.
+      float e = 0.f;
+      for (int x = tid; x < ntiles * TB * TB; x += NT) {
+        const int tt = x >> 10, r = (x >> 5) & (TB - 1), c = x & (TB - 1);
+        const int I = s_tI[tt], J = s_tJ[tt];
+        if (I == J && c < r) continue;
+        const float g = tile(I, J)[r * TP + c];
+        const float v = fabsf((I == J && r == c) ? g - 1.f : g);
+        e = (v > e || v != v) ? v : e;
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        const float w = __shfl_xor_sync(0xffffffffu, e, o);
+        e = (w > e || w != w) ? w : e;
+      }
+      if (lane == 0) s_red[warp] = e;
+      __syncthreads();
+      if (tid == 0) {
+        float m = 0.f;
+        for (int w = 0; w < nw; ++w) m = (s_red[w] > m || s_red[w] != s_red[w]) ? s_red[w] : m;
+        s_near = (float)d * m * m <= 2.98023223876953125e-08f;  // 2^-25
+      }
+      __syncthreads();
+      if (s_near) {
+        for (int x = tid; x < ntiles * TB * TB; x += NT) {
+          const int tt = x >> 10, r = (x >> 5) & (TB - 1), c = x & (TB - 1);
+          const int I = s_tI[tt], J = s_tJ[tt];
+          if (I != J) continue;
+          float* p = tile(I, J) + r * TP + c;
+          *p = c < r ? 0.f : (c == r ? 0.5f * (1.f + *p) : *p);
+        }
+        __syncthreads();
+        for (int x = tid; x < nb * TB * TB; x += NT) {
+          const int K = x >> 10, r = (x >> 5) & (TB - 1), c = x & (TB - 1);
+          const float rv = tile(K, K)[r * TP + c];
+          tiles[(size_t)(ntiles + K) * TB * TB + r * TB + c] =
+              c < r ? 0.f : (c == r ? 1.f / rv : -rv);
+        }
+        break;
+      }
+    }
     const float fill = attempt == 0 ? 1.f : add;
     // Step K = -1 only factors the first diagonal tile; step K >= 0 does the
     // panel of tile row K, updates tile (K+1, K+1), then factors it on warp 0
@@ -301,7 +354,7 @@ __device__ __forceinline__ void chol_body(const float* __restrict__ G, int d, do
     if (!s_bad) break;
   }
   __syncthreads();
-  if (check && warp == 0) {
+  if (check && !s_near && warp == 0) {
     // the last pass of a CholeskyQR: its Gram should be close to I, so every
     // pivot r_ii^2 lies in [1/2, 2] and no retry with the shift was needed
     bool far = attempt > 0 && !force_shift;
