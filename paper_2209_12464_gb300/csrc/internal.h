@@ -165,6 +165,11 @@ struct BMat {
   // 3 x dp x 128
   void* St;
   int use_tc, orth_tc;
+  // q_direct: the last solve of the final orth of Y writes Q straight into
+  // Qout (FP32, leading dimension d) instead of the Y buffer (tensor-core
+  // items with the CUDA-core solve and FP32 outputs: nothing reads Y after
+  // that solve, the last product taking its BF16 parts)
+  int q_direct, pad2;
   void* Qout;
   void* Lout;
   void* Pout;

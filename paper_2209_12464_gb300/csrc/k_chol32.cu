@@ -644,7 +644,7 @@ k_trsm_tiles(const float* __restrict__ Y, int64_t ldy, const float* __restrict__
 }
 
 // Batched: block t -> (matrix, 128-row block); M = rows of buf[src].
-__global__ void __launch_bounds__(2 * SRB)
+__global__ void __launch_bounds__(2 * SRB, 4)
 k_btrsm(const BMat* __restrict__ T, const int* __restrict__ prefix, int count, int src, int dst,
         int make_bt) {
   const int t = blockIdx.x;
@@ -655,7 +655,10 @@ k_btrsm(const BMat* __restrict__ T, const int* __restrict__ prefix, int count, i
   }
   const BMat& b = T[prefix[count + 1 + lo]];  // the launch order's item lo
   const int64_t M = (src == B_Y) ? b.m : b.n;
-  trsm_body<SRB>(bbuf(b, src), b.dp, b.tiles, bbuf(b, dst), b.dp, M, b.d, t - prefix[lo],
+  // make_bt == 2 marks the last solve of the final orth of Y
+  const bool direct = make_bt == 2 && b.q_direct;
+  trsm_body<SRB>(bbuf(b, src), b.dp, b.tiles, direct ? (float*)b.Qout : bbuf(b, dst),
+            direct ? (int64_t)b.d : (int64_t)b.dp, M, b.d, t - prefix[lo],
             (make_bt && b.use_tc) ? (__nv_bfloat16*)b.Bt : nullptr, b.ldbt,
             (make_bt == 2 && b.use_tc) ? (__nv_bfloat16*)b.Btl : nullptr);
 }
@@ -690,6 +693,9 @@ cudaError_t btrsm(const BMat* T, const int* prefix, int total, int count, int sr
   const size_t sm = (size_t)((dmax + 3) / 4 * 4) * (SRB + 4) * sizeof(float);
   cudaError_t e =
       cudaFuncSetAttribute(k_btrsm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  // the whole unified L1 as shared memory, so four CTAs fit per SM
+  e = cudaFuncSetAttribute(k_btrsm, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
   if (e != cudaSuccess) return e;
   k_btrsm<<<total, 2 * SRB, sm, st>>>(T, prefix, count, src, dst, make_bt);
   count_launch();

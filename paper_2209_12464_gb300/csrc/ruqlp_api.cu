@@ -1125,6 +1125,9 @@ ruqlp_status batch_begin(ruqlp_ctx* h, int count, const ruqlp_matrix* A, const r
     b.omega = prm[i].omega;
     b.seed = prm[i].omega_seed;
     b.Qout = out[i].Q;
+    // (rows of Qout on 16 bytes, so the solve's 128-bit stores stay)
+    b.q_direct = (b.use_tc && !b.orth_tc && ot == Ty::F32 && b.d % 4 == 0 &&
+                  ((uintptr_t)b.Qout & 15) == 0) ? 1 : 0;
     b.Lout = out[i].L;
     b.Pout = out[i].P;
     b.status = (DevStatus*)(base + bp.off_status) + i;
