@@ -129,7 +129,7 @@ __device__ __noinline__ bool factor_tile(float* __restrict__ B, float* __restric
 // depend on NT).  Writes the upper tiles R_IJ (I <= J) and the diagonal-tile
 // inverses R_KK^{-1}, FP32, 32 x 32 row-major each, to `tiles`: first the
 // nb (nb+1)/2 R tiles in row-of-tiles order, then the nb inverse tiles.
-// check: this is the last pass of a CholeskyQR whose input should already be
+// CHECK: this is the last pass of a CholeskyQR whose input should already be
 // orthonormal to working accuracy, so every pivot must lie in [1/2, 2]; if
 // one does not, the sketch is numerically rank deficient for CholeskyQR at
 // this precision and RUQLP_FLAG_RANKDEF is raised (the host then redoes the
@@ -137,10 +137,10 @@ __device__ __noinline__ bool factor_tile(float* __restrict__ B, float* __restric
 // sqrt(2^-25 / d) of I entry by entry, the factor is formed to first order
 // in G - I instead of by elimination (the same factor to working precision;
 // no chain of pivots).
-template <int NT>
+template <int NT, bool CHECK>
 __device__ __forceinline__ void chol_body(const float* __restrict__ G, int d, double shift_rel,
                                           int force_shift, float* __restrict__ tiles,
-                                          DevStatus* __restrict__ status, int check) {
+                                          DevStatus* __restrict__ status) {
   extern __shared__ __align__(16) float sm[];
   __shared__ float s_shift;
   __shared__ int s_bad, s_rankdef, s_far, s_near;
@@ -248,7 +248,7 @@ __device__ __forceinline__ void chol_body(const float* __restrict__ G, int d, do
       *p = (i < d) ? *p + add : 1.f;
     }
     __syncthreads();
-    if (check && attempt == 0) {
+    if (CHECK && attempt == 0) {
       // The last pass of a CholeskyQR: G = I + E with E at the level of the
       // previous pass's loss of orthogonality.  R = I + X with X upper
       // triangular solves X + X^T = E - X^T X, so X = Phi(E) (the strict
@@ -354,7 +354,7 @@ __device__ __forceinline__ void chol_body(const float* __restrict__ G, int d, do
     if (!s_bad) break;
   }
   __syncthreads();
-  if (check && !s_near && warp == 0) {
+  if (CHECK && !s_near && warp == 0) {
     // the last pass of a CholeskyQR: its Gram should be close to I, so every
     // pivot r_ii^2 lies in [1/2, 2] and no retry with the shift was needed
     bool far = attempt > 0 && !force_shift;
@@ -381,23 +381,38 @@ __device__ __forceinline__ void chol_body(const float* __restrict__ G, int d, do
   }
 }
 
+// CHECK (the last pass of a CholeskyQR: the near-identity route and the
+// rank-deficiency check) is a separate instantiation: the code it adds
+// around the factorisation made the other passes' factorisation measurably
+// slower (instruction-cache residency of its unrolled body).
+template <bool CHECK>
 __global__ void __launch_bounds__(NTH)
 k_chol_tiles(const float* __restrict__ G, int d, double shift_rel, int force_shift,
              float* __restrict__ tiles, DevStatus* __restrict__ status,
-             const int32_t* __restrict__ gate, int check) {
+             const int32_t* __restrict__ gate) {
   pdl_launch();
   pdl_wait();
   if (gate != nullptr && *gate == 0) return;
-  chol_body<NTH>(G, d, shift_rel, force_shift, tiles, status, check);
+  chol_body<NTH, CHECK>(G, d, shift_rel, force_shift, tiles, status);
 }
 
 // One CTA per matrix of the problem table; small batches of small d take
 // 128-thread CTAs, four per SM.
-template <int NT>
+template <int NT, bool CHECK>
 __global__ void __launch_bounds__(NT, NT == 128 ? 4 : 1)
-k_bchol(const BMat* __restrict__ T, double shift_rel, int force_shift, int check) {
+k_bchol(const BMat* __restrict__ T, double shift_rel, int force_shift) {
   const BMat& b = T[blockIdx.x];
-  chol_body<NT>(b.Gf, b.d, shift_rel, force_shift, b.tiles, b.status, check);
+  chol_body<NT, CHECK>(b.Gf, b.d, shift_rel, force_shift, b.tiles, b.status);
+}
+
+template <int NT, bool CHECK>
+cudaError_t bchol_launch(const BMat* T, int count, double shift_rel, bool force_shift, size_t sm,
+                         cudaStream_t st) {
+  cudaError_t e = cudaFuncSetAttribute(k_bchol<NT, CHECK>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  k_bchol<NT, CHECK><<<count, NT, sm, st>>>(T, shift_rel, force_shift ? 1 : 0);
+  return cudaSuccess;
 }
 
 // X = Y R^{-1} by blocked forward substitution over 32-column tiles:
@@ -672,17 +687,14 @@ cudaError_t bchol(const BMat* T, int count, double shift_rel, bool force_shift, 
   if (count <= 0) return cudaSuccess;
   if (!chol_tiles_supported(dmax)) return cudaErrorInvalidValue;
   const size_t sm = chol_tiles_smem(dmax);
-  if (dmax <= 96) {
-    cudaError_t e =
-        cudaFuncSetAttribute(k_bchol<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (e != cudaSuccess) return e;
-    k_bchol<128><<<count, 128, sm, st>>>(T, shift_rel, force_shift ? 1 : 0, check ? 1 : 0);
-  } else {
-    cudaError_t e =
-        cudaFuncSetAttribute(k_bchol<NTH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (e != cudaSuccess) return e;
-    k_bchol<NTH><<<count, NTH, sm, st>>>(T, shift_rel, force_shift ? 1 : 0, check ? 1 : 0);
-  }
+  cudaError_t e;
+  if (dmax <= 96)
+    e = check ? bchol_launch<128, true>(T, count, shift_rel, force_shift, sm, st)
+              : bchol_launch<128, false>(T, count, shift_rel, force_shift, sm, st);
+  else
+    e = check ? bchol_launch<NTH, true>(T, count, shift_rel, force_shift, sm, st)
+              : bchol_launch<NTH, false>(T, count, shift_rel, force_shift, sm, st);
+  if (e != cudaSuccess) return e;
   count_launch();
   return cudaGetLastError();
 }
@@ -721,11 +733,11 @@ cudaError_t chol_tiles_f32(const float* G, int d, double shift_rel, bool force_s
                            bool check) {
   if (!chol_tiles_supported(d)) return cudaErrorInvalidValue;
   const size_t sm = chol_tiles_smem(d);
-  cudaError_t e =
-      cudaFuncSetAttribute(k_chol_tiles, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  auto kern = check ? k_chol_tiles<true> : k_chol_tiles<false>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
-  e = launch_pdl(k_chol_tiles, dim3(1), dim3(NTH), sm, st, G, d, shift_rel, force_shift ? 1 : 0,
-                 tiles, status, gate, check ? 1 : 0);
+  e = launch_pdl(kern, dim3(1), dim3(NTH), sm, st, G, d, shift_rel, force_shift ? 1 : 0, tiles,
+                 status, gate);
   count_launch();
   return e == cudaSuccess ? cudaGetLastError() : e;
 }
