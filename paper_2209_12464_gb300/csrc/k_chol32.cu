@@ -513,15 +513,16 @@ __device__ __forceinline__ void trsm_body(const float* __restrict__ Y, int64_t l
   }
   auto col4 = [&](int c) { return reinterpret_cast<float4*>(ys + c * YP + rg * 4); };
   int sidx = 0;
+  __syncthreads();  // the staged rows
   for (int J = 0; J < nb; ++J) {
     // block column J holds vJ = min(32, d - 32 J) columns: a thread whose
     // four columns lie past them (not live) neither reads nor writes the
     // staged block in this block column, so the staging holds only the
-    // columns below d rounded up to 4
+    // columns below d rounded up to 4.  A thread's own columns of block J
+    // are read and written only by itself until the diagonal step.
     const int vJ = min(TB, d - J * TB);
     const bool live = cg * 4 < vJ;
     float acc[4][4];
-    __syncthreads();
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       const float4 v = live ? *col4(J * TB + cg * 4 + j) : make_float4(0.f, 0.f, 0.f, 0.f);
@@ -531,17 +532,19 @@ __device__ __forceinline__ void trsm_body(const float* __restrict__ Y, int64_t l
       acc[3][j] = v.w;
     }
     for (int K = 0; K <= J; ++K, ++sidx) {
-      __syncthreads();  // everyone is done with the buffer about to be refilled
-      if (sidx + NPF - 1 < nsteps) fetch((sidx + NPF - 1) % NPF, step_tile(sidx + NPF - 1));
-      asm volatile("cp.async.commit_group;" ::: "memory");
       if (K == J && live) {
         // stage the updated tile of this row block, then multiply by R_JJ^{-1}
 #pragma unroll
         for (int j = 0; j < 4; ++j)
           *col4(J * TB + cg * 4 + j) = make_float4(acc[0][j], acc[1][j], acc[2][j], acc[3][j]);
       }
-      asm volatile("cp.async.wait_group %0;" ::"n"(NPF - 1) : "memory");  // step's tile landed
+      asm volatile("cp.async.wait_group %0;" ::"n"(NPF - 2) : "memory");  // own copies of this step's tile
+      // one barrier per step: every thread's copies of this step's tile have
+      // landed, the staged tile above is visible, and every thread is done
+      // with step sidx - 1, whose buffer the next copy refills
       __syncthreads();
+      if (sidx + NPF - 1 < nsteps) fetch((sidx + NPF - 1) % NPF, step_tile(sidx + NPF - 1));
+      asm volatile("cp.async.commit_group;" ::: "memory");
       const float* R = &Rt[sidx % NPF][0][0];
       // a thread that is not live skips the tile products; the diagonal
       // step sums k < min(vJ, 4 cg + 4) only (the inverse of R_JJ is upper
