@@ -165,6 +165,9 @@ ORTH_CASES = [  # M, d, log10 kappa
     (38912, 64, 2), (38913, 64, 2), (60013, 96, 3),
     # d past the blocked Cholesky's 288 columns, up to the ABI's 512
     (2000, 512, 3), (3001, 417, 2), (12000, 300, 3),
+    # orthonormal Y: every pass sees a Gram near I, and the last one takes
+    # the first-order factor (several diagonal tiles; tall: tensor cores)
+    (4096, 96, 0), (20011, 220, 0), (1000, 288, 0),
 ]
 
 
