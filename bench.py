@@ -518,32 +518,57 @@ def run_batch(args, torch, dev, local, world, rank, dist):
                     "peak_source": "derived: 152 SMs x 128 FP32 FMA/clk x 2 x median SM clock",
                     **common}
 
-    # end to end: pinned host inputs -> device, batched call, outputs -> host
+    # end to end: pinned host inputs -> device, batched call, outputs -> host.
+    # The batch's inputs and outputs each live in one packed buffer (every
+    # item at a 256-byte aligned offset, A_i with its 16-byte row pitch), as
+    # a caller holding a batch would keep them, so each direction is one
+    # copy per buffer rather than one per item.
     e2e = None
     if not args.no_e2e:
-        Ah = [a.cpu().pin_memory() for a in A]
-        Oh = [o.cpu().pin_memory() for o in Om]
-        Qh = [tuple(torch.empty_like(t, device="cpu").pin_memory() for t in o) for o in batch.outs]
-        bi = sum(a.numel() * a.element_size() for a in Ah) + sum(o.numel() * 8 for o in Oh)
-        bo = sum(t.numel() * t.element_size() for o in Qh for t in o)
+        def pack(tensors, dtype):
+            # one device buffer holding each 2-D tensor at an aligned offset
+            es = torch.empty((), dtype=dtype).element_size()
+            offs, tot = [], 0
+            for t in tensors:
+                offs.append(tot)
+                tot += (t.shape[0] * t.stride(0) * es + 255) // 256 * 256
+            buf = torch.empty(tot // es, dtype=dtype, device=dev)
+            views = [buf.as_strided(tuple(t.shape), (t.stride(0), 1), o // es)
+                     for t, o in zip(tensors, offs)]
+            return buf, views
+        Ad, Av = pack(A, A[0].dtype)
+        for v, a in zip(Av, A):
+            v.copy_(a)
+        Omd, Omv = pack(Om, torch.float64)
+        for v, o in zip(Omv, Om):
+            v.copy_(o)
+        outs_t = [(torch.empty(m, k + p, device=dev), torch.empty(k + p, k + p, device=dev),
+                   torch.empty(n, k + p, device=dev)) for m, n, k, p in shapes]
+        Od, Ov = pack([t for o in outs_t for t in o], torch.float32)
+        outs_v = [tuple(Ov[3 * i:3 * i + 3]) for i in range(len(shapes))]
+        be = h.prepare_batch(Av, Omv, ks, B_P, B_Q, ps=ps, outs=outs_v)
+        Ah = Ad.cpu().pin_memory()
+        Oh = Omd.cpu().pin_memory()
+        Rh = torch.empty(Od.shape, dtype=Od.dtype).pin_memory()
+        bi = Ah.numel() * Ah.element_size() + Oh.numel() * Oh.element_size()
+        bo = Rh.numel() * Rh.element_size()
+        be.run()  # first sighting of this batch's buffers
+        be.run()
         ke = max(1, min(args.steps, 3))
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for _ in range(ke):
-            for dsrc, hsrc in zip(A, Ah):
-                dsrc.copy_(hsrc, non_blocking=True)
-            for dsrc, hsrc in zip(Om, Oh):
-                dsrc.copy_(hsrc, non_blocking=True)
-            batch.run()
-            for o, hq in zip(batch.outs, Qh):
-                for t, ht in zip(o, hq):
-                    ht.copy_(t, non_blocking=True)
+            Ad.copy_(Ah, non_blocking=True)
+            Omd.copy_(Oh, non_blocking=True)
+            be.run()
+            Rh.copy_(Od, non_blocking=True)
             torch.cuda.synchronize()
         te = (time.perf_counter() - t0) / ke
         te = max_over_ranks(torch, dist, world, te, dev)
         e2e = {"value": job_rate(world, passes * bytes_a / 1e9, te), "unit": "GB/s",
                "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo, "ms_per_step": te * 1e3,
-               "decompositions_per_s": job_rate(world, len(shapes), te)}
+               "decompositions_per_s": job_rate(world, len(shapes), te),
+               "layout": "inputs and outputs in one packed pinned buffer per kind (3 copies)"}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -238,7 +238,7 @@ class Batch:
     """ctypes arrays of one batched call, built once and reusable."""
 
     def __init__(self, handle, As, omegas, ks, p, q, out_dtype=None, ps=None, qs=None,
-                 seeds=None):
+                 seeds=None, outs=None):
         import torch
         cnt = len(As)
         seeds = list(seeds) if seeds is not None else [0] * cnt
@@ -258,9 +258,13 @@ class Batch:
             d = k + ps[i]
             om = om.contiguous() if om is not None else None
             self.keep.append(om)
-            Q = torch.empty(m, d, dtype=od, device=A.device)
-            L = torch.empty(d, d, dtype=od, device=A.device)
-            P = torch.empty(n, d, dtype=od, device=A.device)
+            if outs is not None:  # caller-owned (Q, L, P), row-major, leading dimension d
+                Q, L, P = outs[i]
+                od = Q.dtype
+            else:
+                Q = torch.empty(m, d, dtype=od, device=A.device)
+                L = torch.empty(d, d, dtype=od, device=A.device)
+                P = torch.empty(n, d, dtype=od, device=A.device)
             self.M[i] = Matrix(0, Dense(m, n, A.stride(0), _dtype_code(A.dtype), A.data_ptr()),
                                Csr())
             self.P[i] = Params(k, ps[i], qs[i], _dtype_code(A.dtype),
@@ -386,10 +390,11 @@ class Handle:
         return Q, L, P, out.flags
 
     def prepare_batch(self, As, omegas, ks, p, q, out_dtype=None, ps=None, qs=None,
-                      seeds=None):
-        """Marshal a batch once (A_i, Omega_i, output tensors); the returned
-        object's run() calls ruqlp_decompose_batch and returns the flags."""
-        return Batch(self, As, omegas, ks, p, q, out_dtype, ps, qs, seeds)
+                      seeds=None, outs=None):
+        """Marshal a batch once (A_i, Omega_i, output tensors: new ones, or
+        the caller's (Q, L, P) per item in outs); the returned object's run()
+        calls ruqlp_decompose_batch and returns the flags."""
+        return Batch(self, As, omegas, ks, p, q, out_dtype, ps, qs, seeds, outs)
 
     def decompose_batch(self, As, omegas, ks, p, q, out_dtype=None, ps=None, qs=None,
                         seeds=None):
