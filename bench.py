@@ -337,6 +337,28 @@ B_WORKLOAD = ("batched: 512 dense matrices, m log-uniform [256,4096], n log-unif
               "k uniform [8,64], p=8, q=1, sigma_i=1 (i<=k) then 1e-2/(i-k)")
 
 
+def two_part_roofline(prof, flops, nbytes, peaks):
+    """The two-part last product B^T = A^T Q: two BF16 MMAs per A tile
+    (2 x 2 x rows x cols x dp flop) over one pass of A (nbytes: A, both BF16
+    parts of the skinny operand, the FP32 output).  Its roofline is the
+    larger of the two times at peak: the tensor pipe (sustained BF16 peak:
+    timed inside the step) for wide sketches, HBM for narrow ones."""
+    cnt, tot = prof
+    avg = tot / max(cnt, 1)
+    tpk = peaks.get("bf16_tflops_sustained", 1700.0)
+    hpk = peaks.get("hbm_gbs", 6800.0)
+    if flops / (tpk * 1e12) >= nbytes / (hpk * 1e9):
+        achieved = flops / (avg * 1e-3) / 1e12
+        return {"bound": "tensor", "achieved": achieved, "peak": tpk, "unit": "TFLOP/s",
+                "frac": achieved / tpk, "alg_flops_per_launch": flops, "avg_launch_ms": avg,
+                "launches": cnt,
+                "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained (of measured)"}
+    achieved = nbytes / (avg * 1e-3) / 1e9
+    return {"bound": "hbm", "achieved": achieved, "peak": hpk, "unit": "GB/s",
+            "frac": achieved / hpk, "alg_bytes_per_launch": nbytes, "avg_launch_ms": avg,
+            "launches": cnt, "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
+
+
 def batch_inputs(torch, dev, count, dtype, gen):
     from paper_2209_12464_gb300 import workloads as wl
     shapes = wl.batch_shapes(B_SEED, count=count, p=B_P)
@@ -475,7 +497,8 @@ def run_batch(args, torch, dev, local, world, rank, dist):
     for _ in range(2):
         batch.run()
     torch.cuda.synchronize()
-    prof = {ph: h.profile(ph) for ph in ("ax", "atx", "orth", "step", "tc_ax", "tc_atx")}
+    prof = {ph: h.profile(ph) for ph in ("ax", "atx", "orth", "step", "tc_ax", "tc_atx",
+                                         "tc_atx2")}
     h.set_option("profile", 0)
     peaks = {}
     try:
@@ -501,9 +524,14 @@ def run_batch(args, torch, dev, local, world, rank, dist):
         roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                     "frac": achieved / hbm_peak, "traffic": None,
                     "kernel": "k_btc_gemm (batched tcgen05 products over a tile list, one pass "
-                              "over every A_i per launch)",
+                              "over every A_i per launch; one-part skinny operand)",
                     "alg_bytes_per_launch": alg, "avg_launch_ms": avg, "launches": cnt,
                     "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)", **common}
+        if prof["tc_atx2"][0]:
+            flops2 = 4.0 * sum(m * n * dp for (m, n, k, p), dp in zip(shapes, dpad))
+            bytes2 = bytes_a + sum(dp * (4 * m + 4 * n) for (m, n, k, p), dp in zip(shapes, dpad))
+            roofline["two_part_launch"] = two_part_roofline(prof["tc_atx2"], flops2, bytes2,
+                                                            peaks)
     else:
         cnt = prof["ax"][0] + prof["atx"][0]
         avg = (prof["ax"][1] + prof["atx"][1]) / max(cnt, 1)
@@ -993,7 +1021,7 @@ def main():
     for _ in range(nprof):
         step()
     torch.cuda.synchronize()
-    phases = ("ax", "atx", "orth", "step", "tc_ax", "tc_atx", "gram", "chol", "trsm")
+    phases = ("ax", "atx", "orth", "step", "tc_ax", "tc_atx", "tc_atx2", "gram", "chol", "trsm")
     prof = {ph: h.profile(ph) for ph in phases}
     h.set_option("profile", 0)
     peaks = {}
@@ -1021,10 +1049,14 @@ def main():
                                       "the units processed to the 20000 x 20000 launch "
                                       "(profiles/k_tc_gemm_dense10240_bf16.md); not measured "
                                       "in this run",
-                    "kernel": "k_tc_gemm (tcgen05 A X / A^T Y, one pass over A per launch)",
+                    "kernel": "k_tc_gemm (tcgen05 A X / A^T Y, one pass over A per launch; "
+                              "one-part skinny operand)",
                     "alg_bytes_per_launch": alg, "avg_launch_ms": avg, "launches": cnt,
                     "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)",
                     "phase_ms": phase_ms, "phase_share": share}
+        if prof["tc_atx2"][0]:
+            roofline["two_part_launch"] = two_part_roofline(
+                prof["tc_atx2"], 4.0 * m * n * dp, bytes_a + 4 * m * dp + 4 * n * dp, peaks)
     else:
         # CUDA-core products: FP32 (or FP64) multiply-add bound
         dom = max(("ax", "atx"), key=lambda ph: prof[ph][1])

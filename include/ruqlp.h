@@ -399,6 +399,8 @@ int ruqlp_tune_file(const char* path);
  *   "step" whole decompositions,
  *   "tc_ax" / "tc_atx" the tensor-core product kernel launches alone
  *   (BF16 path; without operand transposes and the stream-K fix-up),
+ *   "tc_atx2" those of the two-part last product B^T = A^T Q (the skinny
+ *   operand as two BF16 parts: two MMAs per A tile),
  *   "gram" / "chol" / "trsm" the FP32 orth() passes' Gram (with its slab
  *   reduction), blocked Cholesky and triangular solve (single-matrix path).
  * Errors: INVALID (unknown phase, NULL pointers). */

@@ -66,8 +66,11 @@ struct ruqlp_ctx {
   static constexpr int kCopyStreams = 4;
   cudaStream_t copy_streams[kCopyStreams] = {};
   cudaEvent_t copy_ev[kCopyStreams + 1] = {};
-  int64_t prof_count[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
-  double prof_ms[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+  // per profile phase (the kProfNames list of ruqlp_api.cu, which checks
+  // that its length matches)
+  static constexpr int kProfPhases = 10;
+  int64_t prof_count[kProfPhases] = {};
+  double prof_ms[kProfPhases] = {};
   // request loop of ruqlp_submit / ruqlp_poll (created on the first submit)
   ruqlp::Server* server = nullptr;
   std::mutex server_mu;

@@ -51,14 +51,16 @@ ruqlp_status fail(ruqlp_ctx* h, ruqlp_status s, const char* fmt, ...) {
 // Profile categories: sketch products A X, transposed products A^T Y (whole
 // product phases), orth(), the whole decomposition, and the tensor-core
 // product kernel launches alone (k_tc_gemm, without operand transposes or the
-// stream-K fix-up) for A X and A^T Y.
+// stream-K fix-up) for A X, for A^T Y with a one-part skinny operand and for
+// the two-part last product B^T = A^T Q.
 enum {
   PROF_AX = 0, PROF_ATX = 1, PROF_ORTH = 2, PROF_STEP = 3, PROF_TC_AX = 4, PROF_TC_ATX = 5,
-  PROF_GRAM = 6, PROF_CHOL = 7, PROF_TRSM = 8
+  PROF_GRAM = 6, PROF_CHOL = 7, PROF_TRSM = 8, PROF_TC_ATX2 = 9
 };
-const int kProfN = 9;
-const char* kProfNames[kProfN] = {"ax", "atx", "orth", "step", "tc_ax", "tc_atx",
-                                  "gram", "chol", "trsm"};
+const int kProfN = ruqlp_ctx::kProfPhases;
+const char* kProfNames[] = {"ax", "atx", "orth", "step", "tc_ax", "tc_atx",
+                            "gram", "chol", "trsm", "tc_atx2"};
+static_assert(sizeof(kProfNames) / sizeof(kProfNames[0]) == kProfN, "profile phases");
 
 cudaEvent_t ev_get(ruqlp_ctx* h) {
   if (!h->pool.empty()) {
@@ -478,7 +480,8 @@ ruqlp_status product(ruqlp_ctx* h, const Layout& Lo, const Job& J, bool trans, T
                    else {
                      cudaEvent_t b = ev_get(h);
                      cudaEventRecord(b, st);
-                     h->spans.push_back({trans ? PROF_TC_ATX : PROF_TC_AX, a, b});
+                     h->spans.push_back(
+                         {trans ? (split2 ? PROF_TC_ATX2 : PROF_TC_ATX) : PROF_TC_AX, a, b});
                    }
                  } : std::function<void(bool)>(), Btl, h->tc_nsplit, h->test_withhold));
     }
@@ -899,7 +902,7 @@ ruqlp_status batch_launches(ruqlp_ctx* h, const BatchPlan& bp, int count, int q,
     CK(bgemm(trans, ct, Ty::F32, T, pre(pf), tot(pf), count, src, dst, st, split2));
     const auto& list = trans ? bp.tc_tn : bp.tc_nn;
     if (!list.empty()) {  // Bt (and Btl) were written by the step that produced buf[src]
-      ProfScope tc(ph, trans ? PROF_TC_ATX : PROF_TC_AX);
+      ProfScope tc(ph, trans ? (split2 ? PROF_TC_ATX2 : PROF_TC_ATX) : PROF_TC_AX);
       CK(btc_gemm(trans, T, count, (const BTcTile*)(base + (trans ? bp.off_tc_tn : bp.off_tc_nn)),
                   (int)list.size(), base + bp.off_maps, src, dst, bp.dpmax_tc, err, st, split2));
     }
