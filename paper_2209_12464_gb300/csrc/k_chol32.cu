@@ -10,6 +10,9 @@
 //    one per warp, 4 x 4 outputs per lane, so the factorisation needs three
 //    block barriers per tile row, not per column.  The Gram arrives in FP32
 //    (rounded by the slab reduction), so the kernel does no FP64 arithmetic.
+//    The last pass of a CholeskyQR (its own instantiation) checks the pivots
+//    for numerical rank deficiency and, for a Gram within sqrt(2^-25 / d) of
+//    I, writes the factor to first order in G - I instead.
 //  * k_trsm_tiles: Q = Y R^{-1} by blocked forward substitution with those
 //    tiles (rows of Y staged transposed in shared memory, so Q may overwrite
 //    Y).
